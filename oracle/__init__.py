@@ -1,0 +1,392 @@
+"""CPU FP64 oracle of the GRASS sparsify-and-solve path (arXiv 1911.04382).
+
+TEST INFRASTRUCTURE ONLY.  This package is the checker the GPU library is
+compared against.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import it.
+It shares no code with the CUDA library (``paper_1911_04382_gb300``) and never
+imports it.
+
+The numeric kernels are plain single-threaded C (``grass_oracle.c``); the
+orchestration below follows the paper's steps in the paper's order:
+
+* Section II-A, Eq. (formula_laplacian): edges and the diagonal load D.
+* Maximum-weight spanning tree (Kruskal, ties by edge id).
+* Section III-F, Eqs. (formula_rand_vec), (formula_pwr_iter): t-step
+  generalized power iteration h <- L_S^{-1} L_G h from a start block
+  orthogonal to the all-ones vector, L_S made invertible by grounding one
+  row (the limit of the paper's tiny diagonal on a random row).
+* Eqs. (formula_pwr_iter5new), (formula_pwr_iter6): Joule heat of each
+  off-sparsifier edge summed over the r vectors.
+* Section IV-C: lambda_max by generalized power iterations (Rayleigh
+  quotient), lambda_min by the node-degree ratio, Eq. (formula_courant-fischer-3).
+* Eq. (formula_heatratio_final): threshold theta_sigma = (sigma^2 lmin/lmax)^(2t+1).
+* Section IV-D: iterative densification.
+* Section V-A: PCG on L_G + D preconditioned by the sparsifier.
+
+Pinned by ``tests/test_oracle_pins.py`` against dense linear algebra,
+brute force and closed forms.  Unpinned parts (see the tests): the absolute
+inner-CG iteration counts and the lambda_max value beyond the Courant-Fischer
+bound.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_SRC = os.path.join(_HERE, "grass_oracle.c")
+_SO = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+OK, ERR_INVALID, ERR_NOT_SDD, ERR_DISCONNECTED, ERR_NOT_CONVERGED = 0, 1, 2, 3, 5
+
+
+class OracleError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"oracle {what}: status {status}")
+        self.status = status
+
+
+def build(force: bool = False) -> str:
+    """Compile the C oracle into oracle/_build/liboracle.so (gcc, ISO C11,
+    no FMA contraction so x86 and Arm builds round identically)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC",
+                               "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            _lib = C.CDLL(build())
+            _declare(_lib)
+    return _lib
+
+
+_i64, _i32, _f64, _u8 = C.POINTER(C.c_int64), C.POINTER(C.c_int32), C.POINTER(C.c_double), C.POINTER(C.c_uint8)
+
+
+def _declare(L):
+    L.ora_extract.argtypes = [C.c_int64, _i64, _i32, _f64, C.c_int64, _i64, _i32, _i32, _f64, _f64]
+    L.ora_mst_kruskal.argtypes = [C.c_int64, C.c_int64, _i32, _i32, _f64, _u8, _i64]
+    L.ora_tree_orient.argtypes = [C.c_int64, C.c_int64, _i32, _i32, _f64, _u8, C.c_int32, _i32, _f64, _i32]
+    L.ora_tree_solve.argtypes = [C.c_int64, _i32, _f64, _i32, _f64, C.c_int, _f64, _f64]
+    L.ora_tree_solve.restype = None
+    L.ora_lap_apply.argtypes = [C.c_int64, C.c_int64, _i32, _i32, _f64, _u8, C.c_int, _f64, _f64]
+    L.ora_lap_apply.restype = None
+    L.ora_csr_apply.argtypes = [C.c_int64, _i64, _i32, _f64, _f64, _f64]
+    L.ora_csr_apply.restype = None
+    L.ora_heat.argtypes = [C.c_int64, _i32, _i32, _f64, _u8, C.c_int, _f64, _f64]
+    L.ora_heat.restype = C.c_int64
+    L.ora_quad_forms.argtypes = [C.c_int64, _i32, _i32, _f64, _u8, C.c_int, _f64, _f64, _f64]
+    L.ora_quad_forms.restype = None
+    L.ora_s_solve.argtypes = [C.c_int64, C.c_int64, _i32, _i32, _f64, _u8, _i32, _f64, _i32, _f64,
+                              C.c_int, _f64, _f64, C.c_double, C.c_int, _i32]
+    L.ora_s_solve.restype = None
+    L.ora_pcg.argtypes = [C.c_int64, _i64, _i32, _f64, C.c_int64, _i32, _i32, _f64, _u8, _i32, _f64,
+                          _i32, _f64, _f64, _f64, C.c_double, C.c_int, C.c_double, C.c_int, _i32, _f64]
+
+
+def _p(a, t):
+    if a is None:
+        return None
+    return a.ctypes.data_as(t)
+
+
+# --------------------------------------------------------------------------
+# Data held by the oracle
+# --------------------------------------------------------------------------
+
+@dataclass
+class OGraph:
+    """The oracle's view of A = L_G + D: the CSR plus the extracted edges."""
+    n: int
+    rowptr: np.ndarray
+    col: np.ndarray
+    val: np.ndarray
+    eu: np.ndarray = None
+    ev: np.ndarray = None
+    ew: np.ndarray = None
+    D: np.ndarray = None
+
+    @property
+    def m(self) -> int:
+        return int(self.eu.shape[0])
+
+
+@dataclass
+class OTree:
+    in_tree: np.ndarray     # uint8[m]
+    rho: int
+    parent: np.ndarray      # int32[n]
+    pw: np.ndarray          # float64[n]
+    order: np.ndarray       # int32[n], BFS order from rho
+
+
+@dataclass
+class DensifyResult:
+    in_s: np.ndarray
+    rounds: int = 0
+    added: list = field(default_factory=list)
+    lmin: list = field(default_factory=list)
+    lmax: list = field(default_factory=list)
+    theta: list = field(default_factory=list)
+    stopped_similar: bool = False
+
+
+# --------------------------------------------------------------------------
+# Steps
+# --------------------------------------------------------------------------
+
+def extract(n, rowptr, col, val) -> OGraph:
+    """Edges (u<v, w) in id order and the diagonal load D (Eq. formula_laplacian)."""
+    rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    val = np.ascontiguousarray(val, dtype=np.float64)
+    cap = max(1, (int(rowptr[-1]) - 0) // 2 + 1)
+    eu = np.empty(cap, np.int32)
+    ev = np.empty(cap, np.int32)
+    ew = np.empty(cap, np.float64)
+    D = np.empty(n, np.float64)
+    m = C.c_int64(0)
+    st = lib().ora_extract(n, _p(rowptr, _i64), _p(col, _i32), _p(val, _f64), cap, C.byref(m),
+                           _p(eu, _i32), _p(ev, _i32), _p(ew, _f64), _p(D, _f64))
+    if st != OK:
+        raise OracleError(st, "extract")
+    m = m.value
+    return OGraph(n, rowptr, col, val, eu[:m].copy(), ev[:m].copy(), ew[:m].copy(), D)
+
+
+def from_graph(g) -> OGraph:
+    return extract(g.n, g.rowptr, g.col, g.val)
+
+
+def mst(og: OGraph) -> np.ndarray:
+    """Maximum-weight spanning tree, ties broken by smaller edge id."""
+    in_tree = np.zeros(og.m, np.uint8)
+    ncomp = C.c_int64(0)
+    st = lib().ora_mst_kruskal(og.n, og.m, _p(og.eu, _i32), _p(og.ev, _i32), _p(og.ew, _f64),
+                               _p(in_tree, _u8), C.byref(ncomp))
+    if st != OK:
+        raise OracleError(st, f"mst ({ncomp.value} components)")
+    return in_tree
+
+
+def orient(og: OGraph, in_tree: np.ndarray, rho: int = 0) -> OTree:
+    parent = np.empty(og.n, np.int32)
+    pw = np.empty(og.n, np.float64)
+    order = np.empty(og.n, np.int32)
+    st = lib().ora_tree_orient(og.n, og.m, _p(og.eu, _i32), _p(og.ev, _i32), _p(og.ew, _f64),
+                               _p(in_tree, _u8), int(rho), _p(parent, _i32), _p(pw, _f64),
+                               _p(order, _i32))
+    if st != OK:
+        raise OracleError(st, "orient")
+    return OTree(in_tree.copy(), int(rho), parent, pw, order)
+
+
+def build_tree(og: OGraph, rho: int = 0) -> OTree:
+    return orient(og, mst(og), rho)
+
+
+def tree_solve(og: OGraph, tree: OTree, B: np.ndarray, D: np.ndarray | None = None) -> np.ndarray:
+    """(L_T + D)^{-1} B, or the solve grounded at tree.rho when D is None."""
+    B2 = np.ascontiguousarray(B, dtype=np.float64)
+    r = 1 if B2.ndim == 1 else B2.shape[1]
+    X = np.empty_like(B2)
+    Dp = None if D is None else np.ascontiguousarray(D, dtype=np.float64)
+    lib().ora_tree_solve(og.n, _p(tree.parent, _i32), _p(tree.pw, _f64), _p(tree.order, _i32),
+                         _p(Dp, _f64), r, _p(B2, _f64), _p(X, _f64))
+    return X
+
+
+def lap_apply(og: OGraph, X: np.ndarray, mask: np.ndarray | None = None) -> np.ndarray:
+    """L X for the graph Laplacian (no D) of all edges, or of mask[e] != 0."""
+    X2 = np.ascontiguousarray(X, dtype=np.float64)
+    r = 1 if X2.ndim == 1 else X2.shape[1]
+    Y = np.empty_like(X2)
+    lib().ora_lap_apply(og.n, og.m, _p(og.eu, _i32), _p(og.ev, _i32), _p(og.ew, _f64),
+                        _p(mask, _u8), r, _p(X2, _f64), _p(Y, _f64))
+    return Y
+
+
+def csr_apply(og: OGraph, x: np.ndarray) -> np.ndarray:
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.empty_like(x)
+    lib().ora_csr_apply(og.n, _p(og.rowptr, _i64), _p(og.col, _i32), _p(og.val, _f64),
+                        _p(x, _f64), _p(y, _f64))
+    return y
+
+
+def heat(og: OGraph, in_s: np.ndarray, H: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
+    """Joule heat of every edge not in S, in increasing edge id (Eq. 5new/6)."""
+    H2 = np.ascontiguousarray(H, dtype=np.float64)
+    r = 1 if H2.ndim == 1 else H2.shape[1]
+    off = np.flatnonzero(in_s == 0).astype(np.int64)
+    out = np.empty(max(1, off.shape[0]), np.float64)
+    k = lib().ora_heat(og.m, _p(og.eu, _i32), _p(og.ev, _i32), _p(og.ew, _f64), _p(in_s, _u8), r,
+                       _p(H2, _f64), _p(out, _f64))
+    assert k == off.shape[0]
+    return out[:k], off
+
+
+def quad_forms(og: OGraph, in_s: np.ndarray, X: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
+    X2 = np.ascontiguousarray(X, dtype=np.float64)
+    r = 1 if X2.ndim == 1 else X2.shape[1]
+    qG = np.empty(r)
+    qS = np.empty(r)
+    lib().ora_quad_forms(og.m, _p(og.eu, _i32), _p(og.ev, _i32), _p(og.ew, _f64), _p(in_s, _u8), r,
+                         _p(X2, _f64), _p(qG, _f64), _p(qS, _f64))
+    return qG, qS
+
+
+def s_solve(og: OGraph, tree: OTree, in_s: np.ndarray | None, Y: np.ndarray,
+            D: np.ndarray | None = None, tol: float = 1e-12, maxit: int = 1000):
+    """(L_S + D)^{-1} Y: direct tree solve when in_s is None (S = tree), else
+    CG on L_S + D preconditioned by the tree solve.  Returns (X, iters)."""
+    Y2 = np.ascontiguousarray(Y, dtype=np.float64)
+    r = 1 if Y2.ndim == 1 else Y2.shape[1]
+    X = np.empty_like(Y2)
+    it = np.zeros(r, np.int32)
+    Dp = None if D is None else np.ascontiguousarray(D, dtype=np.float64)
+    lib().ora_s_solve(og.n, og.m, _p(og.eu, _i32), _p(og.ev, _i32), _p(og.ew, _f64),
+                      _p(in_s, _u8), _p(tree.parent, _i32), _p(tree.pw, _f64),
+                      _p(tree.order, _i32), _p(Dp, _f64), r, _p(Y2, _f64), _p(X, _f64),
+                      float(tol), int(maxit), _p(it, _i32))
+    return X, it
+
+
+def pow2_rescale(H: np.ndarray) -> np.ndarray:
+    """Multiply by the power of two that puts max|H| in [1, 2): exact in
+    binary floating point, the same factor for every column."""
+    mx = float(np.max(np.abs(H)))
+    if mx == 0.0 or not np.isfinite(mx):
+        return H
+    _, e = np.frexp(mx)
+    return np.ldexp(H, -(int(e) - 1))
+
+
+def _s_mask(tree: OTree, in_s: np.ndarray | None):
+    """None when S is the tree itself (direct solve), else the edge mask."""
+    if in_s is None or np.array_equal(in_s, tree.in_tree):
+        return None
+    return in_s
+
+
+def embed(og: OGraph, tree: OTree, in_s: np.ndarray | None, h0: np.ndarray, t: int,
+          inner_tol: float = 1e-12, inner_maxit: int = 1000) -> np.ndarray:
+    """Eq. (formula_pwr_iter): h_t = (L_S^{-1} L_G)^t h_0, h_0 orthogonal to 1
+    (Eq. formula_rand_vec), each step rescaled by a common power of two."""
+    H = np.asarray(h0, dtype=np.float64)
+    H = H - H.mean(axis=0, keepdims=True)
+    mask = _s_mask(tree, in_s)
+    for _ in range(t):
+        Y = lap_apply(og, H)
+        H, _ = s_solve(og, tree, mask, Y, None, inner_tol, inner_maxit)
+        H = pow2_rescale(H)
+    return H
+
+
+def lambda_min_est(og: OGraph, in_s: np.ndarray) -> float:
+    """Eq. (formula_courant-fischer-3): min over nodes of L_G(p,p)/L_S(p,p),
+    the Laplacian diagonals (weighted degrees, D excluded)."""
+    n = og.n
+    dG = np.bincount(og.eu, og.ew, n) + np.bincount(og.ev, og.ew, n)
+    s = in_s.astype(bool)
+    dS = np.bincount(og.eu[s], og.ew[s], n) + np.bincount(og.ev[s], og.ew[s], n)
+    return float(np.min(dG / dS))
+
+
+def lambda_max_est(og: OGraph, tree: OTree, in_s: np.ndarray, v0: np.ndarray, iters: int,
+                   inner_tol: float = 1e-12, inner_maxit: int = 1000) -> float:
+    """Section IV-C-1: `iters` generalized power iterations from v0 (made
+    orthogonal to 1), then the Rayleigh quotient v^T L_G v / v^T L_S v."""
+    v = np.asarray(v0, dtype=np.float64).reshape(-1, 1)
+    v = v - v.mean()
+    mask = _s_mask(tree, in_s)
+    for _ in range(iters):
+        y = lap_apply(og, v)
+        v, _ = s_solve(og, tree, mask, y, None, inner_tol, inner_maxit)
+        v = pow2_rescale(v)
+    qG, qS = quad_forms(og, in_s, v)
+    return float(qG[0] / qS[0])
+
+
+def theta_sigma(sigma2: float, lmin: float, lmax: float, t: int) -> float:
+    """Eq. (formula_heatratio_final)."""
+    return (sigma2 * lmin / lmax) ** (2 * t + 1)
+
+
+def filter_edges(heat_vals: np.ndarray, off_eids: np.ndarray, theta: float, cap: int = 0) -> np.ndarray:
+    """Keep off-tree edge e iff heat_e >= theta * heat_max.  With cap > 0,
+    keep at most cap of them, by (heat descending, edge id ascending).
+    Returns the kept edge ids in increasing order."""
+    if heat_vals.shape[0] == 0:
+        return np.zeros(0, np.int64)
+    thr = theta * float(np.max(heat_vals))
+    keep = np.flatnonzero(heat_vals >= thr)
+    if cap > 0 and keep.shape[0] > cap:
+        order = np.lexsort((off_eids[keep], -heat_vals[keep]))
+        keep = np.sort(keep[order[:cap]])
+    return off_eids[keep].astype(np.int64)
+
+
+def densify(og: OGraph, tree: OTree, h0s, v0s, sigma2: float, t: int, max_rounds: int,
+            lmax_iters: int = 8, cap: int = 0, inner_tol: float = 1e-12,
+            inner_maxit: int = 1000) -> DensifyResult:
+    """Section IV-D: per round, (1) S updated, (2) lambda estimates,
+    (3) stop when lmax/lmin <= sigma^2, (4) t-step power iteration with the
+    round's r start vectors, (5) filter by theta_sigma, add the kept edges.
+    Step (6)'s similarity check is not applied (the paper leaves it undefined)."""
+    in_s = tree.in_tree.copy()
+    res = DensifyResult(in_s)
+    for rd in range(max_rounds):
+        lmin = lambda_min_est(og, in_s)
+        lmax = lambda_max_est(og, tree, in_s, v0s[rd], lmax_iters, inner_tol, inner_maxit)
+        res.lmin.append(lmin)
+        res.lmax.append(lmax)
+        if lmax / lmin <= sigma2:
+            res.stopped_similar = True
+            break
+        H = embed(og, tree, in_s, h0s[rd], t, inner_tol, inner_maxit)
+        hv, off = heat(og, in_s, H)
+        th = theta_sigma(sigma2, lmin, lmax, t)
+        res.theta.append(th)
+        acc = filter_edges(hv, off, th, cap)
+        res.rounds += 1
+        res.added.append(int(acc.shape[0]))
+        if acc.shape[0] == 0:
+            break
+        in_s = in_s.copy()
+        in_s[acc] = 1
+        res.in_s = in_s
+    res.in_s = in_s
+    return res
+
+
+def pcg(og: OGraph, tree: OTree, in_s: np.ndarray | None, b: np.ndarray, tol: float,
+        maxit: int = 1000, inner_tol: float = 1e-6, inner_maxit: int = 50):
+    """Section V-A: PCG on A = L_G + D preconditioned by L_S + D.
+    Returns (x, iterations, ||b - A x|| / ||b||, status)."""
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    x = np.empty_like(b)
+    it = C.c_int32(0)
+    rel = C.c_double(0.0)
+    mask = _s_mask(tree, in_s)
+    st = lib().ora_pcg(og.n, _p(og.rowptr, _i64), _p(og.col, _i32), _p(og.val, _f64), og.m,
+                       _p(og.eu, _i32), _p(og.ev, _i32), _p(og.ew, _f64), _p(mask, _u8),
+                       _p(tree.parent, _i32), _p(tree.pw, _f64), _p(tree.order, _i32),
+                       _p(og.D, _f64), _p(b, _f64), _p(x, _f64), float(tol), int(maxit),
+                       float(inner_tol), int(inner_maxit), C.byref(it), C.byref(rel))
+    return x, it.value, rel.value, st
