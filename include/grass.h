@@ -1,0 +1,250 @@
+/*
+ * grass.h -- C ABI of the GB300 sparsify-and-solve library.
+ *
+ * The library implements the data-parallel path of GRASS, similarity-aware
+ * spectral graph sparsification (Z. Feng, arXiv 1911.04382), on one GPU:
+ *
+ *   grass_build_tree   maximum-weight spanning tree of L_G and its
+ *                      elimination schedule                     (Sec. III-B, III-H)
+ *   grass_embed        t-step generalized power iteration over r vectors
+ *                      and the Joule heat of every off-sparsifier edge
+ *                                                              (Sec. III-F, IV-B)
+ *   grass_filter       threshold theta_sigma, optional top-K   (Eq. heatratio_final)
+ *   grass_densify      iterative densification rounds          (Sec. IV-D)
+ *   grass_pcg_solve    PCG on L_G + D preconditioned by L_S + D (Sec. V-A)
+ *
+ * Conventions shared by every entry point
+ * ----------------------------------------
+ * - "device" pointers are CUDA device (or managed) memory on the device that
+ *   was current when the context was created; "host" pointers are ordinary
+ *   host memory.  The library never frees caller memory.
+ * - Handles (context, tree, sparsifier) are opaque, owned by the library and
+ *   released by the matching *_destroy call.  A tree or sparsifier is only
+ *   valid with the context (and device) that created it.
+ * - Every call enqueues its GPU work on the context's stream.  Calls that
+ *   return host-side results (counts, scalars, statistics) synchronise that
+ *   stream before returning; the others return as soon as work is enqueued.
+ * - Every call returns a grass_status and never aborts, traps or exits.
+ *   grass_last_error(ctx) gives a one-line description of the last failure.
+ * - Vectors and blocks are row-major: block X of n rows and r columns holds
+ *   X[i*r + j].  "prec" selects float (GRASS_FP32) or double (GRASS_FP64)
+ *   element type for the void* blocks of a call.
+ * - Edge ids: edge e = (u < v, w = -A(u,v)) is numbered by the rank of its
+ *   upper-triangle entry in row-major order of the CSR (explicit zeros are
+ *   not edges).
+ */
+#ifndef GRASS_H
+#define GRASS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GRASS_OK = 0,
+    GRASS_ERR_INVALID = 1,        /* bad argument or malformed / non-symmetric CSR  */
+    GRASS_ERR_NOT_SDD = 2,        /* a row has D(p) = row sum < -1e-12 A(p,p)        */
+    GRASS_ERR_DISCONNECTED = 3,   /* the graph has more than one component           */
+    GRASS_ERR_OOM = 4,            /* device allocation failed                        */
+    GRASS_ERR_NOT_CONVERGED = 5,  /* iteration limit reached; outputs still written  */
+    GRASS_ERR_TIMEOUT = 6,        /* a bounded device-side wait expired               */
+    GRASS_ERR_CUDA = 7            /* any other CUDA runtime error                     */
+} grass_status;
+
+typedef enum { GRASS_FP64 = 0, GRASS_FP32 = 1 } grass_prec;
+
+#define GRASS_MAX_ROUNDS 16
+
+/* Full symmetric CSR of the SDD matrix A = L_G + D (Sec. II-A, Eq.
+ * formula_laplacian): rows sorted by column, no duplicates, off-diagonal
+ * entries <= 0 (-w for an edge), diagonal present.  All pointers device. */
+typedef struct {
+    int64_t n;
+    int64_t nnz;
+    const int64_t *rowptr;   /* [n+1], rowptr[0] = 0, rowptr[n] = nnz */
+    const int32_t *col;      /* [nnz] */
+    const double *val;       /* [nnz] */
+} grass_csr_t;
+
+/* Densification parameters (Sec. IV-D). */
+typedef struct {
+    double sigma2;               /* target relative condition number sigma^2          */
+    int r;                       /* random vectors per round, 1..32                   */
+    int t;                       /* power steps per round, >= 1 (paper: t = 2)        */
+    int max_rounds;              /* densification rounds, 1..GRASS_MAX_ROUNDS         */
+    int lmax_iters;              /* power steps for the lambda_max estimate (< 10)    */
+    int64_t max_add_per_round;   /* <= 0: keep every edge over the threshold          */
+    grass_prec embed_prec;       /* precision of power iteration, SpMM and heat       */
+    double inner_tol;            /* inner CG: stop at ||r|| <= inner_tol ||y||         */
+    int inner_maxit;             /* inner CG: iteration cap                           */
+} grass_params_t;
+
+typedef struct {
+    int rounds;                              /* filter+add passes executed            */
+    int stopped_similar;                     /* 1 if lmax/lmin <= sigma^2 ended it    */
+    int64_t added;                           /* off-tree edges added in total          */
+    int64_t offtree_embedded;                /* off-S edges embedded, summed over rounds */
+    int64_t added_round[GRASS_MAX_ROUNDS];
+    int64_t embedded_round[GRASS_MAX_ROUNDS];
+    double lmin_est[GRASS_MAX_ROUNDS];
+    double lmax_est[GRASS_MAX_ROUNDS];
+    double theta[GRASS_MAX_ROUNDS];
+    double heat_max[GRASS_MAX_ROUNDS];
+    int64_t inner_iters;                     /* inner CG iterations, all solves       */
+    double ms_estimate, ms_embed, ms_filter, ms_update, ms_total;
+} grass_sparsify_stats_t;
+
+typedef struct {
+    int iters;              /* PCG iterations (all refinement passes)          */
+    int refinements;        /* FP64 refinement passes (FP32 mode), else 0       */
+    int64_t inner_iters;    /* inner CG iterations of the preconditioner        */
+    double rel_resid_fp64;  /* ||b - A x||_2 / ||b||_2 recomputed in FP64       */
+    double ms;
+} grass_solve_stats_t;
+
+typedef struct grass_ctx_s *grass_ctx_t;
+typedef struct grass_tree_s *grass_tree_t;
+typedef struct grass_sparsifier_s *grass_sparsifier_t;
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context on the current CUDA device.  stream: a cudaStream_t
+ * passed as void* (NULL = the legacy default stream).  The caller keeps
+ * ownership of the stream.  Errors: INVALID (out == NULL), CUDA, OOM. */
+grass_status grass_ctx_create(grass_ctx_t *out, void *stream);
+void grass_ctx_destroy(grass_ctx_t ctx);
+/* Switch the stream later calls enqueue on (same device). */
+grass_status grass_ctx_set_stream(grass_ctx_t ctx, void *stream);
+/* Text of the last failure of a call on ctx ("" if none).  Valid until the
+ * next call on ctx. */
+const char *grass_last_error(grass_ctx_t ctx);
+/* Number of GPU kernel launches the library issued on ctx so far. */
+int64_t grass_launch_count(grass_ctx_t ctx);
+
+/* ---------------------------------------------------------------- tree */
+
+/* Validate A = L_G + D (Sec. II-A), extract its edges, build the
+ * maximum-weight spanning tree (ties broken by smaller edge id, so the tree
+ * is unique) and the tree's elimination schedule.  The paper's backbone is a
+ * low-stretch tree (Sec. III-B); this library uses the maximum-weight tree.
+ * ground: the row rho at which L_T and L_S are made invertible (the limit of
+ * the tiny diagonal on one row, Sec. III-F); 0 <= ground < n.
+ * The tree copies what it needs from A; A may be freed afterwards.
+ * Errors: INVALID (bad CSR, positive or unmatched off-diagonal, n < 2,
+ * nnz >= 2^31), NOT_SDD, DISCONNECTED, OOM, CUDA. */
+grass_status grass_build_tree(grass_ctx_t ctx, const grass_csr_t *A, int32_t ground,
+                              grass_tree_t *out);
+void grass_tree_destroy(grass_tree_t tree);
+
+/* Sizes: n, m (edges), factor_rounds (contraction rounds of the tree
+ * elimination schedule).  Any pointer may be NULL.  Host outputs. */
+grass_status grass_tree_info(grass_tree_t tree, int64_t *n, int64_t *m, int64_t *factor_rounds);
+
+/* Export the extracted graph (device outputs, m entries each, any may be
+ * NULL): eu[e] < ev[e], ew[e] = w_e; D (n entries) = diagonal load. */
+grass_status grass_tree_graph(grass_ctx_t ctx, grass_tree_t tree, int32_t *eu, int32_t *ev,
+                              double *ew, double *D);
+
+/* Export in_tree[e] = 1 for tree edges, else 0 (device, m bytes). */
+grass_status grass_tree_edges(grass_ctx_t ctx, grass_tree_t tree, uint8_t *in_tree);
+
+/* X = L_T^{-1} B grounded at rho (with_D = 0; X[rho] = 0) or
+ * X = (L_T + D)^{-1} B (with_D = 1), by the tree's elimination schedule
+ * (Sec. III-H: linear-time tree factorization).  B, X: device, n x r.
+ * B and X may alias.  1 <= r <= 32. */
+grass_status grass_tree_solve(grass_ctx_t ctx, grass_tree_t tree, int with_D, int r,
+                              grass_prec prec, const void *B, void *X);
+
+/* Y = L_G X (graph Laplacian, D excluded; Eq. formula_laplacian).
+ * X, Y: device, n x r, must not alias.  1 <= r <= 32. */
+grass_status grass_spmm(grass_ctx_t ctx, grass_tree_t tree, int r, grass_prec prec,
+                        const void *X, void *Y);
+
+/* ---------------------------------------------------------------- sparsifier */
+
+/* New sparsifier S = the tree (Sec. III-B step 1). */
+grass_status grass_sparsifier_create(grass_ctx_t ctx, grass_tree_t tree, grass_sparsifier_t *out);
+void grass_sparsifier_destroy(grass_sparsifier_t S);
+/* Add edges (device ids, count >= 0) to S.  Ids already in S are ignored;
+ * ids out of range give INVALID. */
+grass_status grass_sparsifier_add(grass_ctx_t ctx, grass_sparsifier_t S, const int64_t *eids,
+                                  int64_t count);
+/* Host outputs: edges in S, edges outside S (m_off). */
+grass_status grass_sparsifier_info(grass_sparsifier_t S, int64_t *n_edges, int64_t *m_off);
+/* in_s[e] = 1 if edge e is in S (device, m bytes). */
+grass_status grass_sparsifier_mask(grass_ctx_t ctx, grass_sparsifier_t S, uint8_t *in_s);
+/* Ids of the edges outside S, increasing (device, m_off entries): the order
+ * of the heat array of grass_embed. */
+grass_status grass_sparsifier_offtree(grass_ctx_t ctx, grass_sparsifier_t S, int64_t *eids);
+
+/* ---------------------------------------------------------------- embed / filter */
+
+/* Spectral embedding of the off-S edges (Sec. III-F, Eqs. formula_pwr_iter,
+ * formula_pwr_iter5new, formula_pwr_iter6):
+ *   H <- L_S^{-1} L_G H, t times, from H = h0 (n x r, device, double);
+ * L_S^{-1} grounded at rho; by the tree solve when S is the tree, else by
+ * r-column CG on L_S preconditioned by the tree (inner_tol, inner_maxit).
+ * After each step H is multiplied by the power of two that puts max|H| in
+ * [1,2) (exact; the common factor leaves normalised heats unchanged).
+ * h0 need not be orthogonal to 1: the first product with L_G removes any
+ * constant.  Outputs (device, optional = NULL):
+ *   H_out [n x r] in prec;  heat [m_off] in prec, heat[i] = w_e sum_j
+ *   (H[u][j] - H[v][j])^2 for the i-th off-S edge e = (u,v) in increasing id.
+ * Host output heat_max (optional).  1 <= r <= 32, t >= 1. */
+grass_status grass_embed(grass_ctx_t ctx, grass_sparsifier_t S, const double *h0, int r, int t,
+                         grass_prec prec, double inner_tol, int inner_maxit, void *H_out,
+                         void *heat, double *heat_max);
+
+/* lambda_min estimate (Sec. IV-C-2, Eq. formula_courant-fischer-3):
+ * min over p of L_G(p,p) / L_S(p,p), Laplacian diagonals.  Host output. */
+grass_status grass_lambda_min(grass_ctx_t ctx, grass_sparsifier_t S, double *lmin);
+
+/* lambda_max estimate (Sec. IV-C-1): iters generalized power steps from v0
+ * (device, n doubles), then the Rayleigh quotient v^T L_G v / v^T L_S v
+ * (FP64 sums).  Host output. */
+grass_status grass_lambda_max(grass_ctx_t ctx, grass_sparsifier_t S, const double *v0, int iters,
+                              grass_prec prec, double inner_tol, int inner_maxit, double *lmax);
+
+/* Edge filter (Eq. formula_heatratio_final):
+ *   theta = (sigma2 * lmin / lmax)^(2t+1); keep off-S edge i iff
+ *   heat[i] >= theta * max(heat).
+ * cap > 0 keeps at most cap edges, the largest heats first and the smaller
+ * id among equal heats (radix select).  heat: device [m_off] in prec, the
+ * order of grass_embed.  accepted: device, room for min(m_off, cap) ids,
+ * written in increasing id.  Host outputs n_accepted, theta (optional). */
+grass_status grass_filter(grass_ctx_t ctx, grass_sparsifier_t S, const void *heat, grass_prec prec,
+                          double sigma2, double lmin, double lmax, int t, int64_t cap,
+                          int64_t *accepted, int64_t *n_accepted, double *theta);
+
+/* ---------------------------------------------------------------- densify / solve */
+
+/* Iterative densification (Sec. IV-D).  Per round k < max_rounds:
+ * (2) lambda estimates on the current S, (3) stop if lmax/lmin <= sigma2,
+ * (4) embed with h0 + k*n*r (device, max_rounds*n*r doubles) and the
+ * lambda_max start v0 + k*n (device, max_rounds*n doubles), (5) filter,
+ * add the kept edges.  The paper's step (6) similarity check is not applied.
+ * out: a new sparsifier (tree + added edges).  stats: host, optional. */
+grass_status grass_densify(grass_ctx_t ctx, grass_tree_t tree, const grass_params_t *params,
+                           const double *h0, const double *v0, grass_sparsifier_t *out,
+                           grass_sparsify_stats_t *stats);
+
+/* Solve A x = b, A = L_G + D of the tree's matrix, by PCG (Sec. V-A),
+ * x0 = 0, until ||b - A x||_2 <= tol ||b||_2 (measured in FP64).
+ * Preconditioner M = L_S + D: the tree solve when S is the tree, else r=1 CG
+ * on L_S + D preconditioned by the tree (inner_tol, inner_maxit) and the
+ * flexible PCG update.  prec = GRASS_FP64: FP64 PCG.  prec = GRASS_FP32:
+ * FP32 vectors and matrix, FP64 dot products and alpha/beta, wrapped in FP64
+ * iterative refinement (each pass reduces the residual by refine_tol).
+ * b, x: device, n doubles.  maxit bounds PCG iterations over all passes.
+ * Errors: NOT_CONVERGED (x and stats still written).  stats optional. */
+grass_status grass_pcg_solve(grass_ctx_t ctx, grass_sparsifier_t S, const double *b, double *x,
+                             double tol, int maxit, grass_prec prec, double refine_tol,
+                             double inner_tol, int inner_maxit, grass_solve_stats_t *stats);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GRASS_H */

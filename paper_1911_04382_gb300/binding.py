@@ -1,0 +1,324 @@
+"""ctypes binding of libgrass.so (include/grass.h), same names as the C ABI.
+
+Argument marshalling only: device buffers are torch tensors (or raw integer
+addresses), host results come back as Python values.  Every GPU step runs in
+the library's CUDA kernels; there is no fallback path.  A missing library is
+an error: build it with ``paper_1911_04382_gb300.build()``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+from .build import LIB
+
+GRASS_OK = 0
+GRASS_ERR_INVALID = 1
+GRASS_ERR_NOT_SDD = 2
+GRASS_ERR_DISCONNECTED = 3
+GRASS_ERR_OOM = 4
+GRASS_ERR_NOT_CONVERGED = 5
+GRASS_ERR_TIMEOUT = 6
+GRASS_ERR_CUDA = 7
+GRASS_FP64 = 0
+GRASS_FP32 = 1
+GRASS_MAX_ROUNDS = 16
+
+_STATUS = {0: "OK", 1: "INVALID", 2: "NOT_SDD", 3: "DISCONNECTED", 4: "OOM",
+           5: "NOT_CONVERGED", 6: "TIMEOUT", 7: "CUDA"}
+
+
+class GrassError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where}: GRASS_ERR_{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class grass_csr_t(C.Structure):
+    _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("rowptr", C.c_void_p),
+                ("col", C.c_void_p), ("val", C.c_void_p)]
+
+
+class grass_params_t(C.Structure):
+    _fields_ = [("sigma2", C.c_double), ("r", C.c_int), ("t", C.c_int), ("max_rounds", C.c_int),
+                ("lmax_iters", C.c_int), ("max_add_per_round", C.c_int64),
+                ("embed_prec", C.c_int), ("inner_tol", C.c_double), ("inner_maxit", C.c_int)]
+
+
+_R = GRASS_MAX_ROUNDS
+
+
+class grass_sparsify_stats_t(C.Structure):
+    _fields_ = [("rounds", C.c_int), ("stopped_similar", C.c_int), ("added", C.c_int64),
+                ("offtree_embedded", C.c_int64), ("added_round", C.c_int64 * _R),
+                ("embedded_round", C.c_int64 * _R), ("lmin_est", C.c_double * _R),
+                ("lmax_est", C.c_double * _R), ("theta", C.c_double * _R),
+                ("heat_max", C.c_double * _R), ("inner_iters", C.c_int64),
+                ("ms_estimate", C.c_double), ("ms_embed", C.c_double), ("ms_filter", C.c_double),
+                ("ms_update", C.c_double), ("ms_total", C.c_double)]
+
+    def as_dict(self) -> dict:
+        k = max(self.rounds, 1 if self.stopped_similar else 0)
+        k = min(max(k, self.rounds + (1 if self.stopped_similar else 0)), _R)
+        return {
+            "rounds": self.rounds, "stopped_similar": bool(self.stopped_similar),
+            "added": self.added, "offtree_embedded": self.offtree_embedded,
+            "added_round": list(self.added_round[:self.rounds]),
+            "embedded_round": list(self.embedded_round[:self.rounds]),
+            "lmin_est": list(self.lmin_est[:k]), "lmax_est": list(self.lmax_est[:k]),
+            "theta": list(self.theta[:self.rounds]), "heat_max": list(self.heat_max[:self.rounds]),
+            "inner_iters": self.inner_iters, "ms_estimate": self.ms_estimate,
+            "ms_embed": self.ms_embed, "ms_filter": self.ms_filter, "ms_update": self.ms_update,
+            "ms_total": self.ms_total,
+        }
+
+
+class grass_solve_stats_t(C.Structure):
+    _fields_ = [("iters", C.c_int), ("refinements", C.c_int), ("inner_iters", C.c_int64),
+                ("rel_resid_fp64", C.c_double), ("ms", C.c_double)]
+
+    def as_dict(self) -> dict:
+        return {"iters": self.iters, "refinements": self.refinements,
+                "inner_iters": self.inner_iters, "rel_resid_fp64": self.rel_resid_fp64,
+                "ms": self.ms}
+
+
+_lib = None
+_lock = threading.Lock()
+_vp, _i64, _i32, _d = C.c_void_p, C.c_int64, C.c_int32, C.c_double
+
+
+def lib():
+    """Load libgrass.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB):
+                raise RuntimeError(f"CUDA library {LIB} is missing: run paper_1911_04382_gb300.build()")
+            L = C.CDLL(LIB)
+            sig = {
+                "grass_ctx_create": [C.POINTER(_vp), _vp],
+                "grass_ctx_set_stream": [_vp, _vp],
+                "grass_build_tree": [_vp, C.POINTER(grass_csr_t), _i32, C.POINTER(_vp)],
+                "grass_tree_info": [_vp, C.POINTER(_i64), C.POINTER(_i64), C.POINTER(_i64)],
+                "grass_tree_graph": [_vp, _vp, _vp, _vp, _vp, _vp],
+                "grass_tree_edges": [_vp, _vp, _vp],
+                "grass_tree_solve": [_vp, _vp, C.c_int, C.c_int, C.c_int, _vp, _vp],
+                "grass_spmm": [_vp, _vp, C.c_int, C.c_int, _vp, _vp],
+                "grass_sparsifier_create": [_vp, _vp, C.POINTER(_vp)],
+                "grass_sparsifier_add": [_vp, _vp, _vp, _i64],
+                "grass_sparsifier_info": [_vp, C.POINTER(_i64), C.POINTER(_i64)],
+                "grass_sparsifier_mask": [_vp, _vp, _vp],
+                "grass_sparsifier_offtree": [_vp, _vp, _vp],
+                "grass_embed": [_vp, _vp, _vp, C.c_int, C.c_int, C.c_int, _d, C.c_int, _vp, _vp,
+                                C.POINTER(_d)],
+                "grass_lambda_min": [_vp, _vp, C.POINTER(_d)],
+                "grass_lambda_max": [_vp, _vp, _vp, C.c_int, C.c_int, _d, C.c_int, C.POINTER(_d)],
+                "grass_filter": [_vp, _vp, _vp, C.c_int, _d, _d, _d, C.c_int, _i64, _vp,
+                                 C.POINTER(_i64), C.POINTER(_d)],
+                "grass_densify": [_vp, _vp, C.POINTER(grass_params_t), _vp, _vp, C.POINTER(_vp),
+                                  C.POINTER(grass_sparsify_stats_t)],
+                "grass_pcg_solve": [_vp, _vp, _vp, _vp, _d, C.c_int, C.c_int, _d, _d, C.c_int,
+                                    C.POINTER(grass_solve_stats_t)],
+            }
+            for name, args in sig.items():
+                f = getattr(L, name)
+                f.argtypes = args
+                f.restype = C.c_int
+            for name in ("grass_ctx_destroy", "grass_tree_destroy", "grass_sparsifier_destroy"):
+                getattr(L, name).argtypes = [_vp]
+                getattr(L, name).restype = None
+            L.grass_last_error.argtypes = [_vp]
+            L.grass_last_error.restype = C.c_char_p
+            L.grass_launch_count.argtypes = [_vp]
+            L.grass_launch_count.restype = C.c_int64
+            _lib = L
+    return _lib
+
+
+def _p(x):
+    """Device address of a tensor, an int address, or None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _check(ctx, st: int, where: str, allow=()):
+    if st != GRASS_OK and st not in allow:
+        msg = lib().grass_last_error(ctx).decode() if ctx else ""
+        raise GrassError(st, where, msg)
+    return st
+
+
+# ---------------------------------------------------------------- context
+
+def grass_ctx_create(stream=None) -> int:
+    out = _vp()
+    st = lib().grass_ctx_create(C.byref(out), _stream(stream))
+    if st != GRASS_OK:
+        raise GrassError(st, "grass_ctx_create", "context creation failed")
+    return out.value
+
+
+def grass_ctx_destroy(ctx: int) -> None:
+    lib().grass_ctx_destroy(ctx)
+
+
+def grass_ctx_set_stream(ctx: int, stream=None) -> None:
+    _check(ctx, lib().grass_ctx_set_stream(ctx, _stream(stream)), "grass_ctx_set_stream")
+
+
+def grass_last_error(ctx: int) -> str:
+    return lib().grass_last_error(ctx).decode()
+
+
+def grass_launch_count(ctx: int) -> int:
+    return int(lib().grass_launch_count(ctx))
+
+
+# ---------------------------------------------------------------- tree
+
+def grass_build_tree(ctx: int, rowptr, col, val, ground: int = 0, n: int | None = None,
+                     nnz: int | None = None) -> int:
+    """rowptr (int64 [n+1]), col (int32 [nnz]), val (float64 [nnz]) on the device."""
+    A = grass_csr_t()
+    A.n = int(rowptr.numel() - 1) if n is None else n
+    A.nnz = int(col.numel()) if nnz is None else nnz
+    A.rowptr, A.col, A.val = _p(rowptr), _p(col), _p(val)
+    out = _vp()
+    _check(ctx, lib().grass_build_tree(ctx, C.byref(A), int(ground), C.byref(out)),
+           "grass_build_tree")
+    return out.value
+
+
+def grass_tree_destroy(tree: int) -> None:
+    lib().grass_tree_destroy(tree)
+
+
+def grass_tree_info(tree: int) -> tuple[int, int, int]:
+    n, m, r = _i64(), _i64(), _i64()
+    _check(None, lib().grass_tree_info(tree, C.byref(n), C.byref(m), C.byref(r)), "grass_tree_info")
+    return n.value, m.value, r.value
+
+
+def grass_tree_graph(ctx, tree, eu=None, ev=None, ew=None, D=None) -> None:
+    _check(ctx, lib().grass_tree_graph(ctx, tree, _p(eu), _p(ev), _p(ew), _p(D)), "grass_tree_graph")
+
+
+def grass_tree_edges(ctx, tree, in_tree) -> None:
+    _check(ctx, lib().grass_tree_edges(ctx, tree, _p(in_tree)), "grass_tree_edges")
+
+
+def grass_tree_solve(ctx, tree, with_D: int, r: int, prec: int, B, X) -> None:
+    _check(ctx, lib().grass_tree_solve(ctx, tree, int(with_D), r, prec, _p(B), _p(X)),
+           "grass_tree_solve")
+
+
+def grass_spmm(ctx, tree, r: int, prec: int, X, Y) -> None:
+    _check(ctx, lib().grass_spmm(ctx, tree, r, prec, _p(X), _p(Y)), "grass_spmm")
+
+
+# ---------------------------------------------------------------- sparsifier
+
+def grass_sparsifier_create(ctx, tree) -> int:
+    out = _vp()
+    _check(ctx, lib().grass_sparsifier_create(ctx, tree, C.byref(out)), "grass_sparsifier_create")
+    return out.value
+
+
+def grass_sparsifier_destroy(S) -> None:
+    lib().grass_sparsifier_destroy(S)
+
+
+def grass_sparsifier_add(ctx, S, eids, count: int | None = None) -> None:
+    cnt = int(eids.numel()) if count is None else int(count)
+    _check(ctx, lib().grass_sparsifier_add(ctx, S, _p(eids), cnt), "grass_sparsifier_add")
+
+
+def grass_sparsifier_info(S) -> tuple[int, int]:
+    a, b = _i64(), _i64()
+    _check(None, lib().grass_sparsifier_info(S, C.byref(a), C.byref(b)), "grass_sparsifier_info")
+    return a.value, b.value
+
+
+def grass_sparsifier_mask(ctx, S, in_s) -> None:
+    _check(ctx, lib().grass_sparsifier_mask(ctx, S, _p(in_s)), "grass_sparsifier_mask")
+
+
+def grass_sparsifier_offtree(ctx, S, eids) -> None:
+    _check(ctx, lib().grass_sparsifier_offtree(ctx, S, _p(eids)), "grass_sparsifier_offtree")
+
+
+# ---------------------------------------------------------------- embed / filter
+
+def grass_embed(ctx, S, h0, r: int, t: int, prec: int, inner_tol: float = 1e-10,
+                inner_maxit: int = 1000, H_out=None, heat=None) -> float:
+    hm = _d(0.0)
+    _check(ctx, lib().grass_embed(ctx, S, _p(h0), r, t, prec, inner_tol, inner_maxit, _p(H_out),
+                                  _p(heat), C.byref(hm)), "grass_embed")
+    return hm.value
+
+
+def grass_lambda_min(ctx, S) -> float:
+    v = _d(0.0)
+    _check(ctx, lib().grass_lambda_min(ctx, S, C.byref(v)), "grass_lambda_min")
+    return v.value
+
+
+def grass_lambda_max(ctx, S, v0, iters: int, prec: int, inner_tol: float = 1e-10,
+                     inner_maxit: int = 1000) -> float:
+    v = _d(0.0)
+    _check(ctx, lib().grass_lambda_max(ctx, S, _p(v0), iters, prec, inner_tol, inner_maxit,
+                                       C.byref(v)), "grass_lambda_max")
+    return v.value
+
+
+def grass_filter(ctx, S, heat, prec: int, sigma2: float, lmin: float, lmax: float, t: int,
+                 cap: int, accepted) -> tuple[int, float]:
+    na, th = _i64(0), _d(0.0)
+    _check(ctx, lib().grass_filter(ctx, S, _p(heat), prec, sigma2, lmin, lmax, t, int(cap),
+                                   _p(accepted), C.byref(na), C.byref(th)), "grass_filter")
+    return na.value, th.value
+
+
+# ---------------------------------------------------------------- densify / solve
+
+def make_params(sigma2: float, r: int, t: int, max_rounds: int, lmax_iters: int = 8,
+                max_add_per_round: int = 0, embed_prec: int = GRASS_FP64,
+                inner_tol: float = 1e-10, inner_maxit: int = 1000) -> grass_params_t:
+    P = grass_params_t()
+    P.sigma2, P.r, P.t, P.max_rounds, P.lmax_iters = sigma2, r, t, max_rounds, lmax_iters
+    P.max_add_per_round, P.embed_prec = max_add_per_round, embed_prec
+    P.inner_tol, P.inner_maxit = inner_tol, inner_maxit
+    return P
+
+
+def grass_densify(ctx, tree, params: grass_params_t, h0, v0):
+    """Returns (sparsifier handle, grass_sparsify_stats_t)."""
+    out = _vp()
+    st = grass_sparsify_stats_t()
+    _check(ctx, lib().grass_densify(ctx, tree, C.byref(params), _p(h0), _p(v0), C.byref(out),
+                                    C.byref(st)), "grass_densify")
+    return out.value, st
+
+
+def grass_pcg_solve(ctx, S, b, x, tol: float, maxit: int, prec: int, refine_tol: float = 1e-3,
+                    inner_tol: float = 1e-6, inner_maxit: int = 50):
+    """Returns (status, grass_solve_stats_t); NOT_CONVERGED is returned, not raised."""
+    st = grass_solve_stats_t()
+    s = _check(ctx, lib().grass_pcg_solve(ctx, S, _p(b), _p(x), tol, maxit, prec, refine_tol,
+                                          inner_tol, inner_maxit, C.byref(st)),
+               "grass_pcg_solve", allow=(GRASS_ERR_NOT_CONVERGED,))
+    return s, st

@@ -1,0 +1,526 @@
+// api.cu -- the extern "C" entry points declared in include/grass.h:
+// argument checks, orchestration of the kernels of the other files, the
+// power iteration (Sec. III-F), the lambda estimates (Sec. IV-C) and the
+// densification loop (Sec. IV-D).
+#include <chrono>
+#include <cmath>
+#include <new>
+
+#include "common.cuh"
+
+using namespace grass;
+
+#define API_BEGIN(ctx)                                                   \
+    grass_ctx_t api_ctx_ = (ctx);                                        \
+    try {                                                                \
+        if (api_ctx_) GCK(cudaSetDevice(api_ctx_->device));
+#define API_END                                                          \
+    }                                                                    \
+    catch (const grass::Error &e) {                                      \
+        if (api_ctx_) api_ctx_->err = e.msg;                             \
+        return e.st;                                                     \
+    }                                                                    \
+    catch (const std::bad_alloc &) {                                     \
+        if (api_ctx_) api_ctx_->err = "host allocation failed";          \
+        return GRASS_ERR_OOM;                                            \
+    }                                                                    \
+    catch (...) {                                                        \
+        if (api_ctx_) api_ctx_->err = "unexpected internal error";       \
+        return GRASS_ERR_CUDA;                                           \
+    }                                                                    \
+    return GRASS_OK;
+
+namespace {
+
+double now_ms() {
+    using namespace std::chrono;
+    return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
+size_t esize(grass_prec p) { return p == GRASS_FP64 ? 8 : 4; }
+
+void need(bool ok, const char *msg) {
+    if (!ok) fail(GRASS_ERR_INVALID, msg);
+}
+
+void need_prec(grass_prec p) { need(p == GRASS_FP64 || p == GRASS_FP32, "prec must be GRASS_FP64 or GRASS_FP32"); }
+
+unsigned long long *maxslot(grass_ctx_t ctx, int k) {
+    return (unsigned long long *)(ctx->scal.p + DS_MAX) + k;
+}
+
+double bits_to_double(unsigned long long b) {
+    double d;
+    std::memcpy(&d, &b, sizeof(d));
+    return d;
+}
+
+void ensure_sdd(grass_ctx_t ctx, grass_tree_t T) {
+    if (!T->has_sdd) {
+        tree_factor(ctx, T, true, T->sdd);
+        T->has_sdd = true;
+    }
+}
+
+// Sec. III-F, Eq. (formula_pwr_iter): t steps H <- L_S^{-1} L_G H.  H holds
+// the unscaled last iterate on return; *scale_slot the max-abs bits that
+// give its pending power-of-two factor.  Returns inner CG iterations.
+int64_t power_steps(grass_ctx_t ctx, grass_sparsifier_t S, const double *h0, int r, int t,
+                    grass_prec prec, double inner_tol, int inner_maxit, void *H, void *Y,
+                    int *scale_slot) {
+    const GraphData &g = S->tree->g;
+    const int64_t n = g.n;
+    convert_block(ctx, prec, n * r, h0, H);
+    const void *w = prec == GRASS_FP64 ? (const void *)g.adj_w64.p : (const void *)g.adj_w32.p;
+    int prev = -1, cur = 0;
+    int64_t inner = 0;
+    for (int s = 0; s < t; ++s) {
+        lap_mm(ctx, r, prec, n, g.adj_ptr.p, g.adj_col.p, w, nullptr, H, Y,
+               prev >= 0 ? maxslot(ctx, prev) : nullptr);
+        memset_d(ctx, maxslot(ctx, cur), 0, sizeof(unsigned long long));
+        inner += s_solve(ctx, S, false, r, prec, Y, H, inner_tol, inner_maxit, maxslot(ctx, cur));
+        prev = cur;
+        cur ^= 1;
+    }
+    *scale_slot = prev;
+    return inner;
+}
+
+struct EmbedOut {
+    double heat_max;
+    int64_t inner;
+};
+
+EmbedOut embed_impl(grass_ctx_t ctx, grass_sparsifier_t S, const double *h0, int r, int t,
+                    grass_prec prec, double inner_tol, int inner_maxit, void *H_out, void *heat) {
+    const int64_t n = S->tree->g.n;
+    void *H = ctx->scr<char>(SCR_H, n * r * esize(prec));
+    void *Y = ctx->scr<char>(SCR_Y, n * r * esize(prec));
+    int slot = 0;
+    EmbedOut o{0.0, 0};
+    o.inner = power_steps(ctx, S, h0, r, t, prec, inner_tol, inner_maxit, H, Y, &slot);
+    unsigned long long *hm = maxslot(ctx, 2);
+    heat_offs(ctx, r, prec, S, H, maxslot(ctx, slot), heat, hm);
+    if (H_out) {
+        copy_d(ctx, H_out, H, n * r * esize(prec));
+        apply_pow2(ctx, prec, n * r, H_out, maxslot(ctx, slot));
+    }
+    unsigned long long b = 0;
+    d2h(ctx, &b, hm, sizeof(b));
+    o.heat_max = bits_to_double(b);
+    return o;
+}
+
+// Sec. IV-C-1: iters generalized power steps, then v^T L_G v / v^T L_S v.
+double lambda_max_impl(grass_ctx_t ctx, grass_sparsifier_t S, const double *v0, int iters,
+                       grass_prec prec, double inner_tol, int inner_maxit, int64_t *inner) {
+    const int64_t n = S->tree->g.n;
+    void *v = ctx->scr<char>(SCR_LMAX_V, n * esize(prec));
+    void *y = ctx->scr<char>(SCR_LMAX_Y, n * esize(prec));
+    int slot = -1;
+    if (iters > 0) {
+        *inner += power_steps(ctx, S, v0, 1, iters, prec, inner_tol, inner_maxit, v, y, &slot);
+        apply_pow2(ctx, prec, n, v, maxslot(ctx, slot));
+    } else {
+        convert_block(ctx, prec, n, v0, v);
+    }
+    double *q = ctx->scal.p + DS_RED + 16;
+    quad_forms(ctx, prec, S, v, q);
+    double qq[2];
+    d2h(ctx, qq, q, sizeof(qq));
+    if (!(qq[1] > 0.0)) fail(GRASS_ERR_INVALID, "v^T L_S v is not positive (v0 constant?)");
+    return qq[0] / qq[1];
+}
+
+double theta_sigma(double sigma2, double lmin, double lmax, int t) {
+    // Eq. (formula_heatratio_final)
+    return std::pow(sigma2 * lmin / lmax, 2 * t + 1);
+}
+
+grass_sparsifier_t new_sparsifier(grass_ctx_t ctx, grass_tree_t T) {
+    auto *S = new grass_sparsifier_s();
+    S->ctx = ctx;
+    S->tree = T;
+    try {
+        S->in_s.alloc(T->g.m);
+        copy_d(ctx, S->in_s.p, T->in_tree.p, T->g.m);
+        sparsifier_rebuild(ctx, S);
+    } catch (...) {
+        delete S;
+        throw;
+    }
+    return S;
+}
+
+}  // namespace
+
+extern "C" {
+
+// ---------------------------------------------------------------- context
+
+grass_status grass_ctx_create(grass_ctx_t *out, void *stream) {
+    if (!out) return GRASS_ERR_INVALID;
+    *out = nullptr;
+    grass_ctx_t ctx = nullptr;
+    try {
+        int dev = 0;
+        int count = 0;
+        GCK(cudaGetDeviceCount(&count));
+        if (count <= 0) fail(GRASS_ERR_CUDA, "no CUDA device");
+        GCK(cudaGetDevice(&dev));
+        ctx = new grass_ctx_s();
+        ctx->device = dev;
+        ctx->stream = (cudaStream_t)stream;
+        ctx->flags.alloc(8);
+        ctx->scal.alloc(DS_TOTAL);
+        ctx->partials.alloc((size_t)kRedBlocks * 32 * 2);
+        ctx->counters.alloc(16);
+        GCK(cudaMemset(ctx->counters.p, 0, 16 * sizeof(unsigned int)));
+        GCK(cudaMemset(ctx->flags.p, 0, 8 * sizeof(int)));
+        GCK(cudaMemset(ctx->scal.p, 0, DS_TOTAL * sizeof(double)));
+        GCK(cudaMallocHost((void **)&ctx->hpin, 4096 * sizeof(double)));
+        GCK(cudaDeviceSynchronize());
+    } catch (const grass::Error &e) {
+        delete ctx;
+        return e.st;
+    } catch (...) {
+        delete ctx;
+        return GRASS_ERR_CUDA;
+    }
+    *out = ctx;
+    return GRASS_OK;
+}
+
+void grass_ctx_destroy(grass_ctx_t ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    if (ctx->hpin) cudaFreeHost(ctx->hpin);
+    delete ctx;
+}
+
+grass_status grass_ctx_set_stream(grass_ctx_t ctx, void *stream) {
+    if (!ctx) return GRASS_ERR_INVALID;
+    API_BEGIN(ctx)
+    ctx->sync();
+    ctx->stream = (cudaStream_t)stream;
+    API_END
+}
+
+const char *grass_last_error(grass_ctx_t ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int64_t grass_launch_count(grass_ctx_t ctx) { return ctx ? ctx->launches : 0; }
+
+// ---------------------------------------------------------------- tree
+
+grass_status grass_build_tree(grass_ctx_t ctx, const grass_csr_t *A, int32_t ground,
+                              grass_tree_t *out) {
+    if (!ctx) return GRASS_ERR_INVALID;
+    API_BEGIN(ctx)
+    need(A && out, "null argument");
+    *out = nullptr;
+    need(ground >= 0 && ground < A->n, "ground must be in [0, n)");
+    auto *T = new grass_tree_s();
+    T->ctx = ctx;
+    T->ground = ground;
+    try {
+        graph_extract(ctx, A, T->g);
+        T->in_tree.alloc(T->g.m);
+        mst_boruvka(ctx, T->g, T->in_tree.p);
+        tree_schedule(ctx, T);
+        tree_factor(ctx, T, false, T->lap);
+        ctx->sync();
+    } catch (...) {
+        delete T;
+        throw;
+    }
+    *out = T;
+    API_END
+}
+
+void grass_tree_destroy(grass_tree_t T) {
+    if (!T) return;
+    cudaSetDevice(T->ctx->device);
+    delete T;
+}
+
+grass_status grass_tree_info(grass_tree_t T, int64_t *n, int64_t *m, int64_t *rounds) {
+    if (!T) return GRASS_ERR_INVALID;
+    if (n) *n = T->g.n;
+    if (m) *m = T->g.m;
+    if (rounds) *rounds = T->sched.rounds;
+    return GRASS_OK;
+}
+
+grass_status grass_tree_graph(grass_ctx_t ctx, grass_tree_t T, int32_t *eu, int32_t *ev,
+                              double *ew, double *D) {
+    if (!ctx || !T) return GRASS_ERR_INVALID;
+    API_BEGIN(ctx)
+    const int64_t m = T->g.m, n = T->g.n;
+    if (eu) copy_d(ctx, eu, T->g.eu.p, m * sizeof(int32_t));
+    if (ev) copy_d(ctx, ev, T->g.ev.p, m * sizeof(int32_t));
+    if (ew) copy_d(ctx, ew, T->g.ew64.p, m * sizeof(double));
+    if (D) copy_d(ctx, D, T->g.D64.p, n * sizeof(double));
+    ctx->sync();
+    API_END
+}
+
+grass_status grass_tree_edges(grass_ctx_t ctx, grass_tree_t T, uint8_t *in_tree) {
+    if (!ctx || !T) return GRASS_ERR_INVALID;
+    API_BEGIN(ctx)
+    need(in_tree, "null output");
+    copy_d(ctx, in_tree, T->in_tree.p, T->g.m);
+    ctx->sync();
+    API_END
+}
+
+grass_status grass_tree_solve(grass_ctx_t ctx, grass_tree_t T, int with_D, int r,
+                              grass_prec prec, const void *B, void *X) {
+    if (!ctx || !T) return GRASS_ERR_INVALID;
+    API_BEGIN(ctx)
+    need(B && X, "null block");
+    need_prec(prec);
+    need(r_supported(r), "r must be 1, 2, 4, 8, 16, 24 or 32");
+    if (with_D) ensure_sdd(ctx, T);
+    copy_d(ctx, X, B, T->g.n * r * esize(prec));
+    tree_solve_inplace(ctx, T, with_D ? T->sdd : T->lap, r, prec, X, nullptr);
+    API_END
+}
+
+grass_status grass_spmm(grass_ctx_t ctx, grass_tree_t T, int r, grass_prec prec, const void *X,
+                        void *Y) {
+    if (!ctx || !T) return GRASS_ERR_INVALID;
+    API_BEGIN(ctx)
+    need(X && Y && X != Y, "X, Y must be non-null and distinct");
+    need_prec(prec);
+    need(r_supported(r), "r must be 1, 2, 4, 8, 16, 24 or 32");
+    const GraphData &g = T->g;
+    lap_mm(ctx, r, prec, g.n, g.adj_ptr.p, g.adj_col.p,
+           prec == GRASS_FP64 ? (const void *)g.adj_w64.p : (const void *)g.adj_w32.p, nullptr, X,
+           Y, nullptr);
+    API_END
+}
+
+// ---------------------------------------------------------------- sparsifier
+
+grass_status grass_sparsifier_create(grass_ctx_t ctx, grass_tree_t T, grass_sparsifier_t *out) {
+    if (!ctx || !T || !out) return GRASS_ERR_INVALID;
+    API_BEGIN(ctx)
+    *out = nullptr;
+    *out = new_sparsifier(ctx, T);
+    ctx->sync();
+    API_END
+}
+
+void grass_sparsifier_destroy(grass_sparsifier_t S) {
+    if (!S) return;
+    cudaSetDevice(S->ctx->device);
+    delete S;
+}
+
+grass_status grass_sparsifier_add(grass_ctx_t ctx, grass_sparsifier_t S, const int64_t *eids,
+                                  int64_t count) {
+    if (!ctx || !S) return GRASS_ERR_INVALID;
+    API_BEGIN(ctx)
+    need(count == 0 || eids, "null ids");
+    sparsifier_add(ctx, S, eids, count);
+    ctx->sync();
+    API_END
+}
+
+grass_status grass_sparsifier_info(grass_sparsifier_t S, int64_t *n_edges, int64_t *m_off) {
+    if (!S) return GRASS_ERR_INVALID;
+    if (n_edges) *n_edges = S->n_edges;
+    if (m_off) *m_off = S->m_off;
+    return GRASS_OK;
+}
+
+grass_status grass_sparsifier_mask(grass_ctx_t ctx, grass_sparsifier_t S, uint8_t *in_s) {
+    if (!ctx || !S) return GRASS_ERR_INVALID;
+    API_BEGIN(ctx)
+    need(in_s, "null output");
+    copy_d(ctx, in_s, S->in_s.p, S->tree->g.m);
+    ctx->sync();
+    API_END
+}
+
+__global__ void k_i32_to_i64(int64_t n, const int32_t *a, int64_t *b) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = a[i];
+}
+
+grass_status grass_sparsifier_offtree(grass_ctx_t ctx, grass_sparsifier_t S, int64_t *eids) {
+    if (!ctx || !S) return GRASS_ERR_INVALID;
+    API_BEGIN(ctx)
+    need(eids || S->m_off == 0, "null output");
+    launch(ctx, k_i32_to_i64, cdiv(S->m_off, kBlock), kBlock, 0, S->m_off,
+           (const int32_t *)S->off_eid.p, eids);
+    ctx->sync();
+    API_END
+}
+
+// ---------------------------------------------------------------- embed / filter
+
+grass_status grass_embed(grass_ctx_t ctx, grass_sparsifier_t S, const double *h0, int r, int t,
+                         grass_prec prec, double inner_tol, int inner_maxit, void *H_out,
+                         void *heat, double *heat_max) {
+    if (!ctx || !S) return GRASS_ERR_INVALID;
+    API_BEGIN(ctx)
+    need(h0 != nullptr, "null h0");
+    need_prec(prec);
+    need(r_supported(r), "r must be 1, 2, 4, 8, 16, 24 or 32");
+    need(t >= 1, "t must be >= 1");
+    need(inner_maxit >= 0, "inner_maxit must be >= 0");
+    void *hb = heat ? heat : (void *)ctx->scr<char>(SCR_HEAT, (S->m_off + 1) * esize(prec));
+    EmbedOut o = embed_impl(ctx, S, h0, r, t, prec, inner_tol, inner_maxit, H_out, hb);
+    if (heat_max) *heat_max = o.heat_max;
+    API_END
+}
+
+grass_status grass_lambda_min(grass_ctx_t ctx, grass_sparsifier_t S, double *lmin) {
+    if (!ctx || !S || !lmin) return GRASS_ERR_INVALID;
+    API_BEGIN(ctx)
+    lambda_min(ctx, S, lmin);
+    API_END
+}
+
+grass_status grass_lambda_max(grass_ctx_t ctx, grass_sparsifier_t S, const double *v0, int iters,
+                              grass_prec prec, double inner_tol, int inner_maxit, double *lmax) {
+    if (!ctx || !S || !lmax) return GRASS_ERR_INVALID;
+    API_BEGIN(ctx)
+    need(v0 != nullptr, "null v0");
+    need_prec(prec);
+    need(iters >= 0, "iters must be >= 0");
+    int64_t inner = 0;
+    *lmax = lambda_max_impl(ctx, S, v0, iters, prec, inner_tol, inner_maxit, &inner);
+    API_END
+}
+
+grass_status grass_filter(grass_ctx_t ctx, grass_sparsifier_t S, const void *heat, grass_prec prec,
+                          double sigma2, double lmin, double lmax, int t, int64_t cap,
+                          int64_t *accepted, int64_t *n_accepted, double *theta) {
+    if (!ctx || !S || !n_accepted) return GRASS_ERR_INVALID;
+    API_BEGIN(ctx)
+    need(heat || S->m_off == 0, "null heat");
+    need(accepted || S->m_off == 0, "null output");
+    need_prec(prec);
+    need(sigma2 > 0 && lmin > 0 && lmax > 0 && t >= 1, "sigma2, lmin, lmax must be > 0, t >= 1");
+    double th = theta_sigma(sigma2, lmin, lmax, t);
+    if (theta) *theta = th;
+    *n_accepted = 0;
+    if (S->m_off > 0) {
+        unsigned long long *hm = maxslot(ctx, 3);
+        memset_d(ctx, hm, 0, sizeof(unsigned long long));
+        max_abs_bits(ctx, prec, S->m_off, heat, hm);
+        unsigned long long b = 0;
+        d2h(ctx, &b, hm, sizeof(b));
+        double thr = th * bits_to_double(b);
+        *n_accepted = filter_heat(ctx, S, heat, prec, thr, cap, accepted);
+        ctx->sync();
+    }
+    API_END
+}
+
+// ---------------------------------------------------------------- densify / solve
+
+grass_status grass_densify(grass_ctx_t ctx, grass_tree_t T, const grass_params_t *P,
+                           const double *h0, const double *v0, grass_sparsifier_t *out,
+                           grass_sparsify_stats_t *stats) {
+    if (!ctx || !T || !P || !out) return GRASS_ERR_INVALID;
+    API_BEGIN(ctx)
+    *out = nullptr;
+    need(h0 && v0, "null h0 / v0");
+    need(P->sigma2 > 0, "sigma2 must be > 0");
+    need(r_supported(P->r), "r must be 1, 2, 4, 8, 16, 24 or 32");
+    need(P->t >= 1, "t must be >= 1");
+    need(P->max_rounds >= 1 && P->max_rounds <= GRASS_MAX_ROUNDS, "max_rounds out of range");
+    need(P->lmax_iters >= 0, "lmax_iters must be >= 0");
+    need(P->inner_maxit >= 0, "inner_maxit must be >= 0");
+    need_prec(P->embed_prec);
+    const double t0 = now_ms();
+    grass_sparsify_stats_t st;
+    std::memset(&st, 0, sizeof(st));
+    const int64_t n = T->g.n;
+    const int r = P->r;
+    grass_sparsifier_t S = new_sparsifier(ctx, T);
+    try {
+        void *heat = ctx->scr<char>(SCR_HEAT, (T->g.m + 1) * esize(P->embed_prec));
+        int64_t *acc = ctx->scr<int64_t>(SCR_PCG_E, T->g.m + 1);
+        for (int k = 0; k < P->max_rounds; ++k) {
+            double ta = now_ms();
+            double lmin = 0.0;
+            lambda_min(ctx, S, &lmin);
+            int64_t inner = 0;
+            double lmax = lambda_max_impl(ctx, S, v0 + (int64_t)k * n, P->lmax_iters,
+                                          P->embed_prec, P->inner_tol, P->inner_maxit, &inner);
+            st.lmin_est[k] = lmin;
+            st.lmax_est[k] = lmax;
+            double tb = now_ms();
+            st.ms_estimate += tb - ta;
+            if (lmax / lmin <= P->sigma2) {
+                st.stopped_similar = 1;
+                st.inner_iters += inner;
+                break;
+            }
+            int64_t moff = S->m_off;
+            EmbedOut eo = embed_impl(ctx, S, h0 + (int64_t)k * n * r, r, P->t, P->embed_prec,
+                                     P->inner_tol, P->inner_maxit, nullptr, heat);
+            inner += eo.inner;
+            st.inner_iters += inner;
+            double tc = now_ms();
+            st.ms_embed += tc - tb;
+            double th = theta_sigma(P->sigma2, lmin, lmax, P->t);
+            st.theta[k] = th;
+            st.heat_max[k] = eo.heat_max;
+            st.embedded_round[k] = moff;
+            st.offtree_embedded += moff;
+            int64_t na = filter_heat(ctx, S, heat, P->embed_prec, th * eo.heat_max,
+                                     P->max_add_per_round, acc);
+            double td = now_ms();
+            st.ms_filter += td - tc;
+            st.rounds = k + 1;
+            st.added_round[k] = na;
+            st.added += na;
+            if (na == 0) break;
+            sparsifier_add(ctx, S, acc, na);
+            ctx->sync();
+            st.ms_update += now_ms() - td;
+        }
+        ctx->sync();
+    } catch (...) {
+        delete S;
+        throw;
+    }
+    st.ms_total = now_ms() - t0;
+    if (stats) *stats = st;
+    *out = S;
+    API_END
+}
+
+grass_status grass_pcg_solve(grass_ctx_t ctx, grass_sparsifier_t S, const double *b, double *x,
+                             double tol, int maxit, grass_prec prec, double refine_tol,
+                             double inner_tol, int inner_maxit, grass_solve_stats_t *stats) {
+    if (!ctx || !S) return GRASS_ERR_INVALID;
+    API_BEGIN(ctx)
+    need(b && x, "null b / x");
+    need(tol > 0 && maxit >= 0, "tol must be > 0, maxit >= 0");
+    need_prec(prec);
+    need(prec == GRASS_FP64 || (refine_tol > 0 && refine_tol < 1), "refine_tol must be in (0, 1)");
+    need(inner_maxit >= 0, "inner_maxit must be >= 0");
+    ensure_sdd(ctx, S->tree);
+    double t0 = now_ms();
+    grass_solve_stats_t st;
+    std::memset(&st, 0, sizeof(st));
+    try {
+        pcg_solve(ctx, S, b, x, tol, maxit, prec, refine_tol, inner_tol, inner_maxit, &st);
+    } catch (const grass::Error &e) {
+        st.ms = now_ms() - t0;
+        if (stats) *stats = st;
+        throw;
+    }
+    st.ms = now_ms() - t0;
+    if (stats) *stats = st;
+    API_END
+}
+
+}  // extern "C"

@@ -1,0 +1,313 @@
+// common.cuh -- internal definitions shared by the CUDA sources of the
+// library: error handling, launch accounting, device buffers, the block
+// layout used by every r-column kernel, and the handle structs.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/grass.h"
+
+namespace grass {
+
+// ---------------------------------------------------------------- errors
+
+struct Error {
+    grass_status st;
+    std::string msg;
+};
+
+[[noreturn]] inline void fail(grass_status st, const std::string &msg) { throw Error{st, msg}; }
+
+inline void check_cuda(cudaError_t e, const char *what) {
+    if (e == cudaSuccess) return;
+    cudaGetLastError();   // clear a sticky launch error if any
+    fail(e == cudaErrorMemoryAllocation ? GRASS_ERR_OOM : GRASS_ERR_CUDA,
+         std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define GCK(call) ::grass::check_cuda((call), #call)
+
+// ---------------------------------------------------------------- buffers
+
+// Owning device buffer (synchronous cudaMalloc/cudaFree; long-lived data).
+template <typename T>
+struct DBuf {
+    T *p = nullptr;
+    size_t n = 0;
+    DBuf() = default;
+    DBuf(const DBuf &) = delete;
+    DBuf &operator=(const DBuf &) = delete;
+    ~DBuf() { release(); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+    void alloc(size_t count) {
+        release();
+        if (count == 0) count = 1;
+        GCK(cudaMalloc((void **)&p, count * sizeof(T)));
+        n = count;
+    }
+    // grow-only
+    void reserve(size_t count) {
+        if (count <= n && p) return;
+        alloc(count);
+    }
+    T *get() const { return p; }
+};
+
+// ---------------------------------------------------------------- context
+
+enum ScratchSlot {
+    SCR_SCAN = 0, SCR_SCAN2, SCR_TMP0, SCR_TMP1, SCR_TMP2, SCR_TMP3,
+    SCR_Y, SCR_H, SCR_CG_X, SCR_CG_R, SCR_CG_Z, SCR_CG_P, SCR_CG_Q,
+    SCR_PCG_X, SCR_PCG_R, SCR_PCG_Z, SCR_PCG_P, SCR_PCG_Q, SCR_PCG_ZOLD, SCR_PCG_E,
+    SCR_FILTER, SCR_FILTER2, SCR_HEAT, SCR_LMAX_V, SCR_LMAX_Y,
+    SCR_COUNT
+};
+
+// device scalar area layout (doubles)
+enum {
+    DS_RED = 0,          // 64 doubles: reduction outputs (PCG scalars)
+    DS_CG = 64,          // 12 x 32 doubles: per-column CG scalars
+    DS_MAX = 448,        // 16 x uint64: max-abs bit patterns
+    DS_TOTAL = 512
+};
+
+}  // namespace grass
+
+struct grass_ctx_s {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    int64_t launches = 0;
+    grass::DBuf<int> flags;                 // device error flags
+    grass::DBuf<double> scal;               // device scalars (DS_*)
+    grass::DBuf<double> partials;           // block partial sums
+    grass::DBuf<unsigned int> counters;     // last-block counters
+    double *hpin = nullptr;                 // pinned host staging (4096 doubles)
+    grass::DBuf<char> scratch[grass::SCR_COUNT];
+
+    template <typename T>
+    T *scr(int slot, size_t count) {
+        size_t bytes = count * sizeof(T);
+        auto &b = scratch[slot];
+        if (b.n < bytes || !b.p) {
+            GCK(cudaStreamSynchronize(stream));
+            b.alloc(bytes + 256);
+        }
+        return reinterpret_cast<T *>(b.p);
+    }
+    void sync() { GCK(cudaStreamSynchronize(stream)); }
+};
+
+namespace grass {
+
+// ---------------------------------------------------------------- launches
+
+template <typename... KArgs, typename... Args>
+inline void launch(grass_ctx_t ctx, void (*kernel)(KArgs...), int64_t grid, int block, size_t smem,
+                   Args &&...args) {
+    if (grid <= 0) return;
+    if (grid > 2147483647LL) fail(GRASS_ERR_INVALID, "grid too large");
+    kernel<<<(unsigned)grid, block, smem, ctx->stream>>>(std::forward<Args>(args)...);
+    ctx->launches++;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) check_cuda(e, "kernel launch");
+}
+
+inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+constexpr int kBlock = 256;
+constexpr int kRedBlocks = 608;     // 4 x 152 SMs: fixed grid for deterministic reductions
+
+// ---------------------------------------------------------------- block layout
+// An n x R row-major block is processed by TPR consecutive threads per row,
+// each owning EPT consecutive elements: consecutive threads touch consecutive
+// memory, and TPR divides 32 so a row never straddles a warp.
+template <int R>
+struct Lay {
+    static constexpr int TPR = (R % 8 == 0) ? 8 : (R % 4 == 0) ? 4 : (R % 2 == 0) ? 2 : 1;
+    static constexpr int EPT = R / TPR;
+};
+
+// Dispatch a functor templated on R over the supported column counts.
+#define GRASS_DISPATCH_R(r, FN, ...)                                         \
+    switch (r) {                                                             \
+        case 1: FN<1>(__VA_ARGS__); break;                                   \
+        case 2: FN<2>(__VA_ARGS__); break;                                   \
+        case 4: FN<4>(__VA_ARGS__); break;                                   \
+        case 8: FN<8>(__VA_ARGS__); break;                                   \
+        case 16: FN<16>(__VA_ARGS__); break;                                 \
+        case 24: FN<24>(__VA_ARGS__); break;                                 \
+        case 32: FN<32>(__VA_ARGS__); break;                                 \
+        default: ::grass::fail(GRASS_ERR_INVALID, "r must be 1, 2, 4, 8, 16, 24 or 32"); \
+    }
+
+inline bool r_supported(int r) {
+    return r == 1 || r == 2 || r == 4 || r == 8 || r == 16 || r == 24 || r == 32;
+}
+
+// ---------------------------------------------------------------- graph / tree data
+
+struct GraphData {
+    int64_t n = 0, m = 0;
+    DBuf<int32_t> adj_ptr;            // [n+1] off-diagonal adjacency in CSR order
+    DBuf<int32_t> adj_col;            // [2m]
+    DBuf<int32_t> adj_eid;            // [2m]
+    DBuf<double> adj_w64;             // [2m] w > 0
+    DBuf<float> adj_w32;
+    DBuf<int32_t> eu, ev;             // [m] edges, eu < ev
+    DBuf<double> ew64;                // [m]
+    DBuf<float> ew32;
+    DBuf<double> D64;                 // [n] diagonal load
+    DBuf<float> D32;
+    DBuf<double> degG;                // [n] weighted degree (Laplacian diagonal)
+};
+
+// Elimination schedule of the spanning tree by rake (degree 1) and compress
+// (degree 2) rounds; numeric factors for L_T (lap) and L_T + D (sdd).
+struct TreeFactor {
+    DBuf<double> invd64, b1_64, b2_64, cm64, fill64;
+    DBuf<float> invd32, b1_32, b2_32, cm32;
+    double root_invd = 0.0;
+};
+
+struct TreeSchedule {
+    int rounds = 0;
+    std::vector<int64_t> elim_off;   // host [rounds+1] into elim_list
+    std::vector<int64_t> rcv_off;    // host [rounds+1] into rcv_list
+    DBuf<int32_t> elim_list;         // [n-1]
+    DBuf<int32_t> n1, n2;            // [n] neighbours at elimination (-1: none)
+    DBuf<int32_t> src1, src2;        // [n] weight source: >= 0 tree edge id, < 0: fill of vertex -src-1
+    DBuf<int32_t> rcv_list;          // receivers grouped by round
+    DBuf<int32_t> rcv_beg;           // [#rcv + 1] start into contrib arrays
+    DBuf<int32_t> contrib_v;         // contributor vertex
+    DBuf<uint8_t> contrib_side;      // 0: receiver is n1 of v, 1: n2
+    int64_t n_rcv = 0, n_contrib = 0;
+    DBuf<int64_t> d_offs;            // device copy: rcv_off then elim_off
+};
+
+}  // namespace grass
+
+struct grass_tree_s {
+    grass_ctx_t ctx = nullptr;
+    int32_t ground = 0;
+    grass::GraphData g;
+    grass::DBuf<uint8_t> in_tree;     // [m]
+    grass::TreeSchedule sched;
+    grass::TreeFactor lap;            // L_T grounded at rho
+    grass::TreeFactor sdd;            // L_T + D
+    bool has_sdd = false;
+};
+
+struct grass_sparsifier_s {
+    grass_ctx_t ctx = nullptr;
+    grass_tree_t tree = nullptr;
+    bool is_tree = true;
+    int64_t n_edges = 0, m_off = 0;
+    grass::DBuf<uint8_t> in_s;        // [m]
+    grass::DBuf<int32_t> off_u, off_v, off_eid;   // [m_off] increasing id
+    grass::DBuf<double> off_w64;
+    grass::DBuf<float> off_w32;
+    grass::DBuf<int32_t> s_ptr, s_col;            // S adjacency (when !is_tree)
+    grass::DBuf<double> s_w64;
+    grass::DBuf<float> s_w32;
+    grass::DBuf<double> degS;         // [n]
+};
+
+namespace grass {
+
+// ---------------------------------------------------------------- util API (util.cu)
+
+// out[0..n] = exclusive prefix sums of in[0..n-1]; out[n] = total.  Host
+// receives the total when total_host != nullptr (synchronises).
+void scan_i64(grass_ctx_t ctx, const int64_t *in, int64_t *out, int64_t n, int64_t *total_host);
+
+struct U64x2 {
+    unsigned long long a, b;
+};
+void scan_pair(grass_ctx_t ctx, const U64x2 *in, U64x2 *out, int64_t n, U64x2 *total_host);
+
+// out[j] = sum_i A[i*r+j] * B[i*r+j] (double accumulation, deterministic),
+// written to device doubles out[0..r).
+void dot_cols(grass_ctx_t ctx, int r, grass_prec prec, int64_t n, const void *A, const void *B,
+              double *out);
+// Pulls `count` doubles from device to host (synchronises).
+void d2h(grass_ctx_t ctx, void *dst, const void *src, size_t bytes);
+void h2d(grass_ctx_t ctx, void *dst, const void *src, size_t bytes);
+void memset_d(grass_ctx_t ctx, void *p, int v, size_t bytes);
+void copy_d(grass_ctx_t ctx, void *dst, const void *src, size_t bytes);
+
+// ---------------------------------------------------------------- per-module entry points
+
+void graph_extract(grass_ctx_t ctx, const grass_csr_t *A, GraphData &g);
+void mst_boruvka(grass_ctx_t ctx, const GraphData &g, uint8_t *in_tree);
+void tree_schedule(grass_ctx_t ctx, grass_tree_t T);
+void tree_factor(grass_ctx_t ctx, grass_tree_t T, bool with_D, TreeFactor &f);
+// In-place tree solve of the n x r block Y (prec); optionally tracks the
+// max |x| bit pattern into maxbits (device, uint64 for both precisions).
+void tree_solve_inplace(grass_ctx_t ctx, grass_tree_t T, const TreeFactor &f, int r,
+                        grass_prec prec, void *Y, unsigned long long *maxbits);
+
+// Y = scale * (L X + Dopt .* X) over an adjacency (ptr, col, w).  scale may
+// come from a device max-bits word (pow2 rescale) when scale_from != nullptr.
+void lap_mm(grass_ctx_t ctx, int r, grass_prec prec, int64_t n, const int32_t *ptr,
+            const int32_t *col, const void *w, const void *Dopt, const void *X, void *Y,
+            const unsigned long long *scale_from);
+// Convert an n x r double block to prec (copy or float conversion).
+void convert_block(grass_ctx_t ctx, grass_prec prec, int64_t count, const double *src, void *dst);
+// Multiply an n x r block in place by the pow2 factor derived from maxbits.
+void apply_pow2(grass_ctx_t ctx, grass_prec prec, int64_t count, void *X,
+                const unsigned long long *maxbits);
+// heat over off-S edges; scale from maxbits; heat_max bits (uint64) written.
+void heat_offs(grass_ctx_t ctx, int r, grass_prec prec, grass_sparsifier_t S, const void *H,
+               const unsigned long long *scale_from, void *heat, unsigned long long *heatmax_bits);
+// quadratic forms over all edges and over S edges for a single vector (r=1)
+void quad_forms(grass_ctx_t ctx, grass_prec prec, grass_sparsifier_t S, const void *x,
+                double *qG_qS_dev);
+void max_abs_bits(grass_ctx_t ctx, grass_prec prec, int64_t count, const void *X,
+                  unsigned long long *maxbits);
+
+// ---------------------------------------------------------------- krylov.cu
+
+// X = L_S^{-1} Y (grounded, or (L_S + D)^{-1} Y when with_D), r columns, by
+// the tree solve (S is the tree) or tree-preconditioned CG.  Y is preserved
+// unless S is the tree (then Y may be X).  Returns inner iterations (max over
+// columns).  maxbits: optional max|X| tracking.
+int64_t s_solve(grass_ctx_t ctx, grass_sparsifier_t S, bool with_D, int r, grass_prec prec,
+                const void *Y, void *X, double tol, int maxit, unsigned long long *maxbits);
+
+void pcg_solve(grass_ctx_t ctx, grass_sparsifier_t S, const double *b, double *x, double tol,
+               int maxit, grass_prec prec, double refine_tol, double inner_tol, int inner_maxit,
+               grass_solve_stats_t *st);
+
+// ---------------------------------------------------------------- sparsifier ops (filter.cu)
+
+void sparsifier_rebuild(grass_ctx_t ctx, grass_sparsifier_t S);
+void sparsifier_add(grass_ctx_t ctx, grass_sparsifier_t S, const int64_t *eids, int64_t count);
+void lambda_min(grass_ctx_t ctx, grass_sparsifier_t S, double *out_host);
+int64_t filter_heat(grass_ctx_t ctx, grass_sparsifier_t S, const void *heat, grass_prec prec,
+                    double thr, int64_t cap, int64_t *accepted);
+
+// bits helpers
+__host__ __device__ inline double pow2_scale_from_bits(unsigned long long maxbits_f64) {
+    // maxbits holds the bit pattern of a non-negative double m; the factor
+    // 2^-(floor(log2 m)) puts m in [1, 2).  m == 0 or non-finite: 1.
+    unsigned long long ex = (maxbits_f64 >> 52) & 0x7FFULL;
+    if (ex == 0 || ex == 0x7FF) return 1.0;
+    long long e = (long long)ex - 1023;             // m = 1.f * 2^e
+    unsigned long long bits = (unsigned long long)(1023 - e) << 52;   // 2^-e
+    if (1023 - e <= 0 || 1023 - e >= 2047) return 1.0;
+    double s;
+    memcpy(&s, &bits, sizeof(s));
+    return s;
+}
+
+}  // namespace grass

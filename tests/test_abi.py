@@ -1,0 +1,59 @@
+"""The C ABI library loads and exports every entry point include/grass.h
+declares; the binding declares the same names.  No GPU needed (no compute
+call is made)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "grass.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(grass_[a-z_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    import paper_1911_04382_gb300 as G
+    return G.build()
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for must in ("grass_build_tree", "grass_embed", "grass_filter", "grass_densify",
+                 "grass_pcg_solve"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    L = ctypes.CDLL(libpath)
+    missing = [n for n in _declared() if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_binding_exposes_the_same_names(libpath):
+    import paper_1911_04382_gb300 as G
+    missing = [n for n in _declared() if not hasattr(G, n)]
+    assert not missing, missing
+
+
+def test_null_arguments_are_rejected_without_a_gpu(libpath):
+    L = ctypes.CDLL(libpath)
+    L.grass_ctx_create.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    L.grass_ctx_create.restype = ctypes.c_int
+    assert L.grass_ctx_create(None, None) == 1          # GRASS_ERR_INVALID
+    L.grass_tree_info.argtypes = [ctypes.c_void_p] * 4
+    L.grass_tree_info.restype = ctypes.c_int
+    assert L.grass_tree_info(None, None, None, None) == 1
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    import paper_1911_04382_gb300.binding as B
+    monkeypatch.setattr(B, "LIB", str(tmp_path / "nope.so"))
+    monkeypatch.setattr(B, "_lib", None)
+    with pytest.raises(RuntimeError, match="missing"):
+        B.lib()

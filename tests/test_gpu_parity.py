@@ -1,0 +1,361 @@
+"""GPU library vs the CPU oracle, element by element, through the C ABI.
+
+Tolerances (integer work bit-exact; FP64 heats 1e-10 of heat_max, the bar
+for FP64 embeddings; solves judged by their FP64 residual):
+"""
+import numpy as np
+import pytest
+
+import oracle
+from synth import graphs, rng
+from tests.gpu_util import dev, gpu_graph, host, tree_mask
+from tests.helpers import tiny_graph
+
+pytestmark = pytest.mark.gpu
+
+HEAT_TOL = 1e-10       # per edge, relative to heat_max (FP64)
+SOLVE_TOL = 1e-10      # relative to max |x| (FP64 tree solve)
+
+
+def _graphs_small():
+    return [
+        graphs.config_small_grid(),                                   # 64x64, 4096 nodes
+        graphs.grid2d_uniform(37, 29, seed=11),                        # ragged sizes
+        graphs.grid3d_loguniform(13, 11, 9, seed=12),
+        graphs.ring_chords(3001, seed=13),
+        graphs.power_grid(41, seed=14),
+        tiny_graph(9, 7, 15),
+    ]
+
+
+def _ties_grid():
+    # integer weights: many equal weights, the edge id decides
+    g = graphs.grid((45, 31))
+    m = graphs.n_grid_edges((45, 31))
+    w = 1.0 + (rng.raw64(16, 1, 0, m) % np.uint64(3)).astype(np.float64)
+    u, v = graphs._grid_edges((45, 31))
+    rp, c, val = graphs.csr_from_edges(g.n, u, v, w, 1e-3)
+    return graphs.Graph("ties", g.n, rp, c, val)
+
+
+@pytest.mark.parametrize("which", range(7))
+def test_tree_and_extraction_bit_exact(gpu, which):
+    import torch
+    g = (_graphs_small() + [_ties_grid()])[which]
+    og = oracle.from_graph(g)
+    in_tree_ref = oracle.mst(og)
+    with gpu_graph(g) as (ctx, tree, _):
+        n, m, rounds = gpu.grass_tree_info(tree)
+        assert (n, m) == (g.n, og.m)
+        assert rounds >= 1
+        eu = torch.empty(m, dtype=torch.int32, device="cuda")
+        ev = torch.empty_like(eu)
+        ew = torch.empty(m, dtype=torch.float64, device="cuda")
+        D = torch.empty(n, dtype=torch.float64, device="cuda")
+        gpu.grass_tree_graph(ctx, tree, eu, ev, ew, D)
+        assert np.array_equal(host(eu), og.eu) and np.array_equal(host(ev), og.ev)
+        assert np.array_equal(host(ew), og.ew)
+        assert np.array_equal(host(D), og.D)
+        assert np.array_equal(tree_mask(ctx, tree, m), in_tree_ref)
+
+
+def test_powerlaw_unit_weight_tree_bit_exact(gpu):
+    g = graphs.chung_lu(20000, seed=3)         # all weights tie: ids decide
+    og = oracle.from_graph(g)
+    with gpu_graph(g) as (ctx, tree, _):
+        assert np.array_equal(tree_mask(ctx, tree, og.m), oracle.mst(og))
+
+
+def test_invalid_inputs_are_rejected(gpu):
+    import paper_1911_04382_gb300 as G
+    g = graphs.grid2d_uniform(6, 5, seed=1, D=0.1)
+    ctx = G.grass_ctx_create()
+    try:
+        v = g.val.copy()
+        off = np.flatnonzero(g.col != np.repeat(np.arange(g.n), np.diff(g.rowptr)))[3]
+        v[off] = -v[off]
+        with pytest.raises(G.GrassError) as ei:
+            G.grass_build_tree(ctx, dev(g.rowptr), dev(g.col), dev(v))
+        assert ei.value.status == G.GRASS_ERR_INVALID
+        v = g.val.copy()
+        diag = np.flatnonzero(g.col == np.repeat(np.arange(g.n), np.diff(g.rowptr)))[4]
+        v[diag] -= 5.0
+        with pytest.raises(G.GrassError) as ei:
+            G.grass_build_tree(ctx, dev(g.rowptr), dev(g.col), dev(v))
+        assert ei.value.status == G.GRASS_ERR_NOT_SDD
+        u = np.array([0, 2, 4])
+        w = np.array([1, 3, 5])
+        rp, c, val = graphs.csr_from_edges(6, u, w, np.ones(3))
+        with pytest.raises(G.GrassError) as ei:
+            G.grass_build_tree(ctx, dev(rp), dev(c), dev(val))
+        assert ei.value.status == G.GRASS_ERR_DISCONNECTED
+        # a graph with n-1 edges or more but two components
+        u = np.array([0, 0, 1, 3, 3, 4])
+        w = np.array([1, 2, 2, 4, 5, 5])
+        rp, c, val = graphs.csr_from_edges(6, u, w, np.ones(6))
+        with pytest.raises(G.GrassError) as ei:
+            G.grass_build_tree(ctx, dev(rp), dev(c), dev(val))
+        assert ei.value.status == G.GRASS_ERR_DISCONNECTED
+        assert "component" in G.grass_last_error(ctx)
+    finally:
+        G.grass_ctx_destroy(ctx)
+
+
+@pytest.mark.parametrize("r", [1, 8, 16, 24])
+def test_spmm_matches_oracle(gpu, r):
+    import torch
+    g = graphs.grid3d_loguniform(15, 13, 11, seed=21)
+    og = oracle.from_graph(g)
+    X = rng.gaussian_block(21, 5, g.n, r)
+    ref = oracle.lap_apply(og, X)
+    with gpu_graph(g) as (ctx, tree, _):
+        Xd = dev(X)
+        Y = torch.empty_like(Xd)
+        gpu.grass_spmm(ctx, tree, r, gpu.GRASS_FP64, Xd, Y)
+        assert np.abs(host(Y) - ref).max() <= 1e-12 * np.abs(ref).max()
+        X32 = Xd.float()
+        Y32 = torch.empty_like(X32)
+        gpu.grass_spmm(ctx, tree, r, gpu.GRASS_FP32, X32, Y32)
+        assert np.abs(host(Y32) - ref).max() <= 1e-4 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("gi", range(6))
+@pytest.mark.parametrize("ground", [0, -1])
+def test_tree_solve_matches_oracle(gpu, gi, ground):
+    import torch
+    g = _graphs_small()[gi]
+    rho = ground % g.n
+    og = oracle.from_graph(g)
+    ot = oracle.build_tree(og, rho)
+    r = 8
+    B = rng.gaussian_block(gi, 6, g.n, r)
+    B -= B.mean(axis=0)
+    ref0 = oracle.tree_solve(og, ot, B)             # grounded at rho
+    ref1 = oracle.tree_solve(og, ot, B, og.D)       # L_T + D
+    with gpu_graph(g, rho) as (ctx, tree, _):
+        Bd = dev(B)
+        X = torch.empty_like(Bd)
+        gpu.grass_tree_solve(ctx, tree, 0, r, gpu.GRASS_FP64, Bd, X)
+        x = host(X)
+        assert np.all(x[rho] == 0.0)
+        assert np.abs(x - ref0).max() <= SOLVE_TOL * np.abs(ref0).max()
+        if np.any(og.D > 0):
+            gpu.grass_tree_solve(ctx, tree, 1, r, gpu.GRASS_FP64, Bd, X)
+            assert np.abs(host(X) - ref1).max() <= SOLVE_TOL * np.abs(ref1).max()
+        # in place, single column
+        b1 = dev(B[:, 0].copy())
+        gpu.grass_tree_solve(ctx, tree, 0, 1, gpu.GRASS_FP64, b1, b1)
+        assert np.abs(host(b1) - ref0[:, 0]).max() <= SOLVE_TOL * np.abs(ref0).max()
+        # FP32: same solve, single precision rounding
+        B32 = Bd.float()
+        X32 = torch.empty_like(B32)
+        gpu.grass_tree_solve(ctx, tree, 0, r, gpu.GRASS_FP32, B32, X32)
+        assert np.abs(host(X32) - ref0).max() <= 1e-3 * np.abs(ref0).max()
+
+
+def _heat_parity(gpu, g, t, r, extra_every=0, inner_tol=1e-13, inner_maxit=2000, rho=0):
+    import torch
+    og = oracle.from_graph(g)
+    ot = oracle.build_tree(og, rho)
+    in_s = ot.in_tree.copy()
+    if extra_every:
+        off = np.flatnonzero(in_s == 0)
+        in_s[off[::extra_every]] = 1
+    h0 = rng.gaussian_block(7, rng.STREAM_H0, g.n, r)
+    H_ref = oracle.embed(og, ot, in_s, h0, t, inner_tol, inner_maxit)
+    hv_ref, off_ref = oracle.heat(og, in_s, H_ref)
+    with gpu_graph(g, rho) as (ctx, tree, _):
+        S = gpu.grass_sparsifier_create(ctx, tree)
+        try:
+            if extra_every:
+                add = np.flatnonzero((in_s == 1) & (ot.in_tree == 0)).astype(np.int64)
+                gpu.grass_sparsifier_add(ctx, S, dev(add))
+            ne, moff = gpu.grass_sparsifier_info(S)
+            assert moff == off_ref.shape[0] and ne + moff == og.m
+            ids = torch.empty(moff, dtype=torch.int64, device="cuda")
+            gpu.grass_sparsifier_offtree(ctx, S, ids)
+            assert np.array_equal(host(ids), off_ref)
+            heat = torch.empty(moff, dtype=torch.float64, device="cuda")
+            H = torch.empty(g.n, r, dtype=torch.float64, device="cuda")
+            hmax = gpu.grass_embed(ctx, S, dev(h0), r, t, gpu.GRASS_FP64, inner_tol, inner_maxit,
+                                   H, heat)
+            hv = host(heat)
+            assert hmax == hv.max()
+            err = np.abs(hv / hv.max() - hv_ref / hv_ref.max()).max()
+            assert err <= HEAT_TOL, err
+            # H itself: same grounded vector, same power-of-two scale
+            Hh = host(H)
+            assert np.abs(Hh - H_ref).max() <= 1e-9 * np.abs(H_ref).max()
+            return hv, hv_ref, off_ref, S, ctx, tree
+        finally:
+            gpu.grass_sparsifier_destroy(S)
+
+
+@pytest.mark.parametrize("gi", range(6))
+def test_embed_heat_tree_matches_oracle(gpu, gi):
+    g = _graphs_small()[gi]
+    _heat_parity(gpu, g, t=2, r=8)
+
+
+@pytest.mark.parametrize("t,r", [(1, 1), (3, 16), (2, 24)])
+def test_embed_heat_shapes(gpu, t, r):
+    _heat_parity(gpu, graphs.grid2d_uniform(40, 33, seed=31), t=t, r=r, rho=17)
+
+
+@pytest.mark.parametrize("gi", [0, 2, 4])
+def test_embed_heat_with_inner_cg_matches_oracle(gpu, gi):
+    g = _graphs_small()[gi]
+    _heat_parity(gpu, g, t=2, r=8, extra_every=5)
+
+
+def test_lambda_estimates_match_oracle(gpu):
+    g = graphs.grid2d_uniform(30, 27, seed=41)
+    og = oracle.from_graph(g)
+    ot = oracle.build_tree(og)
+    in_s = ot.in_tree.copy()
+    in_s[np.flatnonzero(in_s == 0)[::7]] = 1
+    v0 = rng.normal(41, rng.STREAM_V0, g.n)
+    with gpu_graph(g) as (ctx, tree, _):
+        S = gpu.grass_sparsifier_create(ctx, tree)
+        try:
+            for mask in (ot.in_tree, in_s):
+                if mask is in_s:
+                    add = np.flatnonzero((in_s == 1) & (ot.in_tree == 0)).astype(np.int64)
+                    gpu.grass_sparsifier_add(ctx, S, dev(add))
+                lmin = gpu.grass_lambda_min(ctx, S)
+                assert lmin == pytest.approx(oracle.lambda_min_est(og, mask), rel=1e-14)
+                lmax = gpu.grass_lambda_max(ctx, S, dev(v0), 8, gpu.GRASS_FP64, 1e-13, 3000)
+                ref = oracle.lambda_max_est(og, ot, mask, v0, 8, 1e-13, 3000)
+                assert lmax == pytest.approx(ref, rel=1e-9)
+        finally:
+            gpu.grass_sparsifier_destroy(S)
+
+
+def _near_threshold(hv, thr):
+    return np.abs(hv - thr) <= 1e-9 * thr
+
+
+@pytest.mark.parametrize("cap", [0, 100, 1])
+def test_filter_matches_oracle(gpu, cap):
+    import torch
+    g = graphs.grid2d_uniform(50, 41, seed=51)
+    og = oracle.from_graph(g)
+    ot = oracle.build_tree(og)
+    H = oracle.embed(og, ot, None, rng.gaussian_block(51, 1, g.n, 8), 2)
+    hv, off = oracle.heat(og, ot.in_tree, H)
+    th = oracle.theta_sigma(100.0, 1.0, 6000.0, 2)
+    ref = oracle.filter_edges(hv, off, th, cap)
+    with gpu_graph(g) as (ctx, tree, _):
+        S = gpu.grass_sparsifier_create(ctx, tree)
+        try:
+            acc = torch.empty(max(1, off.shape[0]), dtype=torch.int64, device="cuda")
+            na, theta = gpu.grass_filter(ctx, S, dev(hv), gpu.GRASS_FP64, 100.0, 1.0, 6000.0, 2,
+                                         cap, acc)
+            assert theta == th
+            assert np.array_equal(host(acc)[:na], ref)
+            # FP32 heats: same rule on the rounded values
+            h32 = hv.astype(np.float32)
+            na32, _ = gpu.grass_filter(ctx, S, dev(h32), gpu.GRASS_FP32, 100.0, 1.0, 6000.0, 2,
+                                       cap, acc)
+            ref32 = oracle.filter_edges(h32.astype(np.float64), off,
+                                        th * float(h32.max()) / float(h32.astype(np.float64).max()),
+                                        cap)
+            assert np.array_equal(host(acc)[:na32], ref32)
+        finally:
+            gpu.grass_sparsifier_destroy(S)
+
+
+def test_filter_ties_take_smaller_ids(gpu):
+    import torch
+    g = graphs.grid2d_uniform(20, 20, seed=52)
+    og = oracle.from_graph(g)
+    ot = oracle.build_tree(og)
+    moff = og.m - (g.n - 1)
+    hv = np.repeat(np.array([3.0, 2.0, 2.0, 1.0]), moff // 4 + 1)[:moff].copy()
+    off = np.flatnonzero(ot.in_tree == 0)
+    with gpu_graph(g) as (ctx, tree, _):
+        S = gpu.grass_sparsifier_create(ctx, tree)
+        try:
+            acc = torch.empty(moff, dtype=torch.int64, device="cuda")
+            for cap in (1, moff // 4 + 3, moff // 2, moff):
+                na, _ = gpu.grass_filter(ctx, S, dev(hv), gpu.GRASS_FP64, 1.0, 1.0, 100.0, 1, cap, acc)
+                ref = oracle.filter_edges(hv, off, (1.0 / 100.0) ** 3, cap)
+                assert np.array_equal(host(acc)[:na], ref)
+        finally:
+            gpu.grass_sparsifier_destroy(S)
+
+
+def _densify_parity(gpu, g, sigma2, r, t, rounds, cap, inner_tol=1e-13, inner_maxit=3000):
+    og = oracle.from_graph(g)
+    ot = oracle.build_tree(og)
+    h0s = [rng.gaussian_block(9, rng.STREAM_H0 + k, g.n, r) for k in range(rounds)]
+    v0s = [rng.normal(9, rng.STREAM_V0 + k, g.n) for k in range(rounds)]
+    res = oracle.densify(og, ot, h0s, v0s, sigma2, t, rounds, 8, cap, inner_tol, inner_maxit)
+    import torch
+    with gpu_graph(g) as (ctx, tree, _):
+        P = gpu.make_params(sigma2, r, t, rounds, 8, cap, gpu.GRASS_FP64, inner_tol, inner_maxit)
+        S, st = gpu.grass_densify(ctx, tree, P, dev(np.concatenate(h0s)), dev(np.concatenate(v0s)))
+        try:
+            in_s = torch.empty(og.m, dtype=torch.uint8, device="cuda")
+            gpu.grass_sparsifier_mask(ctx, S, in_s)
+            got = host(in_s)
+            d = st.as_dict()
+            assert d["rounds"] == res.rounds
+            for k in range(len(res.lmax)):
+                assert d["lmax_est"][k] == pytest.approx(res.lmax[k], rel=1e-8)
+                assert d["lmin_est"][k] == pytest.approx(res.lmin[k], rel=1e-13)
+            diff = np.flatnonzero(got != res.in_s)
+            # only edges within rounding of the threshold may differ
+            assert diff.shape[0] <= max(2, 1e-4 * og.m), diff.shape
+            return d, res
+        finally:
+            gpu.grass_sparsifier_destroy(S)
+
+
+def test_densify_small_grid_one_round(gpu):
+    """The 64x64 grid: r=8, t=2, sigma^2=100, one round, FP64."""
+    d, res = _densify_parity(gpu, graphs.config_small_grid(), 100.0, 8, 2, 1, 0)
+    assert d["added"] == res.added[0]
+
+
+def test_densify_3d_grid_rounds_with_cap(gpu):
+    # sigma^2 = 20: the oracle runs all three rounds (60, 60, 4 edges)
+    d, res = _densify_parity(gpu, graphs.grid3d_loguniform(12, 12, 12, seed=2), 20.0, 16, 2, 3,
+                             cap=60)
+    assert d["rounds"] == 3 and d["added_round"] == res.added
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("extra", [False, True])
+def test_pcg_solves_small_grid(gpu, prec, extra):
+    import torch
+    g = graphs.config_small_grid()
+    og = oracle.from_graph(g)
+    ot = oracle.build_tree(og)
+    b = rng.normal(1, rng.STREAM_RHS, g.n)
+    in_s = None
+    if extra:
+        in_s = ot.in_tree.copy()
+        in_s[np.flatnonzero(in_s == 0)[::3]] = 1
+    tol = 1e-3 if prec == "fp64" else 1e-8
+    x_ref, it_ref, rel_ref, st_ref = oracle.pcg(og, ot, in_s, b, tol, 5000, 1e-8, 200)
+    with gpu_graph(g) as (ctx, tree, _):
+        S = gpu.grass_sparsifier_create(ctx, tree)
+        try:
+            if extra:
+                add = np.flatnonzero((in_s == 1) & (ot.in_tree == 0)).astype(np.int64)
+                gpu.grass_sparsifier_add(ctx, S, dev(add))
+            x = torch.zeros(g.n, dtype=torch.float64, device="cuda")
+            p = gpu.GRASS_FP64 if prec == "fp64" else gpu.GRASS_FP32
+            status, st = gpu.grass_pcg_solve(ctx, S, dev(b), x, tol, 5000, p, 1e-3, 1e-8, 200)
+            assert status == gpu.GRASS_OK
+            # independent FP64 residual
+            A = __import__("scipy.sparse", fromlist=["csr_matrix"]).csr_matrix(
+                (g.val, g.col, g.rowptr), shape=(g.n, g.n))
+            xr = host(x)
+            rel = np.linalg.norm(b - A @ xr) / np.linalg.norm(b)
+            assert rel <= tol and st.rel_resid_fp64 == pytest.approx(rel, rel=1e-6)
+            if prec == "fp64":
+                assert abs(st.iters - it_ref) <= 2
+        finally:
+            gpu.grass_sparsifier_destroy(S)
