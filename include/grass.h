@@ -124,6 +124,38 @@ const char *grass_last_error(grass_ctx_t ctx);
 /* Number of GPU kernel launches the library issued on ctx so far. */
 int64_t grass_launch_count(grass_ctx_t ctx);
 
+/* Bounded device-side waits (no counterpart in the paper).  The tree solve
+ * runs as one cooperative kernel whose rounds are separated by grid
+ * barriers; every barrier wait polls at most `polls` times (0 = default,
+ * about one second) and then ends the kernel, and the call that launched it
+ * returns GRASS_ERR_TIMEOUT with the context still usable.
+ * hold_barriers != 0 is for testing that path: every barrier then waits for
+ * one block more than the grid has, so every wait runs out.  Synchronises. */
+grass_status grass_ctx_set_wait_limit(grass_ctx_t ctx, int64_t polls, int hold_barriers);
+
+/* Kernel timing for roofline measurements (no counterpart in the paper).
+ * family != GRASS_KF_NONE brackets every launch of that kernel family with
+ * CUDA events on the context stream and accumulates, per launch, the
+ * algorithmic bytes the launch must move (each array touched once):
+ *   GRASS_KF_SPMM_G  Y = L_G X:  4(n+1) + 2m(4+s) + 2nrs
+ *   GRASS_KF_SPMM_S  the same over the sparsifier's adjacency (+ns with D)
+ *   GRASS_KF_HEAT    m_off(8+s) + nrs + m_off s
+ *   GRASS_KF_TREE    one whole tree solve (all its launches):
+ *                    4nrs + contributions(4+s) + receivers 8 + n(12+3s)
+ * (n rows, r columns, s = 4 or 8 bytes, m edges.)  Enabling resets the
+ * accumulators.  grass_kernel_timing_read synchronises the stream and
+ * returns the summed event time (ms), the number of timed launches and the
+ * summed algorithmic bytes.  Timing adds two event records per launch. */
+typedef enum {
+    GRASS_KF_NONE = 0,
+    GRASS_KF_SPMM_G = 1,
+    GRASS_KF_SPMM_S = 2,
+    GRASS_KF_HEAT = 3,
+    GRASS_KF_TREE = 4
+} grass_kernel_family;
+grass_status grass_kernel_timing_enable(grass_ctx_t ctx, int family);
+grass_status grass_kernel_timing_read(grass_ctx_t ctx, double *ms, int64_t *launches, double *bytes);
+
 /* ---------------------------------------------------------------- tree */
 
 /* Validate A = L_G + D (Sec. II-A), extract its edges, build the

@@ -100,6 +100,9 @@ def lib():
             sig = {
                 "grass_ctx_create": [C.POINTER(_vp), _vp],
                 "grass_ctx_set_stream": [_vp, _vp],
+                "grass_kernel_timing_enable": [_vp, C.c_int],
+                "grass_ctx_set_wait_limit": [_vp, _i64, C.c_int],
+                "grass_kernel_timing_read": [_vp, C.POINTER(_d), C.POINTER(_i64), C.POINTER(_d)],
                 "grass_build_tree": [_vp, C.POINTER(grass_csr_t), _i32, C.POINTER(_vp)],
                 "grass_tree_info": [_vp, C.POINTER(_i64), C.POINTER(_i64), C.POINTER(_i64)],
                 "grass_tree_graph": [_vp, _vp, _vp, _vp, _vp, _vp],
@@ -186,6 +189,26 @@ def grass_last_error(ctx: int) -> str:
 
 def grass_launch_count(ctx: int) -> int:
     return int(lib().grass_launch_count(ctx))
+
+
+def grass_ctx_set_wait_limit(ctx: int, polls: int = 0, hold_barriers: int = 0) -> None:
+    _check(ctx, lib().grass_ctx_set_wait_limit(ctx, int(polls), int(hold_barriers)),
+           "grass_ctx_set_wait_limit")
+
+
+GRASS_KF_NONE, GRASS_KF_SPMM_G, GRASS_KF_SPMM_S, GRASS_KF_HEAT, GRASS_KF_TREE = 0, 1, 2, 3, 4
+
+
+def grass_kernel_timing_enable(ctx: int, family: int) -> None:
+    _check(ctx, lib().grass_kernel_timing_enable(ctx, int(family)), "grass_kernel_timing_enable")
+
+
+def grass_kernel_timing_read(ctx: int) -> tuple[float, int, float]:
+    """(summed event ms, timed launches, summed algorithmic bytes)."""
+    ms, nl, by = _d(0.0), _i64(0), _d(0.0)
+    _check(ctx, lib().grass_kernel_timing_read(ctx, C.byref(ms), C.byref(nl), C.byref(by)),
+           "grass_kernel_timing_read")
+    return ms.value, nl.value, by.value
 
 
 # ---------------------------------------------------------------- tree

@@ -55,6 +55,20 @@ double bits_to_double(unsigned long long b) {
     return d;
 }
 
+// A bounded device wait that ran out leaves flags[3] set: report it and
+// clear it for the next call.
+void clear_timeout(grass_ctx_t ctx) { memset_d(ctx, ctx->flags.p + 3, 0, sizeof(int)); }
+
+void check_timeout(grass_ctx_t ctx) {
+    int f = 0;
+    d2h(ctx, &f, ctx->flags.p + 3, sizeof(int));
+    if (f) {
+        clear_timeout(ctx);
+        ctx->sync();
+        fail(GRASS_ERR_TIMEOUT, "a bounded device-side wait expired (grid barrier)");
+    }
+}
+
 void ensure_sdd(grass_ctx_t ctx, grass_tree_t T) {
     if (!T->has_sdd) {
         tree_factor(ctx, T, true, T->sdd);
@@ -75,8 +89,8 @@ int64_t power_steps(grass_ctx_t ctx, grass_sparsifier_t S, const double *h0, int
     int prev = -1, cur = 0;
     int64_t inner = 0;
     for (int s = 0; s < t; ++s) {
-        lap_mm(ctx, r, prec, n, g.adj_ptr.p, g.adj_col.p, w, nullptr, H, Y,
-               prev >= 0 ? maxslot(ctx, prev) : nullptr);
+        lap_mm(ctx, r, prec, n, 2 * g.m, g.adj_ptr.p, g.adj_col.p, w, nullptr, H, Y,
+               prev >= 0 ? maxslot(ctx, prev) : nullptr, GRASS_KF_SPMM_G);
         memset_d(ctx, maxslot(ctx, cur), 0, sizeof(unsigned long long));
         inner += s_solve(ctx, S, false, r, prec, Y, H, inner_tol, inner_maxit, maxslot(ctx, cur));
         prev = cur;
@@ -128,6 +142,7 @@ double lambda_max_impl(grass_ctx_t ctx, grass_sparsifier_t S, const double *v0, 
     quad_forms(ctx, prec, S, v, q);
     double qq[2];
     d2h(ctx, qq, q, sizeof(qq));
+    check_timeout(ctx);   // a solve that gave up leaves garbage: report that first
     if (!(qq[1] > 0.0)) fail(GRASS_ERR_INVALID, "v^T L_S v is not positive (v0 constant?)");
     return qq[0] / qq[1];
 }
@@ -179,6 +194,12 @@ grass_status grass_ctx_create(grass_ctx_t *out, void *stream) {
         GCK(cudaMemset(ctx->flags.p, 0, 8 * sizeof(int)));
         GCK(cudaMemset(ctx->scal.p, 0, DS_TOTAL * sizeof(double)));
         GCK(cudaMallocHost((void **)&ctx->hpin, 4096 * sizeof(double)));
+        ctx->gbar.alloc(4);
+        GCK(cudaMemset(ctx->gbar.p, 0, 4 * sizeof(unsigned int)));
+        int coop = 0, sms = 0;
+        GCK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+        GCK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        ctx->num_sms = coop ? sms : 0;   // 0: per-round launches instead of one cooperative kernel
         GCK(cudaDeviceSynchronize());
     } catch (const grass::Error &e) {
         delete ctx;
@@ -210,6 +231,46 @@ grass_status grass_ctx_set_stream(grass_ctx_t ctx, void *stream) {
 const char *grass_last_error(grass_ctx_t ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
 int64_t grass_launch_count(grass_ctx_t ctx) { return ctx ? ctx->launches : 0; }
+
+grass_status grass_ctx_set_wait_limit(grass_ctx_t ctx, int64_t polls, int hold_barriers) {
+    if (!ctx) return GRASS_ERR_INVALID;
+    API_BEGIN(ctx)
+    need(polls >= 0, "polls must be >= 0");
+    ctx->wait_budget = polls > 0 ? (long long)polls : (1LL << 24);
+    unsigned int h = hold_barriers ? 1u : 0u;
+    GCK(cudaMemcpyAsync(ctx->gbar.p + 2, &h, sizeof(h), cudaMemcpyHostToDevice, ctx->stream));
+    ctx->sync();
+    API_END
+}
+
+grass_status grass_kernel_timing_enable(grass_ctx_t ctx, int family) {
+    if (!ctx) return GRASS_ERR_INVALID;
+    API_BEGIN(ctx)
+    need(family >= GRASS_KF_NONE && family <= GRASS_KF_TREE, "unknown kernel family");
+    ctx->sync();
+    ctx->tfam = family;
+    ctx->ev_used = 0;
+    ctx->t_launches = 0;
+    ctx->t_bytes = 0.0;
+    API_END
+}
+
+grass_status grass_kernel_timing_read(grass_ctx_t ctx, double *ms, int64_t *launches,
+                                      double *bytes) {
+    if (!ctx) return GRASS_ERR_INVALID;
+    API_BEGIN(ctx)
+    ctx->sync();
+    double tot = 0.0;
+    for (size_t i = 0; i + 1 < ctx->ev_used; i += 2) {
+        float e = 0.f;
+        GCK(cudaEventElapsedTime(&e, ctx->events[i], ctx->events[i + 1]));
+        tot += e;
+    }
+    if (ms) *ms = tot;
+    if (launches) *launches = ctx->t_launches;
+    if (bytes) *bytes = ctx->t_bytes;
+    API_END
+}
 
 // ---------------------------------------------------------------- tree
 
@@ -283,7 +344,9 @@ grass_status grass_tree_solve(grass_ctx_t ctx, grass_tree_t T, int with_D, int r
     need(r_supported(r), "r must be 1, 2, 4, 8, 16, 24 or 32");
     if (with_D) ensure_sdd(ctx, T);
     copy_d(ctx, X, B, T->g.n * r * esize(prec));
+    clear_timeout(ctx);
     tree_solve_inplace(ctx, T, with_D ? T->sdd : T->lap, r, prec, X, nullptr);
+    check_timeout(ctx);
     API_END
 }
 
@@ -295,9 +358,9 @@ grass_status grass_spmm(grass_ctx_t ctx, grass_tree_t T, int r, grass_prec prec,
     need_prec(prec);
     need(r_supported(r), "r must be 1, 2, 4, 8, 16, 24 or 32");
     const GraphData &g = T->g;
-    lap_mm(ctx, r, prec, g.n, g.adj_ptr.p, g.adj_col.p,
+    lap_mm(ctx, r, prec, g.n, 2 * g.m, g.adj_ptr.p, g.adj_col.p,
            prec == GRASS_FP64 ? (const void *)g.adj_w64.p : (const void *)g.adj_w32.p, nullptr, X,
-           Y, nullptr);
+           Y, nullptr, GRASS_KF_SPMM_G);
     API_END
 }
 
@@ -372,7 +435,9 @@ grass_status grass_embed(grass_ctx_t ctx, grass_sparsifier_t S, const double *h0
     need(t >= 1, "t must be >= 1");
     need(inner_maxit >= 0, "inner_maxit must be >= 0");
     void *hb = heat ? heat : (void *)ctx->scr<char>(SCR_HEAT, (S->m_off + 1) * esize(prec));
+    clear_timeout(ctx);
     EmbedOut o = embed_impl(ctx, S, h0, r, t, prec, inner_tol, inner_maxit, H_out, hb);
+    check_timeout(ctx);
     if (heat_max) *heat_max = o.heat_max;
     API_END
 }
@@ -392,7 +457,9 @@ grass_status grass_lambda_max(grass_ctx_t ctx, grass_sparsifier_t S, const doubl
     need_prec(prec);
     need(iters >= 0, "iters must be >= 0");
     int64_t inner = 0;
+    clear_timeout(ctx);
     *lmax = lambda_max_impl(ctx, S, v0, iters, prec, inner_tol, inner_maxit, &inner);
+    check_timeout(ctx);
     API_END
 }
 
@@ -442,6 +509,7 @@ grass_status grass_densify(grass_ctx_t ctx, grass_tree_t T, const grass_params_t
     std::memset(&st, 0, sizeof(st));
     const int64_t n = T->g.n;
     const int r = P->r;
+    clear_timeout(ctx);
     grass_sparsifier_t S = new_sparsifier(ctx, T);
     try {
         void *heat = ctx->scr<char>(SCR_HEAT, (T->g.m + 1) * esize(P->embed_prec));
@@ -491,6 +559,12 @@ grass_status grass_densify(grass_ctx_t ctx, grass_tree_t T, const grass_params_t
         delete S;
         throw;
     }
+    try {
+        check_timeout(ctx);
+    } catch (...) {
+        delete S;
+        throw;
+    }
     st.ms_total = now_ms() - t0;
     if (stats) *stats = st;
     *out = S;
@@ -512,7 +586,9 @@ grass_status grass_pcg_solve(grass_ctx_t ctx, grass_sparsifier_t S, const double
     grass_solve_stats_t st;
     std::memset(&st, 0, sizeof(st));
     try {
+        clear_timeout(ctx);
         pcg_solve(ctx, S, b, x, tol, maxit, prec, refine_tol, inner_tol, inner_maxit, &st);
+        check_timeout(ctx);
     } catch (const grass::Error &e) {
         st.ms = now_ms() - t0;
         if (stats) *stats = st;

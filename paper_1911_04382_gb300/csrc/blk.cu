@@ -58,10 +58,14 @@ static void lapmm_R(grass_ctx_t ctx, grass_prec prec, int64_t n, const int32_t *
                (const float *)D, (const float *)X, (float *)Y, sf);
 }
 
-void lap_mm(grass_ctx_t ctx, int r, grass_prec prec, int64_t n, const int32_t *ptr,
+void lap_mm(grass_ctx_t ctx, int r, grass_prec prec, int64_t n, int64_t nnz, const int32_t *ptr,
             const int32_t *col, const void *w, const void *Dopt, const void *X, void *Y,
-            const unsigned long long *scale_from) {
+            const unsigned long long *scale_from, int fam) {
+    const double s = prec == GRASS_FP64 ? 8.0 : 4.0;
+    const double bytes = 4.0 * (n + 1) + nnz * (4.0 + s) + 2.0 * n * r * s + (Dopt ? n * s : 0.0);
+    bool timed = ctx->t_begin(fam, bytes);
     GRASS_DISPATCH_R(r, lapmm_R, ctx, prec, n, ptr, col, w, Dopt, X, Y, scale_from);
+    ctx->t_end(timed);
 }
 
 // ---------------------------------------------------------------- conversions, scaling
@@ -103,7 +107,7 @@ __global__ void k_max_abs(int64_t cnt, const T *X, unsigned long long *maxbits) 
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt;
          i += (int64_t)gridDim.x * blockDim.x)
         mx = fmax(mx, fabs((double)X[i]));
-    warp_atomic_max(maxbits, mx);
+    block_atomic_max(maxbits, mx);
 }
 
 void max_abs_bits(grass_ctx_t ctx, grass_prec prec, int64_t count, const void *X,
@@ -148,7 +152,7 @@ __global__ void k_heat(int64_t moff, const int32_t *__restrict__ ou, const int32
         heat[i] = h;
         hval = (double)h;
     }
-    warp_atomic_max(heatmax, hval);
+    block_atomic_max(heatmax, hval);
 }
 
 template <int R>
@@ -170,7 +174,11 @@ static void heat_R(grass_ctx_t ctx, grass_prec prec, grass_sparsifier_t S, const
 void heat_offs(grass_ctx_t ctx, int r, grass_prec prec, grass_sparsifier_t S, const void *H,
                const unsigned long long *scale_from, void *heat, unsigned long long *heatmax_bits) {
     memset_d(ctx, heatmax_bits, 0, sizeof(unsigned long long));
+    const double s = prec == GRASS_FP64 ? 8.0 : 4.0;
+    const double moff = (double)S->m_off, n = (double)S->tree->g.n;
+    bool timed = ctx->t_begin(GRASS_KF_HEAT, moff * (8.0 + s) + n * r * s + moff * s);
     GRASS_DISPATCH_R(r, heat_R, ctx, prec, S, H, scale_from, heat, heatmax_bits);
+    ctx->t_end(timed);
 }
 
 // ---------------------------------------------------------------- quadratic forms

@@ -93,6 +93,37 @@ struct grass_ctx_s {
     grass::DBuf<unsigned int> counters;     // last-block counters
     double *hpin = nullptr;                 // pinned host staging (4096 doubles)
     grass::DBuf<char> scratch[grass::SCR_COUNT];
+    // bounded device waits: barrier state and poll budget (flags[3] = timeout)
+    grass::DBuf<unsigned int> gbar;
+    long long wait_budget = 1LL << 24;
+    int num_sms = 0;
+    // kernel-family timing (grass_kernel_timing_*)
+    int tfam = 0;
+    std::vector<cudaEvent_t> events;
+    size_t ev_used = 0;
+    int64_t t_launches = 0;
+    double t_bytes = 0.0;
+
+    bool t_begin(int fam, double bytes) {
+        if (fam == 0 || fam != tfam) return false;
+        while (events.size() < ev_used + 2) {
+            cudaEvent_t e;
+            GCK(cudaEventCreate(&e));
+            events.push_back(e);
+        }
+        GCK(cudaEventRecord(events[ev_used], stream));
+        t_bytes += bytes;
+        t_launches += 1;
+        return true;
+    }
+    void t_end(bool timed) {
+        if (!timed) return;
+        GCK(cudaEventRecord(events[ev_used + 1], stream));
+        ev_used += 2;
+    }
+    ~grass_ctx_s() {
+        for (auto e : events) cudaEventDestroy(e);
+    }
 
     template <typename T>
     T *scr(int slot, size_t count) {
@@ -217,6 +248,7 @@ struct grass_sparsifier_s {
     grass::DBuf<double> off_w64;
     grass::DBuf<float> off_w32;
     grass::DBuf<int32_t> s_ptr, s_col;            // S adjacency (when !is_tree)
+    int64_t s_nnz = 0;
     grass::DBuf<double> s_w64;
     grass::DBuf<float> s_w32;
     grass::DBuf<double> degS;         // [n]
@@ -258,9 +290,9 @@ void tree_solve_inplace(grass_ctx_t ctx, grass_tree_t T, const TreeFactor &f, in
 
 // Y = scale * (L X + Dopt .* X) over an adjacency (ptr, col, w).  scale may
 // come from a device max-bits word (pow2 rescale) when scale_from != nullptr.
-void lap_mm(grass_ctx_t ctx, int r, grass_prec prec, int64_t n, const int32_t *ptr,
+void lap_mm(grass_ctx_t ctx, int r, grass_prec prec, int64_t n, int64_t nnz, const int32_t *ptr,
             const int32_t *col, const void *w, const void *Dopt, const void *X, void *Y,
-            const unsigned long long *scale_from);
+            const unsigned long long *scale_from, int fam);
 // Convert an n x r double block to prec (copy or float conversion).
 void convert_block(grass_ctx_t ctx, grass_prec prec, int64_t count, const double *src, void *dst);
 // Multiply an n x r block in place by the pow2 factor derived from maxbits.
@@ -295,6 +327,66 @@ void sparsifier_add(grass_ctx_t ctx, grass_sparsifier_t S, const int64_t *eids, 
 void lambda_min(grass_ctx_t ctx, grass_sparsifier_t S, double *out_host);
 int64_t filter_heat(grass_ctx_t ctx, grass_sparsifier_t S, const void *heat, grass_prec prec,
                     double thr, int64_t cap, int64_t *accepted);
+
+// ---------------------------------------------------------------- grid barrier
+// Barrier for cooperative (co-resident) launches.  bar[0] counts arrivals,
+// bar[1] is the generation.  Every wait is bounded: after `budget` polls, or
+// as soon as another block has flagged an error, the block sets *err and
+// leaves; the caller returns from the kernel, so a lost block can never hang
+// the GPU.  All threads of a block get the same answer.
+// bar[2] != 0 (testing only) makes every barrier wait for one more block
+// than the grid has, so every wait runs out.
+__device__ inline bool grid_sync(unsigned int *bar, long long budget, int *err) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        volatile unsigned int *vgen = bar + 1;
+        unsigned int g = *vgen;
+        const unsigned int need = gridDim.x + (((volatile unsigned int *)bar)[2] ? 1u : 0u);
+        __threadfence();
+        unsigned int arrived = atomicAdd(bar, 1u);
+        if (arrived == need - 1) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            long long spins = 0;
+            while (*vgen == g) {
+                if (*(volatile int *)err) {
+                    ok = 0;
+                    break;
+                }
+                if (++spins > budget) {
+                    atomicOr(err, 1);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// block-wide max of a non-negative double, one atomicMax on its bit pattern
+__device__ inline void block_atomic_max(unsigned long long *maxbits, double v) {
+    __shared__ double sm[32];
+    for (int d = 16; d > 0; d >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, d));
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sm[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        int nw = (blockDim.x + 31) >> 5;
+        v = lane < nw ? sm[lane] : 0.0;
+        for (int d = 16; d > 0; d >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, d));
+        if (lane == 0 && v > 0.0) atomicMax(maxbits, (unsigned long long)__double_as_longlong(v));
+    }
+}
 
 // bits helpers
 __host__ __device__ inline double pow2_scale_from_bits(unsigned long long maxbits_f64) {

@@ -85,6 +85,7 @@ void sparsifier_rebuild(grass_ctx_t ctx, grass_sparsifier_t S) {
     if (!S->is_tree) {
         int64_t ns = 0;
         scan_i64(ctx, cnt, off, n, &ns);
+        S->s_nnz = ns;
         S->s_ptr.reserve(n + 1);
         S->s_col.reserve(ns);
         S->s_w64.reserve(ns);

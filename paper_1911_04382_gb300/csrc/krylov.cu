@@ -127,7 +127,8 @@ int64_t s_solve(grass_ctx_t ctx, grass_sparsifier_t S, bool with_D, int r, grass
             d2h(ctx, &nact, cg + CG_NACT * 32, sizeof(double));
             if (nact == 0) break;
         }
-        lap_mm(ctx, r, prec, n, S->s_ptr.p, S->s_col.p, w, D, P, Q, nullptr);
+        lap_mm(ctx, r, prec, n, S->s_nnz, S->s_ptr.p, S->s_col.p, w, D, P, Q, nullptr,
+               GRASS_KF_SPMM_S);
         dot_cols(ctx, r, prec, n, P, Q, cg + CG_PQ * 32);
         launch(ctx, k_cg_alpha, 1, 32, 0, r, tol, cg);
         if (prec == GRASS_FP64)
@@ -224,7 +225,8 @@ static int pcg_core(grass_ctx_t ctx, grass_sparsifier_t S, grass_prec prec, cons
         double rr = 0;
         d2h(ctx, &rr, sc + P_RR, sizeof(double));
         if (std::sqrt(rr) <= tol_abs) break;
-        lap_mm(ctx, 1, prec, n, g.adj_ptr.p, g.adj_col.p, wA, DA, p, q, nullptr);
+        lap_mm(ctx, 1, prec, n, 2 * g.m, g.adj_ptr.p, g.adj_col.p, wA, DA, p, q, nullptr,
+               GRASS_KF_SPMM_G);
         dot_cols(ctx, 1, prec, n, p, q, sc + P_PQ);
         launch(ctx, k_pcg_axpy<T>, grid, kBlock, 0, n, (const double *)(sc + P_RZ0 + cur),
                (const double *)(sc + P_PQ), e, r, (const T *)p, (const T *)q);
@@ -246,7 +248,8 @@ static double true_relres(grass_ctx_t ctx, const GraphData &g, const double *b, 
                           double bnorm, double *rvec) {
     const int64_t n = g.n;
     double *Ax = ctx->scr<double>(SCR_PCG_E, n);
-    lap_mm(ctx, 1, GRASS_FP64, n, g.adj_ptr.p, g.adj_col.p, g.adj_w64.p, g.D64.p, x, Ax, nullptr);
+    lap_mm(ctx, 1, GRASS_FP64, n, 2 * g.m, g.adj_ptr.p, g.adj_col.p, g.adj_w64.p, g.D64.p, x, Ax,
+           nullptr, GRASS_KF_SPMM_G);
     launch(ctx, k_residual64, cdiv(n, kBlock), kBlock, 0, n, b, (const double *)Ax, rvec);
     double *sc = ctx->scal.p + DS_RED;
     dot_cols(ctx, 1, GRASS_FP64, n, rvec, rvec, sc + P_EE);

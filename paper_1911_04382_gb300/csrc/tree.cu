@@ -503,12 +503,105 @@ static int tail_start(const TreeSchedule &S) {
     return k0;
 }
 
+// One cooperative launch per solve: the big rounds are separated by grid
+// barriers instead of kernel boundaries, the small last rounds run in
+// block 0 alone (block barriers), then the big rounds again backwards.
+constexpr int kPersistThreads = 256;
+
+template <typename T, int R>
+__global__ void __launch_bounds__(kPersistThreads)
+    k_tree_persist(int rounds, int k0, const int64_t *rcv_off, const int64_t *elim_off,
+                   const int32_t *rcv, const int32_t *beg, const int32_t *cv, const T *cm,
+                   const int32_t *elist, const int32_t *n1, const int32_t *n2, const T *invd,
+                   const T *b1, const T *b2, int32_t rho, T *Y, unsigned long long *maxbits,
+                   unsigned int *bar, long long budget, int *err) {
+    constexpr int TPR = Lay<R>::TPR, EPT = Lay<R>::EPT;
+    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = (int)(gt % TPR);
+    const int64_t slot = gt / TPR;
+    const int64_t nslots = (int64_t)gridDim.x * blockDim.x / TPR;
+    for (int k = 0; k < k0; ++k) {
+        const int64_t e = rcv_off[k + 1];
+        for (int64_t i = rcv_off[k] + slot; i < e; i += nslots)
+            fwd_item<T, R>(i, c, rcv, beg, cv, cm, Y);
+        if (!grid_sync(bar, budget, err)) return;
+    }
+    double mx = 0.0;
+    if (blockIdx.x == 0) {
+        const int bslot = threadIdx.x / TPR, bslots = blockDim.x / TPR;
+        for (int k = k0; k < rounds; ++k) {
+            for (int64_t i = rcv_off[k] + bslot; i < rcv_off[k + 1]; i += bslots)
+                fwd_item<T, R>(i, c, rcv, beg, cv, cm, Y);
+            __syncthreads();
+        }
+        if (bslot == 0) {
+            T *yr = Y + (int64_t)rho * R + c * EPT;
+            T id = invd[rho];
+#pragma unroll
+            for (int e = 0; e < EPT; ++e) {
+                yr[e] = id * yr[e];
+                mx = fmax(mx, fabs((double)yr[e]));
+            }
+        }
+        __syncthreads();
+        for (int k = rounds - 1; k >= k0; --k) {
+            for (int64_t i = elim_off[k] + bslot; i < elim_off[k + 1]; i += bslots)
+                mx = fmax(mx, bwd_item<T, R>(elist[i], c, n1, n2, invd, b1, b2, Y));
+            __syncthreads();
+        }
+    }
+    if (k0 > 0 && !grid_sync(bar, budget, err)) return;
+    for (int k = k0 - 1; k >= 0; --k) {
+        const int64_t e = elim_off[k + 1];
+        for (int64_t i = elim_off[k] + slot; i < e; i += nslots)
+            mx = fmax(mx, bwd_item<T, R>(elist[i], c, n1, n2, invd, b1, b2, Y));
+        if (k > 0 && !grid_sync(bar, budget, err)) return;
+    }
+    if (maxbits) block_atomic_max(maxbits, mx);
+}
+
+template <typename T, int R>
+static void solve_persistent(const SolveArgs &a, const T *invd, const T *b1, const T *b2,
+                             const T *cm) {
+    grass_ctx_t ctx = a.ctx;
+    const TreeSchedule &S = a.T->sched;
+    static int blocks_per_sm = -1;   // per instantiation
+    if (blocks_per_sm < 0) {
+        int nb = 0;
+        GCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_tree_persist<T, R>,
+                                                          kPersistThreads, 0));
+        blocks_per_sm = nb;
+    }
+    if (blocks_per_sm < 1) fail(GRASS_ERR_CUDA, "persistent tree solve does not fit on an SM");
+    int grid = ctx->num_sms * std::min(blocks_per_sm, 4);
+    int rounds = S.rounds, k0 = tail_start(S);
+    const int64_t *rcv_off = S.d_offs.p, *elim_off = S.d_offs.p + (S.rounds + 1);
+    const int32_t *rcv = S.rcv_list.p, *beg = S.rcv_beg.p, *cv = S.contrib_v.p;
+    const int32_t *elist = S.elim_list.p, *n1 = S.n1.p, *n2 = S.n2.p;
+    int32_t rho = a.T->ground;
+    T *Y = (T *)a.Y;
+    unsigned long long *maxbits = a.maxbits;
+    unsigned int *bar = ctx->gbar.p;
+    long long budget = ctx->wait_budget;
+    int *err = ctx->flags.p + 3;
+    GCK(cudaMemsetAsync(bar, 0, sizeof(unsigned int), ctx->stream));
+    void *args[] = {&rounds, &k0, &rcv_off, &elim_off, &rcv, &beg, &cv, &cm, &elist, &n1, &n2,
+                    &invd, &b1, &b2, &rho, &Y, &maxbits, &bar, &budget, &err};
+    GCK(cudaLaunchCooperativeKernel((const void *)k_tree_persist<T, R>, dim3(grid),
+                                    dim3(kPersistThreads), args, 0, ctx->stream));
+    ctx->launches++;
+}
+
 template <typename T, int R>
 static void solve_T(const SolveArgs &a, const T *invd, const T *b1, const T *b2, const T *cm) {
     constexpr int TPR = Lay<R>::TPR;
     grass_ctx_t ctx = a.ctx;
     const TreeSchedule &S = a.T->sched;
     T *Y = (T *)a.Y;
+    if (ctx->num_sms > 0) {
+        solve_persistent<T, R>(a, invd, b1, b2, cm);
+        return;
+    }
     const int k0 = tail_start(S);
     for (int k = 0; k < k0; ++k) {
         int64_t r0 = S.rcv_off[k], cnt = S.rcv_off[k + 1] - r0;
@@ -542,7 +635,12 @@ static void solve_R(const SolveArgs &a) {
 void tree_solve_inplace(grass_ctx_t ctx, grass_tree_t T, const TreeFactor &f, int r,
                         grass_prec prec, void *Y, unsigned long long *maxbits) {
     SolveArgs a{ctx, T, &f, Y, maxbits, prec};
+    const TreeSchedule &S = T->sched;
+    const double s = prec == GRASS_FP64 ? 8.0 : 4.0, n = (double)T->g.n;
+    const double bytes = 4.0 * n * r * s + S.n_contrib * (4.0 + s) + S.n_rcv * 8.0 + n * (12.0 + 3.0 * s);
+    bool timed = ctx->t_begin(GRASS_KF_TREE, bytes);
     GRASS_DISPATCH_R(r, solve_R, a);
+    ctx->t_end(timed);
 }
 
 }  // namespace grass
