@@ -200,14 +200,34 @@ def build_tree(og: OGraph, rho: int = 0) -> OTree:
     return orient(og, mst(og), rho)
 
 
-def tree_solve(og: OGraph, tree: OTree, B: np.ndarray, D: np.ndarray | None = None) -> np.ndarray:
-    """(L_T + D)^{-1} B, or the solve grounded at tree.rho when D is None."""
-    B2 = np.ascontiguousarray(B, dtype=np.float64)
-    r = 1 if B2.ndim == 1 else B2.shape[1]
+def _tree_solve_once(og, tree, B2, Dp, r):
     X = np.empty_like(B2)
-    Dp = None if D is None else np.ascontiguousarray(D, dtype=np.float64)
     lib().ora_tree_solve(og.n, _p(tree.parent, _i32), _p(tree.pw, _f64), _p(tree.order, _i32),
                          _p(Dp, _f64), r, _p(B2, _f64), _p(X, _f64))
+    return X
+
+
+def tree_solve(og: OGraph, tree: OTree, B: np.ndarray, D: np.ndarray | None = None,
+               refine: int = 2) -> np.ndarray:
+    """(L_T + D)^{-1} B, or the solve grounded at tree.rho when D is None.
+
+    The paper's operator is the exact inverse (Eq. formula_pwr_iter).  Leaf-
+    first elimination forms pivots by subtraction and, on million-vertex
+    trees with weights spread over decades, loses about 1e-8 relative
+    accuracy; `refine` steps of residual correction (r = B - (L_T + D) X in
+    FP64, X += solve(r)) bring the solve to full FP64 accuracy (one step
+    already gives ~1e-14 on the 100^3 grid)."""
+    B2 = np.ascontiguousarray(B, dtype=np.float64)
+    r = 1 if B2.ndim == 1 else B2.shape[1]
+    Dp = None if D is None else np.ascontiguousarray(D, dtype=np.float64)
+    X = _tree_solve_once(og, tree, B2, Dp, r)
+    for _ in range(refine):
+        R = B2 - lap_apply(og, X, tree.in_tree)
+        if Dp is not None:
+            R -= (Dp[:, None] * X) if X.ndim == 2 else Dp * X
+        else:
+            R = R - R.mean(axis=0)      # the grounded system's right side sums to zero
+        X = X + _tree_solve_once(og, tree, np.ascontiguousarray(R), Dp, r)
     return X
 
 
@@ -257,6 +277,8 @@ def s_solve(og: OGraph, tree: OTree, in_s: np.ndarray | None, Y: np.ndarray,
     CG on L_S + D preconditioned by the tree solve.  Returns (X, iters)."""
     Y2 = np.ascontiguousarray(Y, dtype=np.float64)
     r = 1 if Y2.ndim == 1 else Y2.shape[1]
+    if in_s is None:
+        return tree_solve(og, tree, Y2, D), np.zeros(r, np.int32)
     X = np.empty_like(Y2)
     it = np.zeros(r, np.int32)
     Dp = None if D is None else np.ascontiguousarray(D, dtype=np.float64)
