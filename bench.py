@@ -38,10 +38,12 @@ UNIT = "edges/s"
 
 WORKLOADS = {
     # 100^3 7-point grid, log-uniform weights in [1e-2, 1e2], D = 1e-3 I
+    # PCG inner budget: outer iterations stay ~400 for 1..32 inner CG
+    # iterations (measured), so one inner iteration is the fastest setting
     "grid3d_100": dict(kind="grid3d", side=100, seed=2, r=16, t=2, sigma2=200.0, rounds=3,
                        lmax_iters=8, cap_frac=0.02, embed="fp32", inner_tol=1e-2, inner_maxit=30,
                        pcg="fp32", pcg_tol=1e-8, refine_tol=1e-2, pcg_inner_tol=1e-2,
-                       pcg_inner_maxit=8, pcg_maxit=4000),
+                       pcg_inner_maxit=1, pcg_maxit=4000),
     # 64x64 5-point grid, w ~ U[1,10), D = 1e-3 I, plain FP64 method
     "grid2d_64": dict(kind="grid2d", side=64, seed=1, r=8, t=2, sigma2=100.0, rounds=1,
                       lmax_iters=8, cap_frac=0.0, embed="fp64", inner_tol=1e-10, inner_maxit=1000,
@@ -51,10 +53,10 @@ WORKLOADS = {
     "grid3d_40": dict(kind="grid3d", side=40, seed=2, r=16, t=2, sigma2=200.0, rounds=3,
                       lmax_iters=8, cap_frac=0.02, embed="fp32", inner_tol=1e-2, inner_maxit=30,
                       pcg="fp32", pcg_tol=1e-8, refine_tol=1e-2, pcg_inner_tol=1e-2,
-                      pcg_inner_maxit=8, pcg_maxit=4000),
+                      pcg_inner_maxit=1, pcg_maxit=4000),
 }
 
-FAMILIES = {"spmm_g": 1, "spmm_s": 2, "heat": 3, "tree": 4}
+FAMILIES = {"spmm_g": 1, "spmm_s": 2, "heat": 3, "tree": 4, "cg": 5}
 
 
 def make_inputs(w: dict):
@@ -183,6 +185,49 @@ def run_reference(args, w):
     return 0
 
 
+# ---------------------------------------------------------------- kernel captures
+
+KERNEL_SOURCES = ["paper_1911_04382_gb300/csrc/krylov.cu", "paper_1911_04382_gb300/csrc/solve.cu",
+                  "paper_1911_04382_gb300/csrc/tree_solve.cuh",
+                  "paper_1911_04382_gb300/csrc/common.cuh"]
+
+
+def kernel_sources_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for s in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, s), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profile_kernel(G, ctx, which, g, rp, col, val, v0d, w) -> int:
+    """One warm and one timed launch of the fused inner CG (exactly 30
+    iterations, r = 1, FP32, sparsifier = tree + every 197th off-tree edge)
+    or of the tree solve (r = 16, FP32); prints its algorithmic bytes."""
+    import torch
+    tree = G.grass_build_tree(ctx, rp, col, val, 0)
+    if which == "cg":
+        S = G.grass_sparsifier_create(ctx, tree)
+        _, moff = G.grass_sparsifier_info(S)
+        ids = torch.empty(moff, dtype=torch.int64, device="cuda")
+        G.grass_sparsifier_offtree(ctx, S, ids)
+        G.grass_sparsifier_add(ctx, S, ids[::197].contiguous())
+        run = lambda: G.grass_lambda_max(ctx, S, v0d[:g.n], 1, G.GRASS_FP32, 0.0, 30)
+        fam, units = G.GRASS_KF_CG, "30 iterations, r=1"
+    else:
+        B = torch.randn(g.n, 16, dtype=torch.float32, device="cuda")
+        X = torch.empty_like(B)
+        run = lambda: G.grass_tree_solve(ctx, tree, 0, 16, G.GRASS_FP32, B, X)
+        fam, units = G.GRASS_KF_TREE, "one solve, r=16"
+    run()
+    G.grass_kernel_timing_enable(ctx, fam)
+    run()
+    ms, nl, by = G.grass_kernel_timing_read(ctx)
+    print(json.dumps({"profile_kernel": which, "launches": nl, "ms": ms, "algorithmic_bytes": by,
+                      "units": units, "sources": kernel_sources_hash()}), flush=True)
+    return 0
+
+
 # ---------------------------------------------------------------- GPU arm
 
 def main() -> int:
@@ -192,10 +237,14 @@ def main() -> int:
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="grass", choices=["grass", "reference"])
     ap.add_argument("--workload", default="grid3d_100", choices=sorted(WORKLOADS))
-    ap.add_argument("--family", default="tree", choices=sorted(FAMILIES),
+    ap.add_argument("--family", default="cg", choices=sorted(FAMILIES),
                     help="kernel family timed for the roofline object")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-breakdown", action="store_true")
+    ap.add_argument("--profile-step", action="store_true",
+                    help="run exactly one step and exit (for ncu launch lists)")
+    ap.add_argument("--profile-kernel", choices=["cg", "tree"], default=None,
+                    help="one warm launch, then one timed launch of the kernel (for ncu captures)")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     if args.impl == "reference":
@@ -238,9 +287,10 @@ def main() -> int:
                                         w["refine_tol"], w["pcg_inner_tol"], w["pcg_inner_maxit"])
         t3 = time.perf_counter()
         n_s, _ = G.grass_sparsifier_info(S)
+        rounds = G.grass_tree_info(tree)[2]
         G.grass_sparsifier_destroy(S)
         G.grass_tree_destroy(tree)
-        last.update(st=st.as_dict(), sst=sst.as_dict(), status=status, n_s=n_s,
+        last.update(st=st.as_dict(), sst=sst.as_dict(), status=status, n_s=n_s, tree_rounds=rounds,
                     phase_ms={"tree": 1e3 * (t1 - t0), "densify": 1e3 * (t2 - t1),
                               "pcg": 1e3 * (t3 - t2)})
         return st.offtree_embedded
@@ -256,6 +306,17 @@ def main() -> int:
         t = torch.tensor([v], dtype=torch.float64, device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         return float(t.item())
+
+    if args.profile_kernel:
+        return profile_kernel(G, ctx, args.profile_kernel, g, rp, col, val, v0d, w)
+
+    if args.profile_step:
+        e = step(rp, col, val, h0d, v0d, bd, x)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_step": True, "edges": e, "launches": G.grass_launch_count(ctx),
+                          "phase_ms": last.get("phase_ms")}), flush=True)
+        G.grass_ctx_destroy(ctx)
+        return 0
 
     for _ in range(max(args.warmup, 0)):
         step(rp, col, val, h0d, v0d, bd, x)
@@ -327,10 +388,15 @@ def main() -> int:
         pass
     peak = float(peaks.get("hbm_gbs", 6800.0))
     achieved = (kbytes / kl) / ((kms / kl) / 1e3) / 1e9 if kl and kms > 0 else None
+    # DRAM traffic per launch from the committed ncu capture (dram bytes /
+    # algorithmic bytes of the captured launch, times this run's algorithmic
+    # bytes per launch); null when the kernel sources changed since
     traffic_note = None
     try:
         tr = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
-        traffic_note = tr.get(args.workload, {}).get(args.family)
+        rec = tr.get(args.workload, {}).get(args.family)
+        if rec and rec.get("sources") == kernel_sources_hash() and kl:
+            traffic_note = rec["dram_bytes"] / rec["algorithmic_bytes"] * (kbytes / kl)
     except Exception:
         pass
     roofline = {
@@ -367,7 +433,8 @@ def main() -> int:
             "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu,
             "clocks": clk, "edges_embedded_per_step": edges_per_step,
             "phase_ms": last.get("phase_ms"), "densify": last.get("st"), "pcg": last.get("sst"),
-            "sparsifier_edges": last.get("n_s"), "kernels": breakdown,
+            "sparsifier_edges": last.get("n_s"), "tree_factor_rounds": last.get("tree_rounds"),
+            "kernels": breakdown,
         }
         print(json.dumps(line), flush=True)
     G.grass_ctx_destroy(ctx)

@@ -133,6 +133,15 @@ int64_t grass_launch_count(grass_ctx_t ctx);
  * one block more than the grid has, so every wait runs out.  Synchronises. */
 grass_status grass_ctx_set_wait_limit(grass_ctx_t ctx, int64_t polls, int hold_barriers);
 
+/* Launch-shape knobs (no counterpart in the paper), read by the kernels at
+ * launch time; results do not depend on them.  Names:
+ *   "tree_blocks_per_sm"  blocks per SM of the cooperative tree solve (1-8)
+ *   "tree_threads"        threads per block of that kernel (128-1024, x32)
+ *   "tree_tail_items"     rounds at the end whose total work is below this
+ *                         many items run in one block (0 = none)
+ * Errors: INVALID for an unknown name or a value out of range. */
+grass_status grass_ctx_set_param(grass_ctx_t ctx, const char *name, int64_t value);
+
 /* Kernel timing for roofline measurements (no counterpart in the paper).
  * family != GRASS_KF_NONE brackets every launch of that kernel family with
  * CUDA events on the context stream and accumulates, per launch, the
@@ -140,8 +149,12 @@ grass_status grass_ctx_set_wait_limit(grass_ctx_t ctx, int64_t polls, int hold_b
  *   GRASS_KF_SPMM_G  Y = L_G X:  4(n+1) + 2m(4+s) + 2nrs
  *   GRASS_KF_SPMM_S  the same over the sparsifier's adjacency (+ns with D)
  *   GRASS_KF_HEAT    m_off(8+s) + nrs + m_off s
- *   GRASS_KF_TREE    one whole tree solve (all its launches):
- *                    4nrs + contributions(4+s) + receivers 8 + n(12+3s)
+ *   GRASS_KF_TREE    one whole tree solve:
+ *                    4nrs + receivers(16+2s) + (n-1)(16+4s)
+ *   GRASS_KF_CG      one fused inner CG solve on the sparsifier: its
+ *                    iterations (read back from the device) times
+ *                    [SpMV over S + 16nrs + tree solve] plus the start
+ *                    (7nrs + one tree solve)
  * (n rows, r columns, s = 4 or 8 bytes, m edges.)  Enabling resets the
  * accumulators.  grass_kernel_timing_read synchronises the stream and
  * returns the summed event time (ms), the number of timed launches and the
@@ -151,7 +164,8 @@ typedef enum {
     GRASS_KF_SPMM_G = 1,
     GRASS_KF_SPMM_S = 2,
     GRASS_KF_HEAT = 3,
-    GRASS_KF_TREE = 4
+    GRASS_KF_TREE = 4,
+    GRASS_KF_CG = 5
 } grass_kernel_family;
 grass_status grass_kernel_timing_enable(grass_ctx_t ctx, int family);
 grass_status grass_kernel_timing_read(grass_ctx_t ctx, double *ms, int64_t *launches, double *bytes);
@@ -174,6 +188,12 @@ void grass_tree_destroy(grass_tree_t tree);
 /* Sizes: n, m (edges), factor_rounds (contraction rounds of the tree
  * elimination schedule).  Any pointer may be NULL.  Host outputs. */
 grass_status grass_tree_info(grass_tree_t tree, int64_t *n, int64_t *m, int64_t *factor_rounds);
+
+/* Per-round sizes of the elimination schedule (host outputs, room for cap
+ * rounds each, any may be NULL): vertices eliminated, vertices receiving
+ * updates, and updates (contributions), round by round. */
+grass_status grass_tree_schedule_info(grass_tree_t tree, int64_t *eliminated, int64_t *receivers,
+                                      int64_t *contributions, int64_t cap);
 
 /* Export the extracted graph (device outputs, m entries each, any may be
  * NULL): eu[e] < ev[e], ew[e] = w_e; D (n entries) = diagonal load. */

@@ -102,6 +102,9 @@ def lib():
                 "grass_ctx_set_stream": [_vp, _vp],
                 "grass_kernel_timing_enable": [_vp, C.c_int],
                 "grass_ctx_set_wait_limit": [_vp, _i64, C.c_int],
+                "grass_ctx_set_param": [_vp, C.c_char_p, _i64],
+                "grass_tree_schedule_info": [_vp, C.POINTER(_i64), C.POINTER(_i64),
+                                             C.POINTER(_i64), _i64],
                 "grass_kernel_timing_read": [_vp, C.POINTER(_d), C.POINTER(_i64), C.POINTER(_d)],
                 "grass_build_tree": [_vp, C.POINTER(grass_csr_t), _i32, C.POINTER(_vp)],
                 "grass_tree_info": [_vp, C.POINTER(_i64), C.POINTER(_i64), C.POINTER(_i64)],
@@ -191,12 +194,25 @@ def grass_launch_count(ctx: int) -> int:
     return int(lib().grass_launch_count(ctx))
 
 
+def grass_ctx_set_param(ctx: int, name: str, value: int) -> None:
+    _check(ctx, lib().grass_ctx_set_param(ctx, name.encode(), int(value)), "grass_ctx_set_param")
+
+
+def grass_tree_schedule_info(tree: int, cap: int = 4096):
+    """Per-round (eliminated, receivers, contributions) lists."""
+    n, m, rounds = grass_tree_info(tree)
+    k = min(rounds, cap)
+    a, b, c = (_i64 * max(k, 1))(), (_i64 * max(k, 1))(), (_i64 * max(k, 1))()
+    _check(None, lib().grass_tree_schedule_info(tree, a, b, c, k), "grass_tree_schedule_info")
+    return list(a[:k]), list(b[:k]), list(c[:k])
+
+
 def grass_ctx_set_wait_limit(ctx: int, polls: int = 0, hold_barriers: int = 0) -> None:
     _check(ctx, lib().grass_ctx_set_wait_limit(ctx, int(polls), int(hold_barriers)),
            "grass_ctx_set_wait_limit")
 
 
-GRASS_KF_NONE, GRASS_KF_SPMM_G, GRASS_KF_SPMM_S, GRASS_KF_HEAT, GRASS_KF_TREE = 0, 1, 2, 3, 4
+GRASS_KF_NONE, GRASS_KF_SPMM_G, GRASS_KF_SPMM_S, GRASS_KF_HEAT, GRASS_KF_TREE, GRASS_KF_CG = 0, 1, 2, 3, 4, 5
 
 
 def grass_kernel_timing_enable(ctx: int, family: int) -> None:

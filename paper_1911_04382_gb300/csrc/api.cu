@@ -243,15 +243,59 @@ grass_status grass_ctx_set_wait_limit(grass_ctx_t ctx, int64_t polls, int hold_b
     API_END
 }
 
+grass_status grass_ctx_set_param(grass_ctx_t ctx, const char *name, int64_t value) {
+    if (!ctx || !name) return GRASS_ERR_INVALID;
+    API_BEGIN(ctx)
+    std::string k(name);
+    if (k == "tree_blocks_per_sm") {
+        need(value >= 1 && value <= 8, "tree_blocks_per_sm must be in [1, 8]");
+        ctx->tree_bpsm = (int)value;
+    } else if (k == "tree_threads") {
+        need(value >= 128 && value <= kPersistMaxThreads && value % 32 == 0,
+             "tree_threads must be a multiple of 32 in [128, 1024]");
+        ctx->tree_threads = (int)value;
+    } else if (k == "tree_tail_items") {
+        need(value >= 0, "tree_tail_items must be >= 0");
+        ctx->tree_tail_items = value;
+    } else {
+        fail(GRASS_ERR_INVALID, "unknown parameter " + k);
+    }
+    API_END
+}
+
+grass_status grass_tree_schedule_info(grass_tree_t T, int64_t *eliminated, int64_t *receivers,
+                                      int64_t *contributions, int64_t cap) {
+    if (!T || cap < 0) return GRASS_ERR_INVALID;
+    const TreeSchedule &S = T->sched;
+    for (int k = 0; k < S.rounds && k < cap; ++k) {
+        if (eliminated) eliminated[k] = S.elim_off[k + 1] - S.elim_off[k];
+        if (receivers) receivers[k] = S.rcv_off[k + 1] - S.rcv_off[k];
+        if (contributions) {
+            contributions[k] = 0;   // filled below from the host offsets
+        }
+    }
+    if (contributions) {
+        // contributions of round k = rcv_beg[rcv_off[k+1]] - rcv_beg[rcv_off[k]]
+        std::vector<int32_t> beg(S.n_rcv + 1);
+        if (cudaMemcpy(beg.data(), S.rcv_beg.p, beg.size() * sizeof(int32_t),
+                       cudaMemcpyDeviceToHost) != cudaSuccess)
+            return GRASS_ERR_CUDA;
+        for (int k = 0; k < S.rounds && k < cap; ++k)
+            contributions[k] = beg[S.rcv_off[k + 1]] - beg[S.rcv_off[k]];
+    }
+    return GRASS_OK;
+}
+
 grass_status grass_kernel_timing_enable(grass_ctx_t ctx, int family) {
     if (!ctx) return GRASS_ERR_INVALID;
     API_BEGIN(ctx)
-    need(family >= GRASS_KF_NONE && family <= GRASS_KF_TREE, "unknown kernel family");
+    need(family >= GRASS_KF_NONE && family <= GRASS_KF_CG, "unknown kernel family");
     ctx->sync();
     ctx->tfam = family;
     ctx->ev_used = 0;
     ctx->t_launches = 0;
     ctx->t_bytes = 0.0;
+    ctx->iter_launches.clear();
     API_END
 }
 
@@ -266,9 +310,16 @@ grass_status grass_kernel_timing_read(grass_ctx_t ctx, double *ms, int64_t *laun
         GCK(cudaEventElapsedTime(&e, ctx->events[i], ctx->events[i + 1]));
         tot += e;
     }
+    double by = ctx->t_bytes;
+    if (!ctx->iter_launches.empty()) {
+        std::vector<double> snap(2 * ctx->iter_launches.size());
+        d2h(ctx, snap.data(), ctx->iter_snap.p, snap.size() * sizeof(double));
+        for (const auto &l : ctx->iter_launches)
+            by += l.fixed + l.per_iter * (snap[2 * l.slot + 1] - snap[2 * l.slot]);
+    }
     if (ms) *ms = tot;
     if (launches) *launches = ctx->t_launches;
-    if (bytes) *bytes = ctx->t_bytes;
+    if (bytes) *bytes = by;
     API_END
 }
 
@@ -510,6 +561,7 @@ grass_status grass_densify(grass_ctx_t ctx, grass_tree_t T, const grass_params_t
     const int64_t n = T->g.n;
     const int r = P->r;
     clear_timeout(ctx);
+    memset_d(ctx, ctx->scal.p + DS_RED + DS_ITER, 0, sizeof(double));
     grass_sparsifier_t S = new_sparsifier(ctx, T);
     try {
         void *heat = ctx->scr<char>(SCR_HEAT, (T->g.m + 1) * esize(P->embed_prec));
@@ -554,6 +606,9 @@ grass_status grass_densify(grass_ctx_t ctx, grass_tree_t T, const grass_params_t
             ctx->sync();
             st.ms_update += now_ms() - td;
         }
+        double iters = 0.0;
+        d2h(ctx, &iters, ctx->scal.p + DS_RED + DS_ITER, sizeof(double));
+        st.inner_iters += (int64_t)iters;
         ctx->sync();
     } catch (...) {
         delete S;

@@ -217,16 +217,15 @@ __global__ void k_quad(int64_t m, const int32_t *eu, const int32_t *ev, const do
         last = atomicAdd(counter, 1u) == gridDim.x - 1;
     }
     __syncthreads();
-    if (last && threadIdx.x == 0) {
+    if (last && threadIdx.x < 64) {
+        // warp 0 sums qG, warp 1 qS: strided lanes, then a fixed xor tree
         __threadfence();
-        double a = 0.0, b = 0.0;
-        for (unsigned k = 0; k < gridDim.x; ++k) {
-            a += partials[2 * k];
-            b += partials[2 * k + 1];
-        }
-        out[0] = a;
-        out[1] = b;
-        *counter = 0u;
+        const int lane = threadIdx.x & 31, which = threadIdx.x >> 5;
+        double a = 0.0;
+        for (unsigned k = lane; k < gridDim.x; k += 32) a += partials[2 * k + which];
+        for (int d = 16; d > 0; d >>= 1) a += __shfl_xor_sync(0xffffffffu, a, d);
+        if (lane == 0) out[which] = a;
+        if (threadIdx.x == 0) *counter = 0u;
     }
 }
 

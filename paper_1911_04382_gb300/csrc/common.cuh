@@ -5,6 +5,7 @@
 
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <cstring>
 #include <string>
@@ -74,6 +75,7 @@ enum ScratchSlot {
 
 // device scalar area layout (doubles)
 enum {
+    DS_ITER = 40,        // inside DS_RED: inner-CG iteration accumulator
     DS_RED = 0,          // 64 doubles: reduction outputs (PCG scalars)
     DS_CG = 64,          // 12 x 32 doubles: per-column CG scalars
     DS_MAX = 448,        // 16 x uint64: max-abs bit patterns
@@ -97,12 +99,25 @@ struct grass_ctx_s {
     grass::DBuf<unsigned int> gbar;
     long long wait_budget = 1LL << 24;
     int num_sms = 0;
+    // launch-shape knobs (grass_ctx_set_param)
+    int tree_bpsm = 1;
+    int tree_threads = 1024;
+    int64_t tree_tail_items = 4096;
     // kernel-family timing (grass_kernel_timing_*)
     int tfam = 0;
     std::vector<cudaEvent_t> events;
     size_t ev_used = 0;
     int64_t t_launches = 0;
     double t_bytes = 0.0;
+
+    // launches whose bytes scale with a device-side iteration count: bytes =
+    // fixed + per_iter * (counter after - counter before)
+    struct IterLaunch {
+        double fixed, per_iter;
+        size_t slot;
+    };
+    std::vector<IterLaunch> iter_launches;
+    grass::DBuf<double> iter_snap;      // [2 * launches] counter before / after
 
     bool t_begin(int fam, double bytes) {
         if (fam == 0 || fam != tfam) return false;
@@ -115,6 +130,21 @@ struct grass_ctx_s {
         t_bytes += bytes;
         t_launches += 1;
         return true;
+    }
+    // snapshot of a device double counter into slot 2k (+1 for "after")
+    void t_snap(const double *counter, size_t k, int after) {
+        if (iter_snap.n < 2 * (k + 1)) {
+            grass::DBuf<double> nb;
+            nb.alloc(std::max<size_t>(64, 4 * (k + 1)));
+            if (iter_snap.p)
+                GCK(cudaMemcpyAsync(nb.p, iter_snap.p, iter_snap.n * sizeof(double),
+                                    cudaMemcpyDeviceToDevice, stream));
+            GCK(cudaStreamSynchronize(stream));
+            std::swap(nb.p, iter_snap.p);
+            std::swap(nb.n, iter_snap.n);
+        }
+        GCK(cudaMemcpyAsync(iter_snap.p + 2 * k + after, counter, sizeof(double),
+                            cudaMemcpyDeviceToDevice, stream));
     }
     void t_end(bool timed) {
         if (!timed) return;
@@ -157,6 +187,12 @@ inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 constexpr int kBlock = 256;
 constexpr int kRedBlocks = 608;     // 4 x 152 SMs: fixed grid for deterministic reductions
+// Contraction rounds are O(log n) in practice (23 for a million-vertex
+// spanning tree); solves keep the per-round offsets in shared memory.
+constexpr int kMaxRounds = 512;
+// shared memory for the tail of a tree solve (vertices x columns x element)
+constexpr size_t kTailSmem = 160 * 1024;
+constexpr int kPersistMaxThreads = 1024;
 
 // ---------------------------------------------------------------- block layout
 // An n x R row-major block is processed by TPR consecutive threads per row,
@@ -202,12 +238,21 @@ struct GraphData {
     DBuf<double> degG;                // [n] weighted degree (Laplacian diagonal)
 };
 
+struct alignas(32) Dbl4 {
+    double x, y, z, w;
+};
+
 // Elimination schedule of the spanning tree by rake (degree 1) and compress
 // (degree 2) rounds; numeric factors for L_T (lap) and L_T + D (sdd).
 struct TreeFactor {
     DBuf<double> invd64, b1_64, b2_64, cm64, fill64;
     DBuf<float> invd32, b1_32, b2_32, cm32;
     double root_invd = 0.0;
+    // packed per-item coefficients matching fwd_rec / bwd_rec
+    DBuf<double2> fm64;               // [n_rcv] multipliers of the first two contributions
+    DBuf<float2> fm32;
+    DBuf<Dbl4> bc64;                  // [n-1] {1/d, w1/d, w2/d, 0} by elimination position
+    DBuf<float4> bc32;
 };
 
 struct TreeSchedule {
@@ -223,6 +268,18 @@ struct TreeSchedule {
     DBuf<uint8_t> contrib_side;      // 0: receiver is n1 of v, 1: n2
     int64_t n_rcv = 0, n_contrib = 0;
     DBuf<int64_t> d_offs;            // device copy: rcv_off then elim_off
+    // packed records, one load per item:
+    DBuf<int4> fwd_rec;              // [n_rcv] {u, v0, v1 (-1), index of 3rd contribution (-1)}
+    DBuf<int4> bwd_rec;              // [n-1] by elimination position {v, n1, n2 (-1), 0}
+    // shared-memory tail: the vertices alive at round tail_k0 get local ids
+    // 0..tail_n-1 in elimination order (rho last); records with local ids.
+    int tail_k0 = 0;
+    int64_t tail_n = 0;
+    int64_t tail_c0 = 0;             // first contribution index of round tail_k0
+    DBuf<int32_t> tail_vid;          // [tail_n] global id of each local id
+    DBuf<int4> fwd_loc;              // [n_rcv - rcv_off[tail_k0]]
+    DBuf<int4> bwd_loc;              // [n-1 - elim_off[tail_k0]]
+    DBuf<int32_t> contrib_loc;       // local id of contributors from round tail_k0 on
 };
 
 }  // namespace grass
@@ -334,38 +391,55 @@ int64_t filter_heat(grass_ctx_t ctx, grass_sparsifier_t S, const void *heat, gra
 // as soon as another block has flagged an error, the block sets *err and
 // leaves; the caller returns from the kernel, so a lost block can never hang
 // the GPU.  All threads of a block get the same answer.
-// bar[2] != 0 (testing only) makes every barrier wait for one more block
-// than the grid has, so every wait runs out.
-__device__ inline bool grid_sync(unsigned int *bar, long long budget, int *err) {
+// bar[0] only grows within a launch (the host zeroes it before each launch):
+// barrier number b is complete once bar[0] >= (b+1) * gridDim.x, so a block
+// needs one release-add and acquire polls, with no reset round trip.
+// bar[2] != 0 (testing only) raises every target by one arrival that never
+// comes, so every wait runs out.
+__device__ inline unsigned int ld_acquire_u32(const unsigned int *p) {
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ inline unsigned int atom_add_release_u32(unsigned int *p, unsigned int v) {
+    unsigned int old;
+    asm volatile("atom.add.release.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
+__device__ inline void red_add_release_u32(unsigned int *p, unsigned int v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// `epoch` counts the barriers this block has passed in the launch (all
+// blocks pass the same barriers, so barrier b completes when the counter
+// reaches (b+1) * gridDim.x).  The arrival is a one-way reduction: no round
+// trip before polling starts.
+__device__ inline bool grid_sync(unsigned int *bar, long long budget, int *err,
+                                 unsigned int &epoch) {
     __shared__ int s_ok;
     __syncthreads();
+    ++epoch;
     if (threadIdx.x == 0) {
         int ok = 1;
-        volatile unsigned int *vgen = bar + 1;
-        unsigned int g = *vgen;
-        const unsigned int need = gridDim.x + (((volatile unsigned int *)bar)[2] ? 1u : 0u);
-        __threadfence();
-        unsigned int arrived = atomicAdd(bar, 1u);
-        if (arrived == need - 1) {
-            atomicExch(bar, 0u);
-            __threadfence();
-            atomicAdd(bar + 1, 1u);
-        } else {
-            long long spins = 0;
-            while (*vgen == g) {
-                if (*(volatile int *)err) {
-                    ok = 0;
-                    break;
-                }
-                if (++spins > budget) {
-                    atomicOr(err, 1);
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(64);
+        const unsigned int hold = ((volatile unsigned int *)bar)[2] ? 1u : 0u;
+        __threadfence();   // the block's writes (ordered by __syncthreads) before the arrival
+        red_add_release_u32(bar, 1u);
+        const unsigned int target = epoch * gridDim.x + hold;
+        long long spins = 0;
+        while (ld_acquire_u32(bar) < target) {
+            if (*(volatile int *)err) {
+                ok = 0;
+                break;
             }
+            if (++spins > budget) {
+                atomicOr(err, 1);
+                ok = 0;
+                break;
+            }
+            __nanosleep(32);
         }
-        __threadfence();
         s_ok = ok;
     }
     __syncthreads();

@@ -2,7 +2,7 @@
 // r columns) and the PCG solver of A = L_G + D (Sec. V-A).
 #include <cmath>
 
-#include "common.cuh"
+#include "tree_solve.cuh"
 
 namespace grass {
 
@@ -90,6 +90,333 @@ __global__ void k_zero(int64_t total, T *X) {
 
 static size_t esize(grass_prec p) { return p == GRASS_FP64 ? 8 : 4; }
 
+// ---------------------------------------------------------------- fused CG
+// The whole r-column CG on L_S (+D) with the tree preconditioner in one
+// cooperative kernel: the same iteration as the multi-kernel version below,
+// with every dot product reduced by every block from per-block partials in
+// one fixed order (so all blocks hold identical scalars and agree on when to
+// stop), and grid barriers between the phases.
+
+template <typename T>
+struct CGArgs {
+    int64_t n;
+    const int32_t *sptr, *scol;
+    const T *sw, *D;
+    const T *Y;
+    T *X, *Rv, *Z, *P, *Q;
+    double tol;
+    int maxit;
+    double *part;                // [2][gridDim.x][32]
+    double *iter_acc;            // += max over columns of the iterations
+    unsigned long long *maxbits; // optional max |X|
+};
+
+// Per-block column sums of the thread partials v[e] (column c*EPT + e),
+// written to out[0..R): lanes sharing c fold together (xor offsets >= TPR),
+// then one thread per column adds the warps in order.
+template <int R>
+__device__ __forceinline__ void block_cols(const double (&v)[Lay<R>::EPT], int c,
+                                           double (*s_red)[32], double *out) {
+    constexpr int TPR = Lay<R>::TPR, EPT = Lay<R>::EPT;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int e = 0; e < EPT; ++e) {
+        double x = v[e];
+        for (int d = 16; d >= TPR; d >>= 1) x += __shfl_xor_sync(0xffffffffu, x, d);
+        if (lane < TPR) s_red[wid][lane * EPT + e] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < R) {
+        double s = 0.0;
+        for (int w = 0; w < nw; ++w) s += s_red[w][threadIdx.x];
+        out[threadIdx.x] = s;
+    }
+    __syncthreads();
+}
+
+// Column sums over all blocks' partials (same order in every block): warp j
+// takes column j, lanes stride over the blocks, fixed xor tree.
+template <int R>
+__device__ inline void grid_cols(const double *part, double *s_out) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (wid < R) {
+        double s = 0.0;
+        for (unsigned b = lane; b < gridDim.x; b += 32) s += part[(int64_t)b * 32 + wid];
+        for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(0xffffffffu, s, d);
+        if (lane == 0) s_out[wid] = s;
+    }
+    __syncthreads();
+}
+
+template <typename T, int R>
+__global__ void __launch_bounds__(kPersistMaxThreads, 1)
+    k_cg_persist(CGArgs<T> g, TreeKArgs<T> tk) {
+    constexpr int TPR = Lay<R>::TPR, EPT = Lay<R>::EPT;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *ys = reinterpret_cast<T *>(smem_raw);
+    __shared__ double s_red[32][32];
+    __shared__ double s_rz[32], s_rr[32], s_yy[32], s_pq[32], s_new[32], s_al[32];
+    __shared__ int s_act[32], s_brk[32], s_it[32], s_nact;
+    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = (int)(gt % TPR);
+    const int64_t slot = gt / TPR, nslots = (int64_t)gridDim.x * blockDim.x / TPR;
+    double *part0 = g.part, *part1 = g.part + (int64_t)gridDim.x * 32;
+    double *mypart0 = part0 + (int64_t)blockIdx.x * 32, *mypart1 = part1 + (int64_t)blockIdx.x * 32;
+    unsigned int epoch = 0;
+    double mx = 0.0, acc0[EPT], acc1[EPT];
+
+    for (int64_t i = slot; i < g.n; i += nslots) {
+#pragma unroll
+        for (int e = 0; e < EPT; ++e) {
+            int64_t k = i * R + c * EPT + e;
+            T y = g.Y[k];
+            g.X[k] = (T)0;
+            g.Rv[k] = y;
+            g.Z[k] = y;
+        }
+    }
+    if (!grid_sync(tk.bar, tk.budget, tk.err, epoch)) return;
+    if (threadIdx.x < R) {
+        s_brk[threadIdx.x] = 0;
+        s_it[threadIdx.x] = 0;
+    }
+    // Iteration `it` starts with Z = M^{-1} R (the only call site of the
+    // tree solve), then P (it = 0: P = Z; else P = Z + beta P), then the
+    // oracle's loop test ||r|| > tol ||y|| per column, the product and the
+    // updates.  After the updates the test is looked at once more, so no
+    // solve is spent when no column goes on.
+    for (int it = 0;; ++it) {
+        if (!tree_solve_dev<T, R>(tk, g.Z, epoch, mx, ys)) return;
+        if (!grid_sync(tk.bar, tk.budget, tk.err, epoch)) return;
+#pragma unroll
+        for (int e = 0; e < EPT; ++e) acc0[e] = acc1[e] = 0.0;
+        for (int64_t i = slot; i < g.n; i += nslots) {
+#pragma unroll
+            for (int e = 0; e < EPT; ++e) {
+                int64_t k = i * R + c * EPT + e;
+                T z = g.Z[k], rr = g.Rv[k];
+                acc0[e] += (double)rr * (double)z;
+                if (it == 0) {
+                    g.P[k] = z;
+                    acc1[e] += (double)rr * (double)rr;
+                }
+            }
+        }
+        block_cols<R>(acc0, c, s_red, mypart0);
+        if (it == 0) block_cols<R>(acc1, c, s_red, mypart1);
+        if (!grid_sync(tk.bar, tk.budget, tk.err, epoch)) return;
+        if (it == 0) {
+            grid_cols<R>(part0, s_rz);
+            grid_cols<R>(part1, s_rr);
+            if (threadIdx.x < R) s_yy[threadIdx.x] = s_rr[threadIdx.x];
+            __syncthreads();
+        } else {
+            grid_cols<R>(part0, s_new);
+            if (threadIdx.x < R) {
+                int j = threadIdx.x;
+                double beta = s_act[j] ? s_new[j] / s_rz[j] : 0.0;
+                if (s_act[j]) s_rz[j] = s_new[j];
+                s_al[j] = beta;
+            }
+            __syncthreads();
+            for (int64_t i = slot; i < g.n; i += nslots) {
+#pragma unroll
+                for (int e = 0; e < EPT; ++e) {
+                    int j = c * EPT + e;
+                    if (!s_act[j]) continue;
+                    int64_t k = i * R + j;
+                    g.P[k] = g.Z[k] + (T)s_al[j] * g.P[k];
+                }
+            }
+            if (!grid_sync(tk.bar, tk.budget, tk.err, epoch)) return;
+        }
+        if (it >= g.maxit) break;
+        // the oracle's loop test, per column: ||r|| > tol ||y||
+        if (threadIdx.x == 0) s_nact = 0;
+        __syncthreads();
+        if (threadIdx.x < R) {
+            int j = threadIdx.x;
+            int a = !s_brk[j] && sqrt(s_rr[j]) > g.tol * sqrt(s_yy[j]);
+            s_act[j] = a;
+            if (a) atomicAdd(&s_nact, 1);
+        }
+        __syncthreads();
+        if (s_nact == 0) break;
+        // Q = L_S P (+D), partial P.Q
+#pragma unroll
+        for (int e = 0; e < EPT; ++e) acc0[e] = 0.0;
+        for (int64_t i = slot; i < g.n; i += nslots) {
+            T p0[EPT], q[EPT];
+#pragma unroll
+            for (int e = 0; e < EPT; ++e) {
+                p0[e] = g.P[i * R + c * EPT + e];
+                q[e] = (T)0;
+            }
+            for (int32_t j = g.sptr[i]; j < g.sptr[i + 1]; ++j) {
+                const T *pq = g.P + (int64_t)g.scol[j] * R + c * EPT;
+                T w = g.sw[j];
+#pragma unroll
+                for (int e = 0; e < EPT; ++e) q[e] += w * (p0[e] - pq[e]);
+            }
+            if (g.D) {
+                T dd = g.D[i];
+#pragma unroll
+                for (int e = 0; e < EPT; ++e) q[e] += dd * p0[e];
+            }
+#pragma unroll
+            for (int e = 0; e < EPT; ++e) {
+                g.Q[i * R + c * EPT + e] = q[e];
+                acc0[e] += (double)p0[e] * (double)q[e];
+            }
+        }
+        block_cols<R>(acc0, c, s_red, mypart0);
+        if (!grid_sync(tk.bar, tk.budget, tk.err, epoch)) return;
+        grid_cols<R>(part0, s_pq);
+        if (threadIdx.x < R) {
+            int j = threadIdx.x;
+            double pq = s_pq[j];
+            if (s_act[j] && !(pq > 0.0)) {
+                s_brk[j] = 1;
+                s_act[j] = 0;
+            }
+            s_al[j] = s_act[j] ? s_rz[j] / pq : 0.0;
+            if (s_act[j]) s_it[j] += 1;
+        }
+        __syncthreads();
+        // X += alpha P, R -= alpha Q, Z = R, partial R.R
+#pragma unroll
+        for (int e = 0; e < EPT; ++e) acc1[e] = 0.0;
+        for (int64_t i = slot; i < g.n; i += nslots) {
+#pragma unroll
+            for (int e = 0; e < EPT; ++e) {
+                int64_t k = i * R + c * EPT + e;
+                T a = (T)s_al[c * EPT + e];
+                T rr = g.Rv[k];
+                if (a != (T)0) {
+                    g.X[k] += a * g.P[k];
+                    rr -= a * g.Q[k];
+                    g.Rv[k] = rr;
+                }
+                g.Z[k] = rr;
+                acc1[e] += (double)rr * (double)rr;
+            }
+        }
+        block_cols<R>(acc1, c, s_red, mypart1);
+        if (!grid_sync(tk.bar, tk.budget, tk.err, epoch)) return;
+        grid_cols<R>(part1, s_rr);
+        // look ahead: another iteration only if some column passes the test
+        if (it + 1 >= g.maxit) break;
+        if (threadIdx.x == 0) s_nact = 0;
+        __syncthreads();
+        if (threadIdx.x < R) {
+            int j = threadIdx.x;
+            if (!s_brk[j] && sqrt(s_rr[j]) > g.tol * sqrt(s_yy[j])) atomicAdd(&s_nact, 1);
+        }
+        __syncthreads();
+        if (s_nact == 0) break;
+    }
+    if (g.maxbits) {
+        double m = 0.0;
+        for (int64_t k = gt; k < g.n * R; k += (int64_t)gridDim.x * blockDim.x)
+            m = fmax(m, fabs((double)g.X[k]));
+        block_atomic_max(g.maxbits, m);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        int mxit = 0;
+        for (int j = 0; j < R; ++j) mxit = max(mxit, s_it[j]);
+        *g.iter_acc += (double)mxit;
+    }
+}
+
+template <typename T, int R>
+static void cg_persistent(grass_ctx_t ctx, grass_sparsifier_t S, bool with_D, const void *Y,
+                          void *X, double tol, int maxit, unsigned long long *maxbits) {
+    grass_tree_t Tr = S->tree;
+    const GraphData &g = Tr->g;
+    const int64_t n = g.n;
+    const TreeFactor &f = with_D ? Tr->sdd : Tr->lap;
+    size_t smem = 0;
+    TreeKArgs<T> tk = tree_kargs<T, R>(ctx, Tr, f, &smem);
+    CGArgs<T> a;
+    a.n = n;
+    a.sptr = S->s_ptr.p;
+    a.scol = S->s_col.p;
+    const size_t total = (size_t)n * R;
+    if constexpr (sizeof(T) == 8) {
+        a.sw = S->s_w64.p;
+        a.D = with_D ? g.D64.p : nullptr;
+    } else {
+        a.sw = S->s_w32.p;
+        a.D = with_D ? g.D32.p : nullptr;
+    }
+    a.Y = (const T *)Y;
+    a.X = (T *)X;
+    a.Rv = ctx->scr<T>(SCR_CG_R, total);
+    a.Z = ctx->scr<T>(SCR_CG_Z, total);
+    a.P = ctx->scr<T>(SCR_CG_P, total);
+    a.Q = ctx->scr<T>(SCR_CG_Q, total);
+    a.tol = tol;
+    a.maxit = maxit;
+    a.part = ctx->partials.p;
+    a.iter_acc = ctx->scal.p + DS_RED + DS_ITER;
+    a.maxbits = maxbits;
+    static int last_threads = -1, last_grid = 0, last_bpsm = -1;
+    static size_t last_smem = ~size_t(0);
+    const int threads = ctx->tree_threads;
+    if (threads != last_threads || smem != last_smem || ctx->tree_bpsm != last_bpsm) {
+        last_grid = coop_grid(ctx, k_cg_persist<T, R>, threads, smem);
+        last_threads = threads;
+        last_smem = smem;
+        last_bpsm = ctx->tree_bpsm;
+    }
+    if ((size_t)last_grid * 32 * 2 > ctx->partials.n) fail(GRASS_ERR_CUDA, "partials buffer too small");
+    GCK(cudaMemsetAsync(tk.bar, 0, sizeof(unsigned int), ctx->stream));
+    // roofline accounting: algorithmic bytes per iteration and of the start
+    const TreeSchedule &TS = Tr->sched;
+    const double s = (double)sizeof(T), nrs = (double)n * R * s;
+    const double tree_b = 4.0 * nrs + TS.n_rcv * (16.0 + 2.0 * s) + (n - 1) * (16.0 + 4.0 * s);
+    const double spmv_b = 4.0 * (n + 1) + S->s_nnz * (4.0 + s) + 2.0 * nrs + (with_D ? n * s : 0.0);
+    const bool timing = ctx->tfam == GRASS_KF_CG;
+    size_t snap = ctx->iter_launches.size();
+    if (timing) {
+        ctx->t_snap(a.iter_acc, snap, 0);
+        ctx->iter_launches.push_back({7.0 * nrs + tree_b, spmv_b + 16.0 * nrs + tree_b, snap});
+    }
+    bool timed = ctx->t_begin(GRASS_KF_CG, 0.0);
+    void *args[] = {&a, &tk};
+    GCK(cudaLaunchCooperativeKernel((const void *)k_cg_persist<T, R>, dim3(last_grid), dim3(threads),
+                                    args, smem, ctx->stream));
+    ctx->launches++;
+    ctx->t_end(timed);
+    if (timing) ctx->t_snap(a.iter_acc, snap, 1);
+}
+
+struct CGCall {
+    grass_ctx_t ctx;
+    grass_sparsifier_t S;
+    bool with_D;
+    grass_prec prec;
+    const void *Y;
+    void *X;
+    double tol;
+    int maxit;
+    unsigned long long *maxbits;
+};
+
+template <int R>
+static void cg_R(const CGCall &c) {
+    if (c.prec == GRASS_FP64)
+        cg_persistent<double, R>(c.ctx, c.S, c.with_D, c.Y, c.X, c.tol, c.maxit, c.maxbits);
+    else
+        cg_persistent<float, R>(c.ctx, c.S, c.with_D, c.Y, c.X, c.tol, c.maxit, c.maxbits);
+}
+
+__global__ void k_acc_iters(int r, const double *cg_it, double *acc) {
+    double m = 0.0;
+    for (int j = 0; j < r; ++j) m = fmax(m, cg_it[j]);
+    *acc += m;
+}
+
 int64_t s_solve(grass_ctx_t ctx, grass_sparsifier_t S, bool with_D, int r, grass_prec prec,
                 const void *Y, void *X, double tol, int maxit, unsigned long long *maxbits) {
     grass_tree_t T = S->tree;
@@ -100,6 +427,11 @@ int64_t s_solve(grass_ctx_t ctx, grass_sparsifier_t S, bool with_D, int r, grass
     if (S->is_tree) {
         copy_d(ctx, X, Y, total * es);
         tree_solve_inplace(ctx, T, f, r, prec, X, maxbits);
+        return 0;
+    }
+    if (ctx->num_sms > 0) {
+        CGCall call{ctx, S, with_D, prec, Y, X, tol, maxit, maxbits};
+        GRASS_DISPATCH_R(r, cg_R, call);
         return 0;
     }
     double *cg = ctx->scal.p + DS_CG;
@@ -153,11 +485,9 @@ int64_t s_solve(grass_ctx_t ctx, grass_sparsifier_t S, bool with_D, int r, grass
                    (const float *)Z, (float *)P);
     }
     if (maxbits) max_abs_bits(ctx, prec, total, X, maxbits);
-    double its[32];
-    d2h(ctx, its, cg + CG_IT * 32, r * sizeof(double));
-    int64_t mx = 0;
-    for (int j = 0; j < r; ++j) mx = std::max<int64_t>(mx, (int64_t)its[j]);
-    return mx;
+    launch(ctx, k_acc_iters, 1, 1, 0, r, (const double *)(cg + CG_IT * 32),
+           ctx->scal.p + DS_RED + DS_ITER);
+    return 0;
 }
 
 // ---------------------------------------------------------------- PCG
@@ -264,6 +594,7 @@ void pcg_solve(grass_ctx_t ctx, grass_sparsifier_t S, const double *b, double *x
     const GraphData &g = S->tree->g;
     const int64_t n = g.n;
     double *sc = ctx->scal.p + DS_RED;
+    memset_d(ctx, ctx->scal.p + DS_RED + DS_ITER, 0, sizeof(double));
     dot_cols(ctx, 1, GRASS_FP64, n, b, b, sc + P_BB);
     double bb = 0;
     d2h(ctx, &bb, sc + P_BB, sizeof(double));
@@ -303,7 +634,9 @@ void pcg_solve(grass_ctx_t ctx, grass_sparsifier_t S, const double *b, double *x
     if (st) {
         st->iters = iters;
         st->refinements = passes;
-        st->inner_iters = inner;
+        double acc = 0.0;
+        d2h(ctx, &acc, ctx->scal.p + DS_RED + DS_ITER, sizeof(double));
+        st->inner_iters = inner + (int64_t)acc;
         st->rel_resid_fp64 = rel;
     }
     if (!(rel <= tol)) fail(GRASS_ERR_NOT_CONVERGED, "PCG stopped at relative residual " + std::to_string(rel));

@@ -181,6 +181,97 @@ __global__ void k_set_i32(int64_t n, int32_t *a, int32_t v) {
     if (i < n) a[i] = v;
 }
 
+// ---------------------------------------------------------------- packed records
+
+__global__ void k_pack_fwd(int64_t nr, const int32_t *rcv, const int32_t *beg, const int32_t *cv,
+                           int4 *rec) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nr) return;
+    int32_t b = beg[i], e = beg[i + 1];
+    rec[i] = make_int4(rcv[i], cv[b], e - b >= 2 ? cv[b + 1] : -1, e - b >= 3 ? b + 2 : -1);
+}
+
+__global__ void k_pack_bwd(int64_t ne, const int32_t *elist, const int32_t *n1, const int32_t *n2,
+                           int4 *rec) {
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= ne) return;
+    int32_t v = elist[p];
+    rec[p] = make_int4(v, n1[v], n2[v], 0);
+}
+
+__global__ void k_tail_map(int64_t ne_tail, int64_t e0, const int32_t *elist, int32_t rho,
+                           int64_t nt, int32_t *locmap, int32_t *tail_vid) {
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < ne_tail) {
+        int32_t v = elist[e0 + p];
+        locmap[v] = (int32_t)p;
+        tail_vid[p] = v;
+    }
+    if (p == 0) {
+        locmap[rho] = (int32_t)(nt - 1);
+        tail_vid[nt - 1] = rho;
+    }
+}
+
+__global__ void k_tail_fwd(int64_t cnt, const int4 *rec, const int32_t *locmap, int4 *out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= cnt) return;
+    int4 r = rec[i];
+    out[i] = make_int4(locmap[r.x], locmap[r.y], r.z >= 0 ? locmap[r.z] : -1, r.w);
+}
+
+__global__ void k_tail_bwd(int64_t cnt, const int4 *rec, const int32_t *locmap, int4 *out) {
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= cnt) return;
+    int4 r = rec[p];
+    out[p] = make_int4(locmap[r.x], locmap[r.y], r.z >= 0 ? locmap[r.z] : -1, 0);
+}
+
+__global__ void k_tail_contrib(int64_t cnt, const int32_t *cv, const int32_t *locmap,
+                               int32_t *out) {
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < cnt) out[c] = locmap[cv[c]];
+}
+
+// Vertices alive at the tail's first round: at most this many (local ids fit
+// the shared-memory stage of the solve for small r).
+constexpr int64_t kTailMax = 49152;
+
+static void tree_pack(grass_ctx_t ctx, grass_tree_t T) {
+    TreeSchedule &S = T->sched;
+    const int64_t n = T->g.n, ne = n - 1;
+    S.fwd_rec.alloc(S.n_rcv);
+    S.bwd_rec.alloc(ne);
+    launch(ctx, k_pack_fwd, cdiv(S.n_rcv, kBlock), kBlock, 0, S.n_rcv,
+           (const int32_t *)S.rcv_list.p, (const int32_t *)S.rcv_beg.p,
+           (const int32_t *)S.contrib_v.p, S.fwd_rec.p);
+    launch(ctx, k_pack_bwd, cdiv(ne, kBlock), kBlock, 0, ne, (const int32_t *)S.elim_list.p,
+           (const int32_t *)S.n1.p, (const int32_t *)S.n2.p, S.bwd_rec.p);
+    int k0 = 0;
+    while (k0 < S.rounds && n - S.elim_off[k0] > kTailMax) ++k0;
+    S.tail_k0 = k0;
+    S.tail_n = n - S.elim_off[k0];
+    const int64_t e0 = S.elim_off[k0], r0 = S.rcv_off[k0];
+    DBuf<int32_t> locmap;
+    locmap.alloc(n);
+    S.tail_vid.alloc(S.tail_n);
+    launch(ctx, k_tail_map, cdiv(std::max<int64_t>(ne - e0, 1), kBlock), kBlock, 0, ne - e0, e0,
+           (const int32_t *)S.elim_list.p, T->ground, S.tail_n, locmap.p, S.tail_vid.p);
+    S.fwd_loc.alloc(S.n_rcv - r0);
+    S.bwd_loc.alloc(ne - e0);
+    launch(ctx, k_tail_fwd, cdiv(S.n_rcv - r0, kBlock), kBlock, 0, S.n_rcv - r0,
+           (const int4 *)S.fwd_rec.p + r0, (const int32_t *)locmap.p, S.fwd_loc.p);
+    launch(ctx, k_tail_bwd, cdiv(ne - e0, kBlock), kBlock, 0, ne - e0,
+           (const int4 *)S.bwd_rec.p + e0, (const int32_t *)locmap.p, S.bwd_loc.p);
+    int32_t c0 = 0;
+    d2h(ctx, &c0, S.rcv_beg.p + r0, sizeof(int32_t));
+    S.tail_c0 = c0;
+    S.contrib_loc.alloc(S.n_contrib - c0);
+    launch(ctx, k_tail_contrib, cdiv(S.n_contrib - c0, kBlock), kBlock, 0, S.n_contrib - c0,
+           (const int32_t *)S.contrib_v.p + c0, (const int32_t *)locmap.p, S.contrib_loc.p);
+    ctx->sync();
+}
+
 void tree_schedule(grass_ctx_t ctx, grass_tree_t T) {
     const GraphData &g = T->g;
     const int64_t n = g.n;
@@ -223,7 +314,7 @@ void tree_schedule(grass_ctx_t ctx, grass_tree_t T) {
     int64_t alive = n, ebase = 0, rbase = 0, cbase = 0;
     int round = 0;
     while (alive > 1) {
-        if (round > 4096) fail(GRASS_ERR_CUDA, "tree contraction did not finish");
+        if (round >= kMaxRounds) fail(GRASS_ERR_CUDA, "tree contraction did not finish");
         launch(ctx, k_classify, cdiv(n, kBlock), kBlock, 0, n, T->ground,
                (const int32_t *)elim_round.p, (const int32_t *)tptr.p, (const int32_t *)tocc.p,
                cls.p);
@@ -261,6 +352,7 @@ void tree_schedule(grass_ctx_t ctx, grass_tree_t T) {
     }
     S.d_offs.alloc(h.size());
     h2d(ctx, S.d_offs.p, h.data(), h.size() * sizeof(int64_t));
+    tree_pack(ctx, T);
 }
 
 // ---------------------------------------------------------------- numeric factorization
@@ -321,6 +413,26 @@ __global__ void k_to_f32(int64_t cnt, const double *a, float *b) {
     if (i < cnt) b[i] = (float)a[i];
 }
 
+__global__ void k_pack_fm(int64_t nr, const int32_t *beg, const double *cm, double2 *f64,
+                          float2 *f32) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nr) return;
+    int32_t b = beg[i], e = beg[i + 1];
+    double m0 = cm[b], m1 = e - b >= 2 ? cm[b + 1] : 0.0;
+    f64[i] = make_double2(m0, m1);
+    f32[i] = make_float2((float)m0, (float)m1);
+}
+
+__global__ void k_pack_bc(int64_t ne, const int32_t *elist, const double *invd, const double *b1,
+                          const double *b2, Dbl4 *c64, float4 *c32) {
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= ne) return;
+    int32_t v = elist[p];
+    Dbl4 d{invd[v], b1[v], b2[v], 0.0};
+    c64[p] = d;
+    c32[p] = make_float4((float)d.x, (float)d.y, (float)d.z, 0.f);
+}
+
 void tree_factor(grass_ctx_t ctx, grass_tree_t T, bool with_D, TreeFactor &f) {
     const GraphData &g = T->g;
     const TreeSchedule &S = T->sched;
@@ -363,284 +475,16 @@ void tree_factor(grass_ctx_t ctx, grass_tree_t T, bool with_D, TreeFactor &f) {
     launch(ctx, k_to_f32, cdiv(n, kBlock), kBlock, 0, n, (const double *)f.b2_64.p, f.b2_32.p);
     launch(ctx, k_to_f32, cdiv(S.n_contrib, kBlock), kBlock, 0, S.n_contrib,
            (const double *)f.cm64.p, f.cm32.p);
+    f.fm64.alloc(S.n_rcv);
+    f.fm32.alloc(S.n_rcv);
+    f.bc64.alloc(n - 1);
+    f.bc32.alloc(n - 1);
+    launch(ctx, k_pack_fm, cdiv(S.n_rcv, kBlock), kBlock, 0, S.n_rcv, (const int32_t *)S.rcv_beg.p,
+           (const double *)f.cm64.p, f.fm64.p, f.fm32.p);
+    launch(ctx, k_pack_bc, cdiv(n - 1, kBlock), kBlock, 0, n - 1, (const int32_t *)S.elim_list.p,
+           (const double *)f.invd64.p, (const double *)f.b1_64.p, (const double *)f.b2_64.p,
+           f.bc64.p, f.bc32.p);
     d2h(ctx, &f.root_invd, dout, sizeof(double));
-}
-
-// ---------------------------------------------------------------- solves
-
-__device__ inline void atomic_max_abs(unsigned long long *maxbits, double v) {
-    // warp max first, one atomic per warp; |v| >= 0 orders like its bits
-    v = fabs(v);
-    for (int d = 16; d > 0; d >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, d));
-    if ((threadIdx.x & 31) == 0 && v > 0.0)
-        atomicMax(maxbits, (unsigned long long)__double_as_longlong(v));
-}
-
-template <typename T, int R>
-__device__ inline void fwd_item(int64_t i, int c, const int32_t *rcv, const int32_t *beg,
-                                const int32_t *cv, const T *cm, T *Y) {
-    constexpr int EPT = Lay<R>::EPT;
-    int32_t u = rcv[i];
-    T *yu = Y + (int64_t)u * R + c * EPT;
-    T acc[EPT];
-#pragma unroll
-    for (int e = 0; e < EPT; ++e) acc[e] = yu[e];
-    int32_t k1 = beg[i + 1];
-    for (int32_t k = beg[i]; k < k1; ++k) {
-        const T *yv = Y + (int64_t)cv[k] * R + c * EPT;
-        T mlt = cm[k];
-#pragma unroll
-        for (int e = 0; e < EPT; ++e) acc[e] += mlt * yv[e];
-    }
-#pragma unroll
-    for (int e = 0; e < EPT; ++e) yu[e] = acc[e];
-}
-
-template <typename T, int R>
-__device__ inline double bwd_item(int32_t v, int c, const int32_t *n1, const int32_t *n2,
-                                  const T *invd, const T *b1, const T *b2, T *Y) {
-    constexpr int EPT = Lay<R>::EPT;
-    T *yv = Y + (int64_t)v * R + c * EPT;
-    int32_t a = n1[v], b = n2[v];
-    T id = invd[v], c1 = b1[v];
-    const T *xa = Y + (int64_t)a * R + c * EPT;
-    T x[EPT];
-#pragma unroll
-    for (int e = 0; e < EPT; ++e) x[e] = id * yv[e] + c1 * xa[e];
-    if (b >= 0) {
-        T c2 = b2[v];
-        const T *xb = Y + (int64_t)b * R + c * EPT;
-#pragma unroll
-        for (int e = 0; e < EPT; ++e) x[e] += c2 * xb[e];
-    }
-    double mx = 0.0;
-#pragma unroll
-    for (int e = 0; e < EPT; ++e) {
-        yv[e] = x[e];
-        mx = fmax(mx, fabs((double)x[e]));
-    }
-    return mx;
-}
-
-template <typename T, int R>
-__global__ void k_fwd_round(int64_t cnt, const int32_t *rcv, const int32_t *beg, const int32_t *cv,
-                            const T *cm, T *Y) {
-    constexpr int TPR = Lay<R>::TPR;
-    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int64_t i = t / TPR;
-    if (i >= cnt) return;
-    fwd_item<T, R>(i, (int)(t % TPR), rcv, beg, cv, cm, Y);
-}
-
-template <typename T, int R>
-__global__ void k_bwd_round(int64_t cnt, const int32_t *elist, const int32_t *n1,
-                            const int32_t *n2, const T *invd, const T *b1, const T *b2, T *Y,
-                            unsigned long long *maxbits) {
-    constexpr int TPR = Lay<R>::TPR;
-    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int64_t i = t / TPR;
-    double mx = 0.0;
-    if (i < cnt) mx = bwd_item<T, R>(elist[i], (int)(t % TPR), n1, n2, invd, b1, b2, Y);
-    if (maxbits) atomic_max_abs(maxbits, mx);
-}
-
-// The last rounds are small: one block runs them all, forward, the root and
-// backward, with block barriers between rounds instead of kernel launches.
-template <typename T, int R>
-__global__ void k_tail(int k0, int rounds, const int64_t *rcv_off, const int64_t *elim_off,
-                       const int32_t *rcv, const int32_t *beg, const int32_t *cv, const T *cm,
-                       const int32_t *elist, const int32_t *n1, const int32_t *n2, const T *invd,
-                       const T *b1, const T *b2, int32_t rho, T *Y, unsigned long long *maxbits) {
-    constexpr int TPR = Lay<R>::TPR, EPT = Lay<R>::EPT;
-    const int items_per_pass = blockDim.x / TPR;
-    const int c = threadIdx.x % TPR;
-    const int slot = threadIdx.x / TPR;
-    for (int k = k0; k < rounds; ++k) {
-        for (int64_t i = rcv_off[k] + slot; i < rcv_off[k + 1]; i += items_per_pass)
-            fwd_item<T, R>(i, c, rcv, beg, cv, cm, Y);
-        __syncthreads();
-    }
-    double mx = 0.0;
-    if (slot == 0) {
-        T *yr = Y + (int64_t)rho * R + c * EPT;
-        T id = invd[rho];
-#pragma unroll
-        for (int e = 0; e < EPT; ++e) {
-            yr[e] = id * yr[e];
-            mx = fmax(mx, fabs((double)yr[e]));
-        }
-    }
-    __syncthreads();
-    for (int k = rounds - 1; k >= k0; --k) {
-        for (int64_t i = elim_off[k] + slot; i < elim_off[k + 1]; i += items_per_pass)
-            mx = fmax(mx, bwd_item<T, R>(elist[i], c, n1, n2, invd, b1, b2, Y));
-        __syncthreads();
-    }
-    if (maxbits) atomic_max_abs(maxbits, mx);
-}
-
-struct SolveArgs {
-    grass_ctx_t ctx;
-    grass_tree_t T;
-    const TreeFactor *f;
-    void *Y;
-    unsigned long long *maxbits;
-    grass_prec prec;
-};
-
-// Rounds at or after the tail start run inside one block.
-static int tail_start(const TreeSchedule &S) {
-    const int64_t kTailItems = 4096;
-    int k0 = S.rounds;
-    int64_t items = 0;
-    while (k0 > 0) {
-        int k = k0 - 1;
-        int64_t add = (S.rcv_off[k + 1] - S.rcv_off[k]) + (S.elim_off[k + 1] - S.elim_off[k]);
-        if (items + add > kTailItems) break;
-        items += add;
-        k0 = k;
-    }
-    return k0;
-}
-
-// One cooperative launch per solve: the big rounds are separated by grid
-// barriers instead of kernel boundaries, the small last rounds run in
-// block 0 alone (block barriers), then the big rounds again backwards.
-constexpr int kPersistThreads = 256;
-
-template <typename T, int R>
-__global__ void __launch_bounds__(kPersistThreads)
-    k_tree_persist(int rounds, int k0, const int64_t *rcv_off, const int64_t *elim_off,
-                   const int32_t *rcv, const int32_t *beg, const int32_t *cv, const T *cm,
-                   const int32_t *elist, const int32_t *n1, const int32_t *n2, const T *invd,
-                   const T *b1, const T *b2, int32_t rho, T *Y, unsigned long long *maxbits,
-                   unsigned int *bar, long long budget, int *err) {
-    constexpr int TPR = Lay<R>::TPR, EPT = Lay<R>::EPT;
-    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int c = (int)(gt % TPR);
-    const int64_t slot = gt / TPR;
-    const int64_t nslots = (int64_t)gridDim.x * blockDim.x / TPR;
-    for (int k = 0; k < k0; ++k) {
-        const int64_t e = rcv_off[k + 1];
-        for (int64_t i = rcv_off[k] + slot; i < e; i += nslots)
-            fwd_item<T, R>(i, c, rcv, beg, cv, cm, Y);
-        if (!grid_sync(bar, budget, err)) return;
-    }
-    double mx = 0.0;
-    if (blockIdx.x == 0) {
-        const int bslot = threadIdx.x / TPR, bslots = blockDim.x / TPR;
-        for (int k = k0; k < rounds; ++k) {
-            for (int64_t i = rcv_off[k] + bslot; i < rcv_off[k + 1]; i += bslots)
-                fwd_item<T, R>(i, c, rcv, beg, cv, cm, Y);
-            __syncthreads();
-        }
-        if (bslot == 0) {
-            T *yr = Y + (int64_t)rho * R + c * EPT;
-            T id = invd[rho];
-#pragma unroll
-            for (int e = 0; e < EPT; ++e) {
-                yr[e] = id * yr[e];
-                mx = fmax(mx, fabs((double)yr[e]));
-            }
-        }
-        __syncthreads();
-        for (int k = rounds - 1; k >= k0; --k) {
-            for (int64_t i = elim_off[k] + bslot; i < elim_off[k + 1]; i += bslots)
-                mx = fmax(mx, bwd_item<T, R>(elist[i], c, n1, n2, invd, b1, b2, Y));
-            __syncthreads();
-        }
-    }
-    if (k0 > 0 && !grid_sync(bar, budget, err)) return;
-    for (int k = k0 - 1; k >= 0; --k) {
-        const int64_t e = elim_off[k + 1];
-        for (int64_t i = elim_off[k] + slot; i < e; i += nslots)
-            mx = fmax(mx, bwd_item<T, R>(elist[i], c, n1, n2, invd, b1, b2, Y));
-        if (k > 0 && !grid_sync(bar, budget, err)) return;
-    }
-    if (maxbits) block_atomic_max(maxbits, mx);
-}
-
-template <typename T, int R>
-static void solve_persistent(const SolveArgs &a, const T *invd, const T *b1, const T *b2,
-                             const T *cm) {
-    grass_ctx_t ctx = a.ctx;
-    const TreeSchedule &S = a.T->sched;
-    static int blocks_per_sm = -1;   // per instantiation
-    if (blocks_per_sm < 0) {
-        int nb = 0;
-        GCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_tree_persist<T, R>,
-                                                          kPersistThreads, 0));
-        blocks_per_sm = nb;
-    }
-    if (blocks_per_sm < 1) fail(GRASS_ERR_CUDA, "persistent tree solve does not fit on an SM");
-    int grid = ctx->num_sms * std::min(blocks_per_sm, 4);
-    int rounds = S.rounds, k0 = tail_start(S);
-    const int64_t *rcv_off = S.d_offs.p, *elim_off = S.d_offs.p + (S.rounds + 1);
-    const int32_t *rcv = S.rcv_list.p, *beg = S.rcv_beg.p, *cv = S.contrib_v.p;
-    const int32_t *elist = S.elim_list.p, *n1 = S.n1.p, *n2 = S.n2.p;
-    int32_t rho = a.T->ground;
-    T *Y = (T *)a.Y;
-    unsigned long long *maxbits = a.maxbits;
-    unsigned int *bar = ctx->gbar.p;
-    long long budget = ctx->wait_budget;
-    int *err = ctx->flags.p + 3;
-    GCK(cudaMemsetAsync(bar, 0, sizeof(unsigned int), ctx->stream));
-    void *args[] = {&rounds, &k0, &rcv_off, &elim_off, &rcv, &beg, &cv, &cm, &elist, &n1, &n2,
-                    &invd, &b1, &b2, &rho, &Y, &maxbits, &bar, &budget, &err};
-    GCK(cudaLaunchCooperativeKernel((const void *)k_tree_persist<T, R>, dim3(grid),
-                                    dim3(kPersistThreads), args, 0, ctx->stream));
-    ctx->launches++;
-}
-
-template <typename T, int R>
-static void solve_T(const SolveArgs &a, const T *invd, const T *b1, const T *b2, const T *cm) {
-    constexpr int TPR = Lay<R>::TPR;
-    grass_ctx_t ctx = a.ctx;
-    const TreeSchedule &S = a.T->sched;
-    T *Y = (T *)a.Y;
-    if (ctx->num_sms > 0) {
-        solve_persistent<T, R>(a, invd, b1, b2, cm);
-        return;
-    }
-    const int k0 = tail_start(S);
-    for (int k = 0; k < k0; ++k) {
-        int64_t r0 = S.rcv_off[k], cnt = S.rcv_off[k + 1] - r0;
-        launch(ctx, k_fwd_round<T, R>, cdiv(cnt * TPR, kBlock), kBlock, 0, cnt,
-               (const int32_t *)S.rcv_list.p + r0, (const int32_t *)S.rcv_beg.p + r0,
-               (const int32_t *)S.contrib_v.p, cm, Y);
-    }
-    const int64_t *offs = S.d_offs.p;
-    launch(ctx, k_tail<T, R>, 1, 1024, 0, k0, S.rounds, (const int64_t *)offs,
-           (const int64_t *)offs + (S.rounds + 1), (const int32_t *)S.rcv_list.p,
-           (const int32_t *)S.rcv_beg.p, (const int32_t *)S.contrib_v.p, cm,
-           (const int32_t *)S.elim_list.p, (const int32_t *)S.n1.p, (const int32_t *)S.n2.p,
-           invd, b1, b2, a.T->ground, Y, a.maxbits);
-    for (int k = k0 - 1; k >= 0; --k) {
-        int64_t e0 = S.elim_off[k], cnt = S.elim_off[k + 1] - e0;
-        launch(ctx, k_bwd_round<T, R>, cdiv(cnt * TPR, kBlock), kBlock, 0, cnt,
-               (const int32_t *)S.elim_list.p + e0, (const int32_t *)S.n1.p,
-               (const int32_t *)S.n2.p, invd, b1, b2, Y, a.maxbits);
-    }
-}
-
-template <int R>
-static void solve_R(const SolveArgs &a) {
-    const TreeFactor &f = *a.f;
-    if (a.prec == GRASS_FP64)
-        solve_T<double, R>(a, f.invd64.p, f.b1_64.p, f.b2_64.p, f.cm64.p);
-    else
-        solve_T<float, R>(a, f.invd32.p, f.b1_32.p, f.b2_32.p, f.cm32.p);
-}
-
-void tree_solve_inplace(grass_ctx_t ctx, grass_tree_t T, const TreeFactor &f, int r,
-                        grass_prec prec, void *Y, unsigned long long *maxbits) {
-    SolveArgs a{ctx, T, &f, Y, maxbits, prec};
-    const TreeSchedule &S = T->sched;
-    const double s = prec == GRASS_FP64 ? 8.0 : 4.0, n = (double)T->g.n;
-    const double bytes = 4.0 * n * r * s + S.n_contrib * (4.0 + s) + S.n_rcv * 8.0 + n * (12.0 + 3.0 * s);
-    bool timed = ctx->t_begin(GRASS_KF_TREE, bytes);
-    GRASS_DISPATCH_R(r, solve_R, a);
-    ctx->t_end(timed);
 }
 
 }  // namespace grass

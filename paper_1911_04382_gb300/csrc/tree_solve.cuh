@@ -1,0 +1,408 @@
+// tree_solve.cuh -- device code of the tree solve, shared by the stand-alone
+// solve kernel (solve.cu) and the fused CG kernel (krylov.cu).
+//
+// Forward elimination: round by round, every vertex that receives updates
+// adds m * y_v for each neighbour v eliminated in that round.  Backward
+// substitution: rounds in reverse, x_v = y_v / d_v + (w1/d_v) x_n1 +
+// (w2/d_v) x_n2.  The big first rounds run across the whole grid, separated
+// by bounded grid barriers; the small last rounds run in block 0 on the
+// surviving vertices staged in shared memory.  Each item is one packed
+// 16-byte record plus its coefficients, and every thread loads its first
+// record of the next round before waiting at the barrier.
+#pragma once
+
+#include "common.cuh"
+
+namespace grass {
+
+template <typename T>
+struct PackT;
+template <>
+struct PackT<float> {
+    using V2 = float2;
+    using V4 = float4;
+};
+template <>
+struct PackT<double> {
+    using V2 = double2;
+    using V4 = Dbl4;
+};
+
+template <typename T>
+struct TreeKArgs {
+    int rounds, K1;
+    int64_t base, ntl, r0, e0, c0;
+    const int64_t *rcv_off, *elim_off;
+    const int4 *fwd_rec, *bwd_rec, *fwd_loc, *bwd_loc;
+    const typename PackT<T>::V2 *fm;
+    const typename PackT<T>::V4 *bc;
+    const int32_t *beg, *cv, *tail_vid, *contrib_loc;
+    const T *cm;
+    T root_invd;
+    unsigned int *bar;
+    long long budget;
+    int *err;
+};
+
+template <typename T, int R>
+__device__ inline void fwd_packed(int64_t i, int c, int4 r, typename PackT<T>::V2 mm,
+                                  const int32_t *beg, const int32_t *cv, const T *cm, T *Y) {
+    constexpr int EPT = Lay<R>::EPT;
+    T *yu = Y + (int64_t)r.x * R + c * EPT;
+    const T *y0 = Y + (int64_t)r.y * R + c * EPT;
+    T acc[EPT];
+#pragma unroll
+    for (int e = 0; e < EPT; ++e) acc[e] = yu[e] + mm.x * y0[e];
+    if (r.z >= 0) {
+        const T *y1 = Y + (int64_t)r.z * R + c * EPT;
+#pragma unroll
+        for (int e = 0; e < EPT; ++e) acc[e] += mm.y * y1[e];
+    }
+    if (r.w >= 0) {
+        for (int32_t k = r.w; k < beg[i + 1]; ++k) {
+            const T *yv = Y + (int64_t)cv[k] * R + c * EPT;
+            T mlt = cm[k];
+#pragma unroll
+            for (int e = 0; e < EPT; ++e) acc[e] += mlt * yv[e];
+        }
+    }
+#pragma unroll
+    for (int e = 0; e < EPT; ++e) yu[e] = acc[e];
+}
+
+template <typename T, int R>
+__device__ inline double bwd_packed(int c, int4 r, typename PackT<T>::V4 cf, T *Y) {
+    constexpr int EPT = Lay<R>::EPT;
+    T *yv = Y + (int64_t)r.x * R + c * EPT;
+    const T *xa = Y + (int64_t)r.y * R + c * EPT;
+    T x[EPT];
+#pragma unroll
+    for (int e = 0; e < EPT; ++e) x[e] = cf.x * yv[e] + cf.y * xa[e];
+    if (r.z >= 0) {
+        const T *xb = Y + (int64_t)r.z * R + c * EPT;
+#pragma unroll
+        for (int e = 0; e < EPT; ++e) x[e] += cf.z * xb[e];
+    }
+    double mx = 0.0;
+#pragma unroll
+    for (int e = 0; e < EPT; ++e) {
+        yv[e] = x[e];
+        mx = fmax(mx, fabs((double)x[e]));
+    }
+    return mx;
+}
+
+// A thread's items of one round, at most kBatch of them, loaded together so
+// their latencies overlap: item j is index lo + slot + j * nslots.  At 1024
+// threads per block (64 registers) more than one item per batch spills; with
+// 512 threads and 4 items the solve was no faster and the CG phases slower.
+constexpr int kBatch = 1;
+
+template <typename T>
+struct FwdBatch {
+    int4 r[kBatch];
+    typename PackT<T>::V2 m[kBatch];
+    int64_t i0, step;   // item j is i0 + j * step
+    int cnt;
+};
+
+template <typename T>
+struct BwdBatch {
+    int4 r[kBatch];
+    typename PackT<T>::V4 c[kBatch];
+    int cnt;
+};
+
+// loc != nullptr: records with tail-local ids (loc = fwd_loc / bwd_loc,
+// indexed from off0); coefficients always by global index.
+template <typename T>
+__device__ __forceinline__ void load_fwd(FwdBatch<T> &b, const TreeKArgs<T> &a, const int4 *rec,
+                                int64_t off0, int64_t lo, int64_t hi, int64_t slot,
+                                int64_t nslots) {
+    b.cnt = 0;
+    b.i0 = lo + slot;
+    b.step = nslots;
+#pragma unroll
+    for (int j = 0; j < kBatch; ++j) {
+        int64_t i = lo + slot + j * nslots;
+        if (i < hi) {
+            b.r[j] = rec[i - off0];
+            b.m[j] = a.fm[i];
+            b.cnt = j + 1;
+        }
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void load_bwd(BwdBatch<T> &b, const TreeKArgs<T> &a, const int4 *rec,
+                                int64_t off0, int64_t lo, int64_t hi, int64_t slot,
+                                int64_t nslots) {
+    b.cnt = 0;
+#pragma unroll
+    for (int j = 0; j < kBatch; ++j) {
+        int64_t p = lo + slot + j * nslots;
+        if (p < hi) {
+            b.r[j] = rec[p - off0];
+            b.c[j] = a.bc[p];
+            b.cnt = j + 1;
+        }
+    }
+}
+
+// Forward items of a batch on the vector V (global Y, or the tail's shared
+// copy with ids shifted by `base`); all gathers issued before any store.
+template <typename T, int R>
+__device__ __forceinline__ void run_fwd(const FwdBatch<T> &b, const TreeKArgs<T> &a, T *V, int64_t base,
+                               bool local, int c) {
+    constexpr int EPT = Lay<R>::EPT;
+    T yu[kBatch][EPT], y0[kBatch][EPT], y1[kBatch][EPT];
+#pragma unroll
+    for (int j = 0; j < kBatch; ++j) {
+        if (j >= b.cnt) break;
+        const int4 r = b.r[j];
+        const T *pu = V + (r.x - base) * R + c * EPT;
+        const T *p0 = V + (r.y - base) * R + c * EPT;
+#pragma unroll
+        for (int e = 0; e < EPT; ++e) {
+            yu[j][e] = pu[e];
+            y0[j][e] = p0[e];
+            y1[j][e] = (T)0;
+        }
+        if (r.z >= 0) {
+            const T *p1 = V + (r.z - base) * R + c * EPT;
+#pragma unroll
+            for (int e = 0; e < EPT; ++e) y1[j][e] = p1[e];
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < kBatch; ++j) {
+        if (j >= b.cnt) break;
+        const int4 r = b.r[j];
+        const auto mm = b.m[j];
+        T acc[EPT];
+#pragma unroll
+        for (int e = 0; e < EPT; ++e) acc[e] = yu[j][e] + mm.x * y0[j][e];
+        if (r.z >= 0) {
+#pragma unroll
+            for (int e = 0; e < EPT; ++e) acc[e] += mm.y * y1[j][e];
+        }
+        if (r.w >= 0) {
+            const int64_t i = b.i0 + j * b.step;
+            for (int32_t k = r.w; k < a.beg[i + 1]; ++k) {
+                int64_t v = local ? (int64_t)a.contrib_loc[k - a.c0] : (int64_t)a.cv[k];
+                const T *pv = V + (v - base) * R + c * EPT;
+                T mlt = a.cm[k];
+#pragma unroll
+                for (int e = 0; e < EPT; ++e) acc[e] += mlt * pv[e];
+            }
+        }
+        T *pu = V + (r.x - base) * R + c * EPT;
+#pragma unroll
+        for (int e = 0; e < EPT; ++e) pu[e] = acc[e];
+    }
+}
+
+template <typename T, int R>
+__device__ __forceinline__ double run_bwd(const BwdBatch<T> &b, T *V, int64_t base, int c) {
+    constexpr int EPT = Lay<R>::EPT;
+    T yv[kBatch][EPT], xa[kBatch][EPT], xb[kBatch][EPT];
+#pragma unroll
+    for (int j = 0; j < kBatch; ++j) {
+        if (j >= b.cnt) break;
+        const int4 r = b.r[j];
+        const T *pv = V + (r.x - base) * R + c * EPT;
+        const T *pa = V + (r.y - base) * R + c * EPT;
+#pragma unroll
+        for (int e = 0; e < EPT; ++e) {
+            yv[j][e] = pv[e];
+            xa[j][e] = pa[e];
+            xb[j][e] = (T)0;
+        }
+        if (r.z >= 0) {
+            const T *pb = V + (r.z - base) * R + c * EPT;
+#pragma unroll
+            for (int e = 0; e < EPT; ++e) xb[j][e] = pb[e];
+        }
+    }
+    double mx = 0.0;
+#pragma unroll
+    for (int j = 0; j < kBatch; ++j) {
+        if (j >= b.cnt) break;
+        const int4 r = b.r[j];
+        const auto cf = b.c[j];
+        T *pv = V + (r.x - base) * R + c * EPT;
+#pragma unroll
+        for (int e = 0; e < EPT; ++e) {
+            T x = cf.x * yv[j][e] + cf.y * xa[j][e];
+            if (r.z >= 0) x += cf.z * xb[j][e];
+            pv[e] = x;
+            mx = fmax(mx, fabs((double)x));
+        }
+    }
+    return mx;
+}
+
+// Solve in place on Y (n x R).  Called by every thread of a cooperative
+// grid; returns false when a barrier wait ran out (the caller must return).
+// mx accumulates max |x| over the values this thread wrote.  Ends without
+// a trailing grid barrier.
+template <typename T, int R>
+__device__ __forceinline__ bool tree_solve_dev(const TreeKArgs<T> &a, T *Y, unsigned int &epoch,
+                                      double &mx, T *ys) {
+    constexpr int TPR = Lay<R>::TPR;
+    __shared__ int64_t s_roff[kMaxRounds + 1], s_eoff[kMaxRounds + 1];
+    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = (int)(gt % TPR);
+    const int64_t slot = gt / TPR;
+    const int64_t nslots = (int64_t)gridDim.x * blockDim.x / TPR;
+    __syncthreads();
+    for (int k = threadIdx.x; k <= a.rounds; k += blockDim.x) {
+        s_roff[k] = a.rcv_off[k];
+        s_eoff[k] = a.elim_off[k];
+    }
+    __syncthreads();
+    // rounds 0 .. K1-1 forward across the grid; the next round's batch is
+    // loaded before the barrier
+    FwdBatch<T> fb;
+    fb.cnt = 0;
+    if (a.K1 > 0) load_fwd(fb, a, a.fwd_rec, 0, s_roff[0], s_roff[1], slot, nslots);
+    for (int k = 0; k < a.K1; ++k) {
+        run_fwd<T, R>(fb, a, Y, 0, false, c);
+        for (int64_t lo = s_roff[k] + kBatch * nslots; lo < s_roff[k + 1]; lo += kBatch * nslots) {
+            FwdBatch<T> more;
+            load_fwd(more, a, a.fwd_rec, 0, lo, s_roff[k + 1], slot, nslots);
+            run_fwd<T, R>(more, a, Y, 0, false, c);
+        }
+        if (k + 1 < a.K1) load_fwd(fb, a, a.fwd_rec, 0, s_roff[k + 1], s_roff[k + 2], slot, nslots);
+        if (!grid_sync(a.bar, a.budget, a.err, epoch)) return false;
+    }
+    // rounds K1 .. end in block 0, on the tail vertices staged in shared memory
+    if (blockIdx.x == 0) {
+        const int64_t bslot = threadIdx.x / TPR, bslots = blockDim.x / TPR;
+        const int64_t base = a.base, ntl = a.ntl;
+        FwdBatch<T> tb;
+        tb.cnt = 0;
+        if (a.K1 < a.rounds)
+            load_fwd(tb, a, a.fwd_loc, a.r0, s_roff[a.K1], s_roff[a.K1 + 1], bslot, bslots);
+        for (int64_t idx = threadIdx.x; idx < ntl * R; idx += blockDim.x)
+            ys[idx] = Y[(int64_t)a.tail_vid[base + idx / R] * R + idx % R];
+        __syncthreads();
+        for (int k = a.K1; k < a.rounds; ++k) {
+            run_fwd<T, R>(tb, a, ys, base, true, c);
+            for (int64_t lo = s_roff[k] + kBatch * bslots; lo < s_roff[k + 1]; lo += kBatch * bslots) {
+                FwdBatch<T> more;
+                load_fwd(more, a, a.fwd_loc, a.r0, lo, s_roff[k + 1], bslot, bslots);
+                run_fwd<T, R>(more, a, ys, base, true, c);
+            }
+            if (k + 1 < a.rounds)
+                load_fwd(tb, a, a.fwd_loc, a.r0, s_roff[k + 1], s_roff[k + 2], bslot, bslots);
+            __syncthreads();
+        }
+        BwdBatch<T> bb;
+        bb.cnt = 0;
+        if (a.K1 < a.rounds)
+            load_bwd(bb, a, a.bwd_loc, a.e0, s_eoff[a.rounds - 1], s_eoff[a.rounds], bslot, bslots);
+        if (bslot == 0) {
+            constexpr int EPT = Lay<R>::EPT;
+            T *yr = ys + (ntl - 1) * R + c * EPT;   // rho has the last local id
+#pragma unroll
+            for (int e = 0; e < EPT; ++e) yr[e] = a.root_invd * yr[e];
+        }
+        __syncthreads();
+        for (int k = a.rounds - 1; k >= a.K1; --k) {
+            run_bwd<T, R>(bb, ys, base, c);
+            for (int64_t lo = s_eoff[k] + kBatch * bslots; lo < s_eoff[k + 1]; lo += kBatch * bslots) {
+                BwdBatch<T> more;
+                load_bwd(more, a, a.bwd_loc, a.e0, lo, s_eoff[k + 1], bslot, bslots);
+                run_bwd<T, R>(more, ys, base, c);
+            }
+            if (k - 1 >= a.K1)
+                load_bwd(bb, a, a.bwd_loc, a.e0, s_eoff[k - 1], s_eoff[k], bslot, bslots);
+            __syncthreads();
+        }
+        for (int64_t idx = threadIdx.x; idx < ntl * R; idx += blockDim.x) {
+            T v = ys[idx];
+            Y[(int64_t)a.tail_vid[base + idx / R] * R + idx % R] = v;
+            mx = fmax(mx, fabs((double)v));
+        }
+    }
+    // rounds K1-1 .. 0 backward across the grid
+    BwdBatch<T> gb;
+    gb.cnt = 0;
+    if (a.K1 > 0) load_bwd(gb, a, a.bwd_rec, 0, s_eoff[a.K1 - 1], s_eoff[a.K1], slot, nslots);
+    if (a.K1 > 0 && !grid_sync(a.bar, a.budget, a.err, epoch)) return false;
+    for (int k = a.K1 - 1; k >= 0; --k) {
+        mx = fmax(mx, run_bwd<T, R>(gb, Y, 0, c));
+        for (int64_t lo = s_eoff[k] + kBatch * nslots; lo < s_eoff[k + 1]; lo += kBatch * nslots) {
+            BwdBatch<T> more;
+            load_bwd(more, a, a.bwd_rec, 0, lo, s_eoff[k + 1], slot, nslots);
+            mx = fmax(mx, run_bwd<T, R>(more, Y, 0, c));
+        }
+        if (k > 0) {
+            load_bwd(gb, a, a.bwd_rec, 0, s_eoff[k - 1], s_eoff[k], slot, nslots);
+            if (!grid_sync(a.bar, a.budget, a.err, epoch)) return false;
+        }
+    }
+    return true;
+}
+
+// Grid of a cooperative kernel with `threads` threads and `smem` dynamic
+// shared memory: co-resident blocks per SM, capped by tree_blocks_per_sm.
+template <typename K>
+inline int coop_grid(grass_ctx_t ctx, K kernel, int threads, size_t smem) {
+    GCK(cudaFuncSetAttribute((const void *)kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kTailSmem));
+    int nb = 0;
+    GCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, threads, smem));
+    if (nb < 1) fail(GRASS_ERR_CUDA, "cooperative kernel does not fit on an SM");
+    return ctx->num_sms * std::min(nb, ctx->tree_bpsm);
+}
+
+// Host side: the arguments of one solve on tree T with factor f, and the
+// dynamic shared memory its tail needs.
+template <typename T, int R>
+inline TreeKArgs<T> tree_kargs(grass_ctx_t ctx, const grass_tree_s *Tr, const TreeFactor &f,
+                               size_t *smem) {
+    const TreeSchedule &S = Tr->sched;
+    auto alive_at = [&](int k) { return S.tail_n - (S.elim_off[k] - S.elim_off[S.tail_k0]); };
+    int K1 = S.tail_k0;
+    while (K1 < S.rounds && ((size_t)alive_at(K1) * R * sizeof(T) > kTailSmem ||
+                             alive_at(K1) > std::max<int64_t>(ctx->tree_tail_items, 1)))
+        ++K1;
+    const int64_t ntl = alive_at(K1);
+    *smem = (size_t)ntl * R * sizeof(T);
+    TreeKArgs<T> ka;
+    ka.rounds = S.rounds;
+    ka.K1 = K1;
+    ka.base = S.tail_n - ntl;
+    ka.ntl = ntl;
+    ka.r0 = S.rcv_off[S.tail_k0];
+    ka.e0 = S.elim_off[S.tail_k0];
+    ka.c0 = S.tail_c0;
+    ka.rcv_off = S.d_offs.p;
+    ka.elim_off = S.d_offs.p + (S.rounds + 1);
+    ka.fwd_rec = S.fwd_rec.p;
+    ka.bwd_rec = S.bwd_rec.p;
+    ka.fwd_loc = S.fwd_loc.p;
+    ka.bwd_loc = S.bwd_loc.p;
+    if constexpr (sizeof(T) == 8) {
+        ka.fm = f.fm64.p;
+        ka.bc = f.bc64.p;
+        ka.cm = f.cm64.p;
+    } else {
+        ka.fm = f.fm32.p;
+        ka.bc = f.bc32.p;
+        ka.cm = f.cm32.p;
+    }
+    ka.beg = S.rcv_beg.p;
+    ka.cv = S.contrib_v.p;
+    ka.tail_vid = S.tail_vid.p;
+    ka.contrib_loc = S.contrib_loc.p;
+    ka.root_invd = (T)f.root_invd;
+    ka.bar = ctx->gbar.p;
+    ka.budget = ctx->wait_budget;
+    ka.err = ctx->flags.p + 3;
+    return ka;
+}
+
+}  // namespace grass

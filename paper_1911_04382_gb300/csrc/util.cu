@@ -171,24 +171,32 @@ __global__ void k_dot_cols(int64_t total, int r, const T *A, const T *B, double 
         for (int64_t i = g; i < total; i += S) acc += (double)A[i] * (double)B[i];
     sh[threadIdx.x] = acc;
     __syncthreads();
-    if (threadIdx.x < r) {
+    // per-column block sums: warp w reduces columns w, w+8, ...; lane l adds
+    // the block's entries l, l+32, ... of that column, then a fixed xor tree
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int64_t g0 = (int64_t)blockIdx.x * blockDim.x;
+    for (int j = wid; j < r; j += nw) {
         double s = 0.0;
-        for (int k = 0; k < kBlock; ++k) {
-            int64_t gk = (int64_t)blockIdx.x * blockDim.x + k;
-            if (gk < S && (int)(gk % r) == (int)threadIdx.x) s += sh[k];
+        for (int k = lane; k < kBlock; k += 32) {
+            int64_t gk = g0 + k;
+            if (gk < S && (int)(gk % r) == j) s += sh[k];
         }
-        partials[(int64_t)blockIdx.x * 32 + threadIdx.x] = s;
+        for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(0xffffffffu, s, d);
+        if (lane == 0) {
+            partials[(int64_t)j * gridDim.x + blockIdx.x] = s;
+            __threadfence();
+        }
     }
-    __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) last = atomicAdd(counter, 1u) == gridDim.x - 1;
     __syncthreads();
     if (last) {
         __threadfence();
-        if (threadIdx.x < r) {
+        for (int j = wid; j < r; j += nw) {
             double s = 0.0;
-            for (unsigned b = 0; b < gridDim.x; ++b) s += partials[(int64_t)b * 32 + threadIdx.x];
-            out[threadIdx.x] = s;
+            for (unsigned b = lane; b < gridDim.x; b += 32) s += partials[(int64_t)j * gridDim.x + b];
+            for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(0xffffffffu, s, d);
+            if (lane == 0) out[j] = s;
         }
         if (threadIdx.x == 0) *counter = 0u;
     }
