@@ -210,6 +210,31 @@ grass_status grass_tree_edges(grass_ctx_t ctx, grass_tree_t tree, uint8_t *in_tr
 grass_status grass_tree_solve(grass_ctx_t ctx, grass_tree_t tree, int with_D, int r,
                               grass_prec prec, const void *B, void *X);
 
+/* The same solve as grass_tree_solve, same arguments and results, with no
+ * device-memory allocation.  The paper has no counterpart: this entry exists
+ * for callers that cannot let a library allocate once they run (a fixed
+ * device-memory budget already handed to another allocator, or a loop that
+ * must not call cudaMalloc/cudaFree because they synchronise the device).
+ *   Scratch: a 256-byte array compiled into the library (grid-barrier
+ * counter and wait-timeout flag), held by every GPU that loads the library
+ * until the process exits.  Its size does not grow with the tree; the one
+ * limit it sets is that the cooperative grid times the schedule's grid
+ * barriers stays below 2^31 (far above any schedule the library builds);
+ * beyond it the call returns GRASS_ERR_INVALID.
+ *   Set-up: the first call on a device looks up the array's address there
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   Sharing: every call on a device uses the same array, which keeps the
+ * last call's contents; each call zeroes it on ctx's stream before its
+ * kernel.  Calls that overlap on the GPU (other streams, contexts or
+ * threads on the same device) race on it: order them.
+ *   with_D = 1 needs the L_T + D factor, which is built (allocated) by a
+ * first grass_tree_solve with with_D = 1; without it the call returns
+ * GRASS_ERR_INVALID.  The call waits for its kernel (it reads the timeout
+ * flag back): GRASS_ERR_TIMEOUT as for grass_tree_solve.  Other errors:
+ * INVALID for bad arguments, CUDA for a failed launch. */
+grass_status grass_tree_solve_noalloc(grass_ctx_t ctx, grass_tree_t tree, int with_D, int r,
+                                      grass_prec prec, const void *B, void *X);
+
 /* Y = L_G X (graph Laplacian, D excluded; Eq. formula_laplacian).
  * X, Y: device, n x r, must not alias.  1 <= r <= 32. */
 grass_status grass_spmm(grass_ctx_t ctx, grass_tree_t tree, int r, grass_prec prec,

@@ -111,6 +111,7 @@ def lib():
                 "grass_tree_graph": [_vp, _vp, _vp, _vp, _vp, _vp],
                 "grass_tree_edges": [_vp, _vp, _vp],
                 "grass_tree_solve": [_vp, _vp, C.c_int, C.c_int, C.c_int, _vp, _vp],
+                "grass_tree_solve_noalloc": [_vp, _vp, C.c_int, C.c_int, C.c_int, _vp, _vp],
                 "grass_spmm": [_vp, _vp, C.c_int, C.c_int, _vp, _vp],
                 "grass_sparsifier_create": [_vp, _vp, C.POINTER(_vp)],
                 "grass_sparsifier_add": [_vp, _vp, _vp, _i64],
@@ -263,6 +264,13 @@ def grass_tree_edges(ctx, tree, in_tree) -> None:
 def grass_tree_solve(ctx, tree, with_D: int, r: int, prec: int, B, X) -> None:
     _check(ctx, lib().grass_tree_solve(ctx, tree, int(with_D), r, prec, _p(B), _p(X)),
            "grass_tree_solve")
+
+
+def grass_tree_solve_noalloc(ctx, tree, with_D: int, r: int, prec: int, B, X) -> None:
+    """grass_tree_solve without any device allocation (scratch compiled into
+    the library); for callers that must not allocate device memory."""
+    _check(ctx, lib().grass_tree_solve_noalloc(ctx, tree, int(with_D), r, prec, _p(B), _p(X)),
+           "grass_tree_solve_noalloc")
 
 
 def grass_spmm(ctx, tree, r: int, prec: int, X, Y) -> None:
