@@ -321,6 +321,82 @@ grass_status grass_pcg_solve(grass_ctx_t ctx, grass_sparsifier_t S, const double
                              double tol, int maxit, grass_prec prec, double refine_tol,
                              double inner_tol, int inner_maxit, grass_solve_stats_t *stats);
 
+/* ---------------------------------------------------------------- serving */
+
+/* Serving form (no counterpart in the paper, which solves one system at a
+ * time on one core): a request loop that runs whole sparsify-and-solve
+ * requests -- grass_build_tree (ground 0), grass_densify, grass_pcg_solve --
+ * for many callers on one GPU.
+ *   Admission: `slots` worker threads, each with its own context on its own
+ * non-blocking stream.  Requests are taken in arrival order; the oldest
+ * waiting request is admitted as soon as a slot is idle and its footprint
+ * (grass_server_footprint) fits in what the device-memory budget has left,
+ * and the ones behind it wait for it.  A request whose footprint exceeds
+ * the whole budget is refused at submission (OOM).
+ *   State: an admitted request keeps its inputs, tree, sparsifier and
+ * Krylov vectors on the device until it completes, and frees them then.
+ * Requests in flight run concurrently on their slots' streams.
+ *   Results: launch shapes depend on each request alone, so a request's x
+ * and statistics are the same whether it runs alone or among others.
+ * Times are host seconds since the server was created. */
+typedef struct grass_server_s *grass_server_t;
+
+typedef struct {
+    /* host inputs: the caller keeps them alive until grass_server_wait on
+     * the ticket returns */
+    int64_t n, nnz;
+    const int64_t *rowptr;      /* [n+1] full symmetric CSR of L_G + D        */
+    const int32_t *col;         /* [nnz]                                       */
+    const double *val;          /* [nnz]                                       */
+    const double *h0;           /* [max_rounds * n * r] grass_densify's h0     */
+    const double *v0;           /* [max_rounds * n]     grass_densify's v0     */
+    const double *b;            /* [n] right-hand side                         */
+    double *x;                  /* [n] host output, written before completion  */
+    grass_params_t params;      /* densification parameters                    */
+    double tol;                 /* PCG: ||b - A x|| <= tol ||b||              */
+    int maxit;
+    grass_prec pcg_prec;
+    double refine_tol, pcg_inner_tol;
+    int pcg_inner_maxit;
+} grass_request_t;
+
+typedef struct {
+    grass_status status;        /* of the first failing call, else GRASS_OK    */
+    char error[128];            /* its grass_last_error text                   */
+    grass_sparsify_stats_t sparsify;
+    grass_solve_stats_t solve;
+    int64_t footprint_bytes;    /* what admission reserved for it              */
+    double t_submit, t_admit, t_done;   /* seconds since grass_server_create   */
+    double ms_h2d, ms_tree, ms_densify, ms_pcg;   /* phases, host wall time    */
+    int slot;                   /* worker that ran it                          */
+    int in_flight_at_admit;     /* requests running once it was admitted        */
+} grass_result_t;
+
+/* Start `slots` (1..64) workers on CUDA device `device`.  hbm_budget: bytes
+ * of device memory requests may reserve in total (<= 0: 85 % of the memory
+ * free now; capped at the memory free now).  Errors: INVALID, CUDA, OOM. */
+grass_status grass_server_create(int device, int slots, int64_t hbm_budget, grass_server_t *out);
+/* The budget in bytes (-1 for a null server). */
+int64_t grass_server_budget(grass_server_t srv);
+/* Queue a request (copied; its host arrays are read when it is admitted).
+ * *ticket identifies it for grass_server_wait.  Errors: INVALID (bad
+ * request, or the server is stopping), OOM (footprint above the budget). */
+grass_status grass_server_submit(grass_server_t srv, const grass_request_t *req, int64_t *ticket);
+/* Block until the request completes; *out gets its result and the ticket
+ * is released.  Errors: INVALID (unknown ticket). */
+grass_status grass_server_wait(grass_server_t srv, int64_t ticket, grass_result_t *out);
+/* Host snapshot: reserved bytes, requests queued and running, and the most
+ * requests that ran at once so far.  Any pointer may be NULL. */
+grass_status grass_server_stats(grass_server_t srv, int64_t *in_use, int64_t *queued,
+                                int64_t *running, int64_t *max_running);
+/* Wait for every queued and running request, stop the workers, free all. */
+void grass_server_destroy(grass_server_t srv);
+/* Device bytes admission reserves for a request with n rows, nnz stored
+ * entries, r vectors and `rounds` densification rounds: its inputs and an
+ * upper bound of the library's allocations.  Host only (no GPU needed);
+ * -1 for invalid sizes. */
+int64_t grass_server_footprint(int64_t n, int64_t nnz, int r, int rounds);
+
 #ifdef __cplusplus
 }
 #endif

@@ -84,6 +84,23 @@ class grass_solve_stats_t(C.Structure):
                 "ms": self.ms}
 
 
+class grass_request_t(C.Structure):
+    _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("rowptr", C.c_void_p), ("col", C.c_void_p),
+                ("val", C.c_void_p), ("h0", C.c_void_p), ("v0", C.c_void_p), ("b", C.c_void_p),
+                ("x", C.c_void_p), ("params", grass_params_t), ("tol", C.c_double),
+                ("maxit", C.c_int), ("pcg_prec", C.c_int), ("refine_tol", C.c_double),
+                ("pcg_inner_tol", C.c_double), ("pcg_inner_maxit", C.c_int)]
+
+
+class grass_result_t(C.Structure):
+    _fields_ = [("status", C.c_int), ("error", C.c_char * 128),
+                ("sparsify", grass_sparsify_stats_t), ("solve", grass_solve_stats_t),
+                ("footprint_bytes", C.c_int64), ("t_submit", C.c_double), ("t_admit", C.c_double),
+                ("t_done", C.c_double), ("ms_h2d", C.c_double), ("ms_tree", C.c_double),
+                ("ms_densify", C.c_double), ("ms_pcg", C.c_double), ("slot", C.c_int),
+                ("in_flight_at_admit", C.c_int)]
+
+
 _lib = None
 _lock = threading.Lock()
 _vp, _i64, _i32, _d = C.c_void_p, C.c_int64, C.c_int32, C.c_double
@@ -128,12 +145,22 @@ def lib():
                                   C.POINTER(grass_sparsify_stats_t)],
                 "grass_pcg_solve": [_vp, _vp, _vp, _vp, _d, C.c_int, C.c_int, _d, _d, C.c_int,
                                     C.POINTER(grass_solve_stats_t)],
+                "grass_server_create": [C.c_int, C.c_int, _i64, C.POINTER(_vp)],
+                "grass_server_submit": [_vp, C.POINTER(grass_request_t), C.POINTER(_i64)],
+                "grass_server_wait": [_vp, _i64, C.POINTER(grass_result_t)],
+                "grass_server_stats": [_vp, C.POINTER(_i64), C.POINTER(_i64), C.POINTER(_i64),
+                                       C.POINTER(_i64)],
             }
             for name, args in sig.items():
                 f = getattr(L, name)
                 f.argtypes = args
                 f.restype = C.c_int
-            for name in ("grass_ctx_destroy", "grass_tree_destroy", "grass_sparsifier_destroy"):
+            L.grass_server_footprint.argtypes = [_i64, _i64, C.c_int, C.c_int]
+            L.grass_server_footprint.restype = C.c_int64
+            L.grass_server_budget.argtypes = [_vp]
+            L.grass_server_budget.restype = C.c_int64
+            for name in ("grass_ctx_destroy", "grass_tree_destroy", "grass_sparsifier_destroy",
+                         "grass_server_destroy"):
                 getattr(L, name).argtypes = [_vp]
                 getattr(L, name).restype = None
             L.grass_last_error.argtypes = [_vp]
@@ -369,3 +396,90 @@ def grass_pcg_solve(ctx, S, b, x, tol: float, maxit: int, prec: int, refine_tol:
                                           inner_tol, inner_maxit, C.byref(st)),
                "grass_pcg_solve", allow=(GRASS_ERR_NOT_CONVERGED,))
     return s, st
+
+
+# ---------------------------------------------------------------- serving
+
+def grass_server_footprint(n: int, nnz: int, r: int, rounds: int) -> int:
+    return int(lib().grass_server_footprint(n, nnz, r, rounds))
+
+
+def grass_server_create(device: int = 0, slots: int = 4, hbm_budget: int = 0) -> int:
+    out = _vp()
+    _check(None, lib().grass_server_create(device, slots, int(hbm_budget), C.byref(out)),
+           "grass_server_create")
+    return out.value
+
+
+def grass_server_budget(srv) -> int:
+    return int(lib().grass_server_budget(srv))
+
+
+def grass_server_destroy(srv) -> None:
+    lib().grass_server_destroy(srv)
+
+
+def grass_server_stats(srv) -> dict:
+    v = [_i64(0) for _ in range(4)]
+    _check(None, lib().grass_server_stats(srv, *[C.byref(a) for a in v]), "grass_server_stats")
+    return dict(zip(("in_use", "queued", "running", "max_running"), (a.value for a in v)))
+
+
+class Server:
+    """grass_server_* with the host arrays of each request kept alive until
+    its result has been collected (the library reads them on admission)."""
+
+    def __init__(self, device: int = 0, slots: int = 4, hbm_budget: int = 0):
+        self.handle = grass_server_create(device, slots, hbm_budget)
+        self._keep = {}
+        self._mu = threading.Lock()
+
+    def submit(self, rowptr, col, val, h0, v0, b, x, params: grass_params_t, tol: float,
+               maxit: int, pcg_prec: int, refine_tol: float, pcg_inner_tol: float,
+               pcg_inner_maxit: int) -> int:
+        """numpy host arrays: rowptr int64, col int32, val/h0/v0/b/x float64 (x is written)."""
+        arrs = (rowptr, col, val, h0, v0, b, x)
+        q = grass_request_t()
+        q.n, q.nnz = rowptr.shape[0] - 1, col.shape[0]
+        q.rowptr, q.col, q.val, q.h0, q.v0, q.b, q.x = (a.ctypes.data for a in arrs)
+        q.params = params
+        q.tol, q.maxit, q.pcg_prec = tol, maxit, pcg_prec
+        q.refine_tol, q.pcg_inner_tol, q.pcg_inner_maxit = refine_tol, pcg_inner_tol, pcg_inner_maxit
+        t = _i64(0)
+        _check(None, lib().grass_server_submit(self.handle, C.byref(q), C.byref(t)),
+               "grass_server_submit")
+        with self._mu:
+            self._keep[t.value] = arrs
+        return t.value
+
+    def wait(self, ticket: int) -> grass_result_t:
+        res = grass_result_t()
+        _check(None, lib().grass_server_wait(self.handle, ticket, C.byref(res)), "grass_server_wait")
+        with self._mu:
+            self._keep.pop(ticket, None)
+        return res
+
+    def stats(self) -> dict:
+        return grass_server_stats(self.handle)
+
+    def budget(self) -> int:
+        return grass_server_budget(self.handle)
+
+    def close(self) -> None:
+        if self.handle:
+            grass_server_destroy(self.handle)
+            self.handle = None
+
+
+def grass_server_submit(srv, req: grass_request_t) -> int:
+    """Raw submit of a filled grass_request_t (the caller keeps its host
+    arrays alive until grass_server_wait returns); Server.submit does that."""
+    t = _i64(0)
+    _check(None, lib().grass_server_submit(srv, C.byref(req), C.byref(t)), "grass_server_submit")
+    return t.value
+
+
+def grass_server_wait(srv, ticket: int) -> grass_result_t:
+    res = grass_result_t()
+    _check(None, lib().grass_server_wait(srv, ticket, C.byref(res)), "grass_server_wait")
+    return res

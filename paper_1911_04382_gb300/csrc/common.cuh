@@ -103,6 +103,16 @@ struct grass_ctx_s {
     int tree_bpsm = 1;
     int tree_threads = 1024;
     int64_t tree_tail_items = 4096;
+    // co-resident grid of each cooperative kernel shape, per context (no
+    // process-wide state: contexts may run on different host threads)
+    struct CoopEntry {
+        const void *kernel;
+        int threads;
+        size_t smem;
+        int bpsm;
+        int grid;
+    };
+    std::vector<CoopEntry> coop_cache;
     // kernel-family timing (grass_kernel_timing_*)
     int tfam = 0;
     std::vector<cudaEvent_t> events;

@@ -360,16 +360,9 @@ static void cg_persistent(grass_ctx_t ctx, grass_sparsifier_t S, bool with_D, co
     a.part = ctx->partials.p;
     a.iter_acc = ctx->scal.p + DS_RED + DS_ITER;
     a.maxbits = maxbits;
-    static int last_threads = -1, last_grid = 0, last_bpsm = -1;
-    static size_t last_smem = ~size_t(0);
     const int threads = ctx->tree_threads;
-    if (threads != last_threads || smem != last_smem || ctx->tree_bpsm != last_bpsm) {
-        last_grid = coop_grid(ctx, k_cg_persist<T, R>, threads, smem);
-        last_threads = threads;
-        last_smem = smem;
-        last_bpsm = ctx->tree_bpsm;
-    }
-    if ((size_t)last_grid * 32 * 2 > ctx->partials.n) fail(GRASS_ERR_CUDA, "partials buffer too small");
+    const int grid = coop_grid(ctx, k_cg_persist<T, R>, threads, smem, n * Lay<R>::TPR);
+    if ((size_t)grid * 32 * 2 > ctx->partials.n) fail(GRASS_ERR_CUDA, "partials buffer too small");
     GCK(cudaMemsetAsync(tk.bar, 0, sizeof(unsigned int), ctx->stream));
     // roofline accounting: algorithmic bytes per iteration and of the start
     const TreeSchedule &TS = Tr->sched;
@@ -384,7 +377,7 @@ static void cg_persistent(grass_ctx_t ctx, grass_sparsifier_t S, bool with_D, co
     }
     bool timed = ctx->t_begin(GRASS_KF_CG, 0.0);
     void *args[] = {&a, &tk};
-    GCK(cudaLaunchCooperativeKernel((const void *)k_cg_persist<T, R>, dim3(last_grid), dim3(threads),
+    GCK(cudaLaunchCooperativeKernel((const void *)k_cg_persist<T, R>, dim3(grid), dim3(threads),
                                     args, smem, ctx->stream));
     ctx->launches++;
     ctx->t_end(timed);

@@ -68,7 +68,8 @@ void launch_noalloc(const NoallocCall &c) {
     TreeKArgs<T> ka = tree_kargs<T, R>(ctx, c.T, *c.f, &smem);
     ka.bar = c.scratch;
     ka.err = reinterpret_cast<int *>(c.scratch + 8);
-    const int grid = coop_grid(ctx, k_tree_noalloc<T, R>, ctx->tree_threads, smem);
+    const int grid = coop_grid(ctx, k_tree_noalloc<T, R>, ctx->tree_threads, smem,
+                               c.T->g.n * Lay<R>::TPR);
     if ((int64_t)grid * (2 * (int64_t)ka.rounds + 2) >= kMaxArrivals)
         fail(GRASS_ERR_INVALID, "tree schedule too long for the no-allocation barrier counter");
     T *Y = static_cast<T *>(c.Y);

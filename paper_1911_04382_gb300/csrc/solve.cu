@@ -79,18 +79,11 @@ static void solve_T(grass_ctx_t ctx, grass_tree_t Tr, const TreeFactor &f, T *Y,
         solve_rounds<T, R>(ctx, Tr, a, Y, maxbits);
         return;
     }
-    static int last_threads = -1, last_grid = 0, last_bpsm = -1;
-    static size_t last_smem = ~size_t(0);
     const int threads = ctx->tree_threads;
-    if (threads != last_threads || smem != last_smem || ctx->tree_bpsm != last_bpsm) {
-        last_grid = coop_grid(ctx, k_tree_persist<T, R>, threads, smem);
-        last_threads = threads;
-        last_smem = smem;
-        last_bpsm = ctx->tree_bpsm;
-    }
+    const int grid = coop_grid(ctx, k_tree_persist<T, R>, threads, smem, Tr->g.n * Lay<R>::TPR);
     GCK(cudaMemsetAsync(a.bar, 0, sizeof(unsigned int), ctx->stream));
     void *args[] = {&a, &Y, &maxbits};
-    GCK(cudaLaunchCooperativeKernel((const void *)k_tree_persist<T, R>, dim3(last_grid),
+    GCK(cudaLaunchCooperativeKernel((const void *)k_tree_persist<T, R>, dim3(grid),
                                     dim3(threads), args, smem, ctx->stream));
     ctx->launches++;
 }

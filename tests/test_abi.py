@@ -57,3 +57,15 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(B, "_lib", None)
     with pytest.raises(RuntimeError, match="missing"):
         B.lib()
+
+
+def test_server_footprint_is_host_only_and_monotone(libpath):
+    import paper_1911_04382_gb300 as G
+    f = G.grass_server_footprint
+    assert f(0, 10, 8, 1) == -1 and f(10, -1, 8, 1) == -1 and f(10, 10, 0, 1) == -1
+    base = f(10_000, 50_000, 8, 3)
+    # at least the request's own inputs: CSR, h0, v0, b, x
+    n, nnz, r, R = 10_000, 50_000, 8, 3
+    assert base >= 8 * (n + 1) + 12 * nnz + 8 * n * r * R + 8 * n * R + 16 * n
+    assert f(20_000, 50_000, 8, 3) > base and f(10_000, 90_000, 8, 3) > base
+    assert f(10_000, 50_000, 16, 3) > base and f(10_000, 50_000, 8, 4) > base
