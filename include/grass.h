@@ -134,7 +134,9 @@ int64_t grass_launch_count(grass_ctx_t ctx);
 grass_status grass_ctx_set_wait_limit(grass_ctx_t ctx, int64_t polls, int hold_barriers);
 
 /* Launch-shape knobs (no counterpart in the paper), read by the kernels at
- * launch time; results do not depend on them.  Names:
+ * launch time.  Tree-solve results do not depend on them; the fused inner
+ * CG groups its sums by block, so its results can change in the last bits
+ * with the grid these knobs give.  Names:
  *   "tree_blocks_per_sm"  blocks per SM of the cooperative tree solve (1-8)
  *   "tree_threads"        threads per block of that kernel (128-1024, x32)
  *   "tree_tail_items"     rounds at the end whose total work is below this
@@ -320,6 +322,73 @@ grass_status grass_densify(grass_ctx_t ctx, grass_tree_t tree, const grass_param
 grass_status grass_pcg_solve(grass_ctx_t ctx, grass_sparsifier_t S, const double *b, double *x,
                              double tol, int maxit, grass_prec prec, double refine_tol,
                              double inner_tol, int inner_maxit, grass_solve_stats_t *stats);
+
+/* ---------------------------------------------------------------- batching */
+
+/* Batched form (no counterpart in the paper, which handles one graph at a
+ * time): many independent graphs stored as one block-diagonal matrix A (the
+ * union CSR, graph k on rows [seg_off[k], seg_off[k+1]), no entry joining
+ * two graphs).  grass_build_forest extracts every graph, builds the maximum
+ * spanning tree of each (a spanning forest, Sec. III-B) with the graph's
+ * first vertex as its root, and one elimination schedule over the whole
+ * forest (Sec. III-H): every later launch serves all graphs at once.
+ * seg_off: host, nseg+1 entries, seg_off[0] = 0, seg_off[nseg] = n, every
+ * graph >= 2 vertices.  Errors as grass_build_tree; DISCONNECTED when some
+ * graph is; INVALID when an edge joins two graphs.
+ * On a forest, grass_tree_solve solves every graph (each grounded at its
+ * root), grass_spmm and grass_embed work edge by edge (grass_embed's
+ * heat_max is then the maximum over all graphs), and the per-graph calls
+ * are the *_batch ones below; grass_lambda_min/max, grass_filter,
+ * grass_densify and grass_pcg_solve return INVALID. */
+grass_status grass_build_forest(grass_ctx_t ctx, const grass_csr_t *A, int64_t nseg,
+                                const int64_t *seg_off, grass_tree_t *out);
+/* Number of graphs and their vertex and edge-id ranges (host outputs of
+ * nseg+1 entries, any may be NULL).  A tree from grass_build_tree is one
+ * graph. */
+grass_status grass_tree_segments(grass_tree_t tree, int64_t *nseg, int64_t *vtx_off,
+                                 int64_t *edge_off);
+/* One densification round (Sec. IV-D steps 1-5) for every graph of a
+ * forest at once: per graph lambda_min (Eq. courant-fischer-3), lambda_max
+ * (lmax_iters power steps from v0, Rayleigh quotient), the stop test
+ * lambda_max / lambda_min <= sigma^2, theta_sigma (Eq. heatratio_final);
+ * one embedding of r vectors over the whole batch (h0, v0: as
+ * grass_densify, n rows of the union); each graph keeps its off-tree edges
+ * with heat >= theta_k * heat_max_k.  P->max_rounds must be 1 and
+ * P->max_add_per_round <= 0.  stats: aggregate (min lambda_min, max
+ * lambda_max, smallest theta, largest heat_max).  per_graph: host, optional,
+ * 6 doubles per graph: lambda_min, lambda_max, theta (inf: similar, nothing
+ * added), heat_max, edges added, off-tree edges embedded.  Reductions of a
+ * graph run over ranges of its own rows and edges in a fixed order, so its
+ * results do not depend on the other graphs of the batch. */
+grass_status grass_densify_batch(grass_ctx_t ctx, grass_tree_t forest, const grass_params_t *P,
+                                 const double *h0, const double *v0, grass_sparsifier_t *out,
+                                 grass_sparsify_stats_t *stats, double *per_graph);
+/* PCG (Sec. V-A) on every graph of the batch at once, x0 = 0, each graph
+ * with its own scalars, until ||b_k - A_k x_k||_2 <= tol ||b_k||_2 measured
+ * in FP64 for every graph.  Preconditioner M = L_S + D of the graph: the
+ * forest solve, then inner_maxit CG steps on L_S + D preconditioned by it
+ * (flexible outer update).  prec: vectors in FP64 or FP32; dot products and
+ * scalars FP64.  FP64 iterative refinement: after a pass, the graphs whose
+ * FP64 residual r = b - A x still misses tol run another pass on A e = r
+ * (x += e in FP64); stats->refinements counts the passes (at most 8).
+ * One outer iteration is captured into a CUDA graph and replayed when the
+ * context's stream can be captured (not the legacy default stream, kernel
+ * timing off).  b, x: device, n doubles.  stats: iters = most iterations of
+ * any graph, rel_resid_fp64 = largest.  iters_per_graph (int32) and
+ * rel_resid (double): host, nseg entries, optional.  NOT_CONVERGED when
+ * some graph misses tol within maxit iterations (outputs still written). */
+grass_status grass_pcg_solve_batch(grass_ctx_t ctx, grass_sparsifier_t S, const double *b,
+                                   double *x, double tol, int maxit, grass_prec prec,
+                                   int inner_maxit, grass_solve_stats_t *stats,
+                                   int32_t *iters_per_graph, double *rel_resid);
+/* Autotuner (no counterpart in the paper): time the tree (forest) solve of
+ * r columns under each launch shape -- threads per block {256, 512, 1024},
+ * blocks per SM {1, 2, 4}, shared-memory tail {1024, 4096, 16384} items --
+ * and keep the fastest on ctx (as grass_ctx_set_param would).  best: host
+ * [3] = threads, blocks per SM, tail items; best_ms: host, its time per
+ * solve.  Results of every solve are the same under any shape. */
+grass_status grass_autotune(grass_ctx_t ctx, grass_tree_t tree, int r, grass_prec prec,
+                            int64_t *best, double *best_ms);
 
 /* ---------------------------------------------------------------- serving */
 

@@ -145,6 +145,16 @@ def lib():
                                   C.POINTER(grass_sparsify_stats_t)],
                 "grass_pcg_solve": [_vp, _vp, _vp, _vp, _d, C.c_int, C.c_int, _d, _d, C.c_int,
                                     C.POINTER(grass_solve_stats_t)],
+                "grass_build_forest": [_vp, C.POINTER(grass_csr_t), _i64, C.POINTER(_i64),
+                                       C.POINTER(_vp)],
+                "grass_tree_segments": [_vp, C.POINTER(_i64), C.POINTER(_i64), C.POINTER(_i64)],
+                "grass_densify_batch": [_vp, _vp, C.POINTER(grass_params_t), _vp, _vp,
+                                        C.POINTER(_vp), C.POINTER(grass_sparsify_stats_t),
+                                        C.POINTER(_d)],
+                "grass_pcg_solve_batch": [_vp, _vp, _vp, _vp, _d, C.c_int, C.c_int, C.c_int,
+                                          C.POINTER(grass_solve_stats_t), C.POINTER(_i32),
+                                          C.POINTER(_d)],
+                "grass_autotune": [_vp, _vp, C.c_int, C.c_int, C.POINTER(_i64), C.POINTER(_d)],
                 "grass_server_create": [C.c_int, C.c_int, _i64, C.POINTER(_vp)],
                 "grass_server_submit": [_vp, C.POINTER(grass_request_t), C.POINTER(_i64)],
                 "grass_server_wait": [_vp, _i64, C.POINTER(grass_result_t)],
@@ -483,3 +493,58 @@ def grass_server_wait(srv, ticket: int) -> grass_result_t:
     res = grass_result_t()
     _check(None, lib().grass_server_wait(srv, ticket, C.byref(res)), "grass_server_wait")
     return res
+
+
+# ---------------------------------------------------------------- batching
+
+def grass_build_forest(ctx, rowptr, col, val, seg_off) -> int:
+    """Union CSR on the device (as grass_build_tree); seg_off: host sequence
+    of nseg+1 row offsets."""
+    A = grass_csr_t()
+    A.n, A.nnz = int(rowptr.numel() - 1), int(col.numel())
+    A.rowptr, A.col, A.val = _p(rowptr), _p(col), _p(val)
+    off = (_i64 * len(seg_off))(*[int(v) for v in seg_off])
+    out = _vp()
+    _check(ctx, lib().grass_build_forest(ctx, C.byref(A), len(seg_off) - 1, off, C.byref(out)),
+           "grass_build_forest")
+    return out.value
+
+
+def grass_tree_segments(tree) -> tuple[list[int], list[int]]:
+    k = _i64(0)
+    _check(None, lib().grass_tree_segments(tree, C.byref(k), None, None), "grass_tree_segments")
+    v, e = (_i64 * (k.value + 1))(), (_i64 * (k.value + 1))()
+    _check(None, lib().grass_tree_segments(tree, None, v, e), "grass_tree_segments")
+    return list(v), list(e)
+
+
+def grass_densify_batch(ctx, forest, params: grass_params_t, h0, v0, nseg: int):
+    """Returns (sparsifier, grass_sparsify_stats_t, per-graph rows of
+    [lambda_min, lambda_max, theta, heat_max, added, embedded])."""
+    out = _vp()
+    st = grass_sparsify_stats_t()
+    pg = (_d * (6 * nseg))()
+    _check(ctx, lib().grass_densify_batch(ctx, forest, C.byref(params), _p(h0), _p(v0),
+                                          C.byref(out), C.byref(st), pg), "grass_densify_batch")
+    rows = [list(pg[6 * k:6 * k + 6]) for k in range(nseg)]
+    return out.value, st, rows
+
+
+def grass_pcg_solve_batch(ctx, S, b, x, tol: float, maxit: int, prec: int, inner_maxit: int,
+                          nseg: int):
+    """Returns (status, grass_solve_stats_t, iterations per graph, FP64
+    relative residual per graph); NOT_CONVERGED is returned, not raised."""
+    st = grass_solve_stats_t()
+    its = (_i32 * nseg)()
+    res = (_d * nseg)()
+    s = _check(ctx, lib().grass_pcg_solve_batch(ctx, S, _p(b), _p(x), tol, maxit, prec,
+                                                inner_maxit, C.byref(st), its, res),
+               "grass_pcg_solve_batch", allow=(GRASS_ERR_NOT_CONVERGED,))
+    return s, st, list(its), list(res)
+
+
+def grass_autotune(ctx, tree, r: int, prec: int) -> tuple[list[int], float]:
+    best = (_i64 * 3)()
+    ms = _d(0.0)
+    _check(ctx, lib().grass_autotune(ctx, tree, r, prec, best, C.byref(ms)), "grass_autotune")
+    return list(best), ms.value

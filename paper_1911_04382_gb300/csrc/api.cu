@@ -30,7 +30,10 @@ using namespace grass;
     }                                                                    \
     return GRASS_OK;
 
-namespace {
+namespace grass {
+
+// ---------------------------------------------------------------- helpers
+// (shared with the batch entry points of batch.cu)
 
 double now_ms() {
     using namespace std::chrono;
@@ -167,7 +170,44 @@ grass_sparsifier_t new_sparsifier(grass_ctx_t ctx, grass_tree_t T) {
     return S;
 }
 
-}  // namespace
+__global__ void k_mark_roots(int64_t nroots, const int32_t *roots, uint8_t *isroot) {
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < nroots) isroot[roots[q]] = 1;
+}
+
+// Spanning tree (one root) or spanning forest of a batch (one root per graph,
+// the graph's first vertex), its elimination schedule and the L_T factor.
+grass_tree_t build_tree_impl(grass_ctx_t ctx, const grass_csr_t *A,
+                             const std::vector<int64_t> &voff, const std::vector<int32_t> &roots) {
+    auto *T = new grass_tree_s();
+    T->ctx = ctx;
+    T->nroots = (int64_t)roots.size();
+    T->roots_h = roots;
+    T->ground = roots[0];
+    T->g.nseg = (int64_t)roots.size();
+    if (T->g.nseg > 1) T->g.seg_voff = voff;
+    try {
+        graph_extract(ctx, A, T->g);
+        const int64_t n = T->g.n;
+        T->roots.alloc(T->nroots);
+        h2d(ctx, T->roots.p, roots.data(), roots.size() * sizeof(int32_t));
+        T->isroot.alloc(n);
+        memset_d(ctx, T->isroot.p, 0, n);
+        launch(ctx, k_mark_roots, cdiv(T->nroots, kBlock), kBlock, 0, T->nroots,
+               (const int32_t *)T->roots.p, T->isroot.p);
+        T->in_tree.alloc(T->g.m);
+        mst_boruvka(ctx, T->g, T->in_tree.p);
+        tree_schedule(ctx, T);
+        tree_factor(ctx, T, false, T->lap);
+        ctx->sync();
+    } catch (...) {
+        delete T;
+        throw;
+    }
+    return T;
+}
+
+}  // namespace grass
 
 extern "C" {
 
@@ -332,22 +372,36 @@ grass_status grass_build_tree(grass_ctx_t ctx, const grass_csr_t *A, int32_t gro
     need(A && out, "null argument");
     *out = nullptr;
     need(ground >= 0 && ground < A->n, "ground must be in [0, n)");
-    auto *T = new grass_tree_s();
-    T->ctx = ctx;
-    T->ground = ground;
-    try {
-        graph_extract(ctx, A, T->g);
-        T->in_tree.alloc(T->g.m);
-        mst_boruvka(ctx, T->g, T->in_tree.p);
-        tree_schedule(ctx, T);
-        tree_factor(ctx, T, false, T->lap);
-        ctx->sync();
-    } catch (...) {
-        delete T;
-        throw;
-    }
-    *out = T;
+    *out = build_tree_impl(ctx, A, {0, A->n}, {ground});
     API_END
+}
+
+grass_status grass_build_forest(grass_ctx_t ctx, const grass_csr_t *A, int64_t nseg,
+                                const int64_t *seg_off, grass_tree_t *out) {
+    if (!ctx) return GRASS_ERR_INVALID;
+    API_BEGIN(ctx)
+    need(A && out && seg_off, "null argument");
+    *out = nullptr;
+    need(nseg >= 1 && nseg <= (1 << 20), "nseg must be in [1, 2^20]");
+    need(seg_off[0] == 0 && seg_off[nseg] == A->n, "seg_off must start at 0 and end at n");
+    std::vector<int64_t> voff(seg_off, seg_off + nseg + 1);
+    std::vector<int32_t> roots(nseg);
+    for (int64_t k = 0; k < nseg; ++k) {
+        need(voff[k + 1] - voff[k] >= 2, "every graph of the batch needs at least 2 vertices");
+        roots[k] = (int32_t)voff[k];
+    }
+    *out = build_tree_impl(ctx, A, voff, roots);
+    API_END
+}
+
+grass_status grass_tree_segments(grass_tree_t T, int64_t *nseg, int64_t *vtx_off,
+                                 int64_t *edge_off) {
+    if (!T) return GRASS_ERR_INVALID;
+    const GraphData &g = T->g;
+    if (nseg) *nseg = g.nseg;
+    if (vtx_off) std::copy(g.seg_voff.begin(), g.seg_voff.end(), vtx_off);
+    if (edge_off) std::copy(g.seg_eoff.begin(), g.seg_eoff.end(), edge_off);
+    return GRASS_OK;
 }
 
 void grass_tree_destroy(grass_tree_t T) {
@@ -496,6 +550,7 @@ grass_status grass_embed(grass_ctx_t ctx, grass_sparsifier_t S, const double *h0
 grass_status grass_lambda_min(grass_ctx_t ctx, grass_sparsifier_t S, double *lmin) {
     if (!ctx || !S || !lmin) return GRASS_ERR_INVALID;
     API_BEGIN(ctx)
+    need(S->tree->g.nseg == 1, "a batch of graphs: use grass_densify_batch");
     lambda_min(ctx, S, lmin);
     API_END
 }
@@ -504,6 +559,7 @@ grass_status grass_lambda_max(grass_ctx_t ctx, grass_sparsifier_t S, const doubl
                               grass_prec prec, double inner_tol, int inner_maxit, double *lmax) {
     if (!ctx || !S || !lmax) return GRASS_ERR_INVALID;
     API_BEGIN(ctx)
+    need(S->tree->g.nseg == 1, "a batch of graphs: use grass_densify_batch");
     need(v0 != nullptr, "null v0");
     need_prec(prec);
     need(iters >= 0, "iters must be >= 0");
@@ -519,6 +575,7 @@ grass_status grass_filter(grass_ctx_t ctx, grass_sparsifier_t S, const void *hea
                           int64_t *accepted, int64_t *n_accepted, double *theta) {
     if (!ctx || !S || !n_accepted) return GRASS_ERR_INVALID;
     API_BEGIN(ctx)
+    need(S->tree->g.nseg == 1, "a batch of graphs: use grass_densify_batch");
     need(heat || S->m_off == 0, "null heat");
     need(accepted || S->m_off == 0, "null output");
     need_prec(prec);
@@ -547,6 +604,7 @@ grass_status grass_densify(grass_ctx_t ctx, grass_tree_t T, const grass_params_t
     if (!ctx || !T || !P || !out) return GRASS_ERR_INVALID;
     API_BEGIN(ctx)
     *out = nullptr;
+    need(T->g.nseg == 1, "a batch of graphs: use grass_densify_batch");
     need(h0 && v0, "null h0 / v0");
     need(P->sigma2 > 0, "sigma2 must be > 0");
     need(r_supported(P->r), "r must be 1, 2, 4, 8, 16, 24 or 32");
@@ -631,6 +689,7 @@ grass_status grass_pcg_solve(grass_ctx_t ctx, grass_sparsifier_t S, const double
                              double inner_tol, int inner_maxit, grass_solve_stats_t *stats) {
     if (!ctx || !S) return GRASS_ERR_INVALID;
     API_BEGIN(ctx)
+    need(S->tree->g.nseg == 1, "a batch of graphs: use grass_pcg_solve_batch");
     need(b && x, "null b / x");
     need(tol > 0 && maxit >= 0, "tol must be > 0, maxit >= 0");
     need_prec(prec);

@@ -246,6 +246,13 @@ struct GraphData {
     DBuf<double> D64;                 // [n] diagonal load
     DBuf<float> D32;
     DBuf<double> degG;                // [n] weighted degree (Laplacian diagonal)
+    // a batch of independent graphs stored as one block-diagonal matrix:
+    // graph k owns vertices [seg_voff[k], seg_voff[k+1]) and edge ids
+    // [seg_eoff[k], seg_eoff[k+1]); one segment for a single graph
+    int64_t nseg = 1;
+    std::vector<int64_t> seg_voff, seg_eoff;   // host [nseg+1]
+    DBuf<int32_t> seg_of;             // [n] graph of each vertex (nseg > 1 only)
+    DBuf<int64_t> seg_voff_d;         // device copy of seg_voff (nseg > 1 only)
 };
 
 struct alignas(32) Dbl4 {
@@ -257,11 +264,12 @@ struct alignas(32) Dbl4 {
 struct TreeFactor {
     DBuf<double> invd64, b1_64, b2_64, cm64, fill64;
     DBuf<float> invd32, b1_32, b2_32, cm32;
-    double root_invd = 0.0;
+    DBuf<double> rinv64;              // [nroots] 1 / pivot of each root (0: grounded)
+    DBuf<float> rinv32;
     // packed per-item coefficients matching fwd_rec / bwd_rec
     DBuf<double2> fm64;               // [n_rcv] multipliers of the first two contributions
     DBuf<float2> fm32;
-    DBuf<Dbl4> bc64;                  // [n-1] {1/d, w1/d, w2/d, 0} by elimination position
+    DBuf<Dbl4> bc64;                  // [n - nroots] {1/d, w1/d, w2/d, 0} by elimination position
     DBuf<float4> bc32;
 };
 
@@ -269,7 +277,7 @@ struct TreeSchedule {
     int rounds = 0;
     std::vector<int64_t> elim_off;   // host [rounds+1] into elim_list
     std::vector<int64_t> rcv_off;    // host [rounds+1] into rcv_list
-    DBuf<int32_t> elim_list;         // [n-1]
+    DBuf<int32_t> elim_list;         // [n - nroots]
     DBuf<int32_t> n1, n2;            // [n] neighbours at elimination (-1: none)
     DBuf<int32_t> src1, src2;        // [n] weight source: >= 0 tree edge id, < 0: fill of vertex -src-1
     DBuf<int32_t> rcv_list;          // receivers grouped by round
@@ -280,15 +288,16 @@ struct TreeSchedule {
     DBuf<int64_t> d_offs;            // device copy: rcv_off then elim_off
     // packed records, one load per item:
     DBuf<int4> fwd_rec;              // [n_rcv] {u, v0, v1 (-1), index of 3rd contribution (-1)}
-    DBuf<int4> bwd_rec;              // [n-1] by elimination position {v, n1, n2 (-1), 0}
+    DBuf<int4> bwd_rec;              // [n - nroots] by elimination position {v, n1, n2 (-1), 0}
     // shared-memory tail: the vertices alive at round tail_k0 get local ids
-    // 0..tail_n-1 in elimination order (rho last); records with local ids.
+    // 0..tail_n-1 in elimination order (the roots last, in root order);
+    // records with local ids.
     int tail_k0 = 0;
     int64_t tail_n = 0;
     int64_t tail_c0 = 0;             // first contribution index of round tail_k0
     DBuf<int32_t> tail_vid;          // [tail_n] global id of each local id
     DBuf<int4> fwd_loc;              // [n_rcv - rcv_off[tail_k0]]
-    DBuf<int4> bwd_loc;              // [n-1 - elim_off[tail_k0]]
+    DBuf<int4> bwd_loc;              // [n - nroots - elim_off[tail_k0]]
     DBuf<int32_t> contrib_loc;       // local id of contributors from round tail_k0 on
 };
 
@@ -296,7 +305,13 @@ struct TreeSchedule {
 
 struct grass_tree_s {
     grass_ctx_t ctx = nullptr;
-    int32_t ground = 0;
+    int32_t ground = 0;                // roots_h[0]
+    // one root (grounded row) per graph: a spanning tree, or a spanning
+    // forest with one tree per graph of a batch
+    int64_t nroots = 1;
+    std::vector<int32_t> roots_h;
+    grass::DBuf<int32_t> roots;        // [nroots]
+    grass::DBuf<uint8_t> isroot;       // [n]
     grass::GraphData g;
     grass::DBuf<uint8_t> in_tree;     // [m]
     grass::TreeSchedule sched;
@@ -386,6 +401,20 @@ int64_t s_solve(grass_ctx_t ctx, grass_sparsifier_t S, bool with_D, int r, grass
 void pcg_solve(grass_ctx_t ctx, grass_sparsifier_t S, const double *b, double *x, double tol,
                int maxit, grass_prec prec, double refine_tol, double inner_tol, int inner_maxit,
                grass_solve_stats_t *st);
+
+// ---------------------------------------------------------------- api.cu helpers
+
+double now_ms();
+unsigned long long *maxslot(grass_ctx_t ctx, int k);
+double bits_to_double(unsigned long long b);
+void clear_timeout(grass_ctx_t ctx);
+void check_timeout(grass_ctx_t ctx);
+void ensure_sdd(grass_ctx_t ctx, grass_tree_t T);
+int64_t power_steps(grass_ctx_t ctx, grass_sparsifier_t S, const double *h0, int r, int t,
+                    grass_prec prec, double inner_tol, int inner_maxit, void *H, void *Y,
+                    int *scale_slot);
+double theta_sigma(double sigma2, double lmin, double lmax, int t);
+grass_sparsifier_t new_sparsifier(grass_ctx_t ctx, grass_tree_t T);
 
 // ---------------------------------------------------------------- sparsifier ops (filter.cu)
 

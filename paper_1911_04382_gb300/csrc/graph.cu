@@ -111,6 +111,31 @@ __global__ void k_adj(int64_t n, const int64_t *rowptr, const int32_t *col, cons
     }
 }
 
+// graph of every vertex, by binary search over the segment offsets
+__global__ void k_seg_of(int64_t n, int64_t nseg, const int64_t *voff, int32_t *seg_of) {
+    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    int64_t lo = 0, hi = nseg - 1;
+    while (lo < hi) {
+        int64_t mid = (lo + hi + 1) >> 1;
+        if (voff[mid] <= v) lo = mid;
+        else hi = mid - 1;
+    }
+    seg_of[v] = (int32_t)lo;
+}
+
+// a batch is block diagonal: no edge may join two graphs
+__global__ void k_seg_check(int64_t m, const int32_t *eu, const int32_t *ev, const int32_t *seg_of,
+                            int *flags) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < m && seg_of[eu[e]] != seg_of[ev[e]]) atomicOr(flags, 4);
+}
+
+__global__ void k_gather_i64(int64_t cnt, const int64_t *idx, const int64_t *src, int64_t *dst) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < cnt) dst[i] = src[idx[i]];
+}
+
 static void check_flags(grass_ctx_t ctx, const char *stage) {
     int f = 0;
     d2h(ctx, &f, ctx->flags.p, sizeof(int));
@@ -145,7 +170,7 @@ void graph_extract(grass_ctx_t ctx, const grass_csr_t *A, GraphData &g) {
     scan_i64(ctx, ucnt, ebase, n, &m);
     scan_i64(ctx, acnt, aoff, n, &na);
     if (na != 2 * m) fail(GRASS_ERR_INVALID, "off-diagonal pattern is not symmetric");
-    if (m < n - 1) fail(GRASS_ERR_DISCONNECTED, "fewer than n-1 edges");
+    if (m < n - g.nseg) fail(GRASS_ERR_DISCONNECTED, "fewer than n - (number of graphs) edges");
     g.m = m;
     g.eu.alloc(m);
     g.ev.alloc(m);
@@ -163,6 +188,29 @@ void graph_extract(grass_ctx_t ctx, const grass_csr_t *A, GraphData &g) {
            (const int64_t *)aoff, (const int32_t *)entry_eid, g.adj_ptr.p, g.adj_col.p,
            g.adj_eid.p, g.adj_w64.p, g.adj_w32.p, ctx->flags.p);
     check_flags(ctx, "symmetry");
+    if (g.nseg > 1) {
+        // vertex and edge ranges of every graph of the batch
+        const int64_t G = g.nseg;
+        DBuf<int64_t> &voff = g.seg_voff_d;
+        DBuf<int64_t> tmp;
+        voff.alloc(G + 1);
+        tmp.alloc(G + 1);
+        h2d(ctx, voff.p, g.seg_voff.data(), (G + 1) * sizeof(int64_t));
+        g.seg_of.alloc(n);
+        launch(ctx, k_seg_of, cdiv(n, kBlock), kBlock, 0, n, G, (const int64_t *)voff.p, g.seg_of.p);
+        launch(ctx, k_seg_check, cdiv(m, kBlock), kBlock, 0, m, (const int32_t *)g.eu.p,
+               (const int32_t *)g.ev.p, (const int32_t *)g.seg_of.p, ctx->flags.p);
+        int f = 0;
+        d2h(ctx, &f, ctx->flags.p, sizeof(int));
+        if (f & 4) fail(GRASS_ERR_INVALID, "an edge joins two graphs of the batch");
+        launch(ctx, k_gather_i64, cdiv(G + 1, kBlock), kBlock, 0, G + 1, (const int64_t *)voff.p,
+               (const int64_t *)ebase, tmp.p);
+        g.seg_eoff.resize(G + 1);
+        d2h(ctx, g.seg_eoff.data(), tmp.p, (G + 1) * sizeof(int64_t));
+    } else {
+        g.seg_voff = {0, n};
+        g.seg_eoff = {0, m};
+    }
 }
 
 }  // namespace grass

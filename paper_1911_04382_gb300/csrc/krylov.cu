@@ -367,7 +367,8 @@ static void cg_persistent(grass_ctx_t ctx, grass_sparsifier_t S, bool with_D, co
     // roofline accounting: algorithmic bytes per iteration and of the start
     const TreeSchedule &TS = Tr->sched;
     const double s = (double)sizeof(T), nrs = (double)n * R * s;
-    const double tree_b = 4.0 * nrs + TS.n_rcv * (16.0 + 2.0 * s) + (n - 1) * (16.0 + 4.0 * s);
+    const double tree_b = 4.0 * nrs + TS.n_rcv * (16.0 + 2.0 * s) +
+                          (n - (double)Tr->nroots) * (16.0 + 4.0 * s);
     const double spmv_b = 4.0 * (n + 1) + S->s_nnz * (4.0 + s) + 2.0 * nrs + (with_D ? n * s : 0.0);
     const bool timing = ctx->tfam == GRASS_KF_CG;
     size_t snap = ctx->iter_launches.size();

@@ -131,7 +131,7 @@ void mst_boruvka(grass_ctx_t ctx, const GraphData &g, uint8_t *in_tree) {
     launch(ctx, k_iota, cdiv(m, kBlock), kBlock, 0, m, act0.p);
     int32_t *act = act0.p, *act_next = act1.p;
     int64_t na = m, roots = n;
-    for (int round = 0; roots > 1; ++round) {
+    for (int round = 0; roots > g.nseg; ++round) {
         if (round > 64) fail(GRASS_ERR_CUDA, "Boruvka did not converge");
         memset_d(ctx, bw.p, 0, n * sizeof(unsigned long long));
         memset_d(ctx, be.p, 0x7F, n * sizeof(int32_t));     // kNoEdge
@@ -159,10 +159,12 @@ void mst_boruvka(grass_ctx_t ctx, const GraphData &g, uint8_t *in_tree) {
         d2h(ctx, &hooked, nhooked, sizeof(unsigned int));
         if (hooked == 0) {
             fail(GRASS_ERR_DISCONNECTED,
-                 "graph has " + std::to_string(roots) + " connected components");
+                 g.nseg > 1 ? "the batch has " + std::to_string(roots) + " connected components for " +
+                                  std::to_string(g.nseg) + " graphs"
+                            : "graph has " + std::to_string(roots) + " connected components");
         }
         roots -= hooked;
-        if (roots <= 1) break;
+        if (roots <= g.nseg) break;
         launch(ctx, k_bor_flag, cdiv(na, kBlock), kBlock, 0, na, (const int32_t *)act, g.eu.p,
                g.ev.p, (const int32_t *)comp.p, flag.p);
         int64_t kept = 0;

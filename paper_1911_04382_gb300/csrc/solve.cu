@@ -40,11 +40,12 @@ __global__ void k_bwd_round(int64_t e0, int64_t cnt, const int4 *rec,
 }
 
 template <typename T, int R>
-__global__ void k_root(int32_t rho, T root_invd, T *Y, unsigned long long *maxbits) {
+__global__ void k_root(const int32_t *roots, const T *root_invd, T *Y, unsigned long long *maxbits) {
     double mx = 0.0;
+    const int64_t rho = roots[blockIdx.x];   // one block per root
     if (threadIdx.x < R) {
-        T v = root_invd * Y[(int64_t)rho * R + threadIdx.x];
-        Y[(int64_t)rho * R + threadIdx.x] = v;
+        T v = root_invd[blockIdx.x] * Y[rho * R + threadIdx.x];
+        Y[rho * R + threadIdx.x] = v;
         mx = fabs((double)v);
     }
     if (maxbits) block_atomic_max(maxbits, mx);
@@ -60,7 +61,7 @@ static void solve_rounds(grass_ctx_t ctx, grass_tree_t Tr, const TreeKArgs<T> &a
         launch(ctx, k_fwd_round<T, R>, cdiv(cnt * TPR, kBlock), kBlock, 0, r0, cnt, a.fwd_rec, a.fm,
                a.beg, a.cv, a.cm, Y);
     }
-    launch(ctx, k_root<T, R>, 1, 32, 0, Tr->ground, a.root_invd, Y, maxbits);
+    launch(ctx, k_root<T, R>, Tr->nroots, 32, 0, (const int32_t *)Tr->roots.p, a.root_invd, Y, maxbits);
     for (int k = S.rounds - 1; k >= 0; --k) {
         int64_t e0 = S.elim_off[k], cnt = S.elim_off[k + 1] - e0;
         launch(ctx, k_bwd_round<T, R>, cdiv(cnt * TPR, kBlock), kBlock, 0, e0, cnt, a.bwd_rec, a.bc,
@@ -107,7 +108,8 @@ void tree_solve_inplace(grass_ctx_t ctx, grass_tree_t T, const TreeFactor &f, in
                         grass_prec prec, void *Y, unsigned long long *maxbits) {
     const TreeSchedule &S = T->sched;
     const double s = prec == GRASS_FP64 ? 8.0 : 4.0, n = (double)T->g.n;
-    const double bytes = 4.0 * n * r * s + S.n_rcv * (16.0 + 2.0 * s) + (n - 1) * (16.0 + 4.0 * s);
+    const double bytes = 4.0 * n * r * s + S.n_rcv * (16.0 + 2.0 * s) +
+                         (n - (double)T->nroots) * (16.0 + 4.0 * s);
     bool timed = ctx->t_begin(GRASS_KF_TREE, bytes);
     SolveCall c{ctx, T, &f, Y, maxbits, prec};
     GRASS_DISPATCH_R(r, solve_R, c);

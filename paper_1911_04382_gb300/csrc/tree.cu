@@ -9,7 +9,9 @@
 // neighbours get joined by the series edge w1 w2 / d).  Each round is a
 // fixed set of independent eliminations, so the factor is the same
 // Gaussian elimination in another order, with O(log n) rounds.  The
-// grounded row rho is never eliminated; it is what remains at the end.
+// grounded row rho is never eliminated; it is what remains at the end.  A
+// batch of graphs (a spanning forest) has one such root per graph, and the
+// rounds go on until only the roots remain.
 //
 // Pivots are formed without subtraction: with Dp(v) the load collected from
 // already-eliminated neighbours, d_v = Dp(v) + sum of v's current edge
@@ -67,20 +69,28 @@ __global__ void k_tfill(int64_t n, const int32_t *adj_ptr, const int32_t *adj_co
 // ---------------------------------------------------------------- symbolic rounds
 
 // cls: 0 stays, 1 leaf (rake), 2 degree two (compress candidate)
-__global__ void k_classify(int64_t n, int32_t ground, const int32_t *elim_round,
+__global__ void k_classify(int64_t n, const uint8_t *isroot, const int32_t *elim_round,
                            const int32_t *tptr, const int32_t *tocc, uint8_t *cls) {
     int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= n || elim_round[v] >= 0) return;
     int deg = 0;
     for (int32_t s = tptr[v]; s < tptr[v + 1]; ++s) deg += tocc[s] >= 0;
     uint8_t c = 0;
-    if (v != ground) c = deg == 1 ? 1 : (deg == 2 ? 2 : 0);
+    if (!isroot[v]) c = deg == 1 ? 1 : (deg == 2 ? 2 : 0);
     cls[v] = c;
 }
 
+// Vertex id within its own graph: the compress priorities of a graph of a
+// batch are those it has alone, so its elimination order (and rounding) does
+// not depend on where it sits in the batch.
+__device__ inline int32_t local_id(int32_t v, const int32_t *seg_of, const int64_t *voff) {
+    return seg_of ? (int32_t)(v - voff[seg_of[v]]) : v;
+}
+
 __global__ void k_select(int64_t n, int round, const uint8_t *cls, const int32_t *tptr,
-                         const int32_t *tocc, const int32_t *tsrc, int32_t *elim_round,
-                         int32_t *n1, int32_t *n2, int32_t *src1, int32_t *src2) {
+                         const int32_t *tocc, const int32_t *tsrc, const int32_t *seg_of,
+                         const int64_t *voff, int32_t *elim_round, int32_t *n1, int32_t *n2,
+                         int32_t *src1, int32_t *src2) {
     int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= n || elim_round[v] >= 0) return;
     uint8_t c = cls[v];
@@ -109,8 +119,9 @@ __global__ void k_select(int64_t n, int round, const uint8_t *cls, const int32_t
     // compress: v must beat every degree-2 neighbour on a per-round priority.
     uint8_t ca = cls[a], cb = cls[b];
     if (ca == 1 || cb == 1) return;
-    if (ca == 2 && !prio_gt((int32_t)v, a, round)) return;
-    if (cb == 2 && !prio_gt((int32_t)v, b, round)) return;
+    const int32_t lv = local_id((int32_t)v, seg_of, voff);
+    if (ca == 2 && !prio_gt(lv, local_id(a, seg_of, voff), round)) return;
+    if (cb == 2 && !prio_gt(lv, local_id(b, seg_of, voff), round)) return;
     elim_round[v] = round;
     n1[v] = a;
     src1[v] = sa;
@@ -199,17 +210,17 @@ __global__ void k_pack_bwd(int64_t ne, const int32_t *elist, const int32_t *n1, 
     rec[p] = make_int4(v, n1[v], n2[v], 0);
 }
 
-__global__ void k_tail_map(int64_t ne_tail, int64_t e0, const int32_t *elist, int32_t rho,
-                           int64_t nt, int32_t *locmap, int32_t *tail_vid) {
+__global__ void k_tail_map(int64_t ne_tail, int64_t e0, const int32_t *elist, const int32_t *roots,
+                           int64_t nroots, int64_t nt, int32_t *locmap, int32_t *tail_vid) {
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p < ne_tail) {
         int32_t v = elist[e0 + p];
         locmap[v] = (int32_t)p;
         tail_vid[p] = v;
-    }
-    if (p == 0) {
-        locmap[rho] = (int32_t)(nt - 1);
-        tail_vid[nt - 1] = rho;
+    } else if (p < ne_tail + nroots) {
+        int32_t v = roots[p - ne_tail];
+        locmap[v] = (int32_t)(nt - nroots + (p - ne_tail));
+        tail_vid[nt - nroots + (p - ne_tail)] = v;
     }
 }
 
@@ -239,7 +250,7 @@ constexpr int64_t kTailMax = 49152;
 
 static void tree_pack(grass_ctx_t ctx, grass_tree_t T) {
     TreeSchedule &S = T->sched;
-    const int64_t n = T->g.n, ne = n - 1;
+    const int64_t n = T->g.n, ne = n - T->nroots;
     S.fwd_rec.alloc(S.n_rcv);
     S.bwd_rec.alloc(ne);
     launch(ctx, k_pack_fwd, cdiv(S.n_rcv, kBlock), kBlock, 0, S.n_rcv,
@@ -255,8 +266,9 @@ static void tree_pack(grass_ctx_t ctx, grass_tree_t T) {
     DBuf<int32_t> locmap;
     locmap.alloc(n);
     S.tail_vid.alloc(S.tail_n);
-    launch(ctx, k_tail_map, cdiv(std::max<int64_t>(ne - e0, 1), kBlock), kBlock, 0, ne - e0, e0,
-           (const int32_t *)S.elim_list.p, T->ground, S.tail_n, locmap.p, S.tail_vid.p);
+    launch(ctx, k_tail_map, cdiv(ne - e0 + T->nroots, kBlock), kBlock, 0, ne - e0, e0,
+           (const int32_t *)S.elim_list.p, (const int32_t *)T->roots.p, T->nroots, S.tail_n,
+           locmap.p, S.tail_vid.p);
     S.fwd_loc.alloc(S.n_rcv - r0);
     S.bwd_loc.alloc(ne - e0);
     launch(ctx, k_tail_fwd, cdiv(S.n_rcv - r0, kBlock), kBlock, 0, S.n_rcv - r0,
@@ -287,7 +299,7 @@ void tree_schedule(grass_ctx_t ctx, grass_tree_t T) {
            (const uint8_t *)T->in_tree.p, cnt.p);
     int64_t tslots = 0;
     scan_i64(ctx, cnt.p, off.p, n, &tslots);
-    if (tslots != 2 * (n - 1)) fail(GRASS_ERR_CUDA, "tree adjacency size mismatch");
+    if (tslots != 2 * (n - T->nroots)) fail(GRASS_ERR_CUDA, "tree adjacency size mismatch");
     tocc.alloc(tslots);
     tsrc.alloc(tslots);
     launch(ctx, k_tfill, cdiv(n, kBlock), kBlock, 0, n, g.adj_ptr.p, g.adj_col.p, g.adj_eid.p,
@@ -313,14 +325,16 @@ void tree_schedule(grass_ctx_t ctx, grass_tree_t T) {
     S.rcv_off.assign(1, 0);
     int64_t alive = n, ebase = 0, rbase = 0, cbase = 0;
     int round = 0;
-    while (alive > 1) {
+    while (alive > T->nroots) {
         if (round >= kMaxRounds) fail(GRASS_ERR_CUDA, "tree contraction did not finish");
-        launch(ctx, k_classify, cdiv(n, kBlock), kBlock, 0, n, T->ground,
+        launch(ctx, k_classify, cdiv(n, kBlock), kBlock, 0, n, (const uint8_t *)T->isroot.p,
                (const int32_t *)elim_round.p, (const int32_t *)tptr.p, (const int32_t *)tocc.p,
                cls.p);
         launch(ctx, k_select, cdiv(n, kBlock), kBlock, 0, n, round, (const uint8_t *)cls.p,
                (const int32_t *)tptr.p, (const int32_t *)tocc.p, (const int32_t *)tsrc.p,
-               elim_round.p, S.n1.p, S.n2.p, S.src1.p, S.src2.p);
+               g.nseg > 1 ? (const int32_t *)g.seg_of.p : nullptr,
+               g.nseg > 1 ? (const int64_t *)g.seg_voff_d.p : nullptr, elim_round.p, S.n1.p,
+               S.n2.p, S.src1.p, S.src2.p);
         launch(ctx, k_count, cdiv(n, kBlock), kBlock, 0, n, round, (const int32_t *)elim_round.p,
                (const int32_t *)tptr.p, (const int32_t *)tocc.p, val.p);
         U64x2 tot{0, 0};
@@ -398,14 +412,18 @@ __global__ void k_nf_cm(int64_t cnt, const int32_t *cv, const uint8_t *side, con
     cm[k] = side[k] ? b2[v] : b1[v];
 }
 
-__global__ void k_nf_root(int32_t rho, const double *Dp, double *invd, double *b1, double *b2,
-                          double *out) {
+__global__ void k_nf_root(int64_t nroots, const int32_t *roots, const double *Dp, double *invd,
+                          double *b1, double *b2, double *r64, float *r32) {
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nroots) return;
+    const int32_t rho = roots[q];
     double d = Dp[rho];
     double iv = d > 0.0 ? 1.0 / d : 0.0;   // D = 0: grounded, x_rho = 0
     invd[rho] = iv;
     b1[rho] = 0.0;
     b2[rho] = 0.0;
-    *out = iv;
+    r64[q] = iv;
+    r32[q] = (float)iv;
 }
 
 __global__ void k_to_f32(int64_t cnt, const double *a, float *b) {
@@ -460,9 +478,11 @@ void tree_factor(grass_ctx_t ctx, grass_tree_t T, bool with_D, TreeFactor &f) {
                    (const double *)f.b1_64.p, (const double *)f.b2_64.p, Dp.p);
         }
     }
-    double *dout = ctx->scal.p + DS_RED;
-    launch(ctx, k_nf_root, 1, 1, 0, T->ground, (const double *)Dp.p, f.invd64.p, f.b1_64.p,
-           f.b2_64.p, dout);
+    f.rinv64.alloc(T->nroots);
+    f.rinv32.alloc(T->nroots);
+    launch(ctx, k_nf_root, cdiv(T->nroots, kBlock), kBlock, 0, T->nroots,
+           (const int32_t *)T->roots.p, (const double *)Dp.p, f.invd64.p, f.b1_64.p, f.b2_64.p,
+           f.rinv64.p, f.rinv32.p);
     launch(ctx, k_nf_cm, cdiv(S.n_contrib, kBlock), kBlock, 0, S.n_contrib,
            (const int32_t *)S.contrib_v.p, (const uint8_t *)S.contrib_side.p,
            (const double *)f.b1_64.p, (const double *)f.b2_64.p, f.cm64.p);
@@ -477,14 +497,15 @@ void tree_factor(grass_ctx_t ctx, grass_tree_t T, bool with_D, TreeFactor &f) {
            (const double *)f.cm64.p, f.cm32.p);
     f.fm64.alloc(S.n_rcv);
     f.fm32.alloc(S.n_rcv);
-    f.bc64.alloc(n - 1);
-    f.bc32.alloc(n - 1);
+    const int64_t ne = n - T->nroots;
+    f.bc64.alloc(ne);
+    f.bc32.alloc(ne);
     launch(ctx, k_pack_fm, cdiv(S.n_rcv, kBlock), kBlock, 0, S.n_rcv, (const int32_t *)S.rcv_beg.p,
            (const double *)f.cm64.p, f.fm64.p, f.fm32.p);
-    launch(ctx, k_pack_bc, cdiv(n - 1, kBlock), kBlock, 0, n - 1, (const int32_t *)S.elim_list.p,
+    launch(ctx, k_pack_bc, cdiv(ne, kBlock), kBlock, 0, ne, (const int32_t *)S.elim_list.p,
            (const double *)f.invd64.p, (const double *)f.b1_64.p, (const double *)f.b2_64.p,
            f.bc64.p, f.bc32.p);
-    d2h(ctx, &f.root_invd, dout, sizeof(double));
+    ctx->sync();
 }
 
 }  // namespace grass

@@ -38,7 +38,8 @@ struct TreeKArgs {
     const typename PackT<T>::V4 *bc;
     const int32_t *beg, *cv, *tail_vid, *contrib_loc;
     const T *cm;
-    T root_invd;
+    const T *root_invd;   // [nroots], roots in tail order
+    int nroots;
     unsigned int *bar;
     long long budget;
     int *err;
@@ -302,11 +303,12 @@ __device__ __forceinline__ bool tree_solve_dev(const TreeKArgs<T> &a, T *Y, unsi
         bb.cnt = 0;
         if (a.K1 < a.rounds)
             load_bwd(bb, a, a.bwd_loc, a.e0, s_eoff[a.rounds - 1], s_eoff[a.rounds], bslot, bslots);
-        if (bslot == 0) {
+        for (int64_t q = bslot; q < a.nroots; q += bslots) {
             constexpr int EPT = Lay<R>::EPT;
-            T *yr = ys + (ntl - 1) * R + c * EPT;   // rho has the last local id
+            T *yr = ys + (ntl - a.nroots + q) * R + c * EPT;   // the roots come last
+            const T ri = a.root_invd[q];
 #pragma unroll
-            for (int e = 0; e < EPT; ++e) yr[e] = a.root_invd * yr[e];
+            for (int e = 0; e < EPT; ++e) yr[e] = ri * yr[e];
         }
         __syncthreads();
         for (int k = a.rounds - 1; k >= a.K1; --k) {
@@ -411,7 +413,9 @@ inline TreeKArgs<T> tree_kargs(grass_ctx_t ctx, const grass_tree_s *Tr, const Tr
     ka.cv = S.contrib_v.p;
     ka.tail_vid = S.tail_vid.p;
     ka.contrib_loc = S.contrib_loc.p;
-    ka.root_invd = (T)f.root_invd;
+    if constexpr (sizeof(T) == 8) ka.root_invd = f.rinv64.p;
+    else ka.root_invd = f.rinv32.p;
+    ka.nroots = (int)Tr->nroots;
     ka.bar = ctx->gbar.p;
     ka.budget = ctx->wait_budget;
     ka.err = ctx->flags.p + 3;

@@ -264,3 +264,45 @@ def config_powerlaw(n: int = 4_000_000, seed: int = 3) -> Graph:
 
 def config_powergrid(k: int, seed: int = 5) -> Graph:
     return power_grid(k, seed)
+
+
+# --------------------------------------------------------------------------
+# Batches of independent graphs
+# --------------------------------------------------------------------------
+
+def batch_union(gs: list[Graph]) -> tuple[Graph, list[int]]:
+    """Block-diagonal union of several graphs: graph k occupies rows
+    [off[k], off[k+1]) with its own column indices shifted by off[k]."""
+    off = [0]
+    for g in gs:
+        off.append(off[-1] + g.n)
+    rowptr = [np.zeros(1, dtype=np.int64)]
+    cols, vals = [], []
+    base = 0
+    for g, o in zip(gs, off):
+        rowptr.append(g.rowptr[1:] + base)
+        cols.append(g.col.astype(np.int64) + o)
+        vals.append(g.val)
+        base += g.col.shape[0]
+    rp = np.concatenate(rowptr)
+    col = np.concatenate(cols).astype(np.int32)
+    val = np.concatenate(vals)
+    u = Graph(f"batch{len(gs)}", off[-1], rp, col, val, {"graphs": [g.name for g in gs]})
+    return u, off
+
+
+def config_batch(count: int = 256, seed: int = 7, side_lo: int = 32, side_hi: int = 512,
+                 ring_lo: float = 1e3, ring_hi: float = 2e5) -> list[Graph]:
+    """count/2 2D grids with side log-uniform in [side_lo, side_hi] and
+    count/2 rings of n log-uniform in [ring_lo, ring_hi] with n/4 random
+    chords; w ~ U[1,10), D = 1e-3 I.  Graph k uses seed + k."""
+    u = rng.uniform(seed, rng.STREAM_EXTRA, count)
+    gs = []
+    for k in range(count):
+        if k % 2 == 0:
+            side = int(round(side_lo * (side_hi / side_lo) ** u[k]))
+            gs.append(grid2d_uniform(side, side, seed + k))
+        else:
+            n = int(round(ring_lo * (ring_hi / ring_lo) ** u[k]))
+            gs.append(ring_chords(n, seed + k))
+    return gs
