@@ -157,6 +157,10 @@ grass_status grass_ctx_set_param(grass_ctx_t ctx, const char *name, int64_t valu
  *                    iterations (read back from the device) times
  *                    [SpMV over S + 16nrs + tree solve] plus the start
  *                    (7nrs + one tree solve)
+ *   GRASS_KF_PCG     one fused PCG run (grass_pcg_solve, one launch per
+ *                    refinement pass): its outer iterations times
+ *                    [SpMV with A + 12ns + preconditioner] plus its inner
+ *                    CG iterations times [SpMV over S + 16ns + tree solve]
  * (n rows, r columns, s = 4 or 8 bytes, m edges.)  Enabling resets the
  * accumulators.  grass_kernel_timing_read synchronises the stream and
  * returns the summed event time (ms), the number of timed launches and the
@@ -167,7 +171,8 @@ typedef enum {
     GRASS_KF_SPMM_S = 2,
     GRASS_KF_HEAT = 3,
     GRASS_KF_TREE = 4,
-    GRASS_KF_CG = 5
+    GRASS_KF_CG = 5,
+    GRASS_KF_PCG = 6
 } grass_kernel_family;
 grass_status grass_kernel_timing_enable(grass_ctx_t ctx, int family);
 grass_status grass_kernel_timing_read(grass_ctx_t ctx, double *ms, int64_t *launches, double *bytes);
@@ -312,9 +317,10 @@ grass_status grass_densify(grass_ctx_t ctx, grass_tree_t tree, const grass_param
 
 /* Solve A x = b, A = L_G + D of the tree's matrix, by PCG (Sec. V-A),
  * x0 = 0, until ||b - A x||_2 <= tol ||b||_2 (measured in FP64).
- * Preconditioner M = L_S + D: the tree solve when S is the tree, else r=1 CG
- * on L_S + D preconditioned by the tree (inner_tol, inner_maxit) and the
- * flexible PCG update.  prec = GRASS_FP64: FP64 PCG.  prec = GRASS_FP32:
+ * Preconditioner M = L_S + D: the tree solve when S is the tree (or when
+ * inner_maxit = 0), else r=1 CG on L_S + D preconditioned by the tree
+ * (inner_tol, inner_maxit) and the flexible PCG update.  Each PCG run is
+ * one cooperative kernel (no host round trip per iteration).  prec = GRASS_FP64: FP64 PCG.  prec = GRASS_FP32:
  * FP32 vectors and matrix, FP64 dot products and alpha/beta, wrapped in FP64
  * iterative refinement (each pass reduces the residual by refine_tol).
  * b, x: device, n doubles.  maxit bounds PCG iterations over all passes.

@@ -251,6 +251,7 @@ def grass_ctx_set_wait_limit(ctx: int, polls: int = 0, hold_barriers: int = 0) -
 
 
 GRASS_KF_NONE, GRASS_KF_SPMM_G, GRASS_KF_SPMM_S, GRASS_KF_HEAT, GRASS_KF_TREE, GRASS_KF_CG = 0, 1, 2, 3, 4, 5
+GRASS_KF_PCG = 6
 
 
 def grass_kernel_timing_enable(ctx: int, family: int) -> None:

@@ -329,7 +329,7 @@ grass_status grass_tree_schedule_info(grass_tree_t T, int64_t *eliminated, int64
 grass_status grass_kernel_timing_enable(grass_ctx_t ctx, int family) {
     if (!ctx) return GRASS_ERR_INVALID;
     API_BEGIN(ctx)
-    need(family >= GRASS_KF_NONE && family <= GRASS_KF_CG, "unknown kernel family");
+    need(family >= GRASS_KF_NONE && family <= GRASS_KF_PCG, "unknown kernel family");
     ctx->sync();
     ctx->tfam = family;
     ctx->ev_used = 0;

@@ -69,13 +69,14 @@ enum ScratchSlot {
     SCR_SCAN = 0, SCR_SCAN2, SCR_TMP0, SCR_TMP1, SCR_TMP2, SCR_TMP3,
     SCR_Y, SCR_H, SCR_CG_X, SCR_CG_R, SCR_CG_Z, SCR_CG_P, SCR_CG_Q,
     SCR_PCG_X, SCR_PCG_R, SCR_PCG_Z, SCR_PCG_P, SCR_PCG_Q, SCR_PCG_ZOLD, SCR_PCG_E,
-    SCR_FILTER, SCR_FILTER2, SCR_HEAT, SCR_LMAX_V, SCR_LMAX_Y,
+    SCR_FILTER, SCR_FILTER2, SCR_HEAT, SCR_LMAX_V, SCR_LMAX_Y, SCR_PART2,
     SCR_COUNT
 };
 
 // device scalar area layout (doubles)
 enum {
     DS_ITER = 40,        // inside DS_RED: inner-CG iteration accumulator
+    DS_PCG = 42,         // inside DS_RED: fused PCG iterations and final r.r
     DS_RED = 0,          // 64 doubles: reduction outputs (PCG scalars)
     DS_CG = 64,          // 12 x 32 doubles: per-column CG scalars
     DS_MAX = 448,        // 16 x uint64: max-abs bit patterns

@@ -1,6 +1,7 @@
 // krylov.cu -- sparsifier solves (tree solve or tree-preconditioned CG over
 // r columns) and the PCG solver of A = L_G + D (Sec. V-A).
 #include <cmath>
+#include <cstring>
 
 #include "tree_solve.cuh"
 
@@ -148,12 +149,13 @@ __device__ inline void grid_cols(const double *part, double *s_out) {
     __syncthreads();
 }
 
+// The whole inner CG as a device function of a cooperative grid (used by
+// k_cg_persist and inside the fused PCG).  Returns false when a barrier wait
+// ran out (the caller must return).  Ends without a trailing grid barrier.
 template <typename T, int R>
-__global__ void __launch_bounds__(kPersistMaxThreads, 1)
-    k_cg_persist(CGArgs<T> g, TreeKArgs<T> tk) {
+__device__ __forceinline__ bool cg_dev(const CGArgs<T> &g, const TreeKArgs<T> &tk,
+                                       unsigned int &epoch, T *ys) {
     constexpr int TPR = Lay<R>::TPR, EPT = Lay<R>::EPT;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *ys = reinterpret_cast<T *>(smem_raw);
     __shared__ double s_red[32][32];
     __shared__ double s_rz[32], s_rr[32], s_yy[32], s_pq[32], s_new[32], s_al[32];
     __shared__ int s_act[32], s_brk[32], s_it[32], s_nact;
@@ -162,7 +164,6 @@ __global__ void __launch_bounds__(kPersistMaxThreads, 1)
     const int64_t slot = gt / TPR, nslots = (int64_t)gridDim.x * blockDim.x / TPR;
     double *part0 = g.part, *part1 = g.part + (int64_t)gridDim.x * 32;
     double *mypart0 = part0 + (int64_t)blockIdx.x * 32, *mypart1 = part1 + (int64_t)blockIdx.x * 32;
-    unsigned int epoch = 0;
     double mx = 0.0, acc0[EPT], acc1[EPT];
 
     for (int64_t i = slot; i < g.n; i += nslots) {
@@ -175,7 +176,7 @@ __global__ void __launch_bounds__(kPersistMaxThreads, 1)
             g.Z[k] = y;
         }
     }
-    if (!grid_sync(tk.bar, tk.budget, tk.err, epoch)) return;
+    if (!grid_sync(tk.bar, tk.budget, tk.err, epoch)) return false;
     if (threadIdx.x < R) {
         s_brk[threadIdx.x] = 0;
         s_it[threadIdx.x] = 0;
@@ -186,8 +187,8 @@ __global__ void __launch_bounds__(kPersistMaxThreads, 1)
     // updates.  After the updates the test is looked at once more, so no
     // solve is spent when no column goes on.
     for (int it = 0;; ++it) {
-        if (!tree_solve_dev<T, R>(tk, g.Z, epoch, mx, ys)) return;
-        if (!grid_sync(tk.bar, tk.budget, tk.err, epoch)) return;
+        if (!tree_solve_dev<T, R>(tk, g.Z, epoch, mx, ys)) return false;
+        if (!grid_sync(tk.bar, tk.budget, tk.err, epoch)) return false;
 #pragma unroll
         for (int e = 0; e < EPT; ++e) acc0[e] = acc1[e] = 0.0;
         for (int64_t i = slot; i < g.n; i += nslots) {
@@ -204,7 +205,7 @@ __global__ void __launch_bounds__(kPersistMaxThreads, 1)
         }
         block_cols<R>(acc0, c, s_red, mypart0);
         if (it == 0) block_cols<R>(acc1, c, s_red, mypart1);
-        if (!grid_sync(tk.bar, tk.budget, tk.err, epoch)) return;
+        if (!grid_sync(tk.bar, tk.budget, tk.err, epoch)) return false;
         if (it == 0) {
             grid_cols<R>(part0, s_rz);
             grid_cols<R>(part1, s_rr);
@@ -228,7 +229,7 @@ __global__ void __launch_bounds__(kPersistMaxThreads, 1)
                     g.P[k] = g.Z[k] + (T)s_al[j] * g.P[k];
                 }
             }
-            if (!grid_sync(tk.bar, tk.budget, tk.err, epoch)) return;
+            if (!grid_sync(tk.bar, tk.budget, tk.err, epoch)) return false;
         }
         if (it >= g.maxit) break;
         // the oracle's loop test, per column: ||r|| > tol ||y||
@@ -270,7 +271,7 @@ __global__ void __launch_bounds__(kPersistMaxThreads, 1)
             }
         }
         block_cols<R>(acc0, c, s_red, mypart0);
-        if (!grid_sync(tk.bar, tk.budget, tk.err, epoch)) return;
+        if (!grid_sync(tk.bar, tk.budget, tk.err, epoch)) return false;
         grid_cols<R>(part0, s_pq);
         if (threadIdx.x < R) {
             int j = threadIdx.x;
@@ -302,7 +303,7 @@ __global__ void __launch_bounds__(kPersistMaxThreads, 1)
             }
         }
         block_cols<R>(acc1, c, s_red, mypart1);
-        if (!grid_sync(tk.bar, tk.budget, tk.err, epoch)) return;
+        if (!grid_sync(tk.bar, tk.budget, tk.err, epoch)) return false;
         grid_cols<R>(part1, s_rr);
         // look ahead: another iteration only if some column passes the test
         if (it + 1 >= g.maxit) break;
@@ -326,6 +327,15 @@ __global__ void __launch_bounds__(kPersistMaxThreads, 1)
         for (int j = 0; j < R; ++j) mxit = max(mxit, s_it[j]);
         *g.iter_acc += (double)mxit;
     }
+    return true;
+}
+
+template <typename T, int R>
+__global__ void __launch_bounds__(kPersistMaxThreads, 1)
+    k_cg_persist(CGArgs<T> g, TreeKArgs<T> tk) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned int epoch = 0;
+    cg_dev<T, R>(g, tk, epoch, reinterpret_cast<T *>(smem_raw));
 }
 
 template <typename T, int R>
@@ -519,27 +529,243 @@ __global__ void k_add_f32(int64_t n, const float *e, double *x) {
     if (i < n) x[i] += (double)e[i];
 }
 
+// ---------------------------------------------------------------- fused PCG
+// The whole PCG run of pcg_core below in one cooperative launch: the same
+// iteration (SpMV with A = L_G + D, alpha, updates, z = M^{-1} r by the
+// tree solve or the inner CG device function, beta, p), every dot product
+// reduced by every block from per-block partials in one fixed order, so all
+// blocks hold the same scalars and stop together; no host round trip per
+// iteration.
+
+template <typename T>
+struct PCGArgs {
+    int64_t n;
+    const int32_t *aptr, *acol;   // A = L_G + D: off-diagonal adjacency and D
+    const T *aw, *aD;
+    const T *rhs;
+    T *e, *r, *z, *p, *q, *zo;
+    double tol_abs;
+    int maxit;
+    double *part;                 // [2][gridDim.x][32]
+    double *out;                  // [0] += iterations, [1] = final r.r
+};
+
+template <typename T, bool TREE_ONLY>
+__global__ void __launch_bounds__(kPersistMaxThreads, 1)
+    k_pcg_persist(PCGArgs<T> a, CGArgs<T> in, TreeKArgs<T> tk) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *ys = reinterpret_cast<T *>(smem_raw);
+    __shared__ double s_red[32][32];
+    __shared__ double s_v[4];
+    unsigned int epoch = 0;
+    double mx = 0.0;
+    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+    double *P0 = a.part, *P1 = a.part + (int64_t)gridDim.x * 32;
+    double *my0 = P0 + (int64_t)blockIdx.x * 32, *my1 = P1 + (int64_t)blockIdx.x * 32;
+    double acc0[1], acc1[1];
+
+    // e = 0, r = rhs (z = rhs for the tree solve)
+    for (int64_t i = gt; i < a.n; i += nth) {
+        T y = a.rhs[i];
+        a.e[i] = (T)0;
+        a.r[i] = y;
+        if (TREE_ONLY) a.z[i] = y;
+    }
+    if (!grid_sync(tk.bar, tk.budget, tk.err, epoch)) return;
+    // Each pass starts with z = M^{-1} r (the only call site of the
+    // preconditioner), then p, then the test, the product and the updates;
+    // the test is looked at once more after the updates, so no
+    // preconditioner is applied once the run is over.
+    double rz = 0.0, rr = 0.0;
+    int k = 0;
+    for (bool first = true;; first = false) {
+        if constexpr (TREE_ONLY) {
+            if (!tree_solve_dev<T, 1>(tk, a.z, epoch, mx, ys)) return;
+        } else {
+            if (!cg_dev<T, 1>(in, tk, epoch, ys)) return;
+        }
+        if (!grid_sync(tk.bar, tk.budget, tk.err, epoch)) return;
+        // first: rz = r.z, rr = r.r;  later: r.z and r.z_old for beta
+        acc0[0] = acc1[0] = 0.0;
+        for (int64_t i = gt; i < a.n; i += nth) {
+            const double ri = (double)a.r[i];
+            acc0[0] += ri * (double)a.z[i];
+            if (first) acc1[0] += ri * ri;
+            else if (!TREE_ONLY) acc1[0] += ri * (double)a.zo[i];
+        }
+        block_cols<1>(acc0, 0, s_red, my0);
+        block_cols<1>(acc1, 0, s_red, my1);
+        if (!grid_sync(tk.bar, tk.budget, tk.err, epoch)) return;
+        grid_cols<1>(P0, &s_v[0]);
+        grid_cols<1>(P1, &s_v[1]);
+        const double rzn = s_v[0];
+        T beta = (T)0;
+        if (first) rr = s_v[1];
+        else beta = (T)((rzn - (TREE_ONLY ? 0.0 : s_v[1])) / rz);
+        rz = rzn;
+        for (int64_t i = gt; i < a.n; i += nth) a.p[i] = first ? a.z[i] : a.z[i] + beta * a.p[i];
+        if (!grid_sync(tk.bar, tk.budget, tk.err, epoch)) return;
+        if (k >= a.maxit || sqrt(rr) <= a.tol_abs) break;
+        // q = A p, pq
+        acc0[0] = 0.0;
+        for (int64_t i = gt; i < a.n; i += nth) {
+            const T pi = a.p[i];
+            T qi = a.aD[i] * pi;
+            for (int32_t j = a.aptr[i]; j < a.aptr[i + 1]; ++j) qi += a.aw[j] * (pi - a.p[a.acol[j]]);
+            a.q[i] = qi;
+            acc0[0] += (double)pi * (double)qi;
+        }
+        block_cols<1>(acc0, 0, s_red, my0);
+        if (!grid_sync(tk.bar, tk.budget, tk.err, epoch)) return;
+        grid_cols<1>(P0, &s_v[2]);
+        const T alpha = (T)(rz / s_v[2]);
+        // e += alpha p, r -= alpha q (z_old = z; z = r for the tree solve), rr
+        acc1[0] = 0.0;
+        for (int64_t i = gt; i < a.n; i += nth) {
+            a.e[i] += alpha * a.p[i];
+            T ri = a.r[i] - alpha * a.q[i];
+            a.r[i] = ri;
+            if (!TREE_ONLY) a.zo[i] = a.z[i];
+            if (TREE_ONLY) a.z[i] = ri;
+            acc1[0] += (double)ri * (double)ri;
+        }
+        block_cols<1>(acc1, 0, s_red, my1);
+        if (!grid_sync(tk.bar, tk.budget, tk.err, epoch)) return;
+        grid_cols<1>(P1, &s_v[3]);
+        rr = s_v[3];
+        ++k;
+        if (k >= a.maxit || sqrt(rr) <= a.tol_abs) break;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.out[0] += (double)k;
+        a.out[1] = rr;
+    }
+}
+
 // One PCG run on A (prec) for A e = rhs, e0 = 0, until ||r|| <= tol_abs or
 // maxit.  Returns iterations; inner iterations accumulate into *inner.
+template <typename T>
+static int pcg_fused(grass_ctx_t ctx, grass_sparsifier_t S, const T *rhs, T *e, T *r, T *z, T *p,
+                     T *q, T *zold, double tol_abs, int maxit, double inner_tol, int inner_maxit) {
+    grass_tree_t Tr = S->tree;
+    const GraphData &g = Tr->g;
+    const int64_t n = g.n;
+    size_t smem = 0;
+    TreeKArgs<T> tk = tree_kargs<T, 1>(ctx, Tr, Tr->sdd, &smem);
+    const int threads = ctx->tree_threads;
+    const bool tree_only = S->is_tree || inner_maxit <= 0;
+    const void *kern = tree_only ? (const void *)k_pcg_persist<T, true>
+                                 : (const void *)k_pcg_persist<T, false>;
+    const int grid = tree_only ? coop_grid(ctx, k_pcg_persist<T, true>, threads, smem, n)
+                               : coop_grid(ctx, k_pcg_persist<T, false>, threads, smem, n);
+    PCGArgs<T> a;
+    a.n = n;
+    a.aptr = g.adj_ptr.p;
+    a.acol = g.adj_col.p;
+    CGArgs<T> in;
+    std::memset(&in, 0, sizeof(in));
+    in.n = n;
+    if constexpr (sizeof(T) == 8) {
+        a.aw = g.adj_w64.p;
+        a.aD = g.D64.p;
+        in.sw = S->s_w64.p;
+        in.D = g.D64.p;
+    } else {
+        a.aw = g.adj_w32.p;
+        a.aD = g.D32.p;
+        in.sw = S->s_w32.p;
+        in.D = g.D32.p;
+    }
+    a.rhs = rhs;
+    a.e = e;
+    a.r = r;
+    a.z = z;
+    a.p = p;
+    a.q = q;
+    a.zo = zold;
+    a.tol_abs = tol_abs;
+    a.maxit = maxit;
+    a.part = ctx->scr<double>(SCR_PART2, (size_t)grid * 64);
+    double *out = ctx->scal.p + DS_RED + DS_PCG;
+    a.out = out;
+    // the inner CG (sparsifier with off-tree edges): solves (L_S + D) z = r
+    in.sptr = S->s_ptr.p;
+    in.scol = S->s_col.p;
+    in.Y = r;
+    in.X = z;
+    in.Rv = ctx->scr<T>(SCR_CG_R, n);
+    in.Z = ctx->scr<T>(SCR_CG_Z, n);
+    in.P = ctx->scr<T>(SCR_CG_P, n);
+    in.Q = ctx->scr<T>(SCR_CG_Q, n);
+    in.tol = inner_tol;
+    in.maxit = inner_maxit;
+    in.part = ctx->partials.p;
+    in.iter_acc = ctx->scal.p + DS_RED + DS_ITER;
+    in.maxbits = nullptr;
+    if ((size_t)grid * 32 * 2 > ctx->partials.n) fail(GRASS_ERR_CUDA, "partials buffer too small");
+    memset_d(ctx, out, 0, 2 * sizeof(double));
+    GCK(cudaMemsetAsync(tk.bar, 0, sizeof(unsigned int), ctx->stream));
+    // roofline accounting: bytes per outer iteration (SpMV with A, the vector
+    // updates, the tree solve) and per inner CG iteration
+    const TreeSchedule &TS = Tr->sched;
+    const double s = (double)sizeof(T), ns = (double)n * s;
+    const double tree_b = 4.0 * ns + TS.n_rcv * (16.0 + 2.0 * s) +
+                          (n - (double)Tr->nroots) * (16.0 + 4.0 * s);
+    const double spmv_a = 4.0 * (n + 1) + 2.0 * g.m * (4.0 + s) + 3.0 * ns;
+    const double spmv_s = 4.0 * (n + 1) + S->s_nnz * (4.0 + s) + 3.0 * ns;
+    const double per_outer = spmv_a + 12.0 * ns + (tree_only ? tree_b : 7.0 * ns + tree_b);
+    const double per_inner = spmv_s + 16.0 * ns + tree_b;
+    const bool timing = ctx->tfam == GRASS_KF_PCG;
+    size_t snap = ctx->iter_launches.size();
+    if (timing) {
+        ctx->t_snap(out, snap, 0);
+        ctx->t_snap(in.iter_acc, snap + 1, 0);
+        ctx->iter_launches.push_back({per_outer + 3.0 * ns, per_outer, snap});
+        ctx->iter_launches.push_back({0.0, per_inner, snap + 1});
+    }
+    bool timed = ctx->t_begin(GRASS_KF_PCG, 0.0);
+    void *args[] = {&a, &in, &tk};
+    GCK(cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(threads), args, smem, ctx->stream));
+    ctx->launches++;
+    ctx->t_end(timed);
+    if (timing) {
+        ctx->t_snap(out, snap, 1);
+        ctx->t_snap(in.iter_acc, snap + 1, 1);
+    }
+    double h[2] = {0.0, 0.0};
+    d2h(ctx, h, out, sizeof(h));
+    return (int)h[0];
+}
+
 template <typename T>
 static int pcg_core(grass_ctx_t ctx, grass_sparsifier_t S, grass_prec prec, const T *rhs, T *e,
                     double tol_abs, int maxit, double inner_tol, int inner_maxit, int64_t *inner) {
     grass_tree_t Tr = S->tree;
     const GraphData &g = Tr->g;
     const int64_t n = g.n;
-    const bool flexible = !S->is_tree;
+    const bool flexible = !S->is_tree && inner_maxit > 0;
     double *sc = ctx->scal.p + DS_RED;
     T *r = ctx->scr<T>(SCR_PCG_R, n);
     T *z = ctx->scr<T>(SCR_PCG_Z, n);
     T *p = ctx->scr<T>(SCR_PCG_P, n);
     T *q = ctx->scr<T>(SCR_PCG_Q, n);
     T *zold = ctx->scr<T>(SCR_PCG_ZOLD, n);
+    if (ctx->num_sms > 0) return pcg_fused<T>(ctx, S, rhs, e, r, z, p, q, zold, tol_abs, maxit,
+                                               inner_tol, inner_maxit);
     const void *wA = prec == GRASS_FP64 ? (const void *)g.adj_w64.p : (const void *)g.adj_w32.p;
     const void *DA = prec == GRASS_FP64 ? (const void *)g.D64.p : (const void *)g.D32.p;
     int64_t grid = cdiv(n, kBlock);
+    // inner_maxit = 0: the tree solve alone
+    auto precond = [&]() -> int64_t {
+        if (inner_maxit > 0) return s_solve(ctx, S, true, 1, prec, r, z, inner_tol, inner_maxit, nullptr);
+        copy_d(ctx, z, r, n * sizeof(T));
+        tree_solve_inplace(ctx, Tr, Tr->sdd, 1, prec, z, nullptr);
+        return 0;
+    };
     launch(ctx, k_zero<T>, grid, kBlock, 0, n, e);
     copy_d(ctx, r, rhs, n * sizeof(T));
-    *inner += s_solve(ctx, S, true, 1, prec, r, z, inner_tol, inner_maxit, nullptr);
+    *inner += precond();
     copy_d(ctx, p, z, n * sizeof(T));
     int cur = 0;   // rz[cur] holds r.z
     dot_cols(ctx, 1, prec, n, r, z, sc + P_RZ0);
@@ -556,7 +782,7 @@ static int pcg_core(grass_ctx_t ctx, grass_sparsifier_t S, grass_prec prec, cons
                (const double *)(sc + P_PQ), e, r, (const T *)p, (const T *)q);
         dot_cols(ctx, 1, prec, n, r, r, sc + P_RR);
         if (flexible) copy_d(ctx, zold, z, n * sizeof(T));
-        *inner += s_solve(ctx, S, true, 1, prec, r, z, inner_tol, inner_maxit, nullptr);
+        *inner += precond();
         int nxt = 1 - cur;
         dot_cols(ctx, 1, prec, n, r, z, sc + P_RZ0 + nxt);
         if (flexible) dot_cols(ctx, 1, prec, n, r, zold, sc + P_RZO);
