@@ -141,6 +141,10 @@ grass_status grass_ctx_set_wait_limit(grass_ctx_t ctx, int64_t polls, int hold_b
  *   "tree_threads"        threads per block of that kernel (128-1024, x32)
  *   "tree_tail_items"     rounds at the end whose total work is below this
  *                         many items run in one block (0 = none)
+ *   "euler_solve"         1 (default): grounded solves of L_T alone (no D)
+ *                         with one column, inside the inner CG and the
+ *                         power steps, use the Euler-tour scan form (two
+ *                         FP64 prefix sums); 0: the elimination rounds
  * Errors: INVALID for an unknown name or a value out of range. */
 grass_status grass_ctx_set_param(grass_ctx_t ctx, const char *name, int64_t value);
 

@@ -297,6 +297,9 @@ grass_status grass_ctx_set_param(grass_ctx_t ctx, const char *name, int64_t valu
     } else if (k == "tree_tail_items") {
         need(value >= 0, "tree_tail_items must be >= 0");
         ctx->tree_tail_items = value;
+    } else if (k == "euler_solve") {
+        need(value == 0 || value == 1, "euler_solve must be 0 or 1");
+        ctx->euler_solve = (int)value;
     } else {
         fail(GRASS_ERR_INVALID, "unknown parameter " + k);
     }

@@ -70,6 +70,7 @@ enum ScratchSlot {
     SCR_Y, SCR_H, SCR_CG_X, SCR_CG_R, SCR_CG_Z, SCR_CG_P, SCR_CG_Q,
     SCR_PCG_X, SCR_PCG_R, SCR_PCG_Z, SCR_PCG_P, SCR_PCG_Q, SCR_PCG_ZOLD, SCR_PCG_E,
     SCR_FILTER, SCR_FILTER2, SCR_HEAT, SCR_LMAX_V, SCR_LMAX_Y, SCR_PART2,
+    SCR_EU_S, SCR_EU_C, SCR_EU_P, SCR_EU_A,
     SCR_COUNT
 };
 
@@ -104,6 +105,7 @@ struct grass_ctx_s {
     int tree_bpsm = 1;
     int tree_threads = 1024;
     int64_t tree_tail_items = 4096;
+    int euler_solve = 1;   // scan form for grounded r = 1 solves without D
     // co-resident grid of each cooperative kernel shape, per context (no
     // process-wide state: contexts may run on different host threads)
     struct CoopEntry {
@@ -302,6 +304,18 @@ struct TreeSchedule {
     DBuf<int32_t> contrib_loc;       // local id of contributors from round tail_k0 on
 };
 
+// Euler tour of the spanning tree (forest) for the scan form of the
+// grounded solve (D = 0): tour[p] = v at the entry into v, -(v+1) at the
+// exit; ein/eout the two positions of v (-1 for a root); pw the weight of
+// v's edge to its parent.
+struct EulerTour {
+    bool built = false;
+    int64_t L = 0;                   // 2 (n - nroots) positions
+    DBuf<int32_t> tour, ein, eout;
+    DBuf<uint8_t> head;              // [L] 1 at each tree's first position
+    DBuf<double> pw;
+};
+
 }  // namespace grass
 
 struct grass_tree_s {
@@ -316,6 +330,7 @@ struct grass_tree_s {
     grass::GraphData g;
     grass::DBuf<uint8_t> in_tree;     // [m]
     grass::TreeSchedule sched;
+    grass::EulerTour euler;
     grass::TreeFactor lap;            // L_T grounded at rho
     grass::TreeFactor sdd;            // L_T + D
     bool has_sdd = false;
@@ -365,6 +380,10 @@ void copy_d(grass_ctx_t ctx, void *dst, const void *src, size_t bytes);
 void graph_extract(grass_ctx_t ctx, const grass_csr_t *A, GraphData &g);
 void mst_boruvka(grass_ctx_t ctx, const GraphData &g, uint8_t *in_tree);
 void tree_schedule(grass_ctx_t ctx, grass_tree_t T);
+// Euler tour from the tree adjacency (slot lists tptr/tocc, tree edge id of
+// every slot in tsrc; L slots), before the contraction rounds modify it.
+void euler_build(grass_ctx_t ctx, grass_tree_t T, const int32_t *tptr, const int32_t *tocc,
+                 const int32_t *tsrc, int64_t L);
 void tree_factor(grass_ctx_t ctx, grass_tree_t T, bool with_D, TreeFactor &f);
 // In-place tree solve of the n x r block Y (prec); optionally tracks the
 // max |x| bit pattern into maxbits (device, uint64 for both precisions).

@@ -110,6 +110,7 @@ struct CGArgs {
     double *part;                // [2][gridDim.x][32]
     double *iter_acc;            // += max over columns of the iterations
     unsigned long long *maxbits; // optional max |X|
+    EulerKArgs eu;               // scan-form tree solve (r = 1, no D)
 };
 
 // Per-block column sums of the thread partials v[e] (column c*EPT + e),
@@ -152,9 +153,10 @@ __device__ inline void grid_cols(const double *part, double *s_out) {
 // The whole inner CG as a device function of a cooperative grid (used by
 // k_cg_persist and inside the fused PCG).  Returns false when a barrier wait
 // ran out (the caller must return).  Ends without a trailing grid barrier.
-template <typename T, int R>
+template <typename T, int R, bool EU = false>
 __device__ __forceinline__ bool cg_dev(const CGArgs<T> &g, const TreeKArgs<T> &tk,
                                        unsigned int &epoch, T *ys) {
+    static_assert(!EU || R == 1, "the scan-form solve handles one column");
     constexpr int TPR = Lay<R>::TPR, EPT = Lay<R>::EPT;
     __shared__ double s_red[32][32];
     __shared__ double s_rz[32], s_rr[32], s_yy[32], s_pq[32], s_new[32], s_al[32];
@@ -187,7 +189,11 @@ __device__ __forceinline__ bool cg_dev(const CGArgs<T> &g, const TreeKArgs<T> &t
     // updates.  After the updates the test is looked at once more, so no
     // solve is spent when no column goes on.
     for (int it = 0;; ++it) {
-        if (!tree_solve_dev<T, R>(tk, g.Z, epoch, mx, ys)) return false;
+        if constexpr (EU) {
+            if (!euler_solve_dev<T>(g.eu, g.Z, tk.bar, tk.budget, tk.err, epoch, mx)) return false;
+        } else {
+            if (!tree_solve_dev<T, R>(tk, g.Z, epoch, mx, ys)) return false;
+        }
         if (!grid_sync(tk.bar, tk.budget, tk.err, epoch)) return false;
 #pragma unroll
         for (int e = 0; e < EPT; ++e) acc0[e] = acc1[e] = 0.0;
@@ -330,12 +336,12 @@ __device__ __forceinline__ bool cg_dev(const CGArgs<T> &g, const TreeKArgs<T> &t
     return true;
 }
 
-template <typename T, int R>
+template <typename T, int R, bool EU>
 __global__ void __launch_bounds__(kPersistMaxThreads, 1)
     k_cg_persist(CGArgs<T> g, TreeKArgs<T> tk) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned int epoch = 0;
-    cg_dev<T, R>(g, tk, epoch, reinterpret_cast<T *>(smem_raw));
+    cg_dev<T, R, EU>(g, tk, epoch, reinterpret_cast<T *>(smem_raw));
 }
 
 template <typename T, int R>
@@ -370,9 +376,16 @@ static void cg_persistent(grass_ctx_t ctx, grass_sparsifier_t S, bool with_D, co
     a.part = ctx->partials.p;
     a.iter_acc = ctx->scal.p + DS_RED + DS_ITER;
     a.maxbits = maxbits;
+    std::memset(&a.eu, 0, sizeof(a.eu));
     const int threads = ctx->tree_threads;
-    const int grid = coop_grid(ctx, k_cg_persist<T, R>, threads, smem, n * Lay<R>::TPR);
+    // one column and no D: the scan-form tree solve
+    const bool eu = R == 1 && !with_D && ctx->euler_solve && Tr->euler.built;
+    const void *kern = eu ? (const void *)k_cg_persist<T, R, (R == 1)>
+                          : (const void *)k_cg_persist<T, R, false>;
+    const int grid = eu ? coop_grid(ctx, k_cg_persist<T, R, (R == 1)>, threads, smem, n * Lay<R>::TPR)
+                        : coop_grid(ctx, k_cg_persist<T, R, false>, threads, smem, n * Lay<R>::TPR);
     if ((size_t)grid * 32 * 2 > ctx->partials.n) fail(GRASS_ERR_CUDA, "partials buffer too small");
+    if (eu) euler_kargs(ctx, Tr, grid, &a.eu);
     GCK(cudaMemsetAsync(tk.bar, 0, sizeof(unsigned int), ctx->stream));
     // roofline accounting: algorithmic bytes per iteration and of the start
     const TreeSchedule &TS = Tr->sched;
@@ -388,8 +401,7 @@ static void cg_persistent(grass_ctx_t ctx, grass_sparsifier_t S, bool with_D, co
     }
     bool timed = ctx->t_begin(GRASS_KF_CG, 0.0);
     void *args[] = {&a, &tk};
-    GCK(cudaLaunchCooperativeKernel((const void *)k_cg_persist<T, R>, dim3(grid), dim3(threads),
-                                    args, smem, ctx->stream));
+    GCK(cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(threads), args, smem, ctx->stream));
     ctx->launches++;
     ctx->t_end(timed);
     if (timing) ctx->t_snap(a.iter_acc, snap, 1);

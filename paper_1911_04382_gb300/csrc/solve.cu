@@ -16,6 +16,16 @@ __global__ void __launch_bounds__(kPersistMaxThreads, 1)
     if (maxbits) block_atomic_max(maxbits, mx);
 }
 
+// scan form: grounded solve of L_T alone, one column
+template <typename T>
+__global__ void __launch_bounds__(kPersistMaxThreads, 1)
+    k_euler_persist(EulerKArgs e, TreeKArgs<T> a, T *Y, unsigned long long *maxbits) {
+    unsigned int epoch = 0;
+    double mx = 0.0;
+    if (!euler_solve_dev<T>(e, Y, a.bar, a.budget, a.err, epoch, mx)) return;
+    if (maxbits) block_atomic_max(maxbits, mx);
+}
+
 // ---------------------------------------------------------------- per-round path
 
 template <typename T, int R>
@@ -81,6 +91,17 @@ static void solve_T(grass_ctx_t ctx, grass_tree_t Tr, const TreeFactor &f, T *Y,
         return;
     }
     const int threads = ctx->tree_threads;
+    if (R == 1 && &f == &Tr->lap && ctx->euler_solve && Tr->euler.built) {
+        const int grid = coop_grid(ctx, k_euler_persist<T>, threads, 0, Tr->g.n);
+        EulerKArgs e;
+        euler_kargs(ctx, Tr, grid, &e);
+        GCK(cudaMemsetAsync(a.bar, 0, sizeof(unsigned int), ctx->stream));
+        void *eargs[] = {&e, &a, &Y, &maxbits};
+        GCK(cudaLaunchCooperativeKernel((const void *)k_euler_persist<T>, dim3(grid),
+                                        dim3(threads), eargs, 0, ctx->stream));
+        ctx->launches++;
+        return;
+    }
     const int grid = coop_grid(ctx, k_tree_persist<T, R>, threads, smem, Tr->g.n * Lay<R>::TPR);
     GCK(cudaMemsetAsync(a.bar, 0, sizeof(unsigned int), ctx->stream));
     void *args[] = {&a, &Y, &maxbits};

@@ -348,6 +348,270 @@ __device__ __forceinline__ bool tree_solve_dev(const TreeKArgs<T> &a, T *Y, unsi
     return true;
 }
 
+// ---------------------------------------------------------------- scan form (D = 0, r = 1)
+// Grounded solve of L_T x = b along the Euler tour (euler.cu): with S the
+// exclusive prefix sums of b placed at the tour's entries, the current up
+// v's parent edge is c_v = (S[out(v)] - S[in(v)]) / w_v; with S2 the prefix
+// sums of +c at entries and -c at exits, x_v = S2 up to and including
+// in(v).  FP64 sums; each block scans a contiguous stretch of the tour and
+// every block derives the stretch offsets from the per-block totals in one
+// fixed order, so the result does not depend on timing.
+
+struct EulerKArgs {
+    int64_t L, n;
+    const int32_t *tour, *ein, *eout;
+    const uint8_t *head;    // [L] 1 at the first position of every tree's tour
+    const double *pw;
+    double *S, *C, *part;   // [L], [n], [6 * gridDim.x]
+};
+
+constexpr int kEulerMaxGrid = 2048;
+
+// Segmented sums: a pair (v, f) is a sum v that restarts at a head when f;
+// combining a left pair with a right one gives (f_r ? v_r : v_l + v_r, f_l | f_r).
+// Exclusive scan of one pair per thread over the block (fixed order): the
+// value carried into the thread; *tv, *tf = the whole block's pair.
+__device__ inline double block_excl_seg_scan(double v, int f, double *tv, int *tf) {
+    __shared__ double wv[32];
+    __shared__ int wf[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
+    double x = v;
+    int g = f;
+    for (int d = 1; d < 32; d <<= 1) {
+        const double y = __shfl_up_sync(0xffffffffu, x, d);
+        const int h = __shfl_up_sync(0xffffffffu, g, d);
+        if (lane >= d) {
+            if (!g) x += y;
+            g |= h;
+        }
+    }
+    // exclusive within the warp: the inclusive pair of the lane before
+    double ex = __shfl_up_sync(0xffffffffu, x, 1);
+    int exf = __shfl_up_sync(0xffffffffu, g, 1);
+    if (lane == 0) {
+        ex = 0.0;
+        exf = 0;
+    }
+    __syncthreads();
+    if (lane == 31) {
+        wv[wid] = x;
+        wf[wid] = g;
+    }
+    __syncthreads();
+    if (wid == 0) {
+        double w = lane < nw ? wv[lane] : 0.0;
+        int wg = lane < nw ? wf[lane] : 0;
+        for (int d = 1; d < 32; d <<= 1) {
+            const double y = __shfl_up_sync(0xffffffffu, w, d);
+            const int h = __shfl_up_sync(0xffffffffu, wg, d);
+            if (lane >= d) {
+                if (!wg) w += y;
+                wg |= h;
+            }
+        }
+        if (lane < nw) {
+            wv[lane] = w;
+            wf[lane] = wg;
+        }
+    }
+    __syncthreads();
+    // carry into this thread: the warps before, then the lanes before
+    double carry = wid > 0 ? wv[wid - 1] : 0.0;
+    if (exf) carry = ex;
+    else carry += ex;
+    *tv = wv[nw - 1];
+    *tf = wf[nw - 1];
+    return carry;
+}
+
+// carry into every block b from blocks 0..b-1 (segmented), into shared memory
+__device__ inline void block_offsets_seg(const double *pv, const double *pf, double *off) {
+    const int G = (int)gridDim.x;
+    const int per = (G + (int)blockDim.x - 1) / (int)blockDim.x;
+    const int i0 = (int)threadIdx.x * per;
+    double v = 0.0;
+    int f = 0;
+    for (int i = i0; i < i0 + per && i < G; ++i) {
+        if (pf[i] != 0.0) {
+            v = pv[i];
+            f = 1;
+        } else {
+            v += pv[i];
+        }
+    }
+    double tv;
+    int tf;
+    double run = block_excl_seg_scan(v, f, &tv, &tf);
+    for (int i = i0; i < i0 + per && i < G; ++i) {
+        off[i] = run;
+        if (pf[i] != 0.0) run = pv[i];
+        else run += pv[i];
+    }
+    __syncthreads();
+}
+
+constexpr int kEuBatch = 8;   // positions / vertices per thread with loads in flight together
+
+// One segmented scan pass over the block's stretch of the tour: S[p] = sum
+// of val over [latest head <= p, p) inside the block (the carry from earlier
+// blocks is added by the reader: it applies before the block's first head).
+// Each thread owns a contiguous chunk and reads it kEuBatch positions at a
+// time (the tour entries, then the values they point to), so its loads are
+// independent.  Block pair into pv[b], pf[b]; first head into fh[b].
+template <typename VAL>
+__device__ inline void euler_scan_pass(const EulerKArgs &E, int64_t t0, int64_t t1, VAL val,
+                                       double *pv, double *pf, double *fh) {
+    double sv = 0.0;
+    int sf = 0;
+    long long first = LLONG_MAX;
+    for (int64_t p = t0; p < t1; p += kEuBatch) {
+        int32_t tv[kEuBatch];
+        uint8_t hd[kEuBatch];
+        double x[kEuBatch];
+#pragma unroll
+        for (int k = 0; k < kEuBatch; ++k) {
+            const bool in = p + k < t1;
+            tv[k] = in ? E.tour[p + k] : 0;
+            hd[k] = in ? E.head[p + k] : 0;
+        }
+#pragma unroll
+        for (int k = 0; k < kEuBatch; ++k) x[k] = p + k < t1 ? val(tv[k]) : 0.0;
+#pragma unroll
+        for (int k = 0; k < kEuBatch; ++k) {
+            if (hd[k]) {
+                sv = 0.0;
+                sf = 1;
+                if (first == LLONG_MAX) first = p + k;
+            }
+            sv += x[k];
+        }
+    }
+    double bv;
+    int bf;
+    double run = block_excl_seg_scan(sv, sf, &bv, &bf);
+    for (int64_t p = t0; p < t1; p += kEuBatch) {
+        int32_t tv[kEuBatch];
+        uint8_t hd[kEuBatch];
+        double x[kEuBatch];
+#pragma unroll
+        for (int k = 0; k < kEuBatch; ++k) {
+            const bool in = p + k < t1;
+            tv[k] = in ? E.tour[p + k] : 0;
+            hd[k] = in ? E.head[p + k] : 0;
+        }
+#pragma unroll
+        for (int k = 0; k < kEuBatch; ++k) x[k] = p + k < t1 ? val(tv[k]) : 0.0;
+#pragma unroll
+        for (int k = 0; k < kEuBatch; ++k) {
+            if (p + k >= t1) break;
+            if (hd[k]) run = 0.0;
+            E.S[p + k] = run;
+            run += x[k];
+        }
+    }
+    // the block's first head: min over threads
+    __shared__ long long s_first;
+    if (threadIdx.x == 0) s_first = LLONG_MAX;
+    __syncthreads();
+    if (first != LLONG_MAX) atomicMin(&s_first, first);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        pv[blockIdx.x] = bv;
+        pf[blockIdx.x] = bf ? 1.0 : 0.0;
+        fh[blockIdx.x] = (double)s_first;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ bool euler_solve_dev(const EulerKArgs &E, T *Y, unsigned int *bar,
+                                                long long budget, int *err, unsigned int &epoch,
+                                                double &mx) {
+    __shared__ double s_off[kEulerMaxGrid];
+    const int64_t G = gridDim.x;
+    const int64_t per = (E.L + G - 1) / G;
+    const int64_t b0 = min(E.L, (int64_t)blockIdx.x * per), b1 = min(E.L, b0 + per);
+    const int64_t ipt = (per + blockDim.x - 1) / blockDim.x;
+    const int64_t t0 = min(b1, b0 + (int64_t)threadIdx.x * ipt), t1 = min(b1, t0 + ipt);
+    const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+    double *pv = E.part, *pf = E.part + G, *fh = E.part + 2 * G;
+    // global prefix at p: the block-local part, plus the carry from earlier
+    // blocks while p lies before the block's first head
+    auto glob = [&](int64_t p, const double *fhp) {
+        const int64_t b = p / per;
+        return E.S[p] + ((double)p < fhp[b] ? s_off[b] : 0.0);
+    };
+    // vertices in batches: thread g takes v = g + k * nth, k < kEuBatch, per round
+    const int64_t vbase = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    // 1: prefix sums of b at the entries, restarting at every tree
+    euler_scan_pass(E, t0, t1, [&](int32_t v) { return v >= 0 ? (double)Y[v] : 0.0; }, pv, pf, fh);
+    if (!grid_sync(bar, budget, err, epoch)) return false;
+    // 2: currents c_v = (subtree sum of b) / w_v
+    block_offsets_seg(pv, pf, s_off);
+    for (int64_t v0 = vbase; v0 < E.n; v0 += nth * kEuBatch) {
+        int32_t in[kEuBatch], out[kEuBatch];
+#pragma unroll
+        for (int k = 0; k < kEuBatch; ++k) {
+            const int64_t v = v0 + k * nth;
+            in[k] = v < E.n ? E.ein[v] : -1;
+            out[k] = v < E.n ? E.eout[v] : -1;
+        }
+        double d[kEuBatch];
+#pragma unroll
+        for (int k = 0; k < kEuBatch; ++k) d[k] = in[k] >= 0 ? glob(out[k], fh) - glob(in[k], fh) : 0.0;
+#pragma unroll
+        for (int k = 0; k < kEuBatch; ++k) {
+            const int64_t v = v0 + k * nth;
+            if (v < E.n) E.C[v] = in[k] >= 0 ? d[k] / E.pw[v] : 0.0;
+        }
+    }
+    if (!grid_sync(bar, budget, err, epoch)) return false;
+    // 3: prefix sums of +c at entries, -c at exits, restarting at every tree
+    euler_scan_pass(E, t0, t1, [&](int32_t v) { return v >= 0 ? E.C[v] : -E.C[-v - 1]; },
+                    pv + 3 * G, pf + 3 * G, fh + 3 * G);
+    if (!grid_sync(bar, budget, err, epoch)) return false;
+    // 4: x_v = the path sum up to and including v's entry (roots: 0)
+    block_offsets_seg(pv + 3 * G, pf + 3 * G, s_off);
+    for (int64_t v0 = vbase; v0 < E.n; v0 += nth * kEuBatch) {
+        int32_t in[kEuBatch];
+#pragma unroll
+        for (int k = 0; k < kEuBatch; ++k) {
+            const int64_t v = v0 + k * nth;
+            in[k] = v < E.n ? E.ein[v] : -1;
+        }
+        double x[kEuBatch];
+#pragma unroll
+        for (int k = 0; k < kEuBatch; ++k) {
+            const int64_t v = v0 + k * nth;
+            x[k] = in[k] >= 0 ? glob(in[k], fh + 3 * G) + E.C[v] : 0.0;
+        }
+#pragma unroll
+        for (int k = 0; k < kEuBatch; ++k) {
+            const int64_t v = v0 + k * nth;
+            if (v >= E.n) continue;
+            const T xt = (T)x[k];
+            Y[v] = xt;
+            mx = fmax(mx, fabs((double)xt));
+        }
+    }
+    return true;
+}
+
+// Host side: scan-form arguments for a cooperative grid of `grid` blocks.
+inline void euler_kargs(grass_ctx_t ctx, const grass_tree_s *Tr, int grid, EulerKArgs *e) {
+    if (grid > kEulerMaxGrid) fail(GRASS_ERR_INVALID, "grid too large for the scan-form tree solve");
+    const EulerTour &E = Tr->euler;
+    e->L = E.L;
+    e->n = Tr->g.n;
+    e->tour = E.tour.p;
+    e->ein = E.ein.p;
+    e->eout = E.eout.p;
+    e->head = E.head.p;
+    e->pw = E.pw.p;
+    e->S = ctx->scr<double>(SCR_EU_S, E.L + 1);
+    e->C = ctx->scr<double>(SCR_EU_C, Tr->g.n);
+    e->part = ctx->scr<double>(SCR_EU_P, 6 * (size_t)grid + 2);
+}
+
 // Grid of a cooperative kernel with `threads` threads and `smem` dynamic
 // shared memory: co-resident blocks per SM, capped by tree_blocks_per_sm, and
 // no more blocks than `work_threads` threads of work fill (small graphs leave
