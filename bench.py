@@ -206,14 +206,21 @@ def profile_kernel(G, ctx, which, g, rp, col, val, v0d, w) -> int:
     or of the tree solve (r = 16, FP32); prints its algorithmic bytes."""
     import torch
     tree = G.grass_build_tree(ctx, rp, col, val, 0)
-    if which == "cg":
+    if which in ("cg", "pcg"):
         S = G.grass_sparsifier_create(ctx, tree)
         _, moff = G.grass_sparsifier_info(S)
         ids = torch.empty(moff, dtype=torch.int64, device="cuda")
         G.grass_sparsifier_offtree(ctx, S, ids)
         G.grass_sparsifier_add(ctx, S, ids[::197].contiguous())
-        run = lambda: G.grass_lambda_max(ctx, S, v0d[:g.n], 1, G.GRASS_FP32, 0.0, 30)
-        fam, units = G.GRASS_KF_CG, "30 iterations, r=1"
+        if which == "cg":
+            run = lambda: G.grass_lambda_max(ctx, S, v0d[:g.n], 1, G.GRASS_FP32, 0.0, 30)
+            fam, units = G.GRASS_KF_CG, "30 iterations, r=1"
+        else:
+            bq = v0d[:g.n].contiguous()
+            xq = torch.zeros(g.n, dtype=torch.float64, device="cuda")
+            # one FP32 pass of exactly 30 outer iterations (tolerance out of reach)
+            run = lambda: G.grass_pcg_solve(ctx, S, bq, xq, 1e-30, 30, G.GRASS_FP32, 1e-20, 1e-2, 1)
+            fam, units = G.GRASS_KF_PCG, "30 outer iterations, inner 1"
     else:
         B = torch.randn(g.n, 16, dtype=torch.float32, device="cuda")
         X = torch.empty_like(B)
@@ -540,13 +547,13 @@ def main() -> int:
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="grass", choices=["grass", "reference"])
     ap.add_argument("--workload", default="grid3d_100", choices=sorted(WORKLOADS))
-    ap.add_argument("--family", default="cg", choices=sorted(FAMILIES),
+    ap.add_argument("--family", default="pcg", choices=sorted(FAMILIES),
                     help="kernel family timed for the roofline object")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-breakdown", action="store_true")
     ap.add_argument("--profile-step", action="store_true",
                     help="run exactly one step and exit (for ncu launch lists)")
-    ap.add_argument("--profile-kernel", choices=["cg", "tree"], default=None,
+    ap.add_argument("--profile-kernel", choices=["cg", "tree", "pcg"], default=None,
                     help="one warm launch, then one timed launch of the kernel (for ncu captures)")
     ap.add_argument("--no-solve40m", action="store_true",
                     help="skip the 40M-unknown solve (solve_40m key of the line)")

@@ -145,6 +145,11 @@ grass_status grass_ctx_set_wait_limit(grass_ctx_t ctx, int64_t polls, int hold_b
  *                         with one column, inside the inner CG and the
  *                         power steps, use the Euler-tour scan form (two
  *                         FP64 prefix sums); 0: the elimination rounds
+ *   "euler_max_n"         trees built on this context with more vertices
+ *                         than this (default 4,000,000) get no Euler tour
+ *                         and keep the elimination rounds (the tour's FP64
+ *                         arrays then no longer fit the L2 cache and its
+ *                         gathers are slower than the rounds)
  * Errors: INVALID for an unknown name or a value out of range. */
 grass_status grass_ctx_set_param(grass_ctx_t ctx, const char *name, int64_t value);
 

@@ -300,6 +300,9 @@ grass_status grass_ctx_set_param(grass_ctx_t ctx, const char *name, int64_t valu
     } else if (k == "euler_solve") {
         need(value == 0 || value == 1, "euler_solve must be 0 or 1");
         ctx->euler_solve = (int)value;
+    } else if (k == "euler_max_n") {
+        need(value >= 0, "euler_max_n must be >= 0");
+        ctx->euler_max_n = value;
     } else {
         fail(GRASS_ERR_INVALID, "unknown parameter " + k);
     }

@@ -106,6 +106,7 @@ struct grass_ctx_s {
     int tree_threads = 1024;
     int64_t tree_tail_items = 4096;
     int euler_solve = 1;   // scan form for grounded r = 1 solves without D
+    int64_t euler_max_n = 4000000;   // trees larger than this keep the elimination rounds
     // co-resident grid of each cooperative kernel shape, per context (no
     // process-wide state: contexts may run on different host threads)
     struct CoopEntry {

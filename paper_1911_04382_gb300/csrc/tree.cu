@@ -304,7 +304,9 @@ void tree_schedule(grass_ctx_t ctx, grass_tree_t T) {
     tsrc.alloc(tslots);
     launch(ctx, k_tfill, cdiv(n, kBlock), kBlock, 0, n, g.adj_ptr.p, g.adj_col.p, g.adj_eid.p,
            (const uint8_t *)T->in_tree.p, (const int64_t *)off.p, tptr.p, tocc.p, tsrc.p);
-    euler_build(ctx, T, tptr.p, tocc.p, tsrc.p, tslots);
+    // the scan form pays off while its FP64 tour arrays stay near the L2
+    // size; larger trees keep the elimination rounds only
+    if (n <= ctx->euler_max_n) euler_build(ctx, T, tptr.p, tocc.p, tsrc.p, tslots);
     elim_round.alloc(n);
     cls.alloc(n);
     val.alloc(n + 1);

@@ -424,6 +424,61 @@ __device__ inline double block_excl_seg_scan(double v, int f, double *tv, int *t
     return carry;
 }
 
+// The same scan, also giving the flag of the carried pair (a head among the
+// earlier threads).
+__device__ inline double block_excl_seg_scan_f(double v, int f, int *cf, double *tv, int *tf) {
+    __shared__ double wv[32];
+    __shared__ int wf[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
+    double x = v;
+    int g = f;
+    for (int d = 1; d < 32; d <<= 1) {
+        const double y = __shfl_up_sync(0xffffffffu, x, d);
+        const int h = __shfl_up_sync(0xffffffffu, g, d);
+        if (lane >= d) {
+            if (!g) x += y;
+            g |= h;
+        }
+    }
+    double ex = __shfl_up_sync(0xffffffffu, x, 1);
+    int exf = __shfl_up_sync(0xffffffffu, g, 1);
+    if (lane == 0) {
+        ex = 0.0;
+        exf = 0;
+    }
+    __syncthreads();
+    if (lane == 31) {
+        wv[wid] = x;
+        wf[wid] = g;
+    }
+    __syncthreads();
+    if (wid == 0) {
+        double w = lane < nw ? wv[lane] : 0.0;
+        int wg = lane < nw ? wf[lane] : 0;
+        for (int d = 1; d < 32; d <<= 1) {
+            const double y = __shfl_up_sync(0xffffffffu, w, d);
+            const int h = __shfl_up_sync(0xffffffffu, wg, d);
+            if (lane >= d) {
+                if (!wg) w += y;
+                wg |= h;
+            }
+        }
+        if (lane < nw) {
+            wv[lane] = w;
+            wf[lane] = wg;
+        }
+    }
+    __syncthreads();
+    double carry = wid > 0 ? wv[wid - 1] : 0.0;
+    int carf = wid > 0 ? wf[wid - 1] : 0;
+    if (exf) carry = ex;
+    else carry += ex;
+    *cf = carf | exf;
+    *tv = wv[nw - 1];
+    *tf = wf[nw - 1];
+    return carry;
+}
+
 // carry into every block b from blocks 0..b-1 (segmented), into shared memory
 __device__ inline void block_offsets_seg(const double *pv, const double *pf, double *off) {
     const int G = (int)gridDim.x;
@@ -452,72 +507,70 @@ __device__ inline void block_offsets_seg(const double *pv, const double *pf, dou
 
 constexpr int kEuBatch = 8;   // positions / vertices per thread with loads in flight together
 
-// One segmented scan pass over the block's stretch of the tour: S[p] = sum
-// of val over [latest head <= p, p) inside the block (the carry from earlier
-// blocks is added by the reader: it applies before the block's first head).
-// Each thread owns a contiguous chunk and reads it kEuBatch positions at a
-// time (the tour entries, then the values they point to), so its loads are
-// independent.  Block pair into pv[b], pf[b]; first head into fh[b].
+// One segmented scan pass over the block's stretch [b0, b1) of the tour:
+// S[p] = sum of val over [latest head <= p, p) inside the block (the carry
+// from earlier blocks is added by the reader: it applies before the block's
+// first head).  The stretch goes in tiles of blockDim * kEuBatch positions,
+// kEuBatch consecutive ones per thread (coalesced; the values are gathered
+// once and kept in registers); a segmented block scan per tile, the block's
+// running pair carried from tile to tile.  Block pair into pv[b], pf[b];
+// first head into fh[b].
 template <typename VAL>
-__device__ inline void euler_scan_pass(const EulerKArgs &E, int64_t t0, int64_t t1, VAL val,
+__device__ inline void euler_scan_pass(const EulerKArgs &E, int64_t b0, int64_t b1, VAL val,
                                        double *pv, double *pf, double *fh) {
-    double sv = 0.0;
-    int sf = 0;
+    const int64_t tile = (int64_t)blockDim.x * kEuBatch;
+    double cv = 0.0;
+    int cfl = 0;
     long long first = LLONG_MAX;
-    for (int64_t p = t0; p < t1; p += kEuBatch) {
+    for (int64_t base = b0; base < b1; base += tile) {
+        const int64_t p0 = base + (int64_t)threadIdx.x * kEuBatch;
         int32_t tv[kEuBatch];
         uint8_t hd[kEuBatch];
         double x[kEuBatch];
 #pragma unroll
         for (int k = 0; k < kEuBatch; ++k) {
-            const bool in = p + k < t1;
-            tv[k] = in ? E.tour[p + k] : 0;
-            hd[k] = in ? E.head[p + k] : 0;
+            const bool in = p0 + k < b1;
+            tv[k] = in ? E.tour[p0 + k] : 0;
+            hd[k] = in ? E.head[p0 + k] : 0;
         }
 #pragma unroll
-        for (int k = 0; k < kEuBatch; ++k) x[k] = p + k < t1 ? val(tv[k]) : 0.0;
+        for (int k = 0; k < kEuBatch; ++k) x[k] = p0 + k < b1 ? val(tv[k]) : 0.0;
+        double sv = 0.0;
+        int sf = 0;
 #pragma unroll
         for (int k = 0; k < kEuBatch; ++k) {
             if (hd[k]) {
                 sv = 0.0;
                 sf = 1;
-                if (first == LLONG_MAX) first = p + k;
+                if (first == LLONG_MAX) first = p0 + k;
             }
             sv += x[k];
         }
-    }
-    double bv;
-    int bf;
-    double run = block_excl_seg_scan(sv, sf, &bv, &bf);
-    for (int64_t p = t0; p < t1; p += kEuBatch) {
-        int32_t tv[kEuBatch];
-        uint8_t hd[kEuBatch];
-        double x[kEuBatch];
+        int carf, tf;
+        double tvv;
+        const double carry = block_excl_seg_scan_f(sv, sf, &carf, &tvv, &tf);
+        double run = carf ? carry : cv + carry;
 #pragma unroll
         for (int k = 0; k < kEuBatch; ++k) {
-            const bool in = p + k < t1;
-            tv[k] = in ? E.tour[p + k] : 0;
-            hd[k] = in ? E.head[p + k] : 0;
+            if (p0 + k < b1) {
+                if (hd[k]) run = 0.0;
+                E.S[p0 + k] = run;
+                run += x[k];
+            }
         }
-#pragma unroll
-        for (int k = 0; k < kEuBatch; ++k) x[k] = p + k < t1 ? val(tv[k]) : 0.0;
-#pragma unroll
-        for (int k = 0; k < kEuBatch; ++k) {
-            if (p + k >= t1) break;
-            if (hd[k]) run = 0.0;
-            E.S[p + k] = run;
-            run += x[k];
-        }
+        cv = tf ? tvv : cv + tvv;
+        cfl |= tf;
     }
     // the block's first head: min over threads
     __shared__ long long s_first;
+    __syncthreads();
     if (threadIdx.x == 0) s_first = LLONG_MAX;
     __syncthreads();
     if (first != LLONG_MAX) atomicMin(&s_first, first);
     __syncthreads();
     if (threadIdx.x == 0) {
-        pv[blockIdx.x] = bv;
-        pf[blockIdx.x] = bf ? 1.0 : 0.0;
+        pv[blockIdx.x] = cv;
+        pf[blockIdx.x] = cfl ? 1.0 : 0.0;
         fh[blockIdx.x] = (double)s_first;
     }
 }
@@ -530,8 +583,6 @@ __device__ __forceinline__ bool euler_solve_dev(const EulerKArgs &E, T *Y, unsig
     const int64_t G = gridDim.x;
     const int64_t per = (E.L + G - 1) / G;
     const int64_t b0 = min(E.L, (int64_t)blockIdx.x * per), b1 = min(E.L, b0 + per);
-    const int64_t ipt = (per + blockDim.x - 1) / blockDim.x;
-    const int64_t t0 = min(b1, b0 + (int64_t)threadIdx.x * ipt), t1 = min(b1, t0 + ipt);
     const int64_t nth = (int64_t)gridDim.x * blockDim.x;
     double *pv = E.part, *pf = E.part + G, *fh = E.part + 2 * G;
     // global prefix at p: the block-local part, plus the carry from earlier
@@ -543,7 +594,7 @@ __device__ __forceinline__ bool euler_solve_dev(const EulerKArgs &E, T *Y, unsig
     // vertices in batches: thread g takes v = g + k * nth, k < kEuBatch, per round
     const int64_t vbase = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     // 1: prefix sums of b at the entries, restarting at every tree
-    euler_scan_pass(E, t0, t1, [&](int32_t v) { return v >= 0 ? (double)Y[v] : 0.0; }, pv, pf, fh);
+    euler_scan_pass(E, b0, b1, [&](int32_t v) { return v >= 0 ? (double)Y[v] : 0.0; }, pv, pf, fh);
     if (!grid_sync(bar, budget, err, epoch)) return false;
     // 2: currents c_v = (subtree sum of b) / w_v
     block_offsets_seg(pv, pf, s_off);
@@ -566,7 +617,7 @@ __device__ __forceinline__ bool euler_solve_dev(const EulerKArgs &E, T *Y, unsig
     }
     if (!grid_sync(bar, budget, err, epoch)) return false;
     // 3: prefix sums of +c at entries, -c at exits, restarting at every tree
-    euler_scan_pass(E, t0, t1, [&](int32_t v) { return v >= 0 ? E.C[v] : -E.C[-v - 1]; },
+    euler_scan_pass(E, b0, b1, [&](int32_t v) { return v >= 0 ? E.C[v] : -E.C[-v - 1]; },
                     pv + 3 * G, pf + 3 * G, fh + 3 * G);
     if (!grid_sync(bar, budget, err, epoch)) return false;
     // 4: x_v = the path sum up to and including v's entry (roots: 0)
