@@ -538,6 +538,24 @@ def run_batch(G, w=BATCH) -> dict:
     return out
 
 
+# ---------------------------------------------------------------- replicas
+
+def replica_max(dist, v: float, device: str = "cuda") -> float:
+    """Largest of v over the ranks of the process group (v itself alone)."""
+    if dist is None:
+        return v
+    import torch
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(world: int, units_per_step_per_rank: float, ms_per_step_max: float) -> float:
+    """Whole-job throughput of `world` independent replicas timed together:
+    the units all ranks processed per step over the slowest rank's step."""
+    return world * units_per_step_per_rank / (ms_per_step_max / 1e3)
+
+
 # ---------------------------------------------------------------- GPU arm
 
 def main() -> int:
@@ -624,11 +642,7 @@ def main() -> int:
         torch.cuda.synchronize()
 
     def max_over_ranks(v: float) -> float:
-        if dist is None:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return replica_max(dist, v, "cuda")
 
     if args.profile_kernel:
         return profile_kernel(G, ctx, args.profile_kernel, g, rp, col, val, v0d, w)
@@ -669,7 +683,7 @@ def main() -> int:
     G.grass_kernel_timing_enable(ctx, 0)
     ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps)
     edges_per_step = edges / args.steps
-    value = world * edges_per_step / (ms / 1e3)
+    value = replica_value(world, edges_per_step, ms)
 
     # e2e: host (pinned) inputs copied in and the result copied out, every step
     host = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
