@@ -205,7 +205,7 @@ constexpr int kRedBlocks = 608;     // 4 x 152 SMs: fixed grid for deterministic
 // spanning tree); solves keep the per-round offsets in shared memory.
 constexpr int kMaxRounds = 512;
 // shared memory for the tail of a tree solve (vertices x columns x element)
-constexpr size_t kTailSmem = 160 * 1024;
+constexpr size_t kTailSmem = 184 * 1024;   // + up to ~40 KB static shared memory <= 227 KB
 constexpr int kPersistMaxThreads = 1024;
 
 // ---------------------------------------------------------------- block layout
@@ -315,6 +315,7 @@ struct EulerTour {
     DBuf<int32_t> tour, ein, eout;
     DBuf<uint8_t> head;              // [L] 1 at each tree's first position
     DBuf<double> pw;
+    DBuf<double> ipw;                // [n] 1 / pw (roots: 1)
 };
 
 }  // namespace grass

@@ -192,7 +192,7 @@ __device__ __forceinline__ bool cg_dev(const CGArgs<T> &g, const TreeKArgs<T> &t
         if constexpr (EU) {
             if (!euler_solve_dev<T>(g.eu, g.Z, tk.bar, tk.budget, tk.err, epoch, mx)) return false;
         } else {
-            if (!tree_solve_dev<T, R>(tk, g.Z, epoch, mx, ys)) return false;
+            if (!tree_solve_dev<T, R, false>(tk, g.Z, epoch, mx, ys)) return false;
         }
         if (!grid_sync(tk.bar, tk.budget, tk.err, epoch)) return false;
 #pragma unroll
@@ -593,7 +593,7 @@ __global__ void __launch_bounds__(kPersistMaxThreads, 1)
     int k = 0;
     for (bool first = true;; first = false) {
         if constexpr (TREE_ONLY) {
-            if (!tree_solve_dev<T, 1>(tk, a.z, epoch, mx, ys)) return;
+            if (!tree_solve_dev<T, 1, false>(tk, a.z, epoch, mx, ys)) return;
         } else {
             if (!cg_dev<T, 1>(in, tk, epoch, ys)) return;
         }

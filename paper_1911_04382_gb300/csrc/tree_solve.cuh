@@ -114,12 +114,13 @@ struct BwdBatch {
     int cnt;
 };
 
-// loc != nullptr: records with tail-local ids (loc = fwd_loc / bwd_loc,
-// indexed from off0); coefficients always by global index.
+// Item i of a round: record rec[i - off0] and coefficients cf[i - off0]
+// (global arrays with off0 = 0, or the tail's shared-memory copies indexed
+// from the tail's first item).
 template <typename T>
-__device__ __forceinline__ void load_fwd(FwdBatch<T> &b, const TreeKArgs<T> &a, const int4 *rec,
-                                int64_t off0, int64_t lo, int64_t hi, int64_t slot,
-                                int64_t nslots) {
+__device__ __forceinline__ void load_fwd(FwdBatch<T> &b, const int4 *rec,
+                                         const typename PackT<T>::V2 *cf, int64_t off0, int64_t lo,
+                                         int64_t hi, int64_t slot, int64_t nslots) {
     b.cnt = 0;
     b.i0 = lo + slot;
     b.step = nslots;
@@ -128,27 +129,57 @@ __device__ __forceinline__ void load_fwd(FwdBatch<T> &b, const TreeKArgs<T> &a, 
         int64_t i = lo + slot + j * nslots;
         if (i < hi) {
             b.r[j] = rec[i - off0];
-            b.m[j] = a.fm[i];
+            b.m[j] = cf[i - off0];
             b.cnt = j + 1;
         }
     }
 }
 
 template <typename T>
-__device__ __forceinline__ void load_bwd(BwdBatch<T> &b, const TreeKArgs<T> &a, const int4 *rec,
-                                int64_t off0, int64_t lo, int64_t hi, int64_t slot,
-                                int64_t nslots) {
+__device__ __forceinline__ void load_bwd(BwdBatch<T> &b, const int4 *rec,
+                                         const typename PackT<T>::V4 *cf, int64_t off0, int64_t lo,
+                                         int64_t hi, int64_t slot, int64_t nslots) {
     b.cnt = 0;
 #pragma unroll
     for (int j = 0; j < kBatch; ++j) {
         int64_t p = lo + slot + j * nslots;
         if (p < hi) {
             b.r[j] = rec[p - off0];
-            b.c[j] = a.bc[p];
+            b.c[j] = cf[p - off0];
             b.cnt = j + 1;
         }
     }
 }
+
+// Shared-memory layout of the tail: the staged rows (ntl x R values), then
+// its forward and backward records and coefficients, each 32-byte aligned.
+template <typename T, int R>
+struct TailSmem {
+    int4 *frec, *brec;
+    typename PackT<T>::V2 *fm;
+    typename PackT<T>::V4 *bc;
+    __device__ TailSmem(T *ys, int64_t ntl, int64_t nf, int64_t nb) {
+        auto up = [](size_t x) { return (x + 31) & ~size_t(31); };
+        char *p = reinterpret_cast<char *>(ys);
+        size_t o = up((size_t)ntl * R * sizeof(T));
+        frec = reinterpret_cast<int4 *>(p + o);
+        o = up(o + (size_t)nf * sizeof(int4));
+        brec = reinterpret_cast<int4 *>(p + o);
+        o = up(o + (size_t)nb * sizeof(int4));
+        fm = reinterpret_cast<typename PackT<T>::V2 *>(p + o);
+        o = up(o + (size_t)nf * sizeof(typename PackT<T>::V2));
+        bc = reinterpret_cast<typename PackT<T>::V4 *>(p + o);
+    }
+    // bytes of the whole layout (host and device)
+    __host__ __device__ static size_t bytes(int64_t ntl, int64_t nf, int64_t nb) {
+        auto up = [](size_t x) { return (x + 31) & ~size_t(31); };
+        size_t o = up((size_t)ntl * R * sizeof(T));
+        o = up(o + (size_t)nf * sizeof(int4));
+        o = up(o + (size_t)nb * sizeof(int4));
+        o = up(o + (size_t)nf * sizeof(typename PackT<T>::V2));
+        return o + (size_t)nb * sizeof(typename PackT<T>::V4);
+    }
+};
 
 // Forward items of a batch on the vector V (global Y, or the tail's shared
 // copy with ids shifted by `base`); all gathers issued before any store.
@@ -203,7 +234,8 @@ __device__ __forceinline__ void run_fwd(const FwdBatch<T> &b, const TreeKArgs<T>
     }
 }
 
-template <typename T, int R>
+// Returns max |x| over the values written (in T's precision; 0 unless TRACK).
+template <typename T, int R, bool TRACK = true>
 __device__ __forceinline__ double run_bwd(const BwdBatch<T> &b, T *V, int64_t base, int c) {
     constexpr int EPT = Lay<R>::EPT;
     T yv[kBatch][EPT], xa[kBatch][EPT], xb[kBatch][EPT];
@@ -225,7 +257,7 @@ __device__ __forceinline__ double run_bwd(const BwdBatch<T> &b, T *V, int64_t ba
             for (int e = 0; e < EPT; ++e) xb[j][e] = pb[e];
         }
     }
-    double mx = 0.0;
+    T mx = (T)0;
 #pragma unroll
     for (int j = 0; j < kBatch; ++j) {
         if (j >= b.cnt) break;
@@ -237,17 +269,17 @@ __device__ __forceinline__ double run_bwd(const BwdBatch<T> &b, T *V, int64_t ba
             T x = cf.x * yv[j][e] + cf.y * xa[j][e];
             if (r.z >= 0) x += cf.z * xb[j][e];
             pv[e] = x;
-            mx = fmax(mx, fabs((double)x));
+            if (TRACK) mx = fmax(mx, fabs(x));
         }
     }
-    return mx;
+    return (double)mx;
 }
 
 // Solve in place on Y (n x R).  Called by every thread of a cooperative
 // grid; returns false when a barrier wait ran out (the caller must return).
 // mx accumulates max |x| over the values this thread wrote.  Ends without
 // a trailing grid barrier.
-template <typename T, int R>
+template <typename T, int R, bool TRACK = true>
 __device__ __forceinline__ bool tree_solve_dev(const TreeKArgs<T> &a, T *Y, unsigned int &epoch,
                                       double &mx, T *ys) {
     constexpr int TPR = Lay<R>::TPR;
@@ -266,43 +298,56 @@ __device__ __forceinline__ bool tree_solve_dev(const TreeKArgs<T> &a, T *Y, unsi
     // loaded before the barrier
     FwdBatch<T> fb;
     fb.cnt = 0;
-    if (a.K1 > 0) load_fwd(fb, a, a.fwd_rec, 0, s_roff[0], s_roff[1], slot, nslots);
+    if (a.K1 > 0) load_fwd(fb, a.fwd_rec, a.fm, 0, s_roff[0], s_roff[1], slot, nslots);
     for (int k = 0; k < a.K1; ++k) {
         run_fwd<T, R>(fb, a, Y, 0, false, c);
         for (int64_t lo = s_roff[k] + kBatch * nslots; lo < s_roff[k + 1]; lo += kBatch * nslots) {
             FwdBatch<T> more;
-            load_fwd(more, a, a.fwd_rec, 0, lo, s_roff[k + 1], slot, nslots);
+            load_fwd(more, a.fwd_rec, a.fm, 0, lo, s_roff[k + 1], slot, nslots);
             run_fwd<T, R>(more, a, Y, 0, false, c);
         }
-        if (k + 1 < a.K1) load_fwd(fb, a, a.fwd_rec, 0, s_roff[k + 1], s_roff[k + 2], slot, nslots);
+        if (k + 1 < a.K1) load_fwd(fb, a.fwd_rec, a.fm, 0, s_roff[k + 1], s_roff[k + 2], slot, nslots);
         if (!grid_sync(a.bar, a.budget, a.err, epoch)) return false;
     }
-    // rounds K1 .. end in block 0, on the tail vertices staged in shared memory
+    // rounds K1 .. end in block 0, on the tail vertices staged in shared
+    // memory together with the tail's records and coefficients (one bulk
+    // copy; each round then runs from shared memory alone)
     if (blockIdx.x == 0) {
         const int64_t bslot = threadIdx.x / TPR, bslots = blockDim.x / TPR;
         const int64_t base = a.base, ntl = a.ntl;
+        const int64_t f0 = s_roff[a.K1], f1 = s_roff[a.rounds];
+        const int64_t g0 = s_eoff[a.K1], g1 = s_eoff[a.rounds];
+        const TailSmem<T, R> sm(ys, ntl, f1 - f0, g1 - g0);
+        for (int64_t idx = threadIdx.x; idx < ntl * R; idx += blockDim.x)
+            ys[idx] = Y[(int64_t)a.tail_vid[base + idx / R] * R + idx % R];
+        for (int64_t i = threadIdx.x; i < f1 - f0; i += blockDim.x) {
+            sm.frec[i] = a.fwd_loc[f0 - a.r0 + i];
+            sm.fm[i] = a.fm[f0 + i];
+        }
+        for (int64_t i = threadIdx.x; i < g1 - g0; i += blockDim.x) {
+            sm.brec[i] = a.bwd_loc[g0 - a.e0 + i];
+            sm.bc[i] = a.bc[g0 + i];
+        }
+        __syncthreads();
         FwdBatch<T> tb;
         tb.cnt = 0;
         if (a.K1 < a.rounds)
-            load_fwd(tb, a, a.fwd_loc, a.r0, s_roff[a.K1], s_roff[a.K1 + 1], bslot, bslots);
-        for (int64_t idx = threadIdx.x; idx < ntl * R; idx += blockDim.x)
-            ys[idx] = Y[(int64_t)a.tail_vid[base + idx / R] * R + idx % R];
-        __syncthreads();
+            load_fwd(tb, sm.frec, sm.fm, f0, s_roff[a.K1], s_roff[a.K1 + 1], bslot, bslots);
         for (int k = a.K1; k < a.rounds; ++k) {
             run_fwd<T, R>(tb, a, ys, base, true, c);
             for (int64_t lo = s_roff[k] + kBatch * bslots; lo < s_roff[k + 1]; lo += kBatch * bslots) {
                 FwdBatch<T> more;
-                load_fwd(more, a, a.fwd_loc, a.r0, lo, s_roff[k + 1], bslot, bslots);
+                load_fwd(more, sm.frec, sm.fm, f0, lo, s_roff[k + 1], bslot, bslots);
                 run_fwd<T, R>(more, a, ys, base, true, c);
             }
             if (k + 1 < a.rounds)
-                load_fwd(tb, a, a.fwd_loc, a.r0, s_roff[k + 1], s_roff[k + 2], bslot, bslots);
+                load_fwd(tb, sm.frec, sm.fm, f0, s_roff[k + 1], s_roff[k + 2], bslot, bslots);
             __syncthreads();
         }
         BwdBatch<T> bb;
         bb.cnt = 0;
         if (a.K1 < a.rounds)
-            load_bwd(bb, a, a.bwd_loc, a.e0, s_eoff[a.rounds - 1], s_eoff[a.rounds], bslot, bslots);
+            load_bwd(bb, sm.brec, sm.bc, g0, s_eoff[a.rounds - 1], s_eoff[a.rounds], bslot, bslots);
         for (int64_t q = bslot; q < a.nroots; q += bslots) {
             constexpr int EPT = Lay<R>::EPT;
             T *yr = ys + (ntl - a.nroots + q) * R + c * EPT;   // the roots come last
@@ -312,36 +357,40 @@ __device__ __forceinline__ bool tree_solve_dev(const TreeKArgs<T> &a, T *Y, unsi
         }
         __syncthreads();
         for (int k = a.rounds - 1; k >= a.K1; --k) {
-            run_bwd<T, R>(bb, ys, base, c);
+            run_bwd<T, R, false>(bb, ys, base, c);
             for (int64_t lo = s_eoff[k] + kBatch * bslots; lo < s_eoff[k + 1]; lo += kBatch * bslots) {
                 BwdBatch<T> more;
-                load_bwd(more, a, a.bwd_loc, a.e0, lo, s_eoff[k + 1], bslot, bslots);
-                run_bwd<T, R>(more, ys, base, c);
+                load_bwd(more, sm.brec, sm.bc, g0, lo, s_eoff[k + 1], bslot, bslots);
+                run_bwd<T, R, false>(more, ys, base, c);
             }
             if (k - 1 >= a.K1)
-                load_bwd(bb, a, a.bwd_loc, a.e0, s_eoff[k - 1], s_eoff[k], bslot, bslots);
+                load_bwd(bb, sm.brec, sm.bc, g0, s_eoff[k - 1], s_eoff[k], bslot, bslots);
             __syncthreads();
         }
+        T tm = (T)0;
         for (int64_t idx = threadIdx.x; idx < ntl * R; idx += blockDim.x) {
             T v = ys[idx];
             Y[(int64_t)a.tail_vid[base + idx / R] * R + idx % R] = v;
-            mx = fmax(mx, fabs((double)v));
+            if (TRACK) tm = fmax(tm, fabs(v));
         }
+        if (TRACK) mx = fmax(mx, (double)tm);
     }
     // rounds K1-1 .. 0 backward across the grid
     BwdBatch<T> gb;
     gb.cnt = 0;
-    if (a.K1 > 0) load_bwd(gb, a, a.bwd_rec, 0, s_eoff[a.K1 - 1], s_eoff[a.K1], slot, nslots);
+    if (a.K1 > 0) load_bwd(gb, a.bwd_rec, a.bc, 0, s_eoff[a.K1 - 1], s_eoff[a.K1], slot, nslots);
     if (a.K1 > 0 && !grid_sync(a.bar, a.budget, a.err, epoch)) return false;
     for (int k = a.K1 - 1; k >= 0; --k) {
-        mx = fmax(mx, run_bwd<T, R>(gb, Y, 0, c));
+        if (TRACK) mx = fmax(mx, run_bwd<T, R, TRACK>(gb, Y, 0, c));
+        else run_bwd<T, R, false>(gb, Y, 0, c);
         for (int64_t lo = s_eoff[k] + kBatch * nslots; lo < s_eoff[k + 1]; lo += kBatch * nslots) {
             BwdBatch<T> more;
-            load_bwd(more, a, a.bwd_rec, 0, lo, s_eoff[k + 1], slot, nslots);
-            mx = fmax(mx, run_bwd<T, R>(more, Y, 0, c));
+            load_bwd(more, a.bwd_rec, a.bc, 0, lo, s_eoff[k + 1], slot, nslots);
+            if (TRACK) mx = fmax(mx, run_bwd<T, R, TRACK>(more, Y, 0, c));
+            else run_bwd<T, R, false>(more, Y, 0, c);
         }
         if (k > 0) {
-            load_bwd(gb, a, a.bwd_rec, 0, s_eoff[k - 1], s_eoff[k], slot, nslots);
+            load_bwd(gb, a.bwd_rec, a.bc, 0, s_eoff[k - 1], s_eoff[k], slot, nslots);
             if (!grid_sync(a.bar, a.budget, a.err, epoch)) return false;
         }
     }
@@ -361,7 +410,7 @@ struct EulerKArgs {
     int64_t L, n;
     const int32_t *tour, *ein, *eout;
     const uint8_t *head;    // [L] 1 at the first position of every tree's tour
-    const double *pw;
+    const double *ipw;      // [n] 1 / weight of v's parent edge
     double *S, *C, *part;   // [L], [n], [6 * gridDim.x]
 };
 
@@ -587,8 +636,11 @@ __device__ __forceinline__ bool euler_solve_dev(const EulerKArgs &E, T *Y, unsig
     double *pv = E.part, *pf = E.part + G, *fh = E.part + 2 * G;
     // global prefix at p: the block-local part, plus the carry from earlier
     // blocks while p lies before the block's first head
+    // block of a position: 32-bit division (positions < 2^31; 64-bit integer
+    // division is emulated and was a third of phase 2)
+    const uint32_t per32 = (uint32_t)per;
     auto glob = [&](int64_t p, const double *fhp) {
-        const int64_t b = p / per;
+        const uint32_t b = (uint32_t)p / per32;
         return E.S[p] + ((double)p < fhp[b] ? s_off[b] : 0.0);
     };
     // vertices in batches: thread g takes v = g + k * nth, k < kEuBatch, per round
@@ -612,7 +664,7 @@ __device__ __forceinline__ bool euler_solve_dev(const EulerKArgs &E, T *Y, unsig
 #pragma unroll
         for (int k = 0; k < kEuBatch; ++k) {
             const int64_t v = v0 + k * nth;
-            if (v < E.n) E.C[v] = in[k] >= 0 ? d[k] / E.pw[v] : 0.0;
+            if (v < E.n) E.C[v] = in[k] >= 0 ? d[k] * E.ipw[v] : 0.0;
         }
     }
     if (!grid_sync(bar, budget, err, epoch)) return false;
@@ -657,7 +709,7 @@ inline void euler_kargs(grass_ctx_t ctx, const grass_tree_s *Tr, int grid, Euler
     e->ein = E.ein.p;
     e->eout = E.eout.p;
     e->head = E.head.p;
-    e->pw = E.pw.p;
+    e->ipw = E.ipw.p;
     e->S = ctx->scr<double>(SCR_EU_S, E.L + 1);
     e->C = ctx->scr<double>(SCR_EU_C, Tr->g.n);
     e->part = ctx->scr<double>(SCR_EU_P, 6 * (size_t)grid + 2);
@@ -695,12 +747,17 @@ inline TreeKArgs<T> tree_kargs(grass_ctx_t ctx, const grass_tree_s *Tr, const Tr
                                size_t *smem) {
     const TreeSchedule &S = Tr->sched;
     auto alive_at = [&](int k) { return S.tail_n - (S.elim_off[k] - S.elim_off[S.tail_k0]); };
+    // the tail's rows and its records / coefficients must fit the budget
+    auto tail_bytes = [&](int k) {
+        return TailSmem<T, R>::bytes(alive_at(k), S.rcv_off[S.rounds] - S.rcv_off[k],
+                                     S.elim_off[S.rounds] - S.elim_off[k]);
+    };
     int K1 = S.tail_k0;
-    while (K1 < S.rounds && ((size_t)alive_at(K1) * R * sizeof(T) > kTailSmem ||
+    while (K1 < S.rounds && (tail_bytes(K1) > kTailSmem ||
                              alive_at(K1) > std::max<int64_t>(ctx->tree_tail_items, 1)))
         ++K1;
     const int64_t ntl = alive_at(K1);
-    *smem = (size_t)ntl * R * sizeof(T);
+    *smem = tail_bytes(K1);
     TreeKArgs<T> ka;
     ka.rounds = S.rounds;
     ka.K1 = K1;
