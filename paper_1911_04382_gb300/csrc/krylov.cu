@@ -113,6 +113,36 @@ struct CGArgs {
     EulerKArgs eu;               // scan-form tree solve (r = 1, no D)
 };
 
+// A thread's dot-product accumulator.  Double vectors: an FP64 sum, as in
+// the plain definition.  Float vectors: a pair of floats, the running sum and
+// its accumulated error, adding the exact rounding error of every product
+// (an FMA) and of every sum (two-sum): about 48 significant bits per thread
+// with no FP64 arithmetic per element (on GB300 FP64 runs at a small
+// fraction of the FP32 rate and was most of the time of the vector phases).
+// Partials go on to the FP64 block and grid sums.
+template <typename T>
+struct Acc;
+template <>
+struct Acc<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add_prod(double a, double b) { s += a * b; }
+    __device__ __forceinline__ double value() const { return s; }
+};
+template <>
+struct Acc<float> {
+    float hi = 0.f, lo = 0.f;
+    __device__ __forceinline__ void add_prod(float a, float b) {
+        const float p = __fmul_rn(a, b);
+        const float pe = __fmaf_rn(a, b, -p);   // a b = p + pe exactly
+        const float t = __fadd_rn(hi, p);
+        const float bp = __fsub_rn(t, hi);
+        const float se = __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bp)), __fsub_rn(p, bp));   // hi + p = t + se
+        hi = t;
+        lo = __fadd_rn(lo, __fadd_rn(se, pe));
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
 // Per-block column sums of the thread partials v[e] (column c*EPT + e),
 // written to out[0..R): lanes sharing c fold together (xor offsets >= TPR),
 // then one thread per column adds the warps in order.
@@ -134,6 +164,15 @@ __device__ __forceinline__ void block_cols(const double (&v)[Lay<R>::EPT], int c
         out[threadIdx.x] = s;
     }
     __syncthreads();
+}
+
+template <int R, typename T>
+__device__ __forceinline__ void block_cols(const Acc<T> (&a)[Lay<R>::EPT], int c,
+                                           double (*s_red)[32], double *out) {
+    double v[Lay<R>::EPT];
+#pragma unroll
+    for (int e = 0; e < Lay<R>::EPT; ++e) v[e] = a[e].value();
+    block_cols<R>(v, c, s_red, out);
 }
 
 // Column sums over all blocks' partials (same order in every block): warp j
@@ -166,7 +205,8 @@ __device__ __forceinline__ bool cg_dev(const CGArgs<T> &g, const TreeKArgs<T> &t
     const int64_t slot = gt / TPR, nslots = (int64_t)gridDim.x * blockDim.x / TPR;
     double *part0 = g.part, *part1 = g.part + (int64_t)gridDim.x * 32;
     double *mypart0 = part0 + (int64_t)blockIdx.x * 32, *mypart1 = part1 + (int64_t)blockIdx.x * 32;
-    double mx = 0.0, acc0[EPT], acc1[EPT];
+    double mx = 0.0;
+    Acc<T> acc0[EPT], acc1[EPT];
 
     for (int64_t i = slot; i < g.n; i += nslots) {
 #pragma unroll
@@ -196,16 +236,16 @@ __device__ __forceinline__ bool cg_dev(const CGArgs<T> &g, const TreeKArgs<T> &t
         }
         if (!grid_sync(tk.bar, tk.budget, tk.err, epoch)) return false;
 #pragma unroll
-        for (int e = 0; e < EPT; ++e) acc0[e] = acc1[e] = 0.0;
+        for (int e = 0; e < EPT; ++e) acc0[e] = acc1[e] = Acc<T>();
         for (int64_t i = slot; i < g.n; i += nslots) {
 #pragma unroll
             for (int e = 0; e < EPT; ++e) {
                 int64_t k = i * R + c * EPT + e;
                 T z = g.Z[k], rr = g.Rv[k];
-                acc0[e] += (double)rr * (double)z;
+                acc0[e].add_prod(rr, z);
                 if (it == 0) {
                     g.P[k] = z;
-                    acc1[e] += (double)rr * (double)rr;
+                    acc1[e].add_prod(rr, rr);
                 }
             }
         }
@@ -251,7 +291,7 @@ __device__ __forceinline__ bool cg_dev(const CGArgs<T> &g, const TreeKArgs<T> &t
         if (s_nact == 0) break;
         // Q = L_S P (+D), partial P.Q
 #pragma unroll
-        for (int e = 0; e < EPT; ++e) acc0[e] = 0.0;
+        for (int e = 0; e < EPT; ++e) acc0[e] = Acc<T>();
         for (int64_t i = slot; i < g.n; i += nslots) {
             T p0[EPT], q[EPT];
 #pragma unroll
@@ -273,7 +313,7 @@ __device__ __forceinline__ bool cg_dev(const CGArgs<T> &g, const TreeKArgs<T> &t
 #pragma unroll
             for (int e = 0; e < EPT; ++e) {
                 g.Q[i * R + c * EPT + e] = q[e];
-                acc0[e] += (double)p0[e] * (double)q[e];
+                acc0[e].add_prod(p0[e], q[e]);
             }
         }
         block_cols<R>(acc0, c, s_red, mypart0);
@@ -292,7 +332,7 @@ __device__ __forceinline__ bool cg_dev(const CGArgs<T> &g, const TreeKArgs<T> &t
         __syncthreads();
         // X += alpha P, R -= alpha Q, Z = R, partial R.R
 #pragma unroll
-        for (int e = 0; e < EPT; ++e) acc1[e] = 0.0;
+        for (int e = 0; e < EPT; ++e) acc1[e] = Acc<T>();
         for (int64_t i = slot; i < g.n; i += nslots) {
 #pragma unroll
             for (int e = 0; e < EPT; ++e) {
@@ -305,7 +345,7 @@ __device__ __forceinline__ bool cg_dev(const CGArgs<T> &g, const TreeKArgs<T> &t
                     g.Rv[k] = rr;
                 }
                 g.Z[k] = rr;
-                acc1[e] += (double)rr * (double)rr;
+                acc1[e].add_prod(rr, rr);
             }
         }
         block_cols<R>(acc1, c, s_red, mypart1);
@@ -562,6 +602,8 @@ struct PCGArgs {
     double *out;                  // [0] += iterations, [1] = final r.r
 };
 
+constexpr int kU = 4;   // elements per thread with their loads in flight together
+
 template <typename T, bool TREE_ONLY>
 __global__ void __launch_bounds__(kPersistMaxThreads, 1)
     k_pcg_persist(PCGArgs<T> a, CGArgs<T> in, TreeKArgs<T> tk) {
@@ -575,14 +617,24 @@ __global__ void __launch_bounds__(kPersistMaxThreads, 1)
     const int64_t nth = (int64_t)gridDim.x * blockDim.x;
     double *P0 = a.part, *P1 = a.part + (int64_t)gridDim.x * 32;
     double *my0 = P0 + (int64_t)blockIdx.x * 32, *my1 = P1 + (int64_t)blockIdx.x * 32;
-    double acc0[1], acc1[1];
+    Acc<T> acc0[1], acc1[1];
 
     // e = 0, r = rhs (z = rhs for the tree solve)
-    for (int64_t i = gt; i < a.n; i += nth) {
-        T y = a.rhs[i];
-        a.e[i] = (T)0;
-        a.r[i] = y;
-        if (TREE_ONLY) a.z[i] = y;
+    for (int64_t i0 = gt; i0 < a.n; i0 += kU * nth) {
+        T yv[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int64_t i = i0 + u * nth;
+            yv[u] = i < a.n ? a.rhs[i] : (T)0;
+        }
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int64_t i = i0 + u * nth;
+            if (i >= a.n) continue;
+            a.e[i] = (T)0;
+            a.r[i] = yv[u];
+            if (TREE_ONLY) a.z[i] = yv[u];
+        }
     }
     if (!grid_sync(tk.bar, tk.budget, tk.err, epoch)) return;
     // Each pass starts with z = M^{-1} r (the only call site of the
@@ -599,12 +651,25 @@ __global__ void __launch_bounds__(kPersistMaxThreads, 1)
         }
         if (!grid_sync(tk.bar, tk.budget, tk.err, epoch)) return;
         // first: rz = r.z, rr = r.r;  later: r.z and r.z_old for beta
-        acc0[0] = acc1[0] = 0.0;
-        for (int64_t i = gt; i < a.n; i += nth) {
-            const double ri = (double)a.r[i];
-            acc0[0] += ri * (double)a.z[i];
-            if (first) acc1[0] += ri * ri;
-            else if (!TREE_ONLY) acc1[0] += ri * (double)a.zo[i];
+        acc0[0] = acc1[0] = Acc<T>();
+        // element loops take kU elements per thread at a time: all loads
+        // first, then the arithmetic and the stores (same order of sums)
+        for (int64_t i0 = gt; i0 < a.n; i0 += kU * nth) {
+            T rv[kU], zv[kU], ov[kU];
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const int64_t i = i0 + u * nth;
+                const bool in = i < a.n;
+                rv[u] = in ? a.r[i] : (T)0;
+                zv[u] = in ? a.z[i] : (T)0;
+                ov[u] = in && !first && !TREE_ONLY ? a.zo[i] : (T)0;
+            }
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                acc0[0].add_prod(rv[u], zv[u]);
+                if (first) acc1[0].add_prod(rv[u], rv[u]);
+                else if (!TREE_ONLY) acc1[0].add_prod(rv[u], ov[u]);
+            }
         }
         block_cols<1>(acc0, 0, s_red, my0);
         block_cols<1>(acc1, 0, s_red, my1);
@@ -616,31 +681,61 @@ __global__ void __launch_bounds__(kPersistMaxThreads, 1)
         if (first) rr = s_v[1];
         else beta = (T)((rzn - (TREE_ONLY ? 0.0 : s_v[1])) / rz);
         rz = rzn;
-        for (int64_t i = gt; i < a.n; i += nth) a.p[i] = first ? a.z[i] : a.z[i] + beta * a.p[i];
+        for (int64_t i0 = gt; i0 < a.n; i0 += kU * nth) {
+            T zv[kU], pv[kU];
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const int64_t i = i0 + u * nth;
+                const bool in = i < a.n;
+                zv[u] = in ? a.z[i] : (T)0;
+                pv[u] = in && !first ? a.p[i] : (T)0;
+            }
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const int64_t i = i0 + u * nth;
+                if (i < a.n) a.p[i] = first ? zv[u] : zv[u] + beta * pv[u];
+            }
+        }
         if (!grid_sync(tk.bar, tk.budget, tk.err, epoch)) return;
         if (k >= a.maxit || sqrt(rr) <= a.tol_abs) break;
         // q = A p, pq
-        acc0[0] = 0.0;
+        acc0[0] = Acc<T>();
         for (int64_t i = gt; i < a.n; i += nth) {
             const T pi = a.p[i];
             T qi = a.aD[i] * pi;
             for (int32_t j = a.aptr[i]; j < a.aptr[i + 1]; ++j) qi += a.aw[j] * (pi - a.p[a.acol[j]]);
             a.q[i] = qi;
-            acc0[0] += (double)pi * (double)qi;
+            acc0[0].add_prod(pi, qi);
         }
         block_cols<1>(acc0, 0, s_red, my0);
         if (!grid_sync(tk.bar, tk.budget, tk.err, epoch)) return;
         grid_cols<1>(P0, &s_v[2]);
         const T alpha = (T)(rz / s_v[2]);
         // e += alpha p, r -= alpha q (z_old = z; z = r for the tree solve), rr
-        acc1[0] = 0.0;
-        for (int64_t i = gt; i < a.n; i += nth) {
-            a.e[i] += alpha * a.p[i];
-            T ri = a.r[i] - alpha * a.q[i];
-            a.r[i] = ri;
-            if (!TREE_ONLY) a.zo[i] = a.z[i];
-            if (TREE_ONLY) a.z[i] = ri;
-            acc1[0] += (double)ri * (double)ri;
+        acc1[0] = Acc<T>();
+        for (int64_t i0 = gt; i0 < a.n; i0 += kU * nth) {
+            T ev[kU], pv[kU], rv[kU], qv[kU], zv[kU];
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const int64_t i = i0 + u * nth;
+                const bool in = i < a.n;
+                ev[u] = in ? a.e[i] : (T)0;
+                pv[u] = in ? a.p[i] : (T)0;
+                rv[u] = in ? a.r[i] : (T)0;
+                qv[u] = in ? a.q[i] : (T)0;
+                zv[u] = in && !TREE_ONLY ? a.z[i] : (T)0;
+            }
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const int64_t i = i0 + u * nth;
+                if (i >= a.n) continue;
+                a.e[i] = ev[u] + alpha * pv[u];
+                const T ri = rv[u] - alpha * qv[u];
+                a.r[i] = ri;
+                if (!TREE_ONLY) a.zo[i] = zv[u];
+                if (TREE_ONLY) a.z[i] = ri;
+                acc1[0].add_prod(ri, ri);
+            }
         }
         block_cols<1>(acc1, 0, s_red, my1);
         if (!grid_sync(tk.bar, tk.budget, tk.err, epoch)) return;
