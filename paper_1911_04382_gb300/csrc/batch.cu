@@ -216,15 +216,15 @@ __global__ void k_b_matvec(const int64_t *cbeg, const int32_t *cseg, const int *
         if (threadIdx.x == 0) part[c] = 0.0;
         return;
     }
-    double acc = 0.0;
+    Acc<T> ac;
     for (int64_t i = cbeg[c] + threadIdx.x; i < cbeg[c + 1]; i += blockDim.x) {
         const T pi = P[i];
         T q = A.D ? A.D[i] * pi : (T)0;
         for (int32_t j = A.ptr[i]; j < A.ptr[i + 1]; ++j) q += A.w[j] * (pi - P[A.col[j]]);
         Q[i] = q;
-        acc += (double)pi * (double)q;
+        ac.add_prod(pi, q);
     }
-    acc = block_sum(acc, sh);
+    const double acc = block_sum(ac.value(), sh);
     if (threadIdx.x == 0) part[c] = acc;
 }
 
@@ -241,15 +241,15 @@ __global__ void k_b_update(const int64_t *cbeg, const int32_t *cseg, const int *
         return;
     }
     const T a = (T)alpha[k];
-    double acc = 0.0;
+    Acc<T> ac;
     for (int64_t i = cbeg[c] + threadIdx.x; i < cbeg[c + 1]; i += blockDim.x) {
         X[i] += a * P[i];
         T r = R[i] - a * Q[i];
         R[i] = r;
         Z[i] = r;
-        acc += (double)r * (double)r;
+        ac.add_prod(r, r);
     }
-    acc = block_sum(acc, sh);
+    const double acc = block_sum(ac.value(), sh);
     if (threadIdx.x == 0) part[c] = acc;
 }
 
@@ -263,14 +263,14 @@ __global__ void k_b_dot2(const int64_t *cbeg, const int32_t *cseg, const int *ac
         if (threadIdx.x == 0) part[2 * c] = part[2 * c + 1] = 0.0;
         return;
     }
-    double a = 0.0, b = 0.0;
+    Acc<T> aa, ab;
     for (int64_t i = cbeg[c] + threadIdx.x; i < cbeg[c + 1]; i += blockDim.x) {
-        const double r = (double)R[i];
-        a += r * (double)Z[i];
-        if (Zo) b += r * (double)Zo[i];
+        const T r = R[i];
+        aa.add_prod(r, Z[i]);
+        if (Zo) ab.add_prod(r, Zo[i]);
     }
-    a = block_sum(a, sh);
-    b = block_sum(b, sh);
+    const double a = block_sum(aa.value(), sh);
+    const double b = block_sum(ab.value(), sh);
     if (threadIdx.x == 0) {
         part[2 * c] = a;
         part[2 * c + 1] = b;

@@ -316,6 +316,7 @@ struct EulerTour {
     DBuf<uint8_t> head;              // [L] 1 at each tree's first position
     DBuf<double> pw;
     DBuf<double> ipw;                // [n] 1 / pw (roots: 1)
+    DBuf<float> ipw32;
 };
 
 }  // namespace grass
@@ -445,6 +446,36 @@ void sparsifier_add(grass_ctx_t ctx, grass_sparsifier_t S, const int64_t *eids, 
 void lambda_min(grass_ctx_t ctx, grass_sparsifier_t S, double *out_host);
 int64_t filter_heat(grass_ctx_t ctx, grass_sparsifier_t S, const void *heat, grass_prec prec,
                     double thr, int64_t cap, int64_t *accepted);
+
+// A thread's dot-product accumulator.  Double vectors: an FP64 sum, as in
+// the plain definition.  Float vectors: a pair of floats, the running sum and
+// its accumulated error, adding the exact rounding error of every product
+// (an FMA) and of every sum (two-sum): about 48 significant bits per thread
+// with no FP64 arithmetic per element (on GB300 FP64 runs at a small
+// fraction of the FP32 rate and was most of the time of the vector phases).
+// Partials go on to the FP64 block and grid sums.
+template <typename T>
+struct Acc;
+template <>
+struct Acc<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add_prod(double a, double b) { s += a * b; }
+    __device__ __forceinline__ double value() const { return s; }
+};
+template <>
+struct Acc<float> {
+    float hi = 0.f, lo = 0.f;
+    __device__ __forceinline__ void add_prod(float a, float b) {
+        const float p = __fmul_rn(a, b);
+        const float pe = __fmaf_rn(a, b, -p);   // a b = p + pe exactly
+        const float t = __fadd_rn(hi, p);
+        const float bp = __fsub_rn(t, hi);
+        const float se = __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bp)), __fsub_rn(p, bp));   // hi + p = t + se
+        hi = t;
+        lo = __fadd_rn(lo, __fadd_rn(se, pe));
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
 
 // ---------------------------------------------------------------- grid barrier
 // Barrier for cooperative (co-resident) launches.  bar[0] counts arrivals,

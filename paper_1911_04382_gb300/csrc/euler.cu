@@ -110,9 +110,12 @@ __global__ void k_eu_final(int64_t mt, const int32_t *es, const int32_t *owner, 
 
 // roots have no entry; every tree's tour starts at 2 (voff[k] - k) (0 for
 // a single tree): a head of the segmented scans
-__global__ void k_eu_inv(int64_t n, const double *pw, double *ipw) {
+__global__ void k_eu_inv(int64_t n, const double *pw, double *ipw, float *ipw32) {
     int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (v < n) ipw[v] = 1.0 / pw[v];
+    if (v >= n) return;
+    const double r = 1.0 / pw[v];
+    ipw[v] = r;
+    ipw32[v] = (float)r;
 }
 
 __global__ void k_eu_roots(int64_t nr, const int32_t *roots, const int64_t *voff, int32_t *ein,
@@ -180,7 +183,8 @@ void euler_build(grass_ctx_t ctx, grass_tree_t T, const int32_t *tptr, const int
            (const int32_t *)T->roots.p, g.nseg > 1 ? (const int64_t *)g.seg_voff_d.p : nullptr,
            E.ein.p, E.eout.p, E.pw.p, E.head.p);
     E.ipw.alloc(n);
-    launch(ctx, k_eu_inv, cdiv(n, kBlock), kBlock, 0, n, (const double *)E.pw.p, E.ipw.p);
+    E.ipw32.alloc(n);
+    launch(ctx, k_eu_inv, cdiv(n, kBlock), kBlock, 0, n, (const double *)E.pw.p, E.ipw.p, E.ipw32.p);
     E.built = true;
 }
 

@@ -113,36 +113,6 @@ struct CGArgs {
     EulerKArgs eu;               // scan-form tree solve (r = 1, no D)
 };
 
-// A thread's dot-product accumulator.  Double vectors: an FP64 sum, as in
-// the plain definition.  Float vectors: a pair of floats, the running sum and
-// its accumulated error, adding the exact rounding error of every product
-// (an FMA) and of every sum (two-sum): about 48 significant bits per thread
-// with no FP64 arithmetic per element (on GB300 FP64 runs at a small
-// fraction of the FP32 rate and was most of the time of the vector phases).
-// Partials go on to the FP64 block and grid sums.
-template <typename T>
-struct Acc;
-template <>
-struct Acc<double> {
-    double s = 0.0;
-    __device__ __forceinline__ void add_prod(double a, double b) { s += a * b; }
-    __device__ __forceinline__ double value() const { return s; }
-};
-template <>
-struct Acc<float> {
-    float hi = 0.f, lo = 0.f;
-    __device__ __forceinline__ void add_prod(float a, float b) {
-        const float p = __fmul_rn(a, b);
-        const float pe = __fmaf_rn(a, b, -p);   // a b = p + pe exactly
-        const float t = __fadd_rn(hi, p);
-        const float bp = __fsub_rn(t, hi);
-        const float se = __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bp)), __fsub_rn(p, bp));   // hi + p = t + se
-        hi = t;
-        lo = __fadd_rn(lo, __fadd_rn(se, pe));
-    }
-    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
-};
-
 // Per-block column sums of the thread partials v[e] (column c*EPT + e),
 // written to out[0..R): lanes sharing c fold together (xor offsets >= TPR),
 // then one thread per column adds the warps in order.
@@ -425,7 +395,7 @@ static void cg_persistent(grass_ctx_t ctx, grass_sparsifier_t S, bool with_D, co
     const int grid = eu ? coop_grid(ctx, k_cg_persist<T, R, (R == 1)>, threads, smem, n * Lay<R>::TPR)
                         : coop_grid(ctx, k_cg_persist<T, R, false>, threads, smem, n * Lay<R>::TPR);
     if ((size_t)grid * 32 * 2 > ctx->partials.n) fail(GRASS_ERR_CUDA, "partials buffer too small");
-    if (eu) euler_kargs(ctx, Tr, grid, &a.eu);
+    if (eu) euler_kargs<T>(ctx, Tr, grid, &a.eu);
     GCK(cudaMemsetAsync(tk.bar, 0, sizeof(unsigned int), ctx->stream));
     // roofline accounting: algorithmic bytes per iteration and of the start
     const TreeSchedule &TS = Tr->sched;

@@ -94,7 +94,7 @@ static void solve_T(grass_ctx_t ctx, grass_tree_t Tr, const TreeFactor &f, T *Y,
     if (R == 1 && &f == &Tr->lap && ctx->euler_solve && Tr->euler.built) {
         const int grid = coop_grid(ctx, k_euler_persist<T>, threads, 0, Tr->g.n);
         EulerKArgs e;
-        euler_kargs(ctx, Tr, grid, &e);
+        euler_kargs<T>(ctx, Tr, grid, &e);
         GCK(cudaMemsetAsync(a.bar, 0, sizeof(unsigned int), ctx->stream));
         void *eargs[] = {&e, &a, &Y, &maxbits};
         GCK(cudaLaunchCooperativeKernel((const void *)k_euler_persist<T>, dim3(grid),

@@ -410,35 +410,97 @@ struct EulerKArgs {
     int64_t L, n;
     const int32_t *tour, *ein, *eout;
     const uint8_t *head;    // [L] 1 at the first position of every tree's tour
-    const double *ipw;      // [n] 1 / weight of v's parent edge
-    double *S, *C, *part;   // [L], [n], [6 * gridDim.x]
+    const void *ipw;        // [n] 1 / weight of v's parent edge (T)
+    void *S, *C;            // [L] prefix sums (SumOf<T>), [n] currents (T)
+    double *part;           // [6 * gridDim.x]: block pairs and first heads
 };
 
 constexpr int kEulerMaxGrid = 2048;
 
+// Prefix sums of the scan form.  Double vectors: FP64.  Float vectors: a
+// float pair (sum and error, two-sum on every add), about 44 significant
+// bits, enough for the subtree sums taken as differences of prefix sums,
+// with no FP64 arithmetic per tour position.
+struct DF {
+    float hi, lo;
+};
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+    const float s = __fadd_rn(a.hi, b.hi);
+    const float bb = __fsub_rn(s, a.hi);
+    float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+    e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+    const float hi = __fadd_rn(s, e);
+    return DF{hi, __fsub_rn(e, __fsub_rn(hi, s))};
+}
+template <typename T>
+struct SumOf {
+    using type = double;
+};
+template <>
+struct SumOf<float> {
+    using type = DF;
+};
+__device__ __forceinline__ double s_add(double a, double b) { return a + b; }
+__device__ __forceinline__ DF s_add(DF a, DF b) { return df_add(a, b); }
+__device__ __forceinline__ double s_sub(double a, double b) { return a - b; }
+__device__ __forceinline__ DF s_sub(DF a, DF b) { return df_add(a, DF{-b.hi, -b.lo}); }
+template <typename V>
+__device__ __forceinline__ V s_from(double x);
+template <>
+__device__ __forceinline__ double s_from<double>(double x) { return x; }
+template <>
+__device__ __forceinline__ DF s_from<DF>(double x) {
+    const float h = (float)x;
+    return DF{h, (float)(x - (double)h)};
+}
+__device__ __forceinline__ DF s_from_f(float x) { return DF{x, 0.f}; }
+__device__ __forceinline__ double s_val(double a) { return a; }
+__device__ __forceinline__ double s_val(DF a) { return (double)a.hi + (double)a.lo; }
+// to the vector precision (float pairs round to float without FP64 work)
+__device__ __forceinline__ double s_to(double a) { return a; }
+__device__ __forceinline__ float s_to(DF a) { return __fadd_rn(a.hi, a.lo); }
+__device__ __forceinline__ double s_shfl_up(double v, int d) { return __shfl_up_sync(0xffffffffu, v, d); }
+__device__ __forceinline__ DF s_shfl_up(DF v, int d) {
+    return DF{__shfl_up_sync(0xffffffffu, v.hi, d), __shfl_up_sync(0xffffffffu, v.lo, d)};
+}
+__device__ __forceinline__ double s_shfl(double v, int l) { return __shfl_sync(0xffffffffu, v, l); }
+__device__ __forceinline__ DF s_shfl(DF v, int l) {
+    return DF{__shfl_sync(0xffffffffu, v.hi, l), __shfl_sync(0xffffffffu, v.lo, l)};
+}
+template <typename V>
+__device__ __forceinline__ V s_zero() {
+    return s_from<V>(0.0);
+}
+template <typename V, typename T>
+__device__ __forceinline__ V s_of(T x);
+template <>
+__device__ __forceinline__ double s_of<double, double>(double x) { return x; }
+template <>
+__device__ __forceinline__ DF s_of<DF, float>(float x) { return DF{x, 0.f}; }
+
 // Segmented sums: a pair (v, f) is a sum v that restarts at a head when f;
 // combining a left pair with a right one gives (f_r ? v_r : v_l + v_r, f_l | f_r).
 // Exclusive scan of one pair per thread over the block (fixed order): the
-// value carried into the thread; *tv, *tf = the whole block's pair.
-__device__ inline double block_excl_seg_scan(double v, int f, double *tv, int *tf) {
-    __shared__ double wv[32];
+// carried pair into the thread (value and flag); *tv, *tf = the block's pair.
+template <typename V>
+__device__ inline V block_excl_seg_scan(V v, int f, int *cf, V *tv, int *tf) {
+    __shared__ V wv[32];
     __shared__ int wf[32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
-    double x = v;
+    V x = v;
     int g = f;
     for (int d = 1; d < 32; d <<= 1) {
-        const double y = __shfl_up_sync(0xffffffffu, x, d);
+        const V y = s_shfl_up(x, d);
         const int h = __shfl_up_sync(0xffffffffu, g, d);
         if (lane >= d) {
-            if (!g) x += y;
+            if (!g) x = s_add(y, x);
             g |= h;
         }
     }
-    // exclusive within the warp: the inclusive pair of the lane before
-    double ex = __shfl_up_sync(0xffffffffu, x, 1);
+    V ex = s_shfl_up(x, 1);
     int exf = __shfl_up_sync(0xffffffffu, g, 1);
     if (lane == 0) {
-        ex = 0.0;
+        ex = s_zero<V>();
         exf = 0;
     }
     __syncthreads();
@@ -448,13 +510,13 @@ __device__ inline double block_excl_seg_scan(double v, int f, double *tv, int *t
     }
     __syncthreads();
     if (wid == 0) {
-        double w = lane < nw ? wv[lane] : 0.0;
+        V w = lane < nw ? wv[lane] : s_zero<V>();
         int wg = lane < nw ? wf[lane] : 0;
         for (int d = 1; d < 32; d <<= 1) {
-            const double y = __shfl_up_sync(0xffffffffu, w, d);
+            const V y = s_shfl_up(w, d);
             const int h = __shfl_up_sync(0xffffffffu, wg, d);
             if (lane >= d) {
-                if (!wg) w += y;
+                if (!wg) w = s_add(y, w);
                 wg |= h;
             }
         }
@@ -464,64 +526,10 @@ __device__ inline double block_excl_seg_scan(double v, int f, double *tv, int *t
         }
     }
     __syncthreads();
-    // carry into this thread: the warps before, then the lanes before
-    double carry = wid > 0 ? wv[wid - 1] : 0.0;
+    V carry = wid > 0 ? wv[wid - 1] : s_zero<V>();
+    const int carf = wid > 0 ? wf[wid - 1] : 0;
     if (exf) carry = ex;
-    else carry += ex;
-    *tv = wv[nw - 1];
-    *tf = wf[nw - 1];
-    return carry;
-}
-
-// The same scan, also giving the flag of the carried pair (a head among the
-// earlier threads).
-__device__ inline double block_excl_seg_scan_f(double v, int f, int *cf, double *tv, int *tf) {
-    __shared__ double wv[32];
-    __shared__ int wf[32];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
-    double x = v;
-    int g = f;
-    for (int d = 1; d < 32; d <<= 1) {
-        const double y = __shfl_up_sync(0xffffffffu, x, d);
-        const int h = __shfl_up_sync(0xffffffffu, g, d);
-        if (lane >= d) {
-            if (!g) x += y;
-            g |= h;
-        }
-    }
-    double ex = __shfl_up_sync(0xffffffffu, x, 1);
-    int exf = __shfl_up_sync(0xffffffffu, g, 1);
-    if (lane == 0) {
-        ex = 0.0;
-        exf = 0;
-    }
-    __syncthreads();
-    if (lane == 31) {
-        wv[wid] = x;
-        wf[wid] = g;
-    }
-    __syncthreads();
-    if (wid == 0) {
-        double w = lane < nw ? wv[lane] : 0.0;
-        int wg = lane < nw ? wf[lane] : 0;
-        for (int d = 1; d < 32; d <<= 1) {
-            const double y = __shfl_up_sync(0xffffffffu, w, d);
-            const int h = __shfl_up_sync(0xffffffffu, wg, d);
-            if (lane >= d) {
-                if (!wg) w += y;
-                wg |= h;
-            }
-        }
-        if (lane < nw) {
-            wv[lane] = w;
-            wf[lane] = wg;
-        }
-    }
-    __syncthreads();
-    double carry = wid > 0 ? wv[wid - 1] : 0.0;
-    int carf = wid > 0 ? wf[wid - 1] : 0;
-    if (exf) carry = ex;
-    else carry += ex;
+    else carry = s_add(carry, ex);
     *cf = carf | exf;
     *tv = wv[nw - 1];
     *tf = wf[nw - 1];
@@ -529,32 +537,33 @@ __device__ inline double block_excl_seg_scan_f(double v, int f, int *cf, double 
 }
 
 // carry into every block b from blocks 0..b-1 (segmented), into shared memory
-__device__ inline void block_offsets_seg(const double *pv, const double *pf, double *off) {
+template <typename V>
+__device__ inline void block_offsets_seg(const V *pv, const double *pf, V *off) {
     const int G = (int)gridDim.x;
     const int per = (G + (int)blockDim.x - 1) / (int)blockDim.x;
     const int i0 = (int)threadIdx.x * per;
-    double v = 0.0;
+    V v = s_zero<V>();
     int f = 0;
     for (int i = i0; i < i0 + per && i < G; ++i) {
         if (pf[i] != 0.0) {
             v = pv[i];
             f = 1;
         } else {
-            v += pv[i];
+            v = s_add(v, pv[i]);
         }
     }
-    double tv;
-    int tf;
-    double run = block_excl_seg_scan(v, f, &tv, &tf);
+    int cf, tf;
+    V tv;
+    V run = block_excl_seg_scan(v, f, &cf, &tv, &tf);
     for (int i = i0; i < i0 + per && i < G; ++i) {
         off[i] = run;
         if (pf[i] != 0.0) run = pv[i];
-        else run += pv[i];
+        else run = s_add(run, pv[i]);
     }
     __syncthreads();
 }
 
-constexpr int kEuBatch = 8;   // positions / vertices per thread with loads in flight together
+constexpr int kEuBatch = 8;   // consecutive tour positions per thread and tile
 
 // One segmented scan pass over the block's stretch [b0, b1) of the tour:
 // S[p] = sum of val over [latest head <= p, p) inside the block (the carry
@@ -564,18 +573,20 @@ constexpr int kEuBatch = 8;   // positions / vertices per thread with loads in f
 // once and kept in registers); a segmented block scan per tile, the block's
 // running pair carried from tile to tile.  Block pair into pv[b], pf[b];
 // first head into fh[b].
-template <typename VAL>
+template <typename T, typename VAL>
 __device__ inline void euler_scan_pass(const EulerKArgs &E, int64_t b0, int64_t b1, VAL val,
-                                       double *pv, double *pf, double *fh) {
+                                       typename SumOf<T>::type *S, typename SumOf<T>::type *pv,
+                                       double *pf, long long *fh) {
+    using V = typename SumOf<T>::type;
     const int64_t tile = (int64_t)blockDim.x * kEuBatch;
-    double cv = 0.0;
+    V cv = s_zero<V>();
     int cfl = 0;
     long long first = LLONG_MAX;
     for (int64_t base = b0; base < b1; base += tile) {
         const int64_t p0 = base + (int64_t)threadIdx.x * kEuBatch;
         int32_t tv[kEuBatch];
         uint8_t hd[kEuBatch];
-        double x[kEuBatch];
+        T x[kEuBatch];
 #pragma unroll
         for (int k = 0; k < kEuBatch; ++k) {
             const bool in = p0 + k < b1;
@@ -583,31 +594,31 @@ __device__ inline void euler_scan_pass(const EulerKArgs &E, int64_t b0, int64_t 
             hd[k] = in ? E.head[p0 + k] : 0;
         }
 #pragma unroll
-        for (int k = 0; k < kEuBatch; ++k) x[k] = p0 + k < b1 ? val(tv[k]) : 0.0;
-        double sv = 0.0;
+        for (int k = 0; k < kEuBatch; ++k) x[k] = p0 + k < b1 ? val(tv[k]) : (T)0;
+        V sv = s_zero<V>();
         int sf = 0;
 #pragma unroll
         for (int k = 0; k < kEuBatch; ++k) {
             if (hd[k]) {
-                sv = 0.0;
+                sv = s_zero<V>();
                 sf = 1;
                 if (first == LLONG_MAX) first = p0 + k;
             }
-            sv += x[k];
+            sv = s_add(sv, s_of<V, T>(x[k]));
         }
         int carf, tf;
-        double tvv;
-        const double carry = block_excl_seg_scan_f(sv, sf, &carf, &tvv, &tf);
-        double run = carf ? carry : cv + carry;
+        V tvv;
+        const V carry = block_excl_seg_scan(sv, sf, &carf, &tvv, &tf);
+        V run = carf ? carry : s_add(cv, carry);
 #pragma unroll
         for (int k = 0; k < kEuBatch; ++k) {
             if (p0 + k < b1) {
-                if (hd[k]) run = 0.0;
-                E.S[p0 + k] = run;
-                run += x[k];
+                if (hd[k]) run = s_zero<V>();
+                S[p0 + k] = run;
+                run = s_add(run, s_of<V, T>(x[k]));
             }
         }
-        cv = tf ? tvv : cv + tvv;
+        cv = tf ? tvv : s_add(cv, tvv);
         cfl |= tf;
     }
     // the block's first head: min over threads
@@ -620,7 +631,7 @@ __device__ inline void euler_scan_pass(const EulerKArgs &E, int64_t b0, int64_t 
     if (threadIdx.x == 0) {
         pv[blockIdx.x] = cv;
         pf[blockIdx.x] = cfl ? 1.0 : 0.0;
-        fh[blockIdx.x] = (double)s_first;
+        fh[blockIdx.x] = s_first;
     }
 }
 
@@ -628,25 +639,29 @@ template <typename T>
 __device__ __forceinline__ bool euler_solve_dev(const EulerKArgs &E, T *Y, unsigned int *bar,
                                                 long long budget, int *err, unsigned int &epoch,
                                                 double &mx) {
-    __shared__ double s_off[kEulerMaxGrid];
+    using V = typename SumOf<T>::type;
+    __shared__ V s_off[kEulerMaxGrid];
     const int64_t G = gridDim.x;
     const int64_t per = (E.L + G - 1) / G;
     const int64_t b0 = min(E.L, (int64_t)blockIdx.x * per), b1 = min(E.L, b0 + per);
     const int64_t nth = (int64_t)gridDim.x * blockDim.x;
-    double *pv = E.part, *pf = E.part + G, *fh = E.part + 2 * G;
+    V *S = reinterpret_cast<V *>(E.S);
+    T *C = reinterpret_cast<T *>(E.C);
+    V *pv = reinterpret_cast<V *>(E.part);
+    double *pf = E.part + G;
+    long long *fh = reinterpret_cast<long long *>(E.part + 2 * G);
+    const T *ipw = reinterpret_cast<const T *>(E.ipw);
     // global prefix at p: the block-local part, plus the carry from earlier
-    // blocks while p lies before the block's first head
-    // block of a position: 32-bit division (positions < 2^31; 64-bit integer
-    // division is emulated and was a third of phase 2)
+    // blocks while p lies before the block's first head (block of a position:
+    // 32-bit division, positions < 2^31)
     const uint32_t per32 = (uint32_t)per;
-    auto glob = [&](int64_t p, const double *fhp) {
+    auto glob = [&](int64_t p, const long long *fhp) {
         const uint32_t b = (uint32_t)p / per32;
-        return E.S[p] + ((double)p < fhp[b] ? s_off[b] : 0.0);
+        return p < fhp[b] ? s_add(S[p], s_off[b]) : S[p];
     };
-    // vertices in batches: thread g takes v = g + k * nth, k < kEuBatch, per round
     const int64_t vbase = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     // 1: prefix sums of b at the entries, restarting at every tree
-    euler_scan_pass(E, b0, b1, [&](int32_t v) { return v >= 0 ? (double)Y[v] : 0.0; }, pv, pf, fh);
+    euler_scan_pass<T>(E, b0, b1, [&](int32_t v) { return v >= 0 ? Y[v] : (T)0; }, S, pv, pf, fh);
     if (!grid_sync(bar, budget, err, epoch)) return false;
     // 2: currents c_v = (subtree sum of b) / w_v
     block_offsets_seg(pv, pf, s_off);
@@ -658,22 +673,24 @@ __device__ __forceinline__ bool euler_solve_dev(const EulerKArgs &E, T *Y, unsig
             in[k] = v < E.n ? E.ein[v] : -1;
             out[k] = v < E.n ? E.eout[v] : -1;
         }
-        double d[kEuBatch];
+        T d[kEuBatch];
 #pragma unroll
-        for (int k = 0; k < kEuBatch; ++k) d[k] = in[k] >= 0 ? glob(out[k], fh) - glob(in[k], fh) : 0.0;
+        for (int k = 0; k < kEuBatch; ++k)
+            d[k] = in[k] >= 0 ? (T)s_to(s_sub(glob(out[k], fh), glob(in[k], fh))) : (T)0;
 #pragma unroll
         for (int k = 0; k < kEuBatch; ++k) {
             const int64_t v = v0 + k * nth;
-            if (v < E.n) E.C[v] = in[k] >= 0 ? d[k] * E.ipw[v] : 0.0;
+            if (v < E.n) C[v] = in[k] >= 0 ? d[k] * ipw[v] : (T)0;
         }
     }
     if (!grid_sync(bar, budget, err, epoch)) return false;
     // 3: prefix sums of +c at entries, -c at exits, restarting at every tree
-    euler_scan_pass(E, b0, b1, [&](int32_t v) { return v >= 0 ? E.C[v] : -E.C[-v - 1]; },
-                    pv + 3 * G, pf + 3 * G, fh + 3 * G);
+    euler_scan_pass<T>(E, b0, b1, [&](int32_t v) { return v >= 0 ? C[v] : -C[-v - 1]; }, S,
+                       pv + 3 * G, pf + 3 * G, fh + 3 * G);
     if (!grid_sync(bar, budget, err, epoch)) return false;
     // 4: x_v = the path sum up to and including v's entry (roots: 0)
     block_offsets_seg(pv + 3 * G, pf + 3 * G, s_off);
+    T tm = (T)0;
     for (int64_t v0 = vbase; v0 < E.n; v0 += nth * kEuBatch) {
         int32_t in[kEuBatch];
 #pragma unroll
@@ -681,25 +698,26 @@ __device__ __forceinline__ bool euler_solve_dev(const EulerKArgs &E, T *Y, unsig
             const int64_t v = v0 + k * nth;
             in[k] = v < E.n ? E.ein[v] : -1;
         }
-        double x[kEuBatch];
+        T x[kEuBatch];
 #pragma unroll
         for (int k = 0; k < kEuBatch; ++k) {
             const int64_t v = v0 + k * nth;
-            x[k] = in[k] >= 0 ? glob(in[k], fh + 3 * G) + E.C[v] : 0.0;
+            x[k] = in[k] >= 0 ? (T)s_to(s_add(glob(in[k], fh + 3 * G), s_of<V, T>(C[v]))) : (T)0;
         }
 #pragma unroll
         for (int k = 0; k < kEuBatch; ++k) {
             const int64_t v = v0 + k * nth;
             if (v >= E.n) continue;
-            const T xt = (T)x[k];
-            Y[v] = xt;
-            mx = fmax(mx, fabs((double)xt));
+            Y[v] = x[k];
+            tm = fmax(tm, fabs(x[k]));
         }
     }
+    mx = fmax(mx, (double)tm);
     return true;
 }
 
 // Host side: scan-form arguments for a cooperative grid of `grid` blocks.
+template <typename T>
 inline void euler_kargs(grass_ctx_t ctx, const grass_tree_s *Tr, int grid, EulerKArgs *e) {
     if (grid > kEulerMaxGrid) fail(GRASS_ERR_INVALID, "grid too large for the scan-form tree solve");
     const EulerTour &E = Tr->euler;
@@ -709,8 +727,9 @@ inline void euler_kargs(grass_ctx_t ctx, const grass_tree_s *Tr, int grid, Euler
     e->ein = E.ein.p;
     e->eout = E.eout.p;
     e->head = E.head.p;
-    e->ipw = E.ipw.p;
-    e->S = ctx->scr<double>(SCR_EU_S, E.L + 1);
+    if constexpr (sizeof(T) == 8) e->ipw = E.ipw.p;
+    else e->ipw = E.ipw32.p;
+    e->S = ctx->scr<double>(SCR_EU_S, E.L + 1);   // 8-byte sums (double or float pair)
     e->C = ctx->scr<double>(SCR_EU_C, Tr->g.n);
     e->part = ctx->scr<double>(SCR_EU_P, 6 * (size_t)grid + 2);
 }
