@@ -138,7 +138,9 @@ grass_status grass_ctx_set_wait_limit(grass_ctx_t ctx, int64_t polls, int hold_b
  * CG groups its sums by block, so its results can change in the last bits
  * with the grid these knobs give.  Names:
  *   "tree_blocks_per_sm"  blocks per SM of the cooperative tree solve (1-8)
- *   "tree_threads"        threads per block of that kernel (128-1024, x32)
+ *   "tree_threads"        threads per block of that kernel (128-1024, x32);
+ *                         the fused PCG and the fused CG of the elimination
+ *                         form with one column use at most 512 of them
  *   "tree_tail_items"     rounds at the end whose total work is below this
  *                         many items run in one block (0 = none)
  *   "euler_solve"         1 (default): grounded solves of L_T alone (no D)

@@ -207,6 +207,14 @@ constexpr int kMaxRounds = 512;
 // shared memory for the tail of a tree solve (vertices x columns x element)
 constexpr size_t kTailSmem = 184 * 1024;   // + up to ~40 KB static shared memory <= 227 KB
 constexpr int kPersistMaxThreads = 1024;
+// The fused Krylov kernels whose preconditioner is the elimination-round
+// solve (the PCG, the inner CG with D or r > 1 columns of the non-scan form)
+// hold more live values than 64 registers a thread: at most 512 threads per
+// block, so that a thread may keep 128 registers instead of spilling.
+constexpr int kFusedMaxThreads = 512;
+// threads of a persistent kernel launched with the knob value but bounded
+// by the kernel's own maximum
+inline int bounded_threads(int knob, int bound) { return knob < bound ? knob : bound; }
 
 // ---------------------------------------------------------------- block layout
 // An n x R row-major block is processed by TPR consecutive threads per row,

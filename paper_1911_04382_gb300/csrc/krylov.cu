@@ -346,8 +346,12 @@ __device__ __forceinline__ bool cg_dev(const CGArgs<T> &g, const TreeKArgs<T> &t
     return true;
 }
 
+// threads of k_cg_persist: the scan form and r > 1 columns keep 1024
+template <int R, bool EU>
+constexpr int cg_max_threads() { return (EU || R > 1) ? kPersistMaxThreads : kFusedMaxThreads; }
+
 template <typename T, int R, bool EU>
-__global__ void __launch_bounds__(kPersistMaxThreads, 1)
+__global__ void __launch_bounds__(cg_max_threads<R, EU>(), 1)
     k_cg_persist(CGArgs<T> g, TreeKArgs<T> tk) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned int epoch = 0;
@@ -387,9 +391,10 @@ static void cg_persistent(grass_ctx_t ctx, grass_sparsifier_t S, bool with_D, co
     a.iter_acc = ctx->scal.p + DS_RED + DS_ITER;
     a.maxbits = maxbits;
     std::memset(&a.eu, 0, sizeof(a.eu));
-    const int threads = ctx->tree_threads;
     // one column and no D: the scan-form tree solve
     const bool eu = R == 1 && !with_D && ctx->euler_solve && Tr->euler.built;
+    const int threads = bounded_threads(
+        ctx->tree_threads, eu ? cg_max_threads<R, (R == 1)>() : cg_max_threads<R, false>());
     const void *kern = eu ? (const void *)k_cg_persist<T, R, (R == 1)>
                           : (const void *)k_cg_persist<T, R, false>;
     const int grid = eu ? coop_grid(ctx, k_cg_persist<T, R, (R == 1)>, threads, smem, n * Lay<R>::TPR)
@@ -572,10 +577,8 @@ struct PCGArgs {
     double *out;                  // [0] += iterations, [1] = final r.r
 };
 
-constexpr int kU = 4;   // elements per thread with their loads in flight together
-
 template <typename T, bool TREE_ONLY>
-__global__ void __launch_bounds__(kPersistMaxThreads, 1)
+__global__ void __launch_bounds__(kFusedMaxThreads, 1)
     k_pcg_persist(PCGArgs<T> a, CGArgs<T> in, TreeKArgs<T> tk) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *ys = reinterpret_cast<T *>(smem_raw);
@@ -590,21 +593,11 @@ __global__ void __launch_bounds__(kPersistMaxThreads, 1)
     Acc<T> acc0[1], acc1[1];
 
     // e = 0, r = rhs (z = rhs for the tree solve)
-    for (int64_t i0 = gt; i0 < a.n; i0 += kU * nth) {
-        T yv[kU];
-#pragma unroll
-        for (int u = 0; u < kU; ++u) {
-            const int64_t i = i0 + u * nth;
-            yv[u] = i < a.n ? a.rhs[i] : (T)0;
-        }
-#pragma unroll
-        for (int u = 0; u < kU; ++u) {
-            const int64_t i = i0 + u * nth;
-            if (i >= a.n) continue;
-            a.e[i] = (T)0;
-            a.r[i] = yv[u];
-            if (TREE_ONLY) a.z[i] = yv[u];
-        }
+    for (int64_t i = gt; i < a.n; i += nth) {
+        const T y = a.rhs[i];
+        a.e[i] = (T)0;
+        a.r[i] = y;
+        if (TREE_ONLY) a.z[i] = y;
     }
     if (!grid_sync(tk.bar, tk.budget, tk.err, epoch)) return;
     // Each pass starts with z = M^{-1} r (the only call site of the
@@ -622,24 +615,11 @@ __global__ void __launch_bounds__(kPersistMaxThreads, 1)
         if (!grid_sync(tk.bar, tk.budget, tk.err, epoch)) return;
         // first: rz = r.z, rr = r.r;  later: r.z and r.z_old for beta
         acc0[0] = acc1[0] = Acc<T>();
-        // element loops take kU elements per thread at a time: all loads
-        // first, then the arithmetic and the stores (same order of sums)
-        for (int64_t i0 = gt; i0 < a.n; i0 += kU * nth) {
-            T rv[kU], zv[kU], ov[kU];
-#pragma unroll
-            for (int u = 0; u < kU; ++u) {
-                const int64_t i = i0 + u * nth;
-                const bool in = i < a.n;
-                rv[u] = in ? a.r[i] : (T)0;
-                zv[u] = in ? a.z[i] : (T)0;
-                ov[u] = in && !first && !TREE_ONLY ? a.zo[i] : (T)0;
-            }
-#pragma unroll
-            for (int u = 0; u < kU; ++u) {
-                acc0[0].add_prod(rv[u], zv[u]);
-                if (first) acc1[0].add_prod(rv[u], rv[u]);
-                else if (!TREE_ONLY) acc1[0].add_prod(rv[u], ov[u]);
-            }
+        for (int64_t i = gt; i < a.n; i += nth) {
+            const T ri = a.r[i];
+            acc0[0].add_prod(ri, a.z[i]);
+            if (first) acc1[0].add_prod(ri, ri);
+            else if (!TREE_ONLY) acc1[0].add_prod(ri, a.zo[i]);
         }
         block_cols<1>(acc0, 0, s_red, my0);
         block_cols<1>(acc1, 0, s_red, my1);
@@ -651,21 +631,7 @@ __global__ void __launch_bounds__(kPersistMaxThreads, 1)
         if (first) rr = s_v[1];
         else beta = (T)((rzn - (TREE_ONLY ? 0.0 : s_v[1])) / rz);
         rz = rzn;
-        for (int64_t i0 = gt; i0 < a.n; i0 += kU * nth) {
-            T zv[kU], pv[kU];
-#pragma unroll
-            for (int u = 0; u < kU; ++u) {
-                const int64_t i = i0 + u * nth;
-                const bool in = i < a.n;
-                zv[u] = in ? a.z[i] : (T)0;
-                pv[u] = in && !first ? a.p[i] : (T)0;
-            }
-#pragma unroll
-            for (int u = 0; u < kU; ++u) {
-                const int64_t i = i0 + u * nth;
-                if (i < a.n) a.p[i] = first ? zv[u] : zv[u] + beta * pv[u];
-            }
-        }
+        for (int64_t i = gt; i < a.n; i += nth) a.p[i] = first ? a.z[i] : a.z[i] + beta * a.p[i];
         if (!grid_sync(tk.bar, tk.budget, tk.err, epoch)) return;
         if (k >= a.maxit || sqrt(rr) <= a.tol_abs) break;
         // q = A p, pq
@@ -683,29 +649,13 @@ __global__ void __launch_bounds__(kPersistMaxThreads, 1)
         const T alpha = (T)(rz / s_v[2]);
         // e += alpha p, r -= alpha q (z_old = z; z = r for the tree solve), rr
         acc1[0] = Acc<T>();
-        for (int64_t i0 = gt; i0 < a.n; i0 += kU * nth) {
-            T ev[kU], pv[kU], rv[kU], qv[kU], zv[kU];
-#pragma unroll
-            for (int u = 0; u < kU; ++u) {
-                const int64_t i = i0 + u * nth;
-                const bool in = i < a.n;
-                ev[u] = in ? a.e[i] : (T)0;
-                pv[u] = in ? a.p[i] : (T)0;
-                rv[u] = in ? a.r[i] : (T)0;
-                qv[u] = in ? a.q[i] : (T)0;
-                zv[u] = in && !TREE_ONLY ? a.z[i] : (T)0;
-            }
-#pragma unroll
-            for (int u = 0; u < kU; ++u) {
-                const int64_t i = i0 + u * nth;
-                if (i >= a.n) continue;
-                a.e[i] = ev[u] + alpha * pv[u];
-                const T ri = rv[u] - alpha * qv[u];
-                a.r[i] = ri;
-                if (!TREE_ONLY) a.zo[i] = zv[u];
-                if (TREE_ONLY) a.z[i] = ri;
-                acc1[0].add_prod(ri, ri);
-            }
+        for (int64_t i = gt; i < a.n; i += nth) {
+            a.e[i] += alpha * a.p[i];
+            const T ri = a.r[i] - alpha * a.q[i];
+            a.r[i] = ri;
+            if (!TREE_ONLY) a.zo[i] = a.z[i];
+            if (TREE_ONLY) a.z[i] = ri;
+            acc1[0].add_prod(ri, ri);
         }
         block_cols<1>(acc1, 0, s_red, my1);
         if (!grid_sync(tk.bar, tk.budget, tk.err, epoch)) return;
@@ -730,7 +680,7 @@ static int pcg_fused(grass_ctx_t ctx, grass_sparsifier_t S, const T *rhs, T *e, 
     const int64_t n = g.n;
     size_t smem = 0;
     TreeKArgs<T> tk = tree_kargs<T, 1>(ctx, Tr, Tr->sdd, &smem);
-    const int threads = ctx->tree_threads;
+    const int threads = bounded_threads(ctx->tree_threads, kFusedMaxThreads);
     const bool tree_only = S->is_tree || inner_maxit <= 0;
     const void *kern = tree_only ? (const void *)k_pcg_persist<T, true>
                                  : (const void *)k_pcg_persist<T, false>;
