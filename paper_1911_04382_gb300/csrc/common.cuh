@@ -486,27 +486,23 @@ struct Acc<float> {
 };
 
 // ---------------------------------------------------------------- grid barrier
-// Barrier for cooperative (co-resident) launches.  bar[0] counts arrivals,
-// bar[1] is the generation.  Every wait is bounded: after `budget` polls, or
+// Barrier for cooperative (co-resident) launches; bar[0] counts arrivals.
+// Every wait is bounded: after `budget` polls, or
 // as soon as another block has flagged an error, the block sets *err and
 // leaves; the caller returns from the kernel, so a lost block can never hang
 // the GPU.  All threads of a block get the same answer.
 // bar[0] only grows within a launch (the host zeroes it before each launch):
 // barrier number b is complete once bar[0] >= (b+1) * gridDim.x, so a block
-// needs one release-add and acquire polls, with no reset round trip.
+// needs one release-add and then polls, with no reset round trip.
 // bar[2] != 0 (testing only) raises every target by one arrival that never
 // comes, so every wait runs out.
-__device__ inline unsigned int ld_acquire_u32(const unsigned int *p) {
+__device__ inline unsigned int ld_relaxed_u32(const unsigned int *p) {
     unsigned int v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
 
-__device__ inline unsigned int atom_add_release_u32(unsigned int *p, unsigned int v) {
-    unsigned int old;
-    asm volatile("atom.add.release.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
-    return old;
-}
+__device__ inline void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 
 __device__ inline void red_add_release_u32(unsigned int *p, unsigned int v) {
     asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
@@ -514,8 +510,12 @@ __device__ inline void red_add_release_u32(unsigned int *p, unsigned int v) {
 
 // `epoch` counts the barriers this block has passed in the launch (all
 // blocks pass the same barriers, so barrier b completes when the counter
-// reaches (b+1) * gridDim.x).  The arrival is a one-way reduction: no round
-// trip before polling starts.
+// reaches (b+1) * gridDim.x).  Arrival: one release reduction by thread 0,
+// which carries the block's writes (ordered before it by __syncthreads).
+// Wait: relaxed polls of the counter (the error flag and the poll budget
+// are looked at every 64 polls), then one acquire fence, which pairs with
+// the other blocks' release reductions.  The testing flag is read after
+// the arrival, while the other blocks arrive.
 __device__ inline bool grid_sync(unsigned int *bar, long long budget, int *err,
                                  unsigned int &epoch) {
     __shared__ int s_ok;
@@ -523,23 +523,25 @@ __device__ inline bool grid_sync(unsigned int *bar, long long budget, int *err,
     ++epoch;
     if (threadIdx.x == 0) {
         int ok = 1;
-        const unsigned int hold = ((volatile unsigned int *)bar)[2] ? 1u : 0u;
-        __threadfence();   // the block's writes (ordered by __syncthreads) before the arrival
         red_add_release_u32(bar, 1u);
+        const unsigned int hold = ld_relaxed_u32(bar + 2) ? 1u : 0u;
         const unsigned int target = epoch * gridDim.x + hold;
         long long spins = 0;
-        while (ld_acquire_u32(bar) < target) {
-            if (*(volatile int *)err) {
-                ok = 0;
-                break;
-            }
-            if (++spins > budget) {
-                atomicOr(err, 1);
-                ok = 0;
-                break;
+        while (ld_relaxed_u32(bar) < target) {
+            if ((++spins & 63) == 0) {
+                if (*(volatile int *)err) {
+                    ok = 0;
+                    break;
+                }
+                if (spins > budget) {
+                    atomicOr(err, 1);
+                    ok = 0;
+                    break;
+                }
             }
             __nanosleep(32);
         }
+        fence_acq_rel_gpu();
         s_ok = ok;
     }
     __syncthreads();

@@ -147,24 +147,119 @@ __device__ __forceinline__ void block_cols(const Acc<T> (&a)[Lay<R>::EPT], int c
 
 // Column sums over all blocks' partials (same order in every block): warp j
 // takes column j, lanes stride over the blocks, fixed xor tree.
+// The loads of up to U x 32 blocks are issued before the first add (one
+// round trip per U x 32 blocks instead of one per 32); the order of the
+// adds is the plain one (lane, lane + 32, ...).
 template <int R>
 __device__ inline void grid_cols(const double *part, double *s_out) {
+    constexpr int U = R == 1 ? 8 : 2;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     if (wid < R) {
         double s = 0.0;
-        for (unsigned b = lane; b < gridDim.x; b += 32) s += part[(int64_t)b * 32 + wid];
+        for (unsigned b0 = lane; b0 < gridDim.x; b0 += 32 * U) {
+            double v[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const unsigned b = b0 + 32 * u;
+                v[u] = b < gridDim.x ? part[(int64_t)b * 32 + wid] : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (b0 + 32 * u < gridDim.x) s += v[u];
+        }
         for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(0xffffffffu, s, d);
         if (lane == 0) s_out[wid] = s;
     }
     __syncthreads();
 }
 
+// threads of k_cg_persist: the scan form and r > 1 columns keep 1024
+template <int R, bool EU>
+__host__ __device__ constexpr int cg_max_threads() { return (EU || R > 1) ? kPersistMaxThreads : kFusedMaxThreads; }
+
+// Laplacian rows of a CSR (off-diagonal weights w, columns col) applied to
+// x with stride S: q[u] += w_j (xi[u] - x[col_j * S]) over the entries
+// [jb[u], je[u]) of each row, in j order.  The first K entries of every row
+// (indices and weights, then the gathers) are loaded before any arithmetic;
+// a longer row goes on K entries at a time.
+template <typename T, int U, int K, int S>
+__device__ __forceinline__ void lap_rows(const int32_t *col, const T *w, const T *x, int32_t (&jb)[U],
+                                         const int32_t (&je)[U], const T (&xi)[U], T (&q)[U]) {
+    bool more = true;
+    while (more) {
+        int32_t cc[U][K];
+        T wv[U][K], xc[U][K];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                const int32_t j = jb[u] + k;
+                const bool v = j < je[u];
+                cc[u][k] = v ? col[j] : 0;
+                wv[u][k] = v ? w[j] : (T)0;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+#pragma unroll
+            for (int k = 0; k < K; ++k) xc[u][k] = jb[u] + k < je[u] ? x[(int64_t)cc[u][k] * S] : (T)0;
+        }
+        more = false;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+#pragma unroll
+            for (int k = 0; k < K; ++k)
+                if (jb[u] + k < je[u]) q[u] += wv[u][k] * (xi[u] - xc[u][k]);
+            jb[u] += K;
+            more = more || jb[u] < je[u];
+        }
+    }
+}
+
+// Two column sums at once: warps 0..R-1 reduce part0 and warps R..2R-1
+// part1 (each the same order as grid_cols), when the block has 2R warps.
+template <int R>
+__device__ inline void grid_cols2(const double *part0, double *s_out0, const double *part1,
+                                  double *s_out1) {
+    if (2 * R > (int)(blockDim.x >> 5)) {
+        grid_cols<R>(part0, s_out0);
+        grid_cols<R>(part1, s_out1);
+        return;
+    }
+    constexpr int U = R == 1 ? 8 : 2;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (wid < 2 * R) {
+        const double *part = wid < R ? part0 : part1;
+        const int col = wid < R ? wid : wid - R;
+        double s = 0.0;
+        for (unsigned b0 = lane; b0 < gridDim.x; b0 += 32 * U) {
+            double v[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const unsigned b = b0 + 32 * u;
+                v[u] = b < gridDim.x ? part[(int64_t)b * 32 + col] : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (b0 + 32 * u < gridDim.x) s += v[u];
+        }
+        for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(0xffffffffu, s, d);
+        if (lane == 0) (wid < R ? s_out0 : s_out1)[col] = s;
+    }
+    __syncthreads();
+}
+
 // The whole inner CG as a device function of a cooperative grid (used by
 // k_cg_persist and inside the fused PCG).  Returns false when a barrier wait
-// ran out (the caller must return).  Ends without a trailing grid barrier.
+// ran out (the caller must return).  Ends without a trailing grid barrier:
+// every element of X is last written (and read by the max |X| pass) by the
+// thread that owns it under the slot mapping (rows slot, slot + nslots, ...;
+// columns c*EPT ..), so a caller with the same mapping reads X at once.
+// preset: the caller has already set X = 0, R = Z = Y with that mapping and
+// passed a grid barrier since.
 template <typename T, int R, bool EU = false>
 __device__ __forceinline__ bool cg_dev(const CGArgs<T> &g, const TreeKArgs<T> &tk,
-                                       unsigned int &epoch, T *ys) {
+                                       unsigned int &epoch, T *ys, bool preset = false) {
     static_assert(!EU || R == 1, "the scan-form solve handles one column");
     constexpr int TPR = Lay<R>::TPR, EPT = Lay<R>::EPT;
     __shared__ double s_red[32][32];
@@ -178,17 +273,19 @@ __device__ __forceinline__ bool cg_dev(const CGArgs<T> &g, const TreeKArgs<T> &t
     double mx = 0.0;
     Acc<T> acc0[EPT], acc1[EPT];
 
-    for (int64_t i = slot; i < g.n; i += nslots) {
+    if (!preset) {
+        for (int64_t i = slot; i < g.n; i += nslots) {
 #pragma unroll
-        for (int e = 0; e < EPT; ++e) {
-            int64_t k = i * R + c * EPT + e;
-            T y = g.Y[k];
-            g.X[k] = (T)0;
-            g.Rv[k] = y;
-            g.Z[k] = y;
+            for (int e = 0; e < EPT; ++e) {
+                int64_t k = i * R + c * EPT + e;
+                T y = g.Y[k];
+                g.X[k] = (T)0;
+                g.Rv[k] = y;
+                g.Z[k] = y;
+            }
         }
+        if (!grid_sync(tk.bar, tk.budget, tk.err, epoch)) return false;
     }
-    if (!grid_sync(tk.bar, tk.budget, tk.err, epoch)) return false;
     if (threadIdx.x < R) {
         s_brk[threadIdx.x] = 0;
         s_it[threadIdx.x] = 0;
@@ -223,8 +320,7 @@ __device__ __forceinline__ bool cg_dev(const CGArgs<T> &g, const TreeKArgs<T> &t
         if (it == 0) block_cols<R>(acc1, c, s_red, mypart1);
         if (!grid_sync(tk.bar, tk.budget, tk.err, epoch)) return false;
         if (it == 0) {
-            grid_cols<R>(part0, s_rz);
-            grid_cols<R>(part1, s_rr);
+            grid_cols2<R>(part0, s_rz, part1, s_rr);
             if (threadIdx.x < R) s_yy[threadIdx.x] = s_rr[threadIdx.x];
             __syncthreads();
         } else {
@@ -262,6 +358,33 @@ __device__ __forceinline__ bool cg_dev(const CGArgs<T> &g, const TreeKArgs<T> &t
         // Q = L_S P (+D), partial P.Q
 #pragma unroll
         for (int e = 0; e < EPT; ++e) acc0[e] = Acc<T>();
+        if constexpr (EPT == 1 && cg_max_threads<R, EU>() <= kFusedMaxThreads) {
+            // two rows at a time, every load of both rows before the sums
+            constexpr int K = 4;
+            for (int64_t i0 = slot; i0 < g.n; i0 += 2 * nslots) {
+                int32_t jb[2], je[2];
+                T p0[2], q[2], dd[2];
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const int64_t i = i0 + u * nslots;
+                    const bool ok = i < g.n;
+                    p0[u] = ok ? g.P[i * R + c] : (T)0;
+                    dd[u] = ok && g.D ? g.D[i] : (T)0;
+                    jb[u] = ok ? g.sptr[i] : 0;
+                    je[u] = ok ? g.sptr[i + 1] : 0;
+                    q[u] = (T)0;
+                }
+                lap_rows<T, 2, K, R>(g.scol, g.sw, g.P + c, jb, je, p0, q);
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const int64_t i = i0 + u * nslots;
+                    if (i >= g.n) break;
+                    if (g.D) q[u] += dd[u] * p0[u];
+                    g.Q[i * R + c] = q[u];
+                    acc0[0].add_prod(p0[u], q[u]);
+                }
+            }
+        } else {
         for (int64_t i = slot; i < g.n; i += nslots) {
             T p0[EPT], q[EPT];
 #pragma unroll
@@ -285,6 +408,7 @@ __device__ __forceinline__ bool cg_dev(const CGArgs<T> &g, const TreeKArgs<T> &t
                 g.Q[i * R + c * EPT + e] = q[e];
                 acc0[e].add_prod(p0[e], q[e]);
             }
+        }
         }
         block_cols<R>(acc0, c, s_red, mypart0);
         if (!grid_sync(tk.bar, tk.budget, tk.err, epoch)) return false;
@@ -318,11 +442,12 @@ __device__ __forceinline__ bool cg_dev(const CGArgs<T> &g, const TreeKArgs<T> &t
                 acc1[e].add_prod(rr, rr);
             }
         }
+        // look ahead: another iteration only if one is allowed and some
+        // column passes the test
+        if (it + 1 >= g.maxit) break;
         block_cols<R>(acc1, c, s_red, mypart1);
         if (!grid_sync(tk.bar, tk.budget, tk.err, epoch)) return false;
         grid_cols<R>(part1, s_rr);
-        // look ahead: another iteration only if some column passes the test
-        if (it + 1 >= g.maxit) break;
         if (threadIdx.x == 0) s_nact = 0;
         __syncthreads();
         if (threadIdx.x < R) {
@@ -334,8 +459,10 @@ __device__ __forceinline__ bool cg_dev(const CGArgs<T> &g, const TreeKArgs<T> &t
     }
     if (g.maxbits) {
         double m = 0.0;
-        for (int64_t k = gt; k < g.n * R; k += (int64_t)gridDim.x * blockDim.x)
-            m = fmax(m, fabs((double)g.X[k]));
+        for (int64_t i = slot; i < g.n; i += nslots) {
+#pragma unroll
+            for (int e = 0; e < EPT; ++e) m = fmax(m, fabs((double)g.X[i * R + c * EPT + e]));
+        }
         block_atomic_max(g.maxbits, m);
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -345,10 +472,6 @@ __device__ __forceinline__ bool cg_dev(const CGArgs<T> &g, const TreeKArgs<T> &t
     }
     return true;
 }
-
-// threads of k_cg_persist: the scan form and r > 1 columns keep 1024
-template <int R, bool EU>
-constexpr int cg_max_threads() { return (EU || R > 1) ? kPersistMaxThreads : kFusedMaxThreads; }
 
 template <typename T, int R, bool EU>
 __global__ void __launch_bounds__(cg_max_threads<R, EU>(), 1)
@@ -592,12 +715,19 @@ __global__ void __launch_bounds__(kFusedMaxThreads, 1)
     double *my0 = P0 + (int64_t)blockIdx.x * 32, *my1 = P1 + (int64_t)blockIdx.x * 32;
     Acc<T> acc0[1], acc1[1];
 
-    // e = 0, r = rhs (z = rhs for the tree solve)
+    // e = 0, r = rhs; z = rhs for the tree solve, else the inner CG's start
+    // (X = z = 0, R = Z = r) with the inner CG's own element mapping
     for (int64_t i = gt; i < a.n; i += nth) {
         const T y = a.rhs[i];
         a.e[i] = (T)0;
         a.r[i] = y;
-        if (TREE_ONLY) a.z[i] = y;
+        if (TREE_ONLY) {
+            a.z[i] = y;
+        } else {
+            a.z[i] = (T)0;
+            in.Rv[i] = y;
+            in.Z[i] = y;
+        }
     }
     if (!grid_sync(tk.bar, tk.budget, tk.err, epoch)) return;
     // Each pass starts with z = M^{-1} r (the only call site of the
@@ -607,12 +737,14 @@ __global__ void __launch_bounds__(kFusedMaxThreads, 1)
     double rz = 0.0, rr = 0.0;
     int k = 0;
     for (bool first = true;; first = false) {
+        // the inner CG leaves every z[i] written by the thread that reads it
+        // below; the tree solve writes out of order and needs the barrier
         if constexpr (TREE_ONLY) {
             if (!tree_solve_dev<T, 1, false>(tk, a.z, epoch, mx, ys)) return;
+            if (!grid_sync(tk.bar, tk.budget, tk.err, epoch)) return;
         } else {
-            if (!cg_dev<T, 1>(in, tk, epoch, ys)) return;
+            if (!cg_dev<T, 1>(in, tk, epoch, ys, true)) return;
         }
-        if (!grid_sync(tk.bar, tk.budget, tk.err, epoch)) return;
         // first: rz = r.z, rr = r.r;  later: r.z and r.z_old for beta
         acc0[0] = acc1[0] = Acc<T>();
         for (int64_t i = gt; i < a.n; i += nth) {
@@ -624,8 +756,7 @@ __global__ void __launch_bounds__(kFusedMaxThreads, 1)
         block_cols<1>(acc0, 0, s_red, my0);
         block_cols<1>(acc1, 0, s_red, my1);
         if (!grid_sync(tk.bar, tk.budget, tk.err, epoch)) return;
-        grid_cols<1>(P0, &s_v[0]);
-        grid_cols<1>(P1, &s_v[1]);
+        grid_cols2<1>(P0, &s_v[0], P1, &s_v[1]);
         const double rzn = s_v[0];
         T beta = (T)0;
         if (first) rr = s_v[1];
@@ -635,26 +766,51 @@ __global__ void __launch_bounds__(kFusedMaxThreads, 1)
         if (!grid_sync(tk.bar, tk.budget, tk.err, epoch)) return;
         if (k >= a.maxit || sqrt(rr) <= a.tol_abs) break;
         // q = A p, pq
+        // (two rows at a time, every load of both rows before the sums)
         acc0[0] = Acc<T>();
-        for (int64_t i = gt; i < a.n; i += nth) {
-            const T pi = a.p[i];
-            T qi = a.aD[i] * pi;
-            for (int32_t j = a.aptr[i]; j < a.aptr[i + 1]; ++j) qi += a.aw[j] * (pi - a.p[a.acol[j]]);
-            a.q[i] = qi;
-            acc0[0].add_prod(pi, qi);
+        for (int64_t i0 = gt; i0 < a.n; i0 += 2 * nth) {
+            constexpr int K = 4;
+            int32_t jb[2], je[2];
+            T pv[2], qv[2], dv[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int64_t i = i0 + u * nth;
+                const bool ok = i < a.n;
+                pv[u] = ok ? a.p[i] : (T)0;
+                dv[u] = ok ? a.aD[i] : (T)0;
+                jb[u] = ok ? a.aptr[i] : 0;
+                je[u] = ok ? a.aptr[i + 1] : 0;
+            }
+#pragma unroll
+            for (int u = 0; u < 2; ++u) qv[u] = dv[u] * pv[u];
+            lap_rows<T, 2, K, 1>(a.acol, a.aw, a.p, jb, je, pv, qv);
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int64_t i = i0 + u * nth;
+                if (i >= a.n) break;
+                a.q[i] = qv[u];
+                acc0[0].add_prod(pv[u], qv[u]);
+            }
         }
         block_cols<1>(acc0, 0, s_red, my0);
         if (!grid_sync(tk.bar, tk.budget, tk.err, epoch)) return;
         grid_cols<1>(P0, &s_v[2]);
         const T alpha = (T)(rz / s_v[2]);
-        // e += alpha p, r -= alpha q (z_old = z; z = r for the tree solve), rr
+        // e += alpha p, r -= alpha q, rr; z = r for the tree solve, else
+        // z_old = z and the next inner CG's start (X = z = 0, R = Z = r)
         acc1[0] = Acc<T>();
         for (int64_t i = gt; i < a.n; i += nth) {
             a.e[i] += alpha * a.p[i];
             const T ri = a.r[i] - alpha * a.q[i];
             a.r[i] = ri;
-            if (!TREE_ONLY) a.zo[i] = a.z[i];
-            if (TREE_ONLY) a.z[i] = ri;
+            if (TREE_ONLY) {
+                a.z[i] = ri;
+            } else {
+                a.zo[i] = a.z[i];
+                a.z[i] = (T)0;
+                in.Rv[i] = ri;
+                in.Z[i] = ri;
+            }
             acc1[0].add_prod(ri, ri);
         }
         block_cols<1>(acc1, 0, s_red, my1);
