@@ -307,6 +307,7 @@ struct TreeSchedule {
     int tail_k0 = 0;
     int64_t tail_n = 0;
     int64_t tail_c0 = 0;             // first contribution index of round tail_k0
+    std::vector<int64_t> contrib_off;   // host [rounds+1]: first contribution of each round
     DBuf<int32_t> tail_vid;          // [tail_n] global id of each local id
     DBuf<int4> fwd_loc;              // [n_rcv - rcv_off[tail_k0]]
     DBuf<int4> bwd_loc;              // [n - nroots - elim_off[tail_k0]]
@@ -512,8 +513,8 @@ __device__ inline void red_add_release_u32(unsigned int *p, unsigned int v) {
 // blocks pass the same barriers, so barrier b completes when the counter
 // reaches (b+1) * gridDim.x).  Arrival: one release reduction by thread 0,
 // which carries the block's writes (ordered before it by __syncthreads).
-// Wait: relaxed polls of the counter (the error flag and the poll budget
-// are looked at every 64 polls), then one acquire fence, which pairs with
+// Wait: relaxed polls of the counter, back to back (the error flag and the
+// poll budget are looked at every 64 polls), then one acquire fence, which pairs with
 // the other blocks' release reductions.  The testing flag is read after
 // the arrival, while the other blocks arrive.
 __device__ inline bool grid_sync(unsigned int *bar, long long budget, int *err,
@@ -539,7 +540,6 @@ __device__ inline bool grid_sync(unsigned int *bar, long long budget, int *err,
                     break;
                 }
             }
-            __nanosleep(32);
         }
         fence_acq_rel_gpu();
         s_ok = ok;

@@ -478,6 +478,7 @@ __global__ void __launch_bounds__(cg_max_threads<R, EU>(), 1)
     k_cg_persist(CGArgs<T> g, TreeKArgs<T> tk) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned int epoch = 0;
+    if constexpr (!EU) tree_tail_stage<T, R>(tk, reinterpret_cast<T *>(smem_raw));
     cg_dev<T, R, EU>(g, tk, epoch, reinterpret_cast<T *>(smem_raw));
 }
 
@@ -714,6 +715,7 @@ __global__ void __launch_bounds__(kFusedMaxThreads, 1)
     double *P0 = a.part, *P1 = a.part + (int64_t)gridDim.x * 32;
     double *my0 = P0 + (int64_t)blockIdx.x * 32, *my1 = P1 + (int64_t)blockIdx.x * 32;
     Acc<T> acc0[1], acc1[1];
+    tree_tail_stage<T, 1>(tk, ys);
 
     // e = 0, r = rhs; z = rhs for the tree solve, else the inner CG's start
     // (X = z = 0, R = Z = r) with the inner CG's own element mapping

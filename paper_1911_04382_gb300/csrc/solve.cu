@@ -12,6 +12,7 @@ __global__ void __launch_bounds__(kPersistMaxThreads, 1)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned int epoch = 0;
     double mx = 0.0;
+    tree_tail_stage<T, R>(a, reinterpret_cast<T *>(smem_raw));
     if (!tree_solve_dev<T, R>(a, Y, epoch, mx, reinterpret_cast<T *>(smem_raw))) return;
     if (maxbits) block_atomic_max(maxbits, mx);
 }

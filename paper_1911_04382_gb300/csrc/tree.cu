@@ -244,6 +244,13 @@ __global__ void k_tail_contrib(int64_t cnt, const int32_t *cv, const int32_t *lo
     if (c < cnt) out[c] = locmap[cv[c]];
 }
 
+// first contribution index of every round: beg[rcv_off[k]], k = 0..rounds
+__global__ void k_round_contrib(int64_t cnt, const int64_t *rcv_off, const int32_t *beg,
+                                int64_t *out) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < cnt) out[k] = beg[rcv_off[k]];
+}
+
 // Vertices alive at the tail's first round: at most this many (local ids fit
 // the shared-memory stage of the solve for small r).
 constexpr int64_t kTailMax = 49152;
@@ -275,8 +282,13 @@ static void tree_pack(grass_ctx_t ctx, grass_tree_t T) {
            (const int4 *)S.fwd_rec.p + r0, (const int32_t *)locmap.p, S.fwd_loc.p);
     launch(ctx, k_tail_bwd, cdiv(ne - e0, kBlock), kBlock, 0, ne - e0,
            (const int4 *)S.bwd_rec.p + e0, (const int32_t *)locmap.p, S.bwd_loc.p);
-    int32_t c0 = 0;
-    d2h(ctx, &c0, S.rcv_beg.p + r0, sizeof(int32_t));
+    DBuf<int64_t> coff;
+    coff.alloc(S.rounds + 1);
+    launch(ctx, k_round_contrib, cdiv(S.rounds + 1, kBlock), kBlock, 0, (int64_t)S.rounds + 1,
+           (const int64_t *)S.d_offs.p, (const int32_t *)S.rcv_beg.p, coff.p);
+    S.contrib_off.assign(S.rounds + 1, 0);
+    d2h(ctx, S.contrib_off.data(), coff.p, (S.rounds + 1) * sizeof(int64_t));
+    const int64_t c0 = S.contrib_off[k0];
     S.tail_c0 = c0;
     S.contrib_loc.alloc(S.n_contrib - c0);
     launch(ctx, k_tail_contrib, cdiv(S.n_contrib - c0, kBlock), kBlock, 0, S.n_contrib - c0,

@@ -32,6 +32,9 @@ template <typename T>
 struct TreeKArgs {
     int rounds, K1;
     int64_t base, ntl, r0, e0, c0;
+    // the tail (rounds K1..): first forward record and count, first backward
+    // record and count, first contribution index and count
+    int64_t tf0, tnf, tg0, tnb, tc0, ntc;
     const int64_t *rcv_off, *elim_off;
     const int4 *fwd_rec, *bwd_rec, *fwd_loc, *bwd_loc;
     const typename PackT<T>::V2 *fm;
@@ -94,9 +97,9 @@ __device__ inline double bwd_packed(int c, int4 r, typename PackT<T>::V4 cf, T *
 }
 
 // A thread's items of one round, at most kBatch of them, loaded together so
-// their latencies overlap: item j is index lo + slot + j * nslots.  At 1024
-// threads per block (64 registers) more than one item per batch spills; with
-// 512 threads and 4 items the solve was no faster and the CG phases slower.
+// their latencies overlap: item j is index lo + slot + j * nslots.  More
+// than one item per batch spills, at 64 registers a thread (1024 threads)
+// and inside the fused Krylov kernels at 128.
 constexpr int kBatch = 1;
 
 template <typename T>
@@ -152,13 +155,18 @@ __device__ __forceinline__ void load_bwd(BwdBatch<T> &b, const int4 *rec,
 }
 
 // Shared-memory layout of the tail: the staged rows (ntl x R values), then
-// its forward and backward records and coefficients, each 32-byte aligned.
+// its forward and backward records and coefficients, then its contribution
+// lists beyond the two inline ones (ends per record, contributor local ids,
+// multipliers), each 32-byte aligned.  Everything after the rows depends on
+// the tree alone: staged once per launch (tree_tail_stage).
 template <typename T, int R>
 struct TailSmem {
     int4 *frec, *brec;
     typename PackT<T>::V2 *fm;
     typename PackT<T>::V4 *bc;
-    __device__ TailSmem(T *ys, int64_t ntl, int64_t nf, int64_t nb) {
+    int32_t *cend, *cloc;
+    T *cmul;
+    __device__ TailSmem(T *ys, int64_t ntl, int64_t nf, int64_t nb, int64_t nc) {
         auto up = [](size_t x) { return (x + 31) & ~size_t(31); };
         char *p = reinterpret_cast<char *>(ys);
         size_t o = up((size_t)ntl * R * sizeof(T));
@@ -169,29 +177,48 @@ struct TailSmem {
         fm = reinterpret_cast<typename PackT<T>::V2 *>(p + o);
         o = up(o + (size_t)nf * sizeof(typename PackT<T>::V2));
         bc = reinterpret_cast<typename PackT<T>::V4 *>(p + o);
+        o = up(o + (size_t)nb * sizeof(typename PackT<T>::V4));
+        cend = reinterpret_cast<int32_t *>(p + o);
+        o = up(o + (size_t)nf * sizeof(int32_t));
+        cloc = reinterpret_cast<int32_t *>(p + o);
+        o = up(o + (size_t)nc * sizeof(int32_t));
+        cmul = reinterpret_cast<T *>(p + o);
     }
     // bytes of the whole layout (host and device)
-    __host__ __device__ static size_t bytes(int64_t ntl, int64_t nf, int64_t nb) {
+    __host__ __device__ static size_t bytes(int64_t ntl, int64_t nf, int64_t nb, int64_t nc) {
         auto up = [](size_t x) { return (x + 31) & ~size_t(31); };
         size_t o = up((size_t)ntl * R * sizeof(T));
         o = up(o + (size_t)nf * sizeof(int4));
         o = up(o + (size_t)nb * sizeof(int4));
         o = up(o + (size_t)nf * sizeof(typename PackT<T>::V2));
-        return o + (size_t)nb * sizeof(typename PackT<T>::V4);
+        o = up(o + (size_t)nb * sizeof(typename PackT<T>::V4));
+        o = up(o + (size_t)nf * sizeof(int32_t));
+        o = up(o + (size_t)nc * sizeof(int32_t));
+        return o + (size_t)nc * sizeof(T);
     }
 };
 
 // Forward items of a batch on the vector V (global Y, or the tail's shared
-// copy with ids shifted by `base`); all gathers issued before any store.
+// copy with ids shifted by `base`); all gathers issued before any store.  On
+// the global vector the end of a record's contribution list and its first
+// contributor and multiplier load with the inline gathers, so a receiver
+// with more than two contributions costs one more round trip, not three.
 template <typename T, int R>
 __device__ __forceinline__ void run_fwd(const FwdBatch<T> &b, const TreeKArgs<T> &a, T *V, int64_t base,
-                               bool local, int c) {
+                               const TailSmem<T, R> *sm, int c) {
     constexpr int EPT = Lay<R>::EPT;
     T yu[kBatch][EPT], y0[kBatch][EPT], y1[kBatch][EPT];
+    int32_t kend[kBatch], v3[kBatch];
+    T m3[kBatch];
 #pragma unroll
     for (int j = 0; j < kBatch; ++j) {
         if (j >= b.cnt) break;
         const int4 r = b.r[j];
+        if (!sm && r.w >= 0) {
+            kend[j] = a.beg[b.i0 + j * b.step + 1];
+            v3[j] = a.cv[r.w];
+            m3[j] = a.cm[r.w];
+        }
         const T *pu = V + (r.x - base) * R + c * EPT;
         const T *p0 = V + (r.y - base) * R + c * EPT;
 #pragma unroll
@@ -220,12 +247,25 @@ __device__ __forceinline__ void run_fwd(const FwdBatch<T> &b, const TreeKArgs<T>
         }
         if (r.w >= 0) {
             const int64_t i = b.i0 + j * b.step;
-            for (int32_t k = r.w; k < a.beg[i + 1]; ++k) {
-                int64_t v = local ? (int64_t)a.contrib_loc[k - a.c0] : (int64_t)a.cv[k];
-                const T *pv = V + (v - base) * R + c * EPT;
-                T mlt = a.cm[k];
+            if (sm) {
+                // tail: shared copies, indexed from the tail's first record
+                // and first contribution
+                for (int64_t k = r.w - a.tc0; k < sm->cend[i - a.tf0]; ++k) {
+                    const T *pv = V + ((int64_t)sm->cloc[k] - base) * R + c * EPT;
+                    const T mlt = sm->cmul[k];
 #pragma unroll
-                for (int e = 0; e < EPT; ++e) acc[e] += mlt * pv[e];
+                    for (int e = 0; e < EPT; ++e) acc[e] += mlt * pv[e];
+                }
+            } else {
+                const T *p3 = V + ((int64_t)v3[j] - base) * R + c * EPT;
+#pragma unroll
+                for (int e = 0; e < EPT; ++e) acc[e] += m3[j] * p3[e];
+                for (int32_t k = r.w + 1; k < kend[j]; ++k) {
+                    const T *pv = V + ((int64_t)a.cv[k] - base) * R + c * EPT;
+                    const T mlt = a.cm[k];
+#pragma unroll
+                    for (int e = 0; e < EPT; ++e) acc[e] += mlt * pv[e];
+                }
             }
         }
         T *pu = V + (r.x - base) * R + c * EPT;
@@ -275,6 +315,28 @@ __device__ __forceinline__ double run_bwd(const BwdBatch<T> &b, T *V, int64_t ba
     return (double)mx;
 }
 
+// Block 0 copies the tail's records, coefficients and contribution lists
+// into shared memory (after the rows); once per launch, before the first
+// solve (the solve's tail waits on __syncthreads after it).
+template <typename T, int R>
+__device__ inline void tree_tail_stage(const TreeKArgs<T> &a, T *ys) {
+    if (blockIdx.x != 0 || a.K1 >= a.rounds) return;
+    const TailSmem<T, R> sm(ys, a.ntl, a.tnf, a.tnb, a.ntc);
+    for (int64_t i = threadIdx.x; i < a.tnf; i += blockDim.x) {
+        sm.frec[i] = a.fwd_loc[a.tf0 - a.r0 + i];
+        sm.fm[i] = a.fm[a.tf0 + i];
+        sm.cend[i] = (int32_t)(a.beg[a.tf0 + i + 1] - a.tc0);
+    }
+    for (int64_t i = threadIdx.x; i < a.tnb; i += blockDim.x) {
+        sm.brec[i] = a.bwd_loc[a.tg0 - a.e0 + i];
+        sm.bc[i] = a.bc[a.tg0 + i];
+    }
+    for (int64_t k = threadIdx.x; k < a.ntc; k += blockDim.x) {
+        sm.cloc[k] = a.contrib_loc[a.tc0 - a.c0 + k];
+        sm.cmul[k] = a.cm[a.tc0 + k];
+    }
+}
+
 // Solve in place on Y (n x R).  Called by every thread of a cooperative
 // grid; returns false when a barrier wait ran out (the caller must return).
 // mx accumulates max |x| over the values this thread wrote.  Ends without
@@ -300,45 +362,36 @@ __device__ __forceinline__ bool tree_solve_dev(const TreeKArgs<T> &a, T *Y, unsi
     fb.cnt = 0;
     if (a.K1 > 0) load_fwd(fb, a.fwd_rec, a.fm, 0, s_roff[0], s_roff[1], slot, nslots);
     for (int k = 0; k < a.K1; ++k) {
-        run_fwd<T, R>(fb, a, Y, 0, false, c);
+        run_fwd<T, R>(fb, a, Y, 0, (const TailSmem<T, R> *)nullptr, c);
         for (int64_t lo = s_roff[k] + kBatch * nslots; lo < s_roff[k + 1]; lo += kBatch * nslots) {
             FwdBatch<T> more;
             load_fwd(more, a.fwd_rec, a.fm, 0, lo, s_roff[k + 1], slot, nslots);
-            run_fwd<T, R>(more, a, Y, 0, false, c);
+            run_fwd<T, R>(more, a, Y, 0, (const TailSmem<T, R> *)nullptr, c);
         }
         if (k + 1 < a.K1) load_fwd(fb, a.fwd_rec, a.fm, 0, s_roff[k + 1], s_roff[k + 2], slot, nslots);
         if (!grid_sync(a.bar, a.budget, a.err, epoch)) return false;
     }
-    // rounds K1 .. end in block 0, on the tail vertices staged in shared
-    // memory together with the tail's records and coefficients (one bulk
-    // copy; each round then runs from shared memory alone)
+    // rounds K1 .. end in block 0, on the tail vertices gathered into shared
+    // memory; the tail's records, coefficients and contribution lists are
+    // there already (tree_tail_stage), so each round runs from shared memory
     if (blockIdx.x == 0) {
         const int64_t bslot = threadIdx.x / TPR, bslots = blockDim.x / TPR;
         const int64_t base = a.base, ntl = a.ntl;
-        const int64_t f0 = s_roff[a.K1], f1 = s_roff[a.rounds];
-        const int64_t g0 = s_eoff[a.K1], g1 = s_eoff[a.rounds];
-        const TailSmem<T, R> sm(ys, ntl, f1 - f0, g1 - g0);
+        const int64_t f0 = a.tf0, g0 = a.tg0;
+        const TailSmem<T, R> sm(ys, ntl, a.tnf, a.tnb, a.ntc);
         for (int64_t idx = threadIdx.x; idx < ntl * R; idx += blockDim.x)
             ys[idx] = Y[(int64_t)a.tail_vid[base + idx / R] * R + idx % R];
-        for (int64_t i = threadIdx.x; i < f1 - f0; i += blockDim.x) {
-            sm.frec[i] = a.fwd_loc[f0 - a.r0 + i];
-            sm.fm[i] = a.fm[f0 + i];
-        }
-        for (int64_t i = threadIdx.x; i < g1 - g0; i += blockDim.x) {
-            sm.brec[i] = a.bwd_loc[g0 - a.e0 + i];
-            sm.bc[i] = a.bc[g0 + i];
-        }
         __syncthreads();
         FwdBatch<T> tb;
         tb.cnt = 0;
         if (a.K1 < a.rounds)
             load_fwd(tb, sm.frec, sm.fm, f0, s_roff[a.K1], s_roff[a.K1 + 1], bslot, bslots);
         for (int k = a.K1; k < a.rounds; ++k) {
-            run_fwd<T, R>(tb, a, ys, base, true, c);
+            run_fwd<T, R>(tb, a, ys, base, &sm, c);
             for (int64_t lo = s_roff[k] + kBatch * bslots; lo < s_roff[k + 1]; lo += kBatch * bslots) {
                 FwdBatch<T> more;
                 load_fwd(more, sm.frec, sm.fm, f0, lo, s_roff[k + 1], bslot, bslots);
-                run_fwd<T, R>(more, a, ys, base, true, c);
+                run_fwd<T, R>(more, a, ys, base, &sm, c);
             }
             if (k + 1 < a.rounds)
                 load_fwd(tb, sm.frec, sm.fm, f0, s_roff[k + 1], s_roff[k + 2], bslot, bslots);
@@ -769,7 +822,8 @@ inline TreeKArgs<T> tree_kargs(grass_ctx_t ctx, const grass_tree_s *Tr, const Tr
     // the tail's rows and its records / coefficients must fit the budget
     auto tail_bytes = [&](int k) {
         return TailSmem<T, R>::bytes(alive_at(k), S.rcv_off[S.rounds] - S.rcv_off[k],
-                                     S.elim_off[S.rounds] - S.elim_off[k]);
+                                     S.elim_off[S.rounds] - S.elim_off[k],
+                                     S.contrib_off[S.rounds] - S.contrib_off[k]);
     };
     int K1 = S.tail_k0;
     while (K1 < S.rounds && (tail_bytes(K1) > kTailSmem ||
@@ -785,6 +839,12 @@ inline TreeKArgs<T> tree_kargs(grass_ctx_t ctx, const grass_tree_s *Tr, const Tr
     ka.r0 = S.rcv_off[S.tail_k0];
     ka.e0 = S.elim_off[S.tail_k0];
     ka.c0 = S.tail_c0;
+    ka.tf0 = S.rcv_off[K1];
+    ka.tnf = S.rcv_off[S.rounds] - S.rcv_off[K1];
+    ka.tg0 = S.elim_off[K1];
+    ka.tnb = S.elim_off[S.rounds] - S.elim_off[K1];
+    ka.tc0 = S.contrib_off[K1];
+    ka.ntc = S.contrib_off[S.rounds] - S.contrib_off[K1];
     ka.rcv_off = S.d_offs.p;
     ka.elim_off = S.d_offs.p + (S.rounds + 1);
     ka.fwd_rec = S.fwd_rec.p;
