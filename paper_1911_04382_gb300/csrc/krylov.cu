@@ -216,6 +216,54 @@ __device__ __forceinline__ void lap_rows(const int32_t *col, const T *w, const T
     }
 }
 
+// One-column element loops.  FP32 vectors are walked in 16-byte chunks:
+// thread gt takes chunks gt, gt + nth, ... (four floats, one vector access
+// per operand) and the n mod 4 leftover elements go to threads 0, 1, 2.
+// Every such loop over the same vectors uses this mapping, so an element is
+// always read and written by the same thread.  FP64 vectors (which may be
+// the caller's own, 8-byte aligned) take one element per step.
+template <typename T>
+struct Chunk {
+    static constexpr int W = sizeof(T) == 4 ? 4 : 1;
+};
+
+template <typename T, typename F>
+__device__ __forceinline__ void for_chunks(int64_t n, int64_t gt, int64_t nth, F &&f) {
+    constexpr int W = Chunk<T>::W;
+    const int64_t nv = n / W;
+    for (int64_t v = gt; v < nv; v += nth) f(v * W, W);
+    if constexpr (W > 1) {
+        if (gt < n - nv * W) f(nv * W + gt, 1);
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void ld_chunk(const T *p, int cnt, T (&v)[Chunk<T>::W]) {
+    if constexpr (Chunk<T>::W == 4) {
+        if (cnt == 4) {
+            const float4 q = *reinterpret_cast<const float4 *>(p);
+            v[0] = q.x;
+            v[1] = q.y;
+            v[2] = q.z;
+            v[3] = q.w;
+            return;
+        }
+        v[1] = v[2] = v[3] = (T)0;
+    }
+    v[0] = p[0];
+}
+
+template <typename T>
+__device__ __forceinline__ void st_chunk(T *p, int cnt, const T (&v)[Chunk<T>::W]) {
+    if constexpr (Chunk<T>::W == 4) {
+        if (cnt == 4) {
+            *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+            return;
+        }
+    }
+    p[0] = v[0];
+}
+
 // Two column sums at once: warps 0..R-1 reduce part0 and warps R..2R-1
 // part1 (each the same order as grid_cols), when the block has 2R warps.
 template <int R>
@@ -253,9 +301,10 @@ __device__ inline void grid_cols2(const double *part0, double *s_out0, const dou
 // k_cg_persist and inside the fused PCG).  Returns false when a barrier wait
 // ran out (the caller must return).  Ends without a trailing grid barrier:
 // every element of X is last written (and read by the max |X| pass) by the
-// thread that owns it under the slot mapping (rows slot, slot + nslots, ...;
-// columns c*EPT ..), so a caller with the same mapping reads X at once.
-// preset: the caller has already set X = 0, R = Z = Y with that mapping and
+// thread that owns it under the element mapping (one column of the
+// elimination form: the chunks of for_chunks; else rows slot, slot +
+// nslots, ... and columns c*EPT ..), so a caller with the same mapping
+// reads X at once.  preset: the caller has already set X = 0, R = Z = Y and
 // passed a grid barrier since.
 template <typename T, int R, bool EU = false>
 __device__ __forceinline__ bool cg_dev(const CGArgs<T> &g, const TreeKArgs<T> &tk,
@@ -273,7 +322,20 @@ __device__ __forceinline__ bool cg_dev(const CGArgs<T> &g, const TreeKArgs<T> &t
     double mx = 0.0;
     Acc<T> acc0[EPT], acc1[EPT];
 
-    if (!preset) {
+    // one column of the elimination form: the chunked element loops (the
+    // mapping the fused PCG uses for the same vectors)
+    constexpr bool CH = R == 1 && !EU;
+    constexpr int W = Chunk<T>::W;
+    if (!preset && CH) {
+        for_chunks<T>(g.n, gt, (int64_t)gridDim.x * blockDim.x, [&](int64_t i0, int cnt) {
+            T y[W], zero[W] = {};
+            ld_chunk(g.Y + i0, cnt, y);
+            st_chunk(g.X + i0, cnt, zero);
+            st_chunk(g.Rv + i0, cnt, y);
+            st_chunk(g.Z + i0, cnt, y);
+        });
+        if (!grid_sync(tk.bar, tk.budget, tk.err, epoch)) return false;
+    } else if (!preset) {
         for (int64_t i = slot; i < g.n; i += nslots) {
 #pragma unroll
             for (int e = 0; e < EPT; ++e) {
@@ -304,6 +366,20 @@ __device__ __forceinline__ bool cg_dev(const CGArgs<T> &g, const TreeKArgs<T> &t
         if (!grid_sync(tk.bar, tk.budget, tk.err, epoch)) return false;
 #pragma unroll
         for (int e = 0; e < EPT; ++e) acc0[e] = acc1[e] = Acc<T>();
+        if constexpr (CH) {
+            for_chunks<T>(g.n, gt, (int64_t)gridDim.x * blockDim.x, [&](int64_t i0, int cnt) {
+                T z[W], rr[W];
+                ld_chunk(g.Z + i0, cnt, z);
+                ld_chunk(g.Rv + i0, cnt, rr);
+#pragma unroll
+                for (int w = 0; w < W; ++w) {
+                    if (w >= cnt) break;
+                    acc0[0].add_prod(rr[w], z[w]);
+                    if (it == 0) acc1[0].add_prod(rr[w], rr[w]);
+                }
+                if (it == 0) st_chunk(g.P + i0, cnt, z);
+            });
+        } else {
         for (int64_t i = slot; i < g.n; i += nslots) {
 #pragma unroll
             for (int e = 0; e < EPT; ++e) {
@@ -315,6 +391,7 @@ __device__ __forceinline__ bool cg_dev(const CGArgs<T> &g, const TreeKArgs<T> &t
                     acc1[e].add_prod(rr, rr);
                 }
             }
+        }
         }
         block_cols<R>(acc0, c, s_red, mypart0);
         if (it == 0) block_cols<R>(acc1, c, s_red, mypart1);
@@ -332,6 +409,19 @@ __device__ __forceinline__ bool cg_dev(const CGArgs<T> &g, const TreeKArgs<T> &t
                 s_al[j] = beta;
             }
             __syncthreads();
+            if constexpr (CH) {
+                if (s_act[0]) {
+                    const T be = (T)s_al[0];
+                    for_chunks<T>(g.n, gt, (int64_t)gridDim.x * blockDim.x, [&](int64_t i0, int cnt) {
+                        T z[W], pv[W];
+                        ld_chunk(g.Z + i0, cnt, z);
+                        ld_chunk(g.P + i0, cnt, pv);
+#pragma unroll
+                        for (int w = 0; w < W; ++w) pv[w] = z[w] + be * pv[w];
+                        st_chunk(g.P + i0, cnt, pv);
+                    });
+                }
+            } else {
             for (int64_t i = slot; i < g.n; i += nslots) {
 #pragma unroll
                 for (int e = 0; e < EPT; ++e) {
@@ -340,6 +430,7 @@ __device__ __forceinline__ bool cg_dev(const CGArgs<T> &g, const TreeKArgs<T> &t
                     int64_t k = i * R + j;
                     g.P[k] = g.Z[k] + (T)s_al[j] * g.P[k];
                 }
+            }
             }
             if (!grid_sync(tk.bar, tk.budget, tk.err, epoch)) return false;
         }
@@ -427,6 +518,32 @@ __device__ __forceinline__ bool cg_dev(const CGArgs<T> &g, const TreeKArgs<T> &t
         // X += alpha P, R -= alpha Q, Z = R, partial R.R
 #pragma unroll
         for (int e = 0; e < EPT; ++e) acc1[e] = Acc<T>();
+        if constexpr (CH) {
+            const T a = (T)s_al[0];
+            for_chunks<T>(g.n, gt, (int64_t)gridDim.x * blockDim.x, [&](int64_t i0, int cnt) {
+                T rr[W];
+                ld_chunk(g.Rv + i0, cnt, rr);
+                if (a != (T)0) {
+                    T xv[W], pv[W], qv[W];
+                    ld_chunk(g.X + i0, cnt, xv);
+                    ld_chunk(g.P + i0, cnt, pv);
+                    ld_chunk(g.Q + i0, cnt, qv);
+#pragma unroll
+                    for (int w = 0; w < W; ++w) {
+                        xv[w] += a * pv[w];
+                        rr[w] -= a * qv[w];
+                    }
+                    st_chunk(g.X + i0, cnt, xv);
+                    st_chunk(g.Rv + i0, cnt, rr);
+                }
+                st_chunk(g.Z + i0, cnt, rr);
+#pragma unroll
+                for (int w = 0; w < W; ++w) {
+                    if (w >= cnt) break;
+                    acc1[0].add_prod(rr[w], rr[w]);
+                }
+            });
+        } else {
         for (int64_t i = slot; i < g.n; i += nslots) {
 #pragma unroll
             for (int e = 0; e < EPT; ++e) {
@@ -441,6 +558,7 @@ __device__ __forceinline__ bool cg_dev(const CGArgs<T> &g, const TreeKArgs<T> &t
                 g.Z[k] = rr;
                 acc1[e].add_prod(rr, rr);
             }
+        }
         }
         // look ahead: another iteration only if one is allowed and some
         // column passes the test
@@ -459,9 +577,18 @@ __device__ __forceinline__ bool cg_dev(const CGArgs<T> &g, const TreeKArgs<T> &t
     }
     if (g.maxbits) {
         double m = 0.0;
+        if constexpr (CH) {
+            for_chunks<T>(g.n, gt, (int64_t)gridDim.x * blockDim.x, [&](int64_t i0, int cnt) {
+                T xv[W];
+                ld_chunk(g.X + i0, cnt, xv);
+#pragma unroll
+                for (int w = 0; w < W; ++w) m = fmax(m, fabs((double)xv[w]));
+            });
+        } else {
         for (int64_t i = slot; i < g.n; i += nslots) {
 #pragma unroll
             for (int e = 0; e < EPT; ++e) m = fmax(m, fabs((double)g.X[i * R + c * EPT + e]));
+        }
         }
         block_atomic_max(g.maxbits, m);
     }
@@ -524,6 +651,12 @@ static void cg_persistent(grass_ctx_t ctx, grass_sparsifier_t S, bool with_D, co
     const int grid = eu ? coop_grid(ctx, k_cg_persist<T, R, (R == 1)>, threads, smem, n * Lay<R>::TPR)
                         : coop_grid(ctx, k_cg_persist<T, R, false>, threads, smem, n * Lay<R>::TPR);
     if ((size_t)grid * 32 * 2 > ctx->partials.n) fail(GRASS_ERR_CUDA, "partials buffer too small");
+    // the chunked element loops (one FP32 column, elimination form) take
+    // 16-byte accesses; all their vectors are the context's own scratch
+    if (R == 1 && !eu && Chunk<T>::W > 1 &&
+        (((uintptr_t)Y | (uintptr_t)X | (uintptr_t)a.Rv | (uintptr_t)a.Z | (uintptr_t)a.P |
+          (uintptr_t)a.Q) & 15))
+        fail(GRASS_ERR_INVALID, "inner CG vectors must be 16-byte aligned");
     if (eu) euler_kargs<T>(ctx, Tr, grid, &a.eu);
     GCK(cudaMemsetAsync(tk.bar, 0, sizeof(unsigned int), ctx->stream));
     // roofline accounting: algorithmic bytes per iteration and of the start
@@ -715,22 +848,25 @@ __global__ void __launch_bounds__(kFusedMaxThreads, 1)
     double *P0 = a.part, *P1 = a.part + (int64_t)gridDim.x * 32;
     double *my0 = P0 + (int64_t)blockIdx.x * 32, *my1 = P1 + (int64_t)blockIdx.x * 32;
     Acc<T> acc0[1], acc1[1];
+    constexpr int W = Chunk<T>::W;
     tree_tail_stage<T, 1>(tk, ys);
 
+    // Element loops take the chunks of for_chunks (the inner CG's mapping).
     // e = 0, r = rhs; z = rhs for the tree solve, else the inner CG's start
-    // (X = z = 0, R = Z = r) with the inner CG's own element mapping
-    for (int64_t i = gt; i < a.n; i += nth) {
-        const T y = a.rhs[i];
-        a.e[i] = (T)0;
-        a.r[i] = y;
+    // (X = z = 0, R = Z = r)
+    for_chunks<T>(a.n, gt, nth, [&](int64_t i0, int cnt) {
+        T y[W], zero[W] = {};
+        ld_chunk(a.rhs + i0, cnt, y);
+        st_chunk(a.e + i0, cnt, zero);
+        st_chunk(a.r + i0, cnt, y);
         if (TREE_ONLY) {
-            a.z[i] = y;
+            st_chunk(a.z + i0, cnt, y);
         } else {
-            a.z[i] = (T)0;
-            in.Rv[i] = y;
-            in.Z[i] = y;
+            st_chunk(a.z + i0, cnt, zero);
+            st_chunk(in.Rv + i0, cnt, y);
+            st_chunk(in.Z + i0, cnt, y);
         }
-    }
+    });
     if (!grid_sync(tk.bar, tk.budget, tk.err, epoch)) return;
     // Each pass starts with z = M^{-1} r (the only call site of the
     // preconditioner), then p, then the test, the product and the updates;
@@ -749,12 +885,19 @@ __global__ void __launch_bounds__(kFusedMaxThreads, 1)
         }
         // first: rz = r.z, rr = r.r;  later: r.z and r.z_old for beta
         acc0[0] = acc1[0] = Acc<T>();
-        for (int64_t i = gt; i < a.n; i += nth) {
-            const T ri = a.r[i];
-            acc0[0].add_prod(ri, a.z[i]);
-            if (first) acc1[0].add_prod(ri, ri);
-            else if (!TREE_ONLY) acc1[0].add_prod(ri, a.zo[i]);
-        }
+        for_chunks<T>(a.n, gt, nth, [&](int64_t i0, int cnt) {
+            T rv[W], zv[W], ov[W];
+            ld_chunk(a.r + i0, cnt, rv);
+            ld_chunk(a.z + i0, cnt, zv);
+            if (!first && !TREE_ONLY) ld_chunk(a.zo + i0, cnt, ov);
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                if (w >= cnt) break;
+                acc0[0].add_prod(rv[w], zv[w]);
+                if (first) acc1[0].add_prod(rv[w], rv[w]);
+                else if (!TREE_ONLY) acc1[0].add_prod(rv[w], ov[w]);
+            }
+        });
         block_cols<1>(acc0, 0, s_red, my0);
         block_cols<1>(acc1, 0, s_red, my1);
         if (!grid_sync(tk.bar, tk.budget, tk.err, epoch)) return;
@@ -764,7 +907,16 @@ __global__ void __launch_bounds__(kFusedMaxThreads, 1)
         if (first) rr = s_v[1];
         else beta = (T)((rzn - (TREE_ONLY ? 0.0 : s_v[1])) / rz);
         rz = rzn;
-        for (int64_t i = gt; i < a.n; i += nth) a.p[i] = first ? a.z[i] : a.z[i] + beta * a.p[i];
+        for_chunks<T>(a.n, gt, nth, [&](int64_t i0, int cnt) {
+            T zv[W], pv[W];
+            ld_chunk(a.z + i0, cnt, zv);
+            if (!first) {
+                ld_chunk(a.p + i0, cnt, pv);
+#pragma unroll
+                for (int w = 0; w < W; ++w) zv[w] += beta * pv[w];
+            }
+            st_chunk(a.p + i0, cnt, zv);
+        });
         if (!grid_sync(tk.bar, tk.budget, tk.err, epoch)) return;
         if (k >= a.maxit || sqrt(rr) <= a.tol_abs) break;
         // q = A p, pq
@@ -801,20 +953,35 @@ __global__ void __launch_bounds__(kFusedMaxThreads, 1)
         // e += alpha p, r -= alpha q, rr; z = r for the tree solve, else
         // z_old = z and the next inner CG's start (X = z = 0, R = Z = r)
         acc1[0] = Acc<T>();
-        for (int64_t i = gt; i < a.n; i += nth) {
-            a.e[i] += alpha * a.p[i];
-            const T ri = a.r[i] - alpha * a.q[i];
-            a.r[i] = ri;
-            if (TREE_ONLY) {
-                a.z[i] = ri;
-            } else {
-                a.zo[i] = a.z[i];
-                a.z[i] = (T)0;
-                in.Rv[i] = ri;
-                in.Z[i] = ri;
+        for_chunks<T>(a.n, gt, nth, [&](int64_t i0, int cnt) {
+            T ev[W], pv[W], rv[W], qv[W];
+            ld_chunk(a.e + i0, cnt, ev);
+            ld_chunk(a.p + i0, cnt, pv);
+            ld_chunk(a.r + i0, cnt, rv);
+            ld_chunk(a.q + i0, cnt, qv);
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                ev[w] += alpha * pv[w];
+                rv[w] -= alpha * qv[w];
             }
-            acc1[0].add_prod(ri, ri);
-        }
+            st_chunk(a.e + i0, cnt, ev);
+            st_chunk(a.r + i0, cnt, rv);
+            if (TREE_ONLY) {
+                st_chunk(a.z + i0, cnt, rv);
+            } else {
+                T zv[W], zero[W] = {};
+                ld_chunk(a.z + i0, cnt, zv);
+                st_chunk(a.zo + i0, cnt, zv);
+                st_chunk(a.z + i0, cnt, zero);
+                st_chunk(in.Rv + i0, cnt, rv);
+                st_chunk(in.Z + i0, cnt, rv);
+            }
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                if (w >= cnt) break;
+                acc1[0].add_prod(rv[w], rv[w]);
+            }
+        });
         block_cols<1>(acc1, 0, s_red, my1);
         if (!grid_sync(tk.bar, tk.budget, tk.err, epoch)) return;
         grid_cols<1>(P1, &s_v[3]);
@@ -889,6 +1056,10 @@ static int pcg_fused(grass_ctx_t ctx, grass_sparsifier_t S, const T *rhs, T *e, 
     in.iter_acc = ctx->scal.p + DS_RED + DS_ITER;
     in.maxbits = nullptr;
     if ((size_t)grid * 32 * 2 > ctx->partials.n) fail(GRASS_ERR_CUDA, "partials buffer too small");
+    if (Chunk<T>::W > 1 && (((uintptr_t)rhs | (uintptr_t)e | (uintptr_t)r | (uintptr_t)z |
+                             (uintptr_t)p | (uintptr_t)q | (uintptr_t)zold | (uintptr_t)in.Rv |
+                             (uintptr_t)in.Z) & 15))
+        fail(GRASS_ERR_INVALID, "PCG vectors must be 16-byte aligned");
     memset_d(ctx, out, 0, 2 * sizeof(double));
     GCK(cudaMemsetAsync(tk.bar, 0, sizeof(unsigned int), ctx->stream));
     // roofline accounting: bytes per outer iteration (SpMV with A, the vector
