@@ -276,7 +276,7 @@ grass_status grass_ctx_set_wait_limit(grass_ctx_t ctx, int64_t polls, int hold_b
     if (!ctx) return GRASS_ERR_INVALID;
     API_BEGIN(ctx)
     need(polls >= 0, "polls must be >= 0");
-    ctx->wait_budget = polls > 0 ? (long long)polls : (1LL << 24);
+    ctx->wait_budget = polls > 0 ? (long long)polls : (1LL << 23);
     unsigned int h = hold_barriers ? 1u : 0u;
     GCK(cudaMemcpyAsync(ctx->gbar.p + 2, &h, sizeof(h), cudaMemcpyHostToDevice, ctx->stream));
     ctx->sync();

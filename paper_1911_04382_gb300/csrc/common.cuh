@@ -99,12 +99,12 @@ struct grass_ctx_s {
     grass::DBuf<char> scratch[grass::SCR_COUNT];
     // bounded device waits: barrier state and poll budget (flags[3] = timeout)
     grass::DBuf<unsigned int> gbar;
-    long long wait_budget = 1LL << 24;
+    long long wait_budget = 1LL << 23;   // polls; about 0.15 us each on GB300
     int num_sms = 0;
     // launch-shape knobs (grass_ctx_set_param)
     int tree_bpsm = 1;
     int tree_threads = 1024;
-    int64_t tree_tail_items = 4096;
+    int64_t tree_tail_items = 2048;
     int euler_solve = 1;   // scan form for grounded r = 1 solves without D
     int64_t euler_max_n = 4000000;   // trees larger than this keep the elimination rounds
     // co-resident grid of each cooperative kernel shape, per context (no
