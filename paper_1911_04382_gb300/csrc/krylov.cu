@@ -301,9 +301,9 @@ __device__ inline void grid_cols2(const double *part0, double *s_out0, const dou
 // k_cg_persist and inside the fused PCG).  Returns false when a barrier wait
 // ran out (the caller must return).  Ends without a trailing grid barrier:
 // every element of X is last written (and read by the max |X| pass) by the
-// thread that owns it under the element mapping (one column of the
-// elimination form: the chunks of for_chunks; else rows slot, slot +
-// nslots, ... and columns c*EPT ..), so a caller with the same mapping
+// thread that owns it under the element mapping (one column: the chunks of
+// for_chunks; else rows slot, slot + nslots, ... and columns c*EPT ..), so
+// a caller with the same mapping
 // reads X at once.  preset: the caller has already set X = 0, R = Z = Y and
 // passed a grid barrier since.
 template <typename T, int R, bool EU = false>
@@ -322,9 +322,9 @@ __device__ __forceinline__ bool cg_dev(const CGArgs<T> &g, const TreeKArgs<T> &t
     double mx = 0.0;
     Acc<T> acc0[EPT], acc1[EPT];
 
-    // one column of the elimination form: the chunked element loops (the
-    // mapping the fused PCG uses for the same vectors)
-    constexpr bool CH = R == 1 && !EU;
+    // one column: the chunked element loops (the mapping the fused PCG uses
+    // for the same vectors)
+    constexpr bool CH = R == 1;
     constexpr int W = Chunk<T>::W;
     if (!preset && CH) {
         for_chunks<T>(g.n, gt, (int64_t)gridDim.x * blockDim.x, [&](int64_t i0, int cnt) {
@@ -449,7 +449,7 @@ __device__ __forceinline__ bool cg_dev(const CGArgs<T> &g, const TreeKArgs<T> &t
         // Q = L_S P (+D), partial P.Q
 #pragma unroll
         for (int e = 0; e < EPT; ++e) acc0[e] = Acc<T>();
-        if constexpr (EPT == 1 && cg_max_threads<R, EU>() <= kFusedMaxThreads) {
+        if constexpr (EPT == 1 && (EU || cg_max_threads<R, EU>() <= kFusedMaxThreads)) {
             // two rows at a time, every load of both rows before the sums
             constexpr int K = 4;
             for (int64_t i0 = slot; i0 < g.n; i0 += 2 * nslots) {
@@ -651,9 +651,9 @@ static void cg_persistent(grass_ctx_t ctx, grass_sparsifier_t S, bool with_D, co
     const int grid = eu ? coop_grid(ctx, k_cg_persist<T, R, (R == 1)>, threads, smem, n * Lay<R>::TPR)
                         : coop_grid(ctx, k_cg_persist<T, R, false>, threads, smem, n * Lay<R>::TPR);
     if ((size_t)grid * 32 * 2 > ctx->partials.n) fail(GRASS_ERR_CUDA, "partials buffer too small");
-    // the chunked element loops (one FP32 column, elimination form) take
-    // 16-byte accesses; all their vectors are the context's own scratch
-    if (R == 1 && !eu && Chunk<T>::W > 1 &&
+    // the chunked element loops (one FP32 column) take 16-byte accesses;
+    // all their vectors are the context's own scratch
+    if (R == 1 && Chunk<T>::W > 1 &&
         (((uintptr_t)Y | (uintptr_t)X | (uintptr_t)a.Rv | (uintptr_t)a.Z | (uintptr_t)a.P |
           (uintptr_t)a.Q) & 15))
         fail(GRASS_ERR_INVALID, "inner CG vectors must be 16-byte aligned");
