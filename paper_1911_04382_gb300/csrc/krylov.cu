@@ -116,10 +116,12 @@ struct CGArgs {
 // Per-block column sums of the thread partials v[e] (column c*EPT + e),
 // written to out[0..R): lanes sharing c fold together (xor offsets >= TPR),
 // then one thread per column adds the warps in order.
-template <int R>
-__device__ __forceinline__ void block_cols(const double (&v)[Lay<R>::EPT], int c,
+// TPR: lanes per group of columns (a thread of lane l holds columns
+// (l mod TPR) * EPT ..), EPT = R / TPR.
+template <int R, int TPR = Lay<R>::TPR>
+__device__ __forceinline__ void block_cols(const double (&v)[R / TPR], int c,
                                            double (*s_red)[32], double *out) {
-    constexpr int TPR = Lay<R>::TPR, EPT = Lay<R>::EPT;
+    constexpr int EPT = R / TPR;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
     for (int e = 0; e < EPT; ++e) {
@@ -136,13 +138,13 @@ __device__ __forceinline__ void block_cols(const double (&v)[Lay<R>::EPT], int c
     __syncthreads();
 }
 
-template <int R, typename T>
-__device__ __forceinline__ void block_cols(const Acc<T> (&a)[Lay<R>::EPT], int c,
+template <int R, int TPR = Lay<R>::TPR, typename T>
+__device__ __forceinline__ void block_cols(const Acc<T> (&a)[R / TPR], int c,
                                            double (*s_red)[32], double *out) {
-    double v[Lay<R>::EPT];
+    double v[R / TPR];
 #pragma unroll
-    for (int e = 0; e < Lay<R>::EPT; ++e) v[e] = a[e].value();
-    block_cols<R>(v, c, s_red, out);
+    for (int e = 0; e < R / TPR; ++e) v[e] = a[e].value();
+    block_cols<R, TPR>(v, c, s_red, out);
 }
 
 // Column sums over all blocks' partials (same order in every block): warp j
@@ -320,14 +322,24 @@ __device__ __forceinline__ bool cg_dev(const CGArgs<T> &g, const TreeKArgs<T> &t
     double *part0 = g.part, *part1 = g.part + (int64_t)gridDim.x * 32;
     double *mypart0 = part0 + (int64_t)blockIdx.x * 32, *mypart1 = part1 + (int64_t)blockIdx.x * 32;
     double mx = 0.0;
-    Acc<T> acc0[EPT], acc1[EPT];
-
-    // one column: the chunked element loops (the mapping the fused PCG uses
-    // for the same vectors)
-    constexpr bool CH = R == 1;
+    // Element loops in chunks (for_chunks): one column (chunks of rows, the
+    // mapping the fused PCG uses for the same vectors), or for FP32 and
+    // r = 4, 8, 16, 32 the n x r array as flat 4-float chunks; the thread
+    // count is a multiple of r / 4, so a thread's chunks all hold columns
+    // c4 .. c4 + 3 (c4 = 4 (gt mod r/4)): NA sums per thread, laid out for
+    // block_cols as groups of TPA lanes.
+    constexpr bool CH1 = R == 1;
+    constexpr bool CHR = sizeof(T) == 4 && (R == 4 || R == 8 || R == 16 || R == 32);
+    constexpr bool CH = CH1 || CHR;
     constexpr int W = Chunk<T>::W;
+    constexpr int NA = CHR ? 4 : EPT;
+    constexpr int TPA = CHR ? R / 4 : TPR;
+    const int64_t nel = CHR ? g.n * R : g.n;
+    const int c4 = CHR ? (int)(gt % (R / 4)) * 4 : 0;
+    Acc<T> acc0[NA], acc1[NA];
+
     if (!preset && CH) {
-        for_chunks<T>(g.n, gt, (int64_t)gridDim.x * blockDim.x, [&](int64_t i0, int cnt) {
+        for_chunks<T>(nel, gt, (int64_t)gridDim.x * blockDim.x, [&](int64_t i0, int cnt) {
             T y[W], zero[W] = {};
             ld_chunk(g.Y + i0, cnt, y);
             st_chunk(g.X + i0, cnt, zero);
@@ -365,17 +377,17 @@ __device__ __forceinline__ bool cg_dev(const CGArgs<T> &g, const TreeKArgs<T> &t
         }
         if (!grid_sync(tk.bar, tk.budget, tk.err, epoch)) return false;
 #pragma unroll
-        for (int e = 0; e < EPT; ++e) acc0[e] = acc1[e] = Acc<T>();
+        for (int e = 0; e < NA; ++e) acc0[e] = acc1[e] = Acc<T>();
         if constexpr (CH) {
-            for_chunks<T>(g.n, gt, (int64_t)gridDim.x * blockDim.x, [&](int64_t i0, int cnt) {
+            for_chunks<T>(nel, gt, (int64_t)gridDim.x * blockDim.x, [&](int64_t i0, int cnt) {
                 T z[W], rr[W];
                 ld_chunk(g.Z + i0, cnt, z);
                 ld_chunk(g.Rv + i0, cnt, rr);
 #pragma unroll
                 for (int w = 0; w < W; ++w) {
                     if (w >= cnt) break;
-                    acc0[0].add_prod(rr[w], z[w]);
-                    if (it == 0) acc1[0].add_prod(rr[w], rr[w]);
+                    acc0[CHR ? w : 0].add_prod(rr[w], z[w]);
+                    if (it == 0) acc1[CHR ? w : 0].add_prod(rr[w], rr[w]);
                 }
                 if (it == 0) st_chunk(g.P + i0, cnt, z);
             });
@@ -393,8 +405,8 @@ __device__ __forceinline__ bool cg_dev(const CGArgs<T> &g, const TreeKArgs<T> &t
             }
         }
         }
-        block_cols<R>(acc0, c, s_red, mypart0);
-        if (it == 0) block_cols<R>(acc1, c, s_red, mypart1);
+        block_cols<R, TPA>(acc0, c, s_red, mypart0);
+        if (it == 0) block_cols<R, TPA>(acc1, c, s_red, mypart1);
         if (!grid_sync(tk.bar, tk.budget, tk.err, epoch)) return false;
         if (it == 0) {
             grid_cols2<R>(part0, s_rz, part1, s_rr);
@@ -409,7 +421,7 @@ __device__ __forceinline__ bool cg_dev(const CGArgs<T> &g, const TreeKArgs<T> &t
                 s_al[j] = beta;
             }
             __syncthreads();
-            if constexpr (CH) {
+            if constexpr (CH1) {
                 if (s_act[0]) {
                     const T be = (T)s_al[0];
                     for_chunks<T>(g.n, gt, (int64_t)gridDim.x * blockDim.x, [&](int64_t i0, int cnt) {
@@ -421,6 +433,16 @@ __device__ __forceinline__ bool cg_dev(const CGArgs<T> &g, const TreeKArgs<T> &t
                         st_chunk(g.P + i0, cnt, pv);
                     });
                 }
+            } else if constexpr (CHR) {
+                for_chunks<T>(nel, gt, (int64_t)gridDim.x * blockDim.x, [&](int64_t i0, int cnt) {
+                    T z[W], pv[W];
+                    ld_chunk(g.Z + i0, cnt, z);
+                    ld_chunk(g.P + i0, cnt, pv);
+#pragma unroll
+                    for (int w = 0; w < W; ++w)
+                        if (s_act[c4 + w]) pv[w] = z[w] + (T)s_al[c4 + w] * pv[w];
+                    st_chunk(g.P + i0, cnt, pv);
+                });
             } else {
             for (int64_t i = slot; i < g.n; i += nslots) {
 #pragma unroll
@@ -446,9 +468,10 @@ __device__ __forceinline__ bool cg_dev(const CGArgs<T> &g, const TreeKArgs<T> &t
         }
         __syncthreads();
         if (s_nact == 0) break;
-        // Q = L_S P (+D), partial P.Q
+        // Q = L_S P (+D), partial P.Q (row layout)
+        Acc<T> accq[EPT];
 #pragma unroll
-        for (int e = 0; e < EPT; ++e) acc0[e] = Acc<T>();
+        for (int e = 0; e < EPT; ++e) accq[e] = Acc<T>();
         if constexpr (EPT == 1 && (EU || cg_max_threads<R, EU>() <= kFusedMaxThreads)) {
             // two rows at a time, every load of both rows before the sums
             constexpr int K = 4;
@@ -472,7 +495,7 @@ __device__ __forceinline__ bool cg_dev(const CGArgs<T> &g, const TreeKArgs<T> &t
                     if (i >= g.n) break;
                     if (g.D) q[u] += dd[u] * p0[u];
                     g.Q[i * R + c] = q[u];
-                    acc0[0].add_prod(p0[u], q[u]);
+                    accq[0].add_prod(p0[u], q[u]);
                 }
             }
         } else {
@@ -497,11 +520,11 @@ __device__ __forceinline__ bool cg_dev(const CGArgs<T> &g, const TreeKArgs<T> &t
 #pragma unroll
             for (int e = 0; e < EPT; ++e) {
                 g.Q[i * R + c * EPT + e] = q[e];
-                acc0[e].add_prod(p0[e], q[e]);
+                accq[e].add_prod(p0[e], q[e]);
             }
         }
         }
-        block_cols<R>(acc0, c, s_red, mypart0);
+        block_cols<R>(accq, c, s_red, mypart0);
         if (!grid_sync(tk.bar, tk.budget, tk.err, epoch)) return false;
         grid_cols<R>(part0, s_pq);
         if (threadIdx.x < R) {
@@ -517,8 +540,29 @@ __device__ __forceinline__ bool cg_dev(const CGArgs<T> &g, const TreeKArgs<T> &t
         __syncthreads();
         // X += alpha P, R -= alpha Q, Z = R, partial R.R
 #pragma unroll
-        for (int e = 0; e < EPT; ++e) acc1[e] = Acc<T>();
-        if constexpr (CH) {
+        for (int e = 0; e < NA; ++e) acc1[e] = Acc<T>();
+        if constexpr (CHR) {
+            for_chunks<T>(nel, gt, (int64_t)gridDim.x * blockDim.x, [&](int64_t i0, int cnt) {
+                T rr[W], xv[W], pv[W], qv[W];
+                ld_chunk(g.Rv + i0, cnt, rr);
+                ld_chunk(g.X + i0, cnt, xv);
+                ld_chunk(g.P + i0, cnt, pv);
+                ld_chunk(g.Q + i0, cnt, qv);
+#pragma unroll
+                for (int w = 0; w < W; ++w) {
+                    const T a = (T)s_al[c4 + w];
+                    if (a != (T)0) {
+                        xv[w] += a * pv[w];
+                        rr[w] -= a * qv[w];
+                    }
+                }
+                st_chunk(g.X + i0, cnt, xv);
+                st_chunk(g.Rv + i0, cnt, rr);
+                st_chunk(g.Z + i0, cnt, rr);
+#pragma unroll
+                for (int w = 0; w < W; ++w) acc1[w].add_prod(rr[w], rr[w]);
+            });
+        } else if constexpr (CH1) {
             const T a = (T)s_al[0];
             for_chunks<T>(g.n, gt, (int64_t)gridDim.x * blockDim.x, [&](int64_t i0, int cnt) {
                 T rr[W];
@@ -563,7 +607,7 @@ __device__ __forceinline__ bool cg_dev(const CGArgs<T> &g, const TreeKArgs<T> &t
         // look ahead: another iteration only if one is allowed and some
         // column passes the test
         if (it + 1 >= g.maxit) break;
-        block_cols<R>(acc1, c, s_red, mypart1);
+        block_cols<R, TPA>(acc1, c, s_red, mypart1);
         if (!grid_sync(tk.bar, tk.budget, tk.err, epoch)) return false;
         grid_cols<R>(part1, s_rr);
         if (threadIdx.x == 0) s_nact = 0;
@@ -578,7 +622,7 @@ __device__ __forceinline__ bool cg_dev(const CGArgs<T> &g, const TreeKArgs<T> &t
     if (g.maxbits) {
         double m = 0.0;
         if constexpr (CH) {
-            for_chunks<T>(g.n, gt, (int64_t)gridDim.x * blockDim.x, [&](int64_t i0, int cnt) {
+            for_chunks<T>(nel, gt, (int64_t)gridDim.x * blockDim.x, [&](int64_t i0, int cnt) {
                 T xv[W];
                 ld_chunk(g.X + i0, cnt, xv);
 #pragma unroll
