@@ -70,7 +70,7 @@ enum ScratchSlot {
     SCR_Y, SCR_H, SCR_CG_X, SCR_CG_R, SCR_CG_Z, SCR_CG_P, SCR_CG_Q,
     SCR_PCG_X, SCR_PCG_R, SCR_PCG_Z, SCR_PCG_P, SCR_PCG_Q, SCR_PCG_ZOLD, SCR_PCG_E,
     SCR_FILTER, SCR_FILTER2, SCR_HEAT, SCR_LMAX_V, SCR_LMAX_Y, SCR_PART2,
-    SCR_EU_S, SCR_EU_C, SCR_EU_P, SCR_EU_A,
+    SCR_EU_S, SCR_EU_C, SCR_EU_P, SCR_EU_A, SCR_CG_XP,
     SCR_COUNT
 };
 
@@ -326,6 +326,14 @@ struct EulerTour {
     DBuf<double> pw;
     DBuf<double> ipw;                // [n] 1 / pw (roots: 1)
     DBuf<float> ipw32;
+    // Preorder numbering (every tree: its root, then its vertices in the
+    // order the tour enters them; trees in vertex-offset order): pre[v],
+    // vert[k] = v, and the tour and per-vertex arrays in that numbering, for
+    // solvers that keep their vectors in preorder (the tour's entry values
+    // are then read in sequence).
+    DBuf<int32_t> pre, vert, tour_pre, ein_pre, eout_pre;
+    DBuf<double> ipw_pre;
+    DBuf<float> ipw32_pre;
 };
 
 }  // namespace grass
@@ -362,6 +370,13 @@ struct grass_sparsifier_s {
     grass::DBuf<double> s_w64;
     grass::DBuf<float> s_w32;
     grass::DBuf<double> degS;         // [n]
+    // S's adjacency with vertices renumbered in the tree's preorder (rows in
+    // preorder, each row's entries in their original order); built on first
+    // use after each change of S
+    bool pre_ok = false;
+    grass::DBuf<int32_t> p_ptr, p_col;
+    grass::DBuf<double> p_w64;
+    grass::DBuf<float> p_w32;
 };
 
 namespace grass {

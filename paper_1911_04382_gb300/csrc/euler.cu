@@ -128,6 +128,45 @@ __global__ void k_eu_roots(int64_t nr, const int32_t *roots, const int64_t *voff
     head[voff ? 2 * (voff[q] - q) : 0] = 1;
 }
 
+// ---- preorder numbering
+__global__ void k_eu_isentry(int64_t L, const int32_t *tour, int64_t *f) {
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < L) f[p] = tour[p] >= 0 ? 1 : 0;
+}
+
+// pre[v]: a root takes its tree's first slot (the tree's vertex offset); a
+// vertex entered at position p takes (entries before p) + (trees up to and
+// including its own), i.e. one slot after its tree's root and the vertices
+// entered before it
+__global__ void k_eu_pre(int64_t n, const int32_t *ein, const int64_t *epos, const int32_t *seg_of,
+                         const int64_t *voff, int32_t *pre, int32_t *vert) {
+    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    const int64_t t = seg_of ? seg_of[v] : 0;
+    const int64_t k = ein[v] >= 0 ? epos[ein[v]] + t + 1 : (voff ? voff[t] : 0);
+    pre[v] = (int32_t)k;
+    vert[k] = (int32_t)v;
+}
+
+__global__ void k_eu_tourpre(int64_t L, const int32_t *tour, const int32_t *pre, int32_t *out) {
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= L) return;
+    const int32_t t = tour[p];
+    out[p] = t >= 0 ? pre[t] : -(pre[-t - 1] + 1);
+}
+
+__global__ void k_eu_prevals(int64_t n, const int32_t *vert, const int32_t *ein, const int32_t *eout,
+                             const double *ipw, const float *ipw32, int32_t *ein_p, int32_t *eout_p,
+                             double *ipw_p, float *ipw32_p) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int32_t v = vert[k];
+    ein_p[k] = ein[v];
+    eout_p[k] = eout[v];
+    ipw_p[k] = ipw[v];
+    ipw32_p[k] = ipw32[v];
+}
+
 }  // namespace
 
 void euler_build(grass_ctx_t ctx, grass_tree_t T, const int32_t *tptr, const int32_t *tocc,
@@ -185,6 +224,31 @@ void euler_build(grass_ctx_t ctx, grass_tree_t T, const int32_t *tptr, const int
     E.ipw.alloc(n);
     E.ipw32.alloc(n);
     launch(ctx, k_eu_inv, cdiv(n, kBlock), kBlock, 0, n, (const double *)E.pw.p, E.ipw.p, E.ipw32.p);
+    // preorder numbering and the tour / per-vertex arrays in it
+    {
+        DBuf<int64_t> ent, epos;
+        ent.alloc(L + 1);
+        epos.alloc(L + 1);
+        launch(ctx, k_eu_isentry, cdiv(L, kBlock), kBlock, 0, L, (const int32_t *)E.tour.p, ent.p);
+        int64_t ne = 0;
+        scan_i64(ctx, ent.p, epos.p, L, &ne);
+        if (ne != n - T->nroots) fail(GRASS_ERR_CUDA, "Euler tour: entry count mismatch");
+        E.pre.alloc(n);
+        E.vert.alloc(n);
+        launch(ctx, k_eu_pre, cdiv(n, kBlock), kBlock, 0, n, (const int32_t *)E.ein.p,
+               (const int64_t *)epos.p, g.nseg > 1 ? (const int32_t *)g.seg_of.p : nullptr,
+               g.nseg > 1 ? (const int64_t *)g.seg_voff_d.p : nullptr, E.pre.p, E.vert.p);
+        E.tour_pre.alloc(L);
+        launch(ctx, k_eu_tourpre, cdiv(L, kBlock), kBlock, 0, L, (const int32_t *)E.tour.p,
+               (const int32_t *)E.pre.p, E.tour_pre.p);
+        E.ein_pre.alloc(n);
+        E.eout_pre.alloc(n);
+        E.ipw_pre.alloc(n);
+        E.ipw32_pre.alloc(n);
+        launch(ctx, k_eu_prevals, cdiv(n, kBlock), kBlock, 0, n, (const int32_t *)E.vert.p,
+               (const int32_t *)E.ein.p, (const int32_t *)E.eout.p, (const double *)E.ipw.p,
+               (const float *)E.ipw32.p, E.ein_pre.p, E.eout_pre.p, E.ipw_pre.p, E.ipw32_pre.p);
+    }
     E.built = true;
 }
 

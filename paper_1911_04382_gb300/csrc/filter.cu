@@ -94,6 +94,7 @@ void sparsifier_rebuild(grass_ctx_t ctx, grass_sparsifier_t S) {
                g.adj_w64.p, (const uint8_t *)S->in_s.p, (const int64_t *)off, S->s_ptr.p,
                S->s_col.p, S->s_w64.p, S->s_w32.p);
     }
+    S->pre_ok = false;
 }
 
 __global__ void k_mark(int64_t cnt, const int64_t *eids, int64_t m, uint8_t *in_s, int *flags) {

@@ -111,6 +111,11 @@ struct CGArgs {
     double *iter_acc;            // += max over columns of the iterations
     unsigned long long *maxbits; // optional max |X|
     EulerKArgs eu;               // scan-form tree solve (r = 1, no D)
+    // one column, scan form: perm != nullptr when the solve runs in another
+    // numbering (X, Rv, Z, P, Q and the CSR indexed by k, vertex perm[k]); Y
+    // is then read and the result written to Xout in vertex ids
+    const int32_t *perm;
+    T *Xout;
 };
 
 // Per-block column sums of the thread partials v[e] (column c*EPT + e),
@@ -341,7 +346,15 @@ __device__ __forceinline__ bool cg_dev(const CGArgs<T> &g, const TreeKArgs<T> &t
     if (!preset && CH) {
         for_chunks<T>(nel, gt, (int64_t)gridDim.x * blockDim.x, [&](int64_t i0, int cnt) {
             T y[W], zero[W] = {};
-            ld_chunk(g.Y + i0, cnt, y);
+            bool gathered = false;
+            if constexpr (EU) {
+                if (g.perm) {
+#pragma unroll
+                    for (int w = 0; w < W; ++w) y[w] = w < cnt ? g.Y[g.perm[i0 + w]] : (T)0;
+                    gathered = true;
+                }
+            }
+            if (!gathered) ld_chunk(g.Y + i0, cnt, y);
             st_chunk(g.X + i0, cnt, zero);
             st_chunk(g.Rv + i0, cnt, y);
             st_chunk(g.Z + i0, cnt, y);
@@ -636,6 +649,18 @@ __device__ __forceinline__ bool cg_dev(const CGArgs<T> &g, const TreeKArgs<T> &t
         }
         block_atomic_max(g.maxbits, m);
     }
+    if constexpr (CH1 && EU) {
+        // back to vertex ids: each thread scatters the elements it owns
+        if (g.perm) {
+            for_chunks<T>(g.n, gt, (int64_t)gridDim.x * blockDim.x, [&](int64_t i0, int cnt) {
+                T xv[W];
+                ld_chunk(g.X + i0, cnt, xv);
+#pragma unroll
+                for (int w = 0; w < W; ++w)
+                    if (w < cnt) g.Xout[g.perm[i0 + w]] = xv[w];
+            });
+        }
+    }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         int mxit = 0;
         for (int j = 0; j < R; ++j) mxit = max(mxit, s_it[j]);
@@ -651,6 +676,52 @@ __global__ void __launch_bounds__(cg_max_threads<R, EU>(), 1)
     unsigned int epoch = 0;
     if constexpr (!EU) tree_tail_stage<T, R>(tk, reinterpret_cast<T *>(smem_raw));
     cg_dev<T, R, EU>(g, tk, epoch, reinterpret_cast<T *>(smem_raw));
+}
+
+// S's adjacency in the tree's preorder numbering (row k = the row of vertex
+// vert[k], columns renumbered, entries in their original order)
+__global__ void k_pre_count(int64_t n, const int32_t *vert, const int32_t *sptr, int64_t *cnt) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) cnt[k] = sptr[vert[k] + 1] - sptr[vert[k]];
+}
+
+__global__ void k_pre_fill(int64_t n, const int32_t *vert, const int32_t *pre, const int32_t *sptr,
+                           const int32_t *scol, const double *sw64, const float *sw32,
+                           const int64_t *off, int32_t *pptr, int32_t *pcol, double *pw64,
+                           float *pw32) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int32_t v = vert[k];
+    int64_t o = off[k];
+    pptr[k] = (int32_t)o;
+    if (k == n - 1) pptr[n] = (int32_t)off[n];
+    for (int32_t j = sptr[v]; j < sptr[v + 1]; ++j, ++o) {
+        pcol[o] = pre[scol[j]];
+        pw64[o] = sw64[j];
+        pw32[o] = sw32[j];
+    }
+}
+
+static void sparsifier_pre(grass_ctx_t ctx, grass_sparsifier_t S) {
+    if (S->pre_ok) return;
+    const EulerTour &E = S->tree->euler;
+    const int64_t n = S->tree->g.n;
+    int64_t *cnt = ctx->scr<int64_t>(SCR_TMP2, n + 1);
+    int64_t *off = ctx->scr<int64_t>(SCR_TMP3, n + 1);
+    launch(ctx, k_pre_count, cdiv(n, kBlock), kBlock, 0, n, (const int32_t *)E.vert.p,
+           (const int32_t *)S->s_ptr.p, cnt);
+    int64_t nnz = 0;
+    scan_i64(ctx, cnt, off, n, &nnz);
+    if (nnz != S->s_nnz) fail(GRASS_ERR_CUDA, "preorder sparsifier: entry count mismatch");
+    S->p_ptr.reserve(n + 1);
+    S->p_col.reserve(nnz);
+    S->p_w64.reserve(nnz);
+    S->p_w32.reserve(nnz);
+    launch(ctx, k_pre_fill, cdiv(n, kBlock), kBlock, 0, n, (const int32_t *)E.vert.p,
+           (const int32_t *)E.pre.p, (const int32_t *)S->s_ptr.p, (const int32_t *)S->s_col.p,
+           (const double *)S->s_w64.p, (const float *)S->s_w32.p, (const int64_t *)off,
+           S->p_ptr.p, S->p_col.p, S->p_w64.p, S->p_w32.p);
+    S->pre_ok = true;
 }
 
 template <typename T, int R>
@@ -685,9 +756,23 @@ static void cg_persistent(grass_ctx_t ctx, grass_sparsifier_t S, bool with_D, co
     a.part = ctx->partials.p;
     a.iter_acc = ctx->scal.p + DS_RED + DS_ITER;
     a.maxbits = maxbits;
+    a.perm = nullptr;
+    a.Xout = nullptr;
     std::memset(&a.eu, 0, sizeof(a.eu));
-    // one column and no D: the scan-form tree solve
+    // one column and no D: the scan-form tree solve, with the CG's vectors
+    // and S in the tree's preorder (the tour then reads them in sequence);
+    // Y is gathered at the start and X scattered at the end
     const bool eu = R == 1 && !with_D && ctx->euler_solve && Tr->euler.built;
+    if (eu) {
+        sparsifier_pre(ctx, S);
+        a.sptr = S->p_ptr.p;
+        a.scol = S->p_col.p;
+        if constexpr (sizeof(T) == 8) a.sw = S->p_w64.p;
+        else a.sw = S->p_w32.p;
+        a.perm = Tr->euler.vert.p;
+        a.Xout = (T *)X;
+        a.X = ctx->scr<T>(SCR_CG_XP, total);
+    }
     const int threads = bounded_threads(
         ctx->tree_threads, eu ? cg_max_threads<R, (R == 1)>() : cg_max_threads<R, false>());
     const void *kern = eu ? (const void *)k_cg_persist<T, R, (R == 1)>
@@ -696,12 +781,13 @@ static void cg_persistent(grass_ctx_t ctx, grass_sparsifier_t S, bool with_D, co
                         : coop_grid(ctx, k_cg_persist<T, R, false>, threads, smem, n * Lay<R>::TPR);
     if ((size_t)grid * 32 * 2 > ctx->partials.n) fail(GRASS_ERR_CUDA, "partials buffer too small");
     // the chunked element loops (one FP32 column) take 16-byte accesses;
-    // all their vectors are the context's own scratch
+    // all their vectors are the context's own scratch (Y is gathered by
+    // single loads when the solve runs in preorder)
     if (R == 1 && Chunk<T>::W > 1 &&
-        (((uintptr_t)Y | (uintptr_t)X | (uintptr_t)a.Rv | (uintptr_t)a.Z | (uintptr_t)a.P |
-          (uintptr_t)a.Q) & 15))
+        (((a.perm ? (uintptr_t)0 : (uintptr_t)Y) | (uintptr_t)a.X | (uintptr_t)a.Rv |
+          (uintptr_t)a.Z | (uintptr_t)a.P | (uintptr_t)a.Q) & 15))
         fail(GRASS_ERR_INVALID, "inner CG vectors must be 16-byte aligned");
-    if (eu) euler_kargs<T>(ctx, Tr, grid, &a.eu);
+    if (eu) euler_kargs<T>(ctx, Tr, grid, &a.eu, true);
     GCK(cudaMemsetAsync(tk.bar, 0, sizeof(unsigned int), ctx->stream));
     // roofline accounting: algorithmic bytes per iteration and of the start
     const TreeSchedule &TS = Tr->sched;

@@ -769,19 +769,21 @@ __device__ __forceinline__ bool euler_solve_dev(const EulerKArgs &E, T *Y, unsig
     return true;
 }
 
-// Host side: scan-form arguments for a cooperative grid of `grid` blocks.
+// Host side: scan-form arguments for a cooperative grid of `grid` blocks;
+// pre: the vectors are in the tree's preorder numbering (else vertex ids).
 template <typename T>
-inline void euler_kargs(grass_ctx_t ctx, const grass_tree_s *Tr, int grid, EulerKArgs *e) {
+inline void euler_kargs(grass_ctx_t ctx, const grass_tree_s *Tr, int grid, EulerKArgs *e,
+                        bool pre = false) {
     if (grid > kEulerMaxGrid) fail(GRASS_ERR_INVALID, "grid too large for the scan-form tree solve");
     const EulerTour &E = Tr->euler;
     e->L = E.L;
     e->n = Tr->g.n;
-    e->tour = E.tour.p;
-    e->ein = E.ein.p;
-    e->eout = E.eout.p;
+    e->tour = pre ? E.tour_pre.p : E.tour.p;
+    e->ein = pre ? E.ein_pre.p : E.ein.p;
+    e->eout = pre ? E.eout_pre.p : E.eout.p;
     e->head = E.head.p;
-    if constexpr (sizeof(T) == 8) e->ipw = E.ipw.p;
-    else e->ipw = E.ipw32.p;
+    if constexpr (sizeof(T) == 8) e->ipw = pre ? E.ipw_pre.p : E.ipw.p;
+    else e->ipw = pre ? E.ipw32_pre.p : E.ipw32.p;
     e->S = ctx->scr<double>(SCR_EU_S, E.L + 1);   // 8-byte sums (double or float pair)
     e->C = ctx->scr<double>(SCR_EU_C, Tr->g.n);
     e->part = ctx->scr<double>(SCR_EU_P, 6 * (size_t)grid + 2);
