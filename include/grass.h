@@ -142,8 +142,8 @@ grass_status grass_ctx_set_wait_limit(grass_ctx_t ctx, int64_t polls, int hold_b
  *                         the fused PCG and the fused CG of the elimination
  *                         form with one column use at most 512 of them
  *   "tree_tail_items"     rounds at the end whose total work is below this
- *                         many items run in one block (default 2048;
- *                         0 = none)
+ *                         many items run in one block (work: surviving
+ *                         vertices x max(1, r/4); default 2048; 0 = none)
  *   "euler_solve"         1 (default): grounded solves of L_T alone (no D)
  *                         with one column, inside the inner CG and the
  *                         power steps, use the Euler-tour scan form (two

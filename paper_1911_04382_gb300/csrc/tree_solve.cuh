@@ -821,7 +821,8 @@ inline TreeKArgs<T> tree_kargs(grass_ctx_t ctx, const grass_tree_s *Tr, const Tr
                                size_t *smem) {
     const TreeSchedule &S = Tr->sched;
     auto alive_at = [&](int k) { return S.tail_n - (S.elim_off[k] - S.elim_off[S.tail_k0]); };
-    // the tail's rows and its records / coefficients must fit the budget
+    // the tail's rows and its records / coefficients must fit the budget,
+    // and its work (vertices x max(1, r/4)) stay within tree_tail_items
     auto tail_bytes = [&](int k) {
         return TailSmem<T, R>::bytes(alive_at(k), S.rcv_off[S.rounds] - S.rcv_off[k],
                                      S.elim_off[S.rounds] - S.elim_off[k],
@@ -829,7 +830,7 @@ inline TreeKArgs<T> tree_kargs(grass_ctx_t ctx, const grass_tree_s *Tr, const Tr
     };
     int K1 = S.tail_k0;
     while (K1 < S.rounds && (tail_bytes(K1) > kTailSmem ||
-                             alive_at(K1) > std::max<int64_t>(ctx->tree_tail_items, 1)))
+                             alive_at(K1) * std::max(1, R / 4) > std::max<int64_t>(ctx->tree_tail_items, 1)))
         ++K1;
     const int64_t ntl = alive_at(K1);
     *smem = tail_bytes(K1);
