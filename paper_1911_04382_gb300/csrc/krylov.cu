@@ -789,7 +789,12 @@ static void cg_persistent(grass_ctx_t ctx, grass_sparsifier_t S, bool with_D, co
         fail(GRASS_ERR_INVALID, "inner CG vectors must be 16-byte aligned");
     if (eu) euler_kargs<T>(ctx, Tr, grid, &a.eu, true);
     GCK(cudaMemsetAsync(tk.bar, 0, sizeof(unsigned int), ctx->stream));
-    // roofline accounting: algorithmic bytes per iteration and of the start
+    // roofline accounting, each array counted once per phase that touches
+    // it: per iteration the tree solve, the SpMV with S (CSR, P read, Q
+    // written, D), dots Z, R + P update Z, P, P + update R, X, P, Q read and
+    // X, R, Z written (12 nrs; the first iteration's P = Z copies, 2 nrs
+    // less); the start Y read and X, R, Z written (4 nrs); the end max |X|
+    // (nrs) and, in preorder, the scatter of X (2 nrs)
     const TreeSchedule &TS = Tr->sched;
     const double s = (double)sizeof(T), nrs = (double)n * R * s;
     const double tree_b = 4.0 * nrs + TS.n_rcv * (16.0 + 2.0 * s) +
@@ -799,7 +804,8 @@ static void cg_persistent(grass_ctx_t ctx, grass_sparsifier_t S, bool with_D, co
     size_t snap = ctx->iter_launches.size();
     if (timing) {
         ctx->t_snap(a.iter_acc, snap, 0);
-        ctx->iter_launches.push_back({7.0 * nrs + tree_b, spmv_b + 16.0 * nrs + tree_b, snap});
+        const double start = 2.0 * nrs + (maxbits ? nrs : 0.0) + (a.perm ? 2.0 * nrs : 0.0);
+        ctx->iter_launches.push_back({start, tree_b + spmv_b + 12.0 * nrs, snap});
     }
     bool timed = ctx->t_begin(GRASS_KF_CG, 0.0);
     void *args[] = {&a, &tk};
@@ -964,7 +970,7 @@ struct PCGArgs {
     double *out;                  // [0] += iterations, [1] = final r.r
 };
 
-template <typename T, bool TREE_ONLY>
+template <typename T, int MODE>
 __global__ void __launch_bounds__(kFusedMaxThreads, 1)
     k_pcg_persist(PCGArgs<T> a, CGArgs<T> in, TreeKArgs<T> tk) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -989,7 +995,7 @@ __global__ void __launch_bounds__(kFusedMaxThreads, 1)
         ld_chunk(a.rhs + i0, cnt, y);
         st_chunk(a.e + i0, cnt, zero);
         st_chunk(a.r + i0, cnt, y);
-        if (TREE_ONLY) {
+        if (MODE != 0) {
             st_chunk(a.z + i0, cnt, y);
         } else {
             st_chunk(a.z + i0, cnt, zero);
@@ -998,6 +1004,146 @@ __global__ void __launch_bounds__(kFusedMaxThreads, 1)
         }
     });
     if (!grid_sync(tk.bar, tk.budget, tk.err, epoch)) return;
+    if constexpr (MODE == 2) {
+        // One inner CG step from zero on (L_S + D), in closed form: with
+        // z0 = T^{-1} r (the tree solve) the step is z = alpha_in z0,
+        // alpha_in = r.z0 / z0'(L_S + D) z0.  One phase gives the quadratic
+        // form (row by row) and r.z0, r.z0_prev (r.r on the first pass); the
+        // outer scalars follow from them (r.z = alpha_in r.z0, r.z_old =
+        // alpha_prev r.z0_prev).  z0 and z0_prev alternate between the two
+        // buffers; the update writes the next solve's input r into the older.
+        T *zc = a.z, *zp = a.zo;
+        double rz = 0.0, rr = 0.0, aprev = 0.0;
+        int k = 0, steps = 0;
+        for (bool first = true;; first = false) {
+            if (!tree_solve_dev<T, 1, false>(tk, zc, epoch, mx, ys)) return;
+            if (!grid_sync(tk.bar, tk.budget, tk.err, epoch)) return;
+            Acc<T> aq, arz, ax;
+            for (int64_t i0 = gt; i0 < a.n; i0 += 2 * nth) {
+                constexpr int K = 4;
+                int32_t jb[2], je[2];
+                T zv[2], qv[2], dv[2], rv[2], ov[2];
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const int64_t i = i0 + u * nth;
+                    const bool ok = i < a.n;
+                    zv[u] = ok ? zc[i] : (T)0;
+                    dv[u] = ok ? in.D[i] : (T)0;
+                    rv[u] = ok ? a.r[i] : (T)0;
+                    ov[u] = ok && !first ? zp[i] : (T)0;
+                    jb[u] = ok ? in.sptr[i] : 0;
+                    je[u] = ok ? in.sptr[i + 1] : 0;
+                    qv[u] = (T)0;
+                }
+                lap_rows<T, 2, K, 1>(in.scol, in.sw, zc, jb, je, zv, qv);
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    if (i0 + u * nth >= a.n) break;
+                    qv[u] += dv[u] * zv[u];
+                    aq.add_prod(zv[u], qv[u]);
+                    arz.add_prod(rv[u], zv[u]);
+                    if (first) ax.add_prod(rv[u], rv[u]);
+                    else ax.add_prod(rv[u], ov[u]);
+                }
+            }
+            {
+                double v4[4] = {aq.value(), arz.value(), ax.value(), 0.0};
+                block_cols<4, 1>(v4, 0, s_red, my0);
+            }
+            if (!grid_sync(tk.bar, tk.budget, tk.err, epoch)) return;
+            __shared__ double s_q[4];
+            grid_cols<4>(P0, s_q);
+            const double quad = s_q[0], rz0 = s_q[1];
+            const double ain = quad > 0.0 ? rz0 / quad : 0.0;
+            const double rzn = ain * rz0;
+            ++steps;
+            T beta = (T)0;
+            if (first) rr = s_q[2];
+            else beta = (T)((rzn - aprev * s_q[2]) / rz);
+            rz = rzn;
+            aprev = ain;
+            const T ai = (T)ain;
+            // p = alpha_in z0 + beta p
+            for_chunks<T>(a.n, gt, nth, [&](int64_t i0, int cnt) {
+                T zv[W], pv[W];
+                ld_chunk(zc + i0, cnt, zv);
+                if (!first) ld_chunk(a.p + i0, cnt, pv);
+#pragma unroll
+                for (int w = 0; w < W; ++w) zv[w] = first ? ai * zv[w] : ai * zv[w] + beta * pv[w];
+                st_chunk(a.p + i0, cnt, zv);
+            });
+            if (!grid_sync(tk.bar, tk.budget, tk.err, epoch)) return;
+            if (k >= a.maxit || sqrt(rr) <= a.tol_abs) break;
+            // q = A p, pq (two rows at a time, every load of both rows first)
+            acc0[0] = Acc<T>();
+            for (int64_t i0 = gt; i0 < a.n; i0 += 2 * nth) {
+                constexpr int K = 4;
+                int32_t jb[2], je[2];
+                T pv[2], qv[2], dv[2];
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const int64_t i = i0 + u * nth;
+                    const bool ok = i < a.n;
+                    pv[u] = ok ? a.p[i] : (T)0;
+                    dv[u] = ok ? a.aD[i] : (T)0;
+                    jb[u] = ok ? a.aptr[i] : 0;
+                    je[u] = ok ? a.aptr[i + 1] : 0;
+                }
+#pragma unroll
+                for (int u = 0; u < 2; ++u) qv[u] = dv[u] * pv[u];
+                lap_rows<T, 2, K, 1>(a.acol, a.aw, a.p, jb, je, pv, qv);
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const int64_t i = i0 + u * nth;
+                    if (i >= a.n) break;
+                    a.q[i] = qv[u];
+                    acc0[0].add_prod(pv[u], qv[u]);
+                }
+            }
+            block_cols<1>(acc0, 0, s_red, my0);
+            if (!grid_sync(tk.bar, tk.budget, tk.err, epoch)) return;
+            grid_cols<1>(P0, &s_v[2]);
+            const T alpha = (T)(rz / s_v[2]);
+            // e += alpha p, r -= alpha q, rr; the next solve's input r goes
+            // into the buffer of z0_prev
+            acc1[0] = Acc<T>();
+            for_chunks<T>(a.n, gt, nth, [&](int64_t i0, int cnt) {
+                T ev[W], pv[W], rv[W], qv[W];
+                ld_chunk(a.e + i0, cnt, ev);
+                ld_chunk(a.p + i0, cnt, pv);
+                ld_chunk(a.r + i0, cnt, rv);
+                ld_chunk(a.q + i0, cnt, qv);
+#pragma unroll
+                for (int w = 0; w < W; ++w) {
+                    ev[w] += alpha * pv[w];
+                    rv[w] -= alpha * qv[w];
+                }
+                st_chunk(a.e + i0, cnt, ev);
+                st_chunk(a.r + i0, cnt, rv);
+                st_chunk(zp + i0, cnt, rv);
+#pragma unroll
+                for (int w = 0; w < W; ++w) {
+                    if (w >= cnt) break;
+                    acc1[0].add_prod(rv[w], rv[w]);
+                }
+            });
+            block_cols<1>(acc1, 0, s_red, my1);
+            if (!grid_sync(tk.bar, tk.budget, tk.err, epoch)) return;
+            grid_cols<1>(P1, &s_v[3]);
+            rr = s_v[3];
+            T *t = zc;
+            zc = zp;
+            zp = t;
+            ++k;
+            if (k >= a.maxit || sqrt(rr) <= a.tol_abs) break;
+        }
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            a.out[0] += (double)k;
+            a.out[1] = rr;
+            *in.iter_acc += (double)steps;
+        }
+        return;
+    }
     // Each pass starts with z = M^{-1} r (the only call site of the
     // preconditioner), then p, then the test, the product and the updates;
     // the test is looked at once more after the updates, so no
@@ -1007,7 +1153,7 @@ __global__ void __launch_bounds__(kFusedMaxThreads, 1)
     for (bool first = true;; first = false) {
         // the inner CG leaves every z[i] written by the thread that reads it
         // below; the tree solve writes out of order and needs the barrier
-        if constexpr (TREE_ONLY) {
+        if constexpr ((MODE == 1)) {
             if (!tree_solve_dev<T, 1, false>(tk, a.z, epoch, mx, ys)) return;
             if (!grid_sync(tk.bar, tk.budget, tk.err, epoch)) return;
         } else {
@@ -1019,13 +1165,13 @@ __global__ void __launch_bounds__(kFusedMaxThreads, 1)
             T rv[W], zv[W], ov[W];
             ld_chunk(a.r + i0, cnt, rv);
             ld_chunk(a.z + i0, cnt, zv);
-            if (!first && !TREE_ONLY) ld_chunk(a.zo + i0, cnt, ov);
+            if (!first && !(MODE == 1)) ld_chunk(a.zo + i0, cnt, ov);
 #pragma unroll
             for (int w = 0; w < W; ++w) {
                 if (w >= cnt) break;
                 acc0[0].add_prod(rv[w], zv[w]);
                 if (first) acc1[0].add_prod(rv[w], rv[w]);
-                else if (!TREE_ONLY) acc1[0].add_prod(rv[w], ov[w]);
+                else if (!(MODE == 1)) acc1[0].add_prod(rv[w], ov[w]);
             }
         });
         block_cols<1>(acc0, 0, s_red, my0);
@@ -1035,7 +1181,7 @@ __global__ void __launch_bounds__(kFusedMaxThreads, 1)
         const double rzn = s_v[0];
         T beta = (T)0;
         if (first) rr = s_v[1];
-        else beta = (T)((rzn - (TREE_ONLY ? 0.0 : s_v[1])) / rz);
+        else beta = (T)((rzn - ((MODE == 1) ? 0.0 : s_v[1])) / rz);
         rz = rzn;
         for_chunks<T>(a.n, gt, nth, [&](int64_t i0, int cnt) {
             T zv[W], pv[W];
@@ -1096,7 +1242,7 @@ __global__ void __launch_bounds__(kFusedMaxThreads, 1)
             }
             st_chunk(a.e + i0, cnt, ev);
             st_chunk(a.r + i0, cnt, rv);
-            if (TREE_ONLY) {
+            if ((MODE == 1)) {
                 st_chunk(a.z + i0, cnt, rv);
             } else {
                 T zv[W], zero[W] = {};
@@ -1136,11 +1282,15 @@ static int pcg_fused(grass_ctx_t ctx, grass_sparsifier_t S, const T *rhs, T *e, 
     size_t smem = 0;
     TreeKArgs<T> tk = tree_kargs<T, 1>(ctx, Tr, Tr->sdd, &smem);
     const int threads = bounded_threads(ctx->tree_threads, kFusedMaxThreads);
-    const bool tree_only = S->is_tree || inner_maxit <= 0;
-    const void *kern = tree_only ? (const void *)k_pcg_persist<T, true>
-                                 : (const void *)k_pcg_persist<T, false>;
-    const int grid = tree_only ? coop_grid(ctx, k_pcg_persist<T, true>, threads, smem, n)
-                               : coop_grid(ctx, k_pcg_persist<T, false>, threads, smem, n);
+    // 1: the tree solve alone; 2: one inner CG step on the sparsifier, in
+    // closed form; 0: the inner CG as a device function
+    const int mode = (S->is_tree || inner_maxit <= 0) ? 1 : (inner_maxit == 1 ? 2 : 0);
+    const void *kern = mode == 1 ? (const void *)k_pcg_persist<T, 1>
+                     : mode == 2 ? (const void *)k_pcg_persist<T, 2>
+                                 : (const void *)k_pcg_persist<T, 0>;
+    const int grid = mode == 1 ? coop_grid(ctx, k_pcg_persist<T, 1>, threads, smem, n)
+                   : mode == 2 ? coop_grid(ctx, k_pcg_persist<T, 2>, threads, smem, n)
+                               : coop_grid(ctx, k_pcg_persist<T, 0>, threads, smem, n);
     PCGArgs<T> a;
     a.n = n;
     a.aptr = g.adj_ptr.p;
@@ -1168,7 +1318,7 @@ static int pcg_fused(grass_ctx_t ctx, grass_sparsifier_t S, const T *rhs, T *e, 
     a.zo = zold;
     a.tol_abs = tol_abs;
     a.maxit = maxit;
-    a.part = ctx->scr<double>(SCR_PART2, (size_t)grid * 64);
+    a.part = ctx->scr<double>(SCR_PART2, (size_t)grid * 64);   // two [grid][32] partial arrays
     double *out = ctx->scal.p + DS_RED + DS_PCG;
     a.out = out;
     // the inner CG (sparsifier with off-tree edges): solves (L_S + D) z = r
@@ -1192,22 +1342,40 @@ static int pcg_fused(grass_ctx_t ctx, grass_sparsifier_t S, const T *rhs, T *e, 
         fail(GRASS_ERR_INVALID, "PCG vectors must be 16-byte aligned");
     memset_d(ctx, out, 0, 2 * sizeof(double));
     GCK(cudaMemsetAsync(tk.bar, 0, sizeof(unsigned int), ctx->stream));
-    // roofline accounting: bytes per outer iteration (SpMV with A, the vector
-    // updates, the tree solve) and per inner CG iteration
+    // roofline accounting, each array counted once per phase that touches it
+    // (s bytes an element): per outer iteration and per inner CG iteration.
+    //  tree solve: tree_b;  SpMV with A: CSR + p, D read, q written;
+    //  mode 1: dots r, z; p: z, p, p; update: e, p, r, q read, e, r, z
+    //          written -> 12 ns;
+    //  mode 2: the quadratic form over S's CSR with z, D read; dots r, z0_prev;
+    //          p: z, p, p; update: e, p, r, q read, e, r, z written -> 14 ns;
+    //  mode 0: outer dots r, z, z_old; p: z, p, p; update: e, p, r, q, z read,
+    //          e, r, z_old, z, R, Z written -> 17 ns, less 2 ns for the inner
+    //          CG's first iteration; inner: tree_b, SpMV with S, 12 ns.
     const TreeSchedule &TS = Tr->sched;
     const double s = (double)sizeof(T), ns = (double)n * s;
     const double tree_b = 4.0 * ns + TS.n_rcv * (16.0 + 2.0 * s) +
                           (n - (double)Tr->nroots) * (16.0 + 4.0 * s);
     const double spmv_a = 4.0 * (n + 1) + 2.0 * g.m * (4.0 + s) + 3.0 * ns;
-    const double spmv_s = 4.0 * (n + 1) + S->s_nnz * (4.0 + s) + 3.0 * ns;
-    const double per_outer = spmv_a + 12.0 * ns + (tree_only ? tree_b : 7.0 * ns + tree_b);
-    const double per_inner = spmv_s + 16.0 * ns + tree_b;
+    const double csr_s = 4.0 * (n + 1) + S->s_nnz * (4.0 + s);
+    double per_outer, per_inner = 0.0, start;
+    if (mode == 1) {
+        per_outer = tree_b + spmv_a + 12.0 * ns;
+        start = 4.0 * ns;
+    } else if (mode == 2) {
+        per_outer = tree_b + spmv_a + csr_s + 2.0 * ns + 12.0 * ns;
+        start = 4.0 * ns;
+    } else {
+        per_outer = spmv_a + 15.0 * ns;
+        per_inner = tree_b + csr_s + 3.0 * ns + 12.0 * ns;
+        start = 6.0 * ns;
+    }
     const bool timing = ctx->tfam == GRASS_KF_PCG;
     size_t snap = ctx->iter_launches.size();
     if (timing) {
         ctx->t_snap(out, snap, 0);
         ctx->t_snap(in.iter_acc, snap + 1, 0);
-        ctx->iter_launches.push_back({per_outer + 3.0 * ns, per_outer, snap});
+        ctx->iter_launches.push_back({start, per_outer, snap});
         ctx->iter_launches.push_back({0.0, per_inner, snap + 1});
     }
     bool timed = ctx->t_begin(GRASS_KF_PCG, 0.0);
