@@ -332,6 +332,7 @@ struct EulerTour {
     // solvers that keep their vectors in preorder (the tour's entry values
     // are then read in sequence).
     DBuf<int32_t> pre, vert, tour_pre, ein_pre, eout_pre;
+    DBuf<uint8_t> head_pre;          // [n] 1 at every tree's root slot
     DBuf<double> ipw_pre;
     DBuf<float> ipw32_pre;
 };

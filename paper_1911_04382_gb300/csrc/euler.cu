@@ -155,6 +155,12 @@ __global__ void k_eu_tourpre(int64_t L, const int32_t *tour, const int32_t *pre,
     out[p] = t >= 0 ? pre[t] : -(pre[-t - 1] + 1);
 }
 
+// every tree's root slot in the preorder (the tree's vertex offset)
+__global__ void k_eu_headpre(int64_t nr, const int64_t *voff, uint8_t *head_pre) {
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < nr) head_pre[voff ? voff[q] : 0] = 1;
+}
+
 __global__ void k_eu_prevals(int64_t n, const int32_t *vert, const int32_t *ein, const int32_t *eout,
                              const double *ipw, const float *ipw32, int32_t *ein_p, int32_t *eout_p,
                              double *ipw_p, float *ipw32_p) {
@@ -241,6 +247,10 @@ void euler_build(grass_ctx_t ctx, grass_tree_t T, const int32_t *tptr, const int
         E.tour_pre.alloc(L);
         launch(ctx, k_eu_tourpre, cdiv(L, kBlock), kBlock, 0, L, (const int32_t *)E.tour.p,
                (const int32_t *)E.pre.p, E.tour_pre.p);
+        E.head_pre.alloc(n);
+        memset_d(ctx, E.head_pre.p, 0, n);
+        launch(ctx, k_eu_headpre, cdiv(T->nroots, kBlock), kBlock, 0, T->nroots,
+               g.nseg > 1 ? (const int64_t *)g.seg_voff_d.p : nullptr, E.head_pre.p);
         E.ein_pre.alloc(n);
         E.eout_pre.alloc(n);
         E.ipw_pre.alloc(n);

@@ -384,7 +384,7 @@ __device__ __forceinline__ bool cg_dev(const CGArgs<T> &g, const TreeKArgs<T> &t
     // solve is spent when no column goes on.
     for (int it = 0;; ++it) {
         if constexpr (EU) {
-            if (!euler_solve_dev<T>(g.eu, g.Z, tk.bar, tk.budget, tk.err, epoch, mx)) return false;
+            if (!euler_solve_dev<T, true>(g.eu, g.Z, tk.bar, tk.budget, tk.err, epoch, mx)) return false;
         } else {
             if (!tree_solve_dev<T, R, false>(tk, g.Z, epoch, mx, ys)) return false;
         }

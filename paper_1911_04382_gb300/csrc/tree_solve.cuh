@@ -463,6 +463,11 @@ struct EulerKArgs {
     int64_t L, n;
     const int32_t *tour, *ein, *eout;
     const uint8_t *head;    // [L] 1 at the first position of every tree's tour
+    // preorder form (pre = 1): the vectors are in the tree's preorder;
+    // head_n [n] marks every tree's root slot, D [n] holds step 2's values
+    int pre;
+    const uint8_t *head_n;
+    void *D;
     const void *ipw;        // [n] 1 / weight of v's parent edge (T)
     void *S, *C;            // [L] prefix sums (SumOf<T>), [n] currents (T)
     double *part;           // [6 * gridDim.x]: block pairs and first heads
@@ -618,16 +623,17 @@ __device__ inline void block_offsets_seg(const V *pv, const double *pf, V *off) 
 
 constexpr int kEuBatch = 8;   // consecutive tour positions per thread and tile
 
-// One segmented scan pass over the block's stretch [b0, b1) of the tour:
-// S[p] = sum of val over [latest head <= p, p) inside the block (the carry
-// from earlier blocks is added by the reader: it applies before the block's
-// first head).  The stretch goes in tiles of blockDim * kEuBatch positions,
+// One segmented scan pass over the block's stretch [b0, b1) of a sequence
+// (the tour's positions, or the preorder's slots) with heads head[p]:
+// S[p] = sum of val(p, head[p]) over [latest head <= p, p) inside the block
+// (the carry from earlier blocks is added by the reader: it applies before
+// the block's first head).  The stretch goes in tiles of blockDim * kEuBatch positions,
 // kEuBatch consecutive ones per thread (coalesced; the values are gathered
 // once and kept in registers); a segmented block scan per tile, the block's
 // running pair carried from tile to tile.  Block pair into pv[b], pf[b];
 // first head into fh[b].
 template <typename T, typename VAL>
-__device__ inline void euler_scan_pass(const EulerKArgs &E, int64_t b0, int64_t b1, VAL val,
+__device__ inline void euler_scan_pass(const uint8_t *head, int64_t b0, int64_t b1, VAL val,
                                        typename SumOf<T>::type *S, typename SumOf<T>::type *pv,
                                        double *pf, long long *fh) {
     using V = typename SumOf<T>::type;
@@ -637,17 +643,12 @@ __device__ inline void euler_scan_pass(const EulerKArgs &E, int64_t b0, int64_t 
     long long first = LLONG_MAX;
     for (int64_t base = b0; base < b1; base += tile) {
         const int64_t p0 = base + (int64_t)threadIdx.x * kEuBatch;
-        int32_t tv[kEuBatch];
         uint8_t hd[kEuBatch];
         T x[kEuBatch];
 #pragma unroll
-        for (int k = 0; k < kEuBatch; ++k) {
-            const bool in = p0 + k < b1;
-            tv[k] = in ? E.tour[p0 + k] : 0;
-            hd[k] = in ? E.head[p0 + k] : 0;
-        }
+        for (int k = 0; k < kEuBatch; ++k) hd[k] = p0 + k < b1 ? head[p0 + k] : 0;
 #pragma unroll
-        for (int k = 0; k < kEuBatch; ++k) x[k] = p0 + k < b1 ? val(tv[k]) : (T)0;
+        for (int k = 0; k < kEuBatch; ++k) x[k] = p0 + k < b1 ? val(p0 + k, hd[k] != 0) : (T)0;
         V sv = s_zero<V>();
         int sf = 0;
 #pragma unroll
@@ -688,12 +689,113 @@ __device__ inline void euler_scan_pass(const EulerKArgs &E, int64_t b0, int64_t 
     }
 }
 
+// The preorder form (Y, the tour's per-vertex arrays and the heads in the
+// tree's preorder; k's subtree is the slot range [k, k + size_k) with
+// size_k = (out_k - in_k + 1) / 2):
+//  1. S1 = exclusive prefix sums of b over the slots (0 at the roots),
+//     restarting at every root;
+//  2. c_k = (S1 inclusive at k + size_k - 1  -  S1 exclusive at k) / w_k;
+//  3. d_k = c_k - sum of c_j over the vertices j whose subtrees end at
+//     k - 1 (the tour's exits between the entries of k - 1 and k; none
+//     after a root), 0 at the roots; S3 = exclusive prefix sums of d;
+//  4. x_k = S3 at k + d_k: the sum of c over k's ancestors and k itself (the
+//     slots j <= k whose subtree has not ended before k).
+// Scans of n slots in place of 2 (n - roots) tour positions, read in order.
 template <typename T>
-__device__ __forceinline__ bool euler_solve_dev(const EulerKArgs &E, T *Y, unsigned int *bar,
-                                                long long budget, int *err, unsigned int &epoch,
-                                                double &mx) {
+__device__ __forceinline__ bool euler_solve_pre(const EulerKArgs &E, T *Y, unsigned int *bar,
+                                             long long budget, int *err, unsigned int &epoch,
+                                             double &mx, typename SumOf<T>::type *s_off) {
     using V = typename SumOf<T>::type;
-    __shared__ V s_off[kEulerMaxGrid];
+    const int64_t G = gridDim.x, N = E.n;
+    const int64_t per = (N + G - 1) / G;
+    const int64_t b0 = min(N, (int64_t)blockIdx.x * per), b1 = min(N, b0 + per);
+    const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+    V *S = reinterpret_cast<V *>(E.S);
+    T *C = reinterpret_cast<T *>(E.C);
+    T *D = reinterpret_cast<T *>(E.D);
+    V *pv = reinterpret_cast<V *>(E.part);
+    double *pf = E.part + G;
+    long long *fh = reinterpret_cast<long long *>(E.part + 2 * G);
+    const T *ipw = reinterpret_cast<const T *>(E.ipw);
+    const uint32_t per32 = (uint32_t)per;
+    auto glob = [&](int64_t p, const long long *fhp) {
+        const uint32_t b = (uint32_t)p / per32;
+        return p < fhp[b] ? s_add(S[p], s_off[b]) : S[p];
+    };
+    const int64_t vbase = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    // 1
+    euler_scan_pass<T>(E.head_n, b0, b1, [&](int64_t p, bool hd) { return hd ? (T)0 : Y[p]; }, S,
+                       pv, pf, fh);
+    if (!grid_sync(bar, budget, err, epoch)) return false;
+    // 2
+    block_offsets_seg(pv, pf, s_off);
+    for (int64_t v0 = vbase; v0 < N; v0 += nth * kEuBatch) {
+        int32_t in[kEuBatch], out[kEuBatch];
+#pragma unroll
+        for (int k = 0; k < kEuBatch; ++k) {
+            const int64_t v = v0 + k * nth;
+            in[k] = v < N ? E.ein[v] : -1;
+            out[k] = v < N ? E.eout[v] : -1;
+        }
+        T c[kEuBatch];
+#pragma unroll
+        for (int k = 0; k < kEuBatch; ++k) {
+            const int64_t v = v0 + k * nth;
+            c[k] = (T)0;
+            if (in[k] >= 0) {
+                const int64_t last = v + (out[k] - in[k] + 1) / 2 - 1;
+                const V hi = s_add(glob(last, fh), s_of<V, T>(Y[last]));
+                c[k] = (T)s_to(s_sub(hi, glob(v, fh))) * ipw[v];
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kEuBatch; ++k) {
+            const int64_t v = v0 + k * nth;
+            if (v < N) C[v] = c[k];
+        }
+    }
+    if (!grid_sync(bar, budget, err, epoch)) return false;
+    // 3
+    euler_scan_pass<T>(E.head_n, b0, b1, [&](int64_t p, bool hd) {
+        if (hd) {
+            D[p] = (T)0;
+            return (T)0;
+        }
+        T d = C[p];
+        if (!E.head_n[p - 1]) {
+            for (int32_t q = E.ein[p - 1] + 1; q < E.ein[p]; ++q) d -= C[-E.tour[q] - 1];
+        }
+        D[p] = d;
+        return d;
+    }, S, pv + 3 * G, pf + 3 * G, fh + 3 * G);
+    if (!grid_sync(bar, budget, err, epoch)) return false;
+    // 4
+    block_offsets_seg(pv + 3 * G, pf + 3 * G, s_off);
+    T tm = (T)0;
+    for (int64_t v0 = vbase; v0 < N; v0 += nth * kEuBatch) {
+        T x[kEuBatch];
+#pragma unroll
+        for (int k = 0; k < kEuBatch; ++k) {
+            const int64_t v = v0 + k * nth;
+            x[k] = v < N && !E.head_n[v] ? (T)s_to(s_add(glob(v, fh + 3 * G), s_of<V, T>(D[v]))) : (T)0;
+        }
+#pragma unroll
+        for (int k = 0; k < kEuBatch; ++k) {
+            const int64_t v = v0 + k * nth;
+            if (v >= N) continue;
+            Y[v] = x[k];
+            tm = fmax(tm, fabs(x[k]));
+        }
+    }
+    mx = fmax(mx, (double)tm);
+    return true;
+}
+
+template <typename T>
+__device__ __forceinline__ bool euler_solve_tour(const EulerKArgs &E, T *Y, unsigned int *bar,
+                                                long long budget, int *err, unsigned int &epoch,
+                                                double &mx, typename SumOf<T>::type *s_off) {
+    using V = typename SumOf<T>::type;
     const int64_t G = gridDim.x;
     const int64_t per = (E.L + G - 1) / G;
     const int64_t b0 = min(E.L, (int64_t)blockIdx.x * per), b1 = min(E.L, b0 + per);
@@ -714,7 +816,10 @@ __device__ __forceinline__ bool euler_solve_dev(const EulerKArgs &E, T *Y, unsig
     };
     const int64_t vbase = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     // 1: prefix sums of b at the entries, restarting at every tree
-    euler_scan_pass<T>(E, b0, b1, [&](int32_t v) { return v >= 0 ? Y[v] : (T)0; }, S, pv, pf, fh);
+    euler_scan_pass<T>(E.head, b0, b1, [&](int64_t p, bool) {
+        const int32_t v = E.tour[p];
+        return v >= 0 ? Y[v] : (T)0;
+    }, S, pv, pf, fh);
     if (!grid_sync(bar, budget, err, epoch)) return false;
     // 2: currents c_v = (subtree sum of b) / w_v
     block_offsets_seg(pv, pf, s_off);
@@ -738,8 +843,10 @@ __device__ __forceinline__ bool euler_solve_dev(const EulerKArgs &E, T *Y, unsig
     }
     if (!grid_sync(bar, budget, err, epoch)) return false;
     // 3: prefix sums of +c at entries, -c at exits, restarting at every tree
-    euler_scan_pass<T>(E, b0, b1, [&](int32_t v) { return v >= 0 ? C[v] : -C[-v - 1]; }, S,
-                       pv + 3 * G, pf + 3 * G, fh + 3 * G);
+    euler_scan_pass<T>(E.head, b0, b1, [&](int64_t p, bool) {
+        const int32_t v = E.tour[p];
+        return v >= 0 ? C[v] : -C[-v - 1];
+    }, S, pv + 3 * G, pf + 3 * G, fh + 3 * G);
     if (!grid_sync(bar, budget, err, epoch)) return false;
     // 4: x_v = the path sum up to and including v's entry (roots: 0)
     block_offsets_seg(pv + 3 * G, pf + 3 * G, s_off);
@@ -769,6 +876,17 @@ __device__ __forceinline__ bool euler_solve_dev(const EulerKArgs &E, T *Y, unsig
     return true;
 }
 
+
+// PRE: the preorder form (E.pre set by euler_kargs), else the tour form.
+template <typename T, bool PRE = false>
+__device__ __forceinline__ bool euler_solve_dev(const EulerKArgs &E, T *Y, unsigned int *bar,
+                                                long long budget, int *err, unsigned int &epoch,
+                                                double &mx) {
+    __shared__ typename SumOf<T>::type s_off[kEulerMaxGrid];
+    if constexpr (PRE) return euler_solve_pre<T>(E, Y, bar, budget, err, epoch, mx, s_off);
+    else return euler_solve_tour<T>(E, Y, bar, budget, err, epoch, mx, s_off);
+}
+
 // Host side: scan-form arguments for a cooperative grid of `grid` blocks;
 // pre: the vectors are in the tree's preorder numbering (else vertex ids).
 template <typename T>
@@ -782,6 +900,9 @@ inline void euler_kargs(grass_ctx_t ctx, const grass_tree_s *Tr, int grid, Euler
     e->ein = pre ? E.ein_pre.p : E.ein.p;
     e->eout = pre ? E.eout_pre.p : E.eout.p;
     e->head = E.head.p;
+    e->pre = pre ? 1 : 0;
+    e->head_n = pre ? E.head_pre.p : nullptr;
+    e->D = pre ? (void *)ctx->scr<double>(SCR_EU_A, Tr->g.n) : nullptr;
     if constexpr (sizeof(T) == 8) e->ipw = pre ? E.ipw_pre.p : E.ipw.p;
     else e->ipw = pre ? E.ipw32_pre.p : E.ipw32.p;
     e->S = ctx->scr<double>(SCR_EU_S, E.L + 1);   // 8-byte sums (double or float pair)
