@@ -223,54 +223,6 @@ __device__ __forceinline__ void lap_rows(const int32_t *col, const T *w, const T
     }
 }
 
-// One-column element loops.  FP32 vectors are walked in 16-byte chunks:
-// thread gt takes chunks gt, gt + nth, ... (four floats, one vector access
-// per operand) and the n mod 4 leftover elements go to threads 0, 1, 2.
-// Every such loop over the same vectors uses this mapping, so an element is
-// always read and written by the same thread.  FP64 vectors (which may be
-// the caller's own, 8-byte aligned) take one element per step.
-template <typename T>
-struct Chunk {
-    static constexpr int W = sizeof(T) == 4 ? 4 : 1;
-};
-
-template <typename T, typename F>
-__device__ __forceinline__ void for_chunks(int64_t n, int64_t gt, int64_t nth, F &&f) {
-    constexpr int W = Chunk<T>::W;
-    const int64_t nv = n / W;
-    for (int64_t v = gt; v < nv; v += nth) f(v * W, W);
-    if constexpr (W > 1) {
-        if (gt < n - nv * W) f(nv * W + gt, 1);
-    }
-}
-
-template <typename T>
-__device__ __forceinline__ void ld_chunk(const T *p, int cnt, T (&v)[Chunk<T>::W]) {
-    if constexpr (Chunk<T>::W == 4) {
-        if (cnt == 4) {
-            const float4 q = *reinterpret_cast<const float4 *>(p);
-            v[0] = q.x;
-            v[1] = q.y;
-            v[2] = q.z;
-            v[3] = q.w;
-            return;
-        }
-        v[1] = v[2] = v[3] = (T)0;
-    }
-    v[0] = p[0];
-}
-
-template <typename T>
-__device__ __forceinline__ void st_chunk(T *p, int cnt, const T (&v)[Chunk<T>::W]) {
-    if constexpr (Chunk<T>::W == 4) {
-        if (cnt == 4) {
-            *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
-            return;
-        }
-    }
-    p[0] = v[0];
-}
-
 // Two column sums at once: warps 0..R-1 reduce part0 and warps R..2R-1
 // part1 (each the same order as grid_cols), when the block has 2R warps.
 template <int R>
@@ -383,12 +335,14 @@ __device__ __forceinline__ bool cg_dev(const CGArgs<T> &g, const TreeKArgs<T> &t
     // updates.  After the updates the test is looked at once more, so no
     // solve is spent when no column goes on.
     for (int it = 0;; ++it) {
+        // the scan form writes Z with the element loops' own mapping (no
+        // barrier); the elimination rounds write out of order
         if constexpr (EU) {
             if (!euler_solve_dev<T, true>(g.eu, g.Z, tk.bar, tk.budget, tk.err, epoch, mx)) return false;
         } else {
             if (!tree_solve_dev<T, R, false>(tk, g.Z, epoch, mx, ys)) return false;
+            if (!grid_sync(tk.bar, tk.budget, tk.err, epoch)) return false;
         }
-        if (!grid_sync(tk.bar, tk.budget, tk.err, epoch)) return false;
 #pragma unroll
         for (int e = 0; e < NA; ++e) acc0[e] = acc1[e] = Acc<T>();
         if constexpr (CH) {

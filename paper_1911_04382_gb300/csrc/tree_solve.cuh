@@ -450,6 +450,54 @@ __device__ __forceinline__ bool tree_solve_dev(const TreeKArgs<T> &a, T *Y, unsi
     return true;
 }
 
+// One-column element loops.  FP32 vectors are walked in 16-byte chunks:
+// thread gt takes chunks gt, gt + nth, ... (four floats, one vector access
+// per operand) and the n mod 4 leftover elements go to threads 0, 1, 2.
+// Every such loop over the same vectors uses this mapping, so an element is
+// always read and written by the same thread.  FP64 vectors (which may be
+// the caller's own, 8-byte aligned) take one element per step.
+template <typename T>
+struct Chunk {
+    static constexpr int W = sizeof(T) == 4 ? 4 : 1;
+};
+
+template <typename T, typename F>
+__device__ __forceinline__ void for_chunks(int64_t n, int64_t gt, int64_t nth, F &&f) {
+    constexpr int W = Chunk<T>::W;
+    const int64_t nv = n / W;
+    for (int64_t v = gt; v < nv; v += nth) f(v * W, W);
+    if constexpr (W > 1) {
+        if (gt < n - nv * W) f(nv * W + gt, 1);
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void ld_chunk(const T *p, int cnt, T (&v)[Chunk<T>::W]) {
+    if constexpr (Chunk<T>::W == 4) {
+        if (cnt == 4) {
+            const float4 q = *reinterpret_cast<const float4 *>(p);
+            v[0] = q.x;
+            v[1] = q.y;
+            v[2] = q.z;
+            v[3] = q.w;
+            return;
+        }
+        v[1] = v[2] = v[3] = (T)0;
+    }
+    v[0] = p[0];
+}
+
+template <typename T>
+__device__ __forceinline__ void st_chunk(T *p, int cnt, const T (&v)[Chunk<T>::W]) {
+    if constexpr (Chunk<T>::W == 4) {
+        if (cnt == 4) {
+            *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+            return;
+        }
+    }
+    p[0] = v[0];
+}
+
 // ---------------------------------------------------------------- scan form (D = 0, r = 1)
 // Grounded solve of L_T x = b along the Euler tour (euler.cu): with S the
 // exclusive prefix sums of b placed at the tour's entries, the current up
@@ -769,24 +817,22 @@ __device__ __forceinline__ bool euler_solve_pre(const EulerKArgs &E, T *Y, unsig
         return d;
     }, S, pv + 3 * G, pf + 3 * G, fh + 3 * G);
     if (!grid_sync(bar, budget, err, epoch)) return false;
-    // 4
+    // 4, in the chunks of for_chunks: the one-column element loops that
+    // follow read Y with this mapping, so no barrier is needed after it
     block_offsets_seg(pv + 3 * G, pf + 3 * G, s_off);
     T tm = (T)0;
-    for (int64_t v0 = vbase; v0 < N; v0 += nth * kEuBatch) {
-        T x[kEuBatch];
+    constexpr int W = Chunk<T>::W;
+    for_chunks<T>(N, vbase, nth, [&](int64_t i0, int cnt) {
+        T x[W];
 #pragma unroll
-        for (int k = 0; k < kEuBatch; ++k) {
-            const int64_t v = v0 + k * nth;
-            x[k] = v < N && !E.head_n[v] ? (T)s_to(s_add(glob(v, fh + 3 * G), s_of<V, T>(D[v]))) : (T)0;
+        for (int w = 0; w < W; ++w) {
+            const int64_t v = i0 + w;
+            x[w] = w < cnt && !E.head_n[v] ? (T)s_to(s_add(glob(v, fh + 3 * G), s_of<V, T>(D[v])))
+                                           : (T)0;
+            tm = fmax(tm, fabs(x[w]));
         }
-#pragma unroll
-        for (int k = 0; k < kEuBatch; ++k) {
-            const int64_t v = v0 + k * nth;
-            if (v >= N) continue;
-            Y[v] = x[k];
-            tm = fmax(tm, fabs(x[k]));
-        }
-    }
+        st_chunk(Y + i0, cnt, x);
+    });
     mx = fmax(mx, (double)tm);
     return true;
 }
