@@ -7,7 +7,8 @@ leave remainders:
 * the two-row Laplacian products, which load four entries of a row at a
   time (3D grid rows have six; the power-law graph's hubs have hundreds);
 * the inner CG in both forms (scan form and elimination rounds) and the
-  fused PCG with and without off-tree edges in the sparsifier.
+  fused PCG with and without off-tree edges in the sparsifier, and its
+  closed-form single inner step on FP64 vectors.
 
 Tolerances: FP32 vectors with float-pair dot products reach a relative
 residual of 1e-6 in the inner solves, so an embedding's heats, normalised
@@ -99,6 +100,32 @@ def test_fp32_pcg_ragged_sizes(gpu, gi, extra):
     xr = host(x)
     rel = np.linalg.norm(b - A @ xr) / np.linalg.norm(b)
     assert rel <= tol and st.rel_resid_fp64 == pytest.approx(rel, rel=1e-6)
+
+
+@pytest.mark.parametrize("gi", range(3))
+def test_fp64_pcg_one_inner_step(gpu, gi):
+    """FP64 vectors with one inner step per outer iteration: the closed-form
+    step on doubles (one element per step, no 16-byte chunks)."""
+    import torch
+    g = _pcg_cases()[gi]
+    og = oracle.from_graph(g)
+    ot = oracle.build_tree(og)
+    b = rng.normal(85 + gi, rng.STREAM_RHS, g.n)
+    tol = 1e-9
+    with gpu_graph(g) as (ctx, tree, _):
+        S = gpu.grass_sparsifier_create(ctx, tree)
+        try:
+            _, add = _with_extra(og, ot, 3)
+            gpu.grass_sparsifier_add(ctx, S, dev(add))
+            x = torch.zeros(g.n, dtype=torch.float64, device="cuda")
+            status, st = gpu.grass_pcg_solve(ctx, S, dev(b), x, tol, 20000, gpu.GRASS_FP64,
+                                             1e-3, 1e-2, 1)
+            assert status == gpu.GRASS_OK and st.inner_iters == st.iters
+        finally:
+            gpu.grass_sparsifier_destroy(S)
+    A = sp.csr_matrix((g.val, g.col, g.rowptr), shape=(g.n, g.n))
+    rel = np.linalg.norm(b - A @ host(x)) / np.linalg.norm(b)
+    assert rel <= tol
 
 
 @pytest.mark.parametrize("euler", [1, 0])
