@@ -192,11 +192,18 @@ KERNEL_SOURCES = ["paper_1911_04382_gb300/csrc/krylov.cu", "paper_1911_04382_gb3
                   "paper_1911_04382_gb300/csrc/common.cuh"]
 
 
-def kernel_sources_hash() -> str:
+def kernel_sources_hash(read=None) -> str:
+    """Hash of the kernel sources' code: comments and blank lines removed,
+    so a comment edit keeps a capture's record valid.  read(path) -> text
+    (default: the working tree)."""
     import hashlib
+    import re
+    read = read or (lambda s: open(os.path.join(ROOT, s)).read())
     h = hashlib.sha256()
     for s in KERNEL_SOURCES:
-        h.update(open(os.path.join(ROOT, s), "rb").read())
+        t = re.sub(r"/\*.*?\*/", "", read(s), flags=re.S)
+        t = re.sub(r"//[^\n]*", "", t)
+        h.update("\n".join(ln.rstrip() for ln in t.splitlines() if ln.strip()).encode())
     return h.hexdigest()[:16]
 
 

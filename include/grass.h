@@ -145,9 +145,12 @@ grass_status grass_ctx_set_wait_limit(grass_ctx_t ctx, int64_t polls, int hold_b
  *                         many items run in one block (work: surviving
  *                         vertices x max(1, r/4); default 2048; 0 = none)
  *   "euler_solve"         1 (default): grounded solves of L_T alone (no D)
- *                         with one column, inside the inner CG and the
- *                         power steps, use the Euler-tour scan form (two
- *                         FP64 prefix sums); 0: the elimination rounds
+ *                         with one column use the scan form (two segmented
+ *                         prefix sums: along the Euler tour for a solve on
+ *                         its own, over the preorder's vertex slots inside
+ *                         the inner CG and the power steps, whose vectors
+ *                         are then kept in preorder); 0: the elimination
+ *                         rounds
  *   "euler_max_n"         trees built on this context with more vertices
  *                         than this (default 4,000,000) get no Euler tour
  *                         and keep the elimination rounds (the tour's FP64
@@ -159,7 +162,8 @@ grass_status grass_ctx_set_param(grass_ctx_t ctx, const char *name, int64_t valu
 /* Kernel timing for roofline measurements (no counterpart in the paper).
  * family != GRASS_KF_NONE brackets every launch of that kernel family with
  * CUDA events on the context stream and accumulates, per launch, the
- * algorithmic bytes the launch must move (each array touched once):
+ * algorithmic bytes the launch must move (each array counted once per
+ * phase that touches it):
  *   GRASS_KF_SPMM_G  Y = L_G X:  4(n+1) + 2m(4+s) + 2nrs
  *   GRASS_KF_SPMM_S  the same over the sparsifier's adjacency (+ns with D)
  *   GRASS_KF_HEAT    m_off(8+s) + nrs + m_off s
@@ -167,12 +171,15 @@ grass_status grass_ctx_set_param(grass_ctx_t ctx, const char *name, int64_t valu
  *                    4nrs + receivers(16+2s) + (n-1)(16+4s)
  *   GRASS_KF_CG      one fused inner CG solve on the sparsifier: its
  *                    iterations (read back from the device) times
- *                    [SpMV over S + 16nrs + tree solve] plus the start
- *                    (7nrs + one tree solve)
+ *                    [tree solve + SpMV over S + 12nrs] plus 2nrs (+nrs
+ *                    for max |X|, +2nrs for a preorder scatter)
  *   GRASS_KF_PCG     one fused PCG run (grass_pcg_solve, one launch per
  *                    refinement pass): its outer iterations times
- *                    [SpMV with A + 12ns + preconditioner] plus its inner
- *                    CG iterations times [SpMV over S + 16ns + tree solve]
+ *                    [tree solve + SpMV with A + 12ns] (tree preconditioner),
+ *                    [tree solve + SpMV with A + S's CSR + 14ns] (one inner
+ *                    step, in closed form) or [SpMV with A + 15ns] plus the
+ *                    inner CG iterations times [tree solve + SpMV over S +
+ *                    12ns] (inner CG); plus 4ns (6ns with the inner CG)
  * (n rows, r columns, s = 4 or 8 bytes, m edges.)  Enabling resets the
  * accumulators.  grass_kernel_timing_read synchronises the stream and
  * returns the summed event time (ms), the number of timed launches and the

@@ -13,7 +13,10 @@
 // its two ends); the slot after (u -> v) is the one after (v -> u) in v's
 // slot list, cyclically; each tree's circuit starts at the first slot of its
 // root and is cut where it returns to the root.  Positions come from list
-// ranking by pointer jumping (distance to the end of the circuit).
+// ranking by pointer jumping (distance to the end of the circuit).  The
+// preorder numbering (each tree's root, then its vertices in the order the
+// tour enters them) and the tour's arrays in that numbering serve solvers
+// that keep their vectors in preorder.
 #include "common.cuh"
 
 namespace grass {

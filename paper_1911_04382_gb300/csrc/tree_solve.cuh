@@ -503,9 +503,11 @@ __device__ __forceinline__ void st_chunk(T *p, int cnt, const T (&v)[Chunk<T>::W
 // exclusive prefix sums of b placed at the tour's entries, the current up
 // v's parent edge is c_v = (S[out(v)] - S[in(v)]) / w_v; with S2 the prefix
 // sums of +c at entries and -c at exits, x_v = S2 up to and including
-// in(v).  FP64 sums; each block scans a contiguous stretch of the tour and
-// every block derives the stretch offsets from the per-block totals in one
-// fixed order, so the result does not depend on timing.
+// in(v).  The same in the tree's preorder over the n vertex slots
+// (euler_solve_pre).  FP64 (or float-pair) sums; each block scans a
+// contiguous stretch and every block derives the stretch offsets from the
+// per-block totals in one fixed order, so the result does not depend on
+// timing.
 
 struct EulerKArgs {
     int64_t L, n;
