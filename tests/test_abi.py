@@ -69,3 +69,20 @@ def test_server_footprint_is_host_only_and_monotone(libpath):
     assert base >= 8 * (n + 1) + 12 * nnz + 8 * n * r * R + 8 * n * R + 16 * n
     assert f(20_000, 50_000, 8, 3) > base and f(10_000, 90_000, 8, 3) > base
     assert f(10_000, 50_000, 16, 3) > base and f(10_000, 50_000, 8, 4) > base
+
+
+def test_kernel_source_hash_ignores_comments():
+    """The capture records in profiles/traffic.json stay valid across comment
+    edits but not across code edits."""
+    import bench
+    src = {"a": "int x; // one\n/* block\n comment */\nint y;\n\n", "b": "float z;\n"}
+    base = bench.KERNEL_SOURCES
+    try:
+        bench.KERNEL_SOURCES = ["a", "b"]
+        h0 = bench.kernel_sources_hash(lambda s: src[s])
+        src["a"] = "int x;  // two\n\nint y;\n"
+        assert bench.kernel_sources_hash(lambda s: src[s]) == h0
+        src["a"] = "int x; int y;\n"
+        assert bench.kernel_sources_hash(lambda s: src[s]) != h0
+    finally:
+        bench.KERNEL_SOURCES = base
