@@ -72,7 +72,7 @@ typedef struct {
 /* Densification parameters (Sec. IV-D). */
 typedef struct {
     double sigma2;               /* target relative condition number sigma^2          */
-    int r;                       /* random vectors per round, 1..32                   */
+    int r;                       /* random vectors per round: 1, 2, 4, 8, 16, 24, 32  */
     int t;                       /* power steps per round, >= 1 (paper: t = 2)        */
     int max_rounds;              /* densification rounds, 1..GRASS_MAX_ROUNDS         */
     int lmax_iters;              /* power steps for the lambda_max estimate (< 10)    */
@@ -232,7 +232,7 @@ grass_status grass_tree_edges(grass_ctx_t ctx, grass_tree_t tree, uint8_t *in_tr
 /* X = L_T^{-1} B grounded at rho (with_D = 0; X[rho] = 0) or
  * X = (L_T + D)^{-1} B (with_D = 1), by the tree's elimination schedule
  * (Sec. III-H: linear-time tree factorization).  B, X: device, n x r.
- * B and X may alias.  1 <= r <= 32. */
+ * B and X may alias.  r in {1, 2, 4, 8, 16, 24, 32} (other values: INVALID). */
 grass_status grass_tree_solve(grass_ctx_t ctx, grass_tree_t tree, int with_D, int r,
                               grass_prec prec, const void *B, void *X);
 
@@ -247,11 +247,13 @@ grass_status grass_tree_solve(grass_ctx_t ctx, grass_tree_t tree, int with_D, in
  * limit it sets is that the cooperative grid times the schedule's grid
  * barriers stays below 2^31 (far above any schedule the library builds);
  * beyond it the call returns GRASS_ERR_INVALID.
- *   Set-up: the first call on a device looks up the array's address there
- * (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   Set-up: the first call in a CUDA context (once per device, and again
+ * after the application resets the device) looks up the array's address
+ * there (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  This note concerns the set-up only.
  *   Sharing: every call on a device uses the same array, which keeps the
  * last call's contents; each call zeroes it on ctx's stream before its
- * kernel.  Calls that overlap on the GPU (other streams, contexts or
+ * kernel and copies in ctx's barrier-hold setting (grass_ctx_set_wait_limit).  Calls that overlap on the GPU (other streams, contexts or
  * threads on the same device) race on it: order them.
  *   with_D = 1 needs the L_T + D factor, which is built (allocated) by a
  * first grass_tree_solve with with_D = 1; without it the call returns
@@ -262,7 +264,7 @@ grass_status grass_tree_solve_noalloc(grass_ctx_t ctx, grass_tree_t tree, int wi
                                       grass_prec prec, const void *B, void *X);
 
 /* Y = L_G X (graph Laplacian, D excluded; Eq. formula_laplacian).
- * X, Y: device, n x r, must not alias.  1 <= r <= 32. */
+ * X, Y: device, n x r, must not alias.  r in {1, 2, 4, 8, 16, 24, 32}. */
 grass_status grass_spmm(grass_ctx_t ctx, grass_tree_t tree, int r, grass_prec prec,
                         const void *X, void *Y);
 
@@ -296,7 +298,7 @@ grass_status grass_sparsifier_offtree(grass_ctx_t ctx, grass_sparsifier_t S, int
  * constant.  Outputs (device, optional = NULL):
  *   H_out [n x r] in prec;  heat [m_off] in prec, heat[i] = w_e sum_j
  *   (H[u][j] - H[v][j])^2 for the i-th off-S edge e = (u,v) in increasing id.
- * Host output heat_max (optional).  1 <= r <= 32, t >= 1. */
+ * Host output heat_max (optional).  r in {1, 2, 4, 8, 16, 24, 32}, t >= 1. */
 grass_status grass_embed(grass_ctx_t ctx, grass_sparsifier_t S, const double *h0, int r, int t,
                          grass_prec prec, double inner_tol, int inner_maxit, void *H_out,
                          void *heat, double *heat_max);

@@ -144,6 +144,10 @@ class DensifyResult:
     lmax: list = field(default_factory=list)
     theta: list = field(default_factory=list)
     stopped_similar: bool = False
+    # per round, when densify(record=True): the heats of the off-S edges,
+    # their ids, the threshold theta * heat_max and, with a cap, the heat of
+    # the last edge the cap kept (None without one)
+    trace: list = field(default_factory=list)
 
 
 # --------------------------------------------------------------------------
@@ -366,7 +370,7 @@ def filter_edges(heat_vals: np.ndarray, off_eids: np.ndarray, theta: float, cap:
 
 def densify(og: OGraph, tree: OTree, h0s, v0s, sigma2: float, t: int, max_rounds: int,
             lmax_iters: int = 8, cap: int = 0, inner_tol: float = 1e-12,
-            inner_maxit: int = 1000) -> DensifyResult:
+            inner_maxit: int = 1000, record: bool = False) -> DensifyResult:
     """Section IV-D: per round, (1) S updated, (2) lambda estimates,
     (3) stop when lmax/lmin <= sigma^2, (4) t-step power iteration with the
     round's r start vectors, (5) filter by theta_sigma, add the kept edges.
@@ -386,6 +390,12 @@ def densify(og: OGraph, tree: OTree, h0s, v0s, sigma2: float, t: int, max_rounds
         th = theta_sigma(sigma2, lmin, lmax, t)
         res.theta.append(th)
         acc = filter_edges(hv, off, th, cap)
+        if record:
+            thr = th * float(np.max(hv)) if hv.shape[0] else 0.0
+            kth = None
+            if cap > 0 and acc.shape[0] == cap:
+                kth = float(np.min(hv[np.searchsorted(off, acc)]))
+            res.trace.append(dict(heat=hv, off=off, thr=thr, cap_heat=kth))
         res.rounds += 1
         res.added.append(int(acc.shape[0]))
         if acc.shape[0] == 0:

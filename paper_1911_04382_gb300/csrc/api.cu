@@ -454,7 +454,7 @@ grass_status grass_tree_solve(grass_ctx_t ctx, grass_tree_t T, int with_D, int r
     need_prec(prec);
     need(r_supported(r), "r must be 1, 2, 4, 8, 16, 24 or 32");
     if (with_D) ensure_sdd(ctx, T);
-    copy_d(ctx, X, B, T->g.n * r * esize(prec));
+    if (X != B) copy_d(ctx, X, B, T->g.n * r * esize(prec));
     clear_timeout(ctx);
     tree_solve_inplace(ctx, T, with_D ? T->sdd : T->lap, r, prec, X, nullptr);
     check_timeout(ctx);

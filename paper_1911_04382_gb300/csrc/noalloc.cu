@@ -9,34 +9,66 @@
 // device.  grass_tree_solve_noalloc gives them the same solve with its
 // scratch in the file-scope array below: 256 bytes that every GPU which loads
 // this library holds until the process exits, whatever the tree's size.
+#include <cuda.h>
+
 #include <mutex>
+#include <utility>
+#include <vector>
 
 #include "tree_solve.cuh"
 
 namespace grass {
 namespace {
 
-// [0] barrier arrival counter, [2] barrier hold flag (always 0 here),
-// [8] wait-timeout flag; the rest is unused.  One array per device, shared
-// by every call on that device.
+// [0] barrier arrival counter, [2] barrier hold flag (the context's
+// setting, copied in by every call), [8] wait-timeout flag; the rest is
+// unused.  One array per device, shared by every call on that device.
 constexpr int kNoallocWords = 64;
 static __device__ __align__(256) unsigned int g_noalloc_scratch[kNoallocWords];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_addr_mu;
-unsigned int *g_addr[kMaxDevices] = {nullptr};
+// The array's device address, looked up once per CUDA context (that is, per
+// device, and again if the application resets the device and the module is
+// loaded into a new context).  Contexts are told apart by their driver id,
+// which is never reused within a process; the two driver calls are taken
+// through the runtime's entry-point query, so the library needs no link
+// against the driver library.
+using CtxGetCurrentFn = CUresult (*)(CUcontext *);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long *);
 
-// Device address of the array on device `dev`, looked up on the first call
-// there (that device must be current).
-unsigned int *scratch_address(int dev) {
-    if (dev < 0 || dev >= kMaxDevices) fail(GRASS_ERR_INVALID, "device ordinal out of range");
-    std::lock_guard<std::mutex> lock(g_addr_mu);
-    if (!g_addr[dev]) {
-        void *p = nullptr;
-        GCK(cudaGetSymbolAddress(&p, g_noalloc_scratch));
-        g_addr[dev] = static_cast<unsigned int *>(p);
+std::mutex g_addr_mu;
+std::vector<std::pair<unsigned long long, unsigned int *>> g_addr;   // (context id, address)
+CtxGetCurrentFn g_get_current = nullptr;
+CtxGetIdFn g_get_id = nullptr;
+
+unsigned long long current_context_id() {
+    if (!g_get_current || !g_get_id) {
+        void *f1 = nullptr, *f2 = nullptr;
+        cudaDriverEntryPointQueryResult q1, q2;
+        GCK(cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1));
+        GCK(cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2));
+        if (q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2)
+            fail(GRASS_ERR_CUDA, "driver entry points cuCtxGetCurrent / cuCtxGetId not found");
+        g_get_current = reinterpret_cast<CtxGetCurrentFn>(f1);
+        g_get_id = reinterpret_cast<CtxGetIdFn>(f2);
     }
-    return g_addr[dev];
+    CUcontext c = nullptr;
+    unsigned long long id = 0;
+    if (g_get_current(&c) != CUDA_SUCCESS || !c || g_get_id(c, &id) != CUDA_SUCCESS)
+        fail(GRASS_ERR_CUDA, "no current CUDA context");
+    return id;
+}
+
+// Device address of the array in the current context (the caller has made
+// the context's device current).
+unsigned int *scratch_address() {
+    std::lock_guard<std::mutex> lock(g_addr_mu);
+    const unsigned long long id = current_context_id();
+    for (const auto &e : g_addr)
+        if (e.first == id) return e.second;
+    void *p = nullptr;
+    GCK(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    g_addr.emplace_back(id, static_cast<unsigned int *>(p));
+    return g_addr.back().second;
 }
 
 template <typename T, int R>
@@ -106,12 +138,15 @@ extern "C" grass_status grass_tree_solve_noalloc(grass_ctx_t ctx, grass_tree_t T
         reject(ctx->num_sms > 0, "the device cannot launch cooperative kernels");
         reject(!with_D || T->has_sdd,
                "the L_T + D factor is not built; one grass_tree_solve call with with_D=1 builds it");
-        unsigned int *scratch = scratch_address(ctx->device);
+        unsigned int *scratch = scratch_address();
         const size_t bytes = (size_t)T->g.n * r * (prec == GRASS_FP64 ? 8 : 4);
         if (B != X)
             GCK(cudaMemcpyAsync(X, B, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
-        // the array keeps the previous call's counter and flag: start both at zero
+        // the array keeps the previous call's counter and flag: start both at
+        // zero; the hold flag follows grass_ctx_set_wait_limit on ctx
         GCK(cudaMemsetAsync(scratch, 0, kNoallocWords * sizeof(unsigned int), ctx->stream));
+        GCK(cudaMemcpyAsync(scratch + 2, ctx->gbar.p + 2, sizeof(unsigned int),
+                            cudaMemcpyDeviceToDevice, ctx->stream));
         NoallocCall c{ctx, T, with_D ? &T->sdd : &T->lap, X, prec, scratch};
         GRASS_DISPATCH_R(r, noalloc_R, c);
         int timed_out = 0;

@@ -235,6 +235,21 @@ def _near_threshold(hv, thr):
     return np.abs(hv - thr) <= 1e-9 * thr
 
 
+def _near_decision(trace, e):
+    """Edge e sat within 1e-9 (relative) of the threshold, or of the cap's
+    boundary heat, in some round of the oracle's densification."""
+    for rd in trace:
+        i = np.searchsorted(rd["off"], e)
+        if i >= rd["off"].shape[0] or rd["off"][i] != e:
+            continue
+        h = rd["heat"][i]
+        if _near_threshold(h, rd["thr"]):
+            return True
+        if rd["cap_heat"] is not None and _near_threshold(h, rd["cap_heat"]):
+            return True
+    return False
+
+
 @pytest.mark.parametrize("cap", [0, 100, 1])
 def test_filter_matches_oracle(gpu, cap):
     import torch
@@ -290,7 +305,8 @@ def _densify_parity(gpu, g, sigma2, r, t, rounds, cap, inner_tol=1e-13, inner_ma
     ot = oracle.build_tree(og)
     h0s = [rng.gaussian_block(9, rng.STREAM_H0 + k, g.n, r) for k in range(rounds)]
     v0s = [rng.normal(9, rng.STREAM_V0 + k, g.n) for k in range(rounds)]
-    res = oracle.densify(og, ot, h0s, v0s, sigma2, t, rounds, 8, cap, inner_tol, inner_maxit)
+    res = oracle.densify(og, ot, h0s, v0s, sigma2, t, rounds, 8, cap, inner_tol, inner_maxit,
+                         record=True)
     import torch
     with gpu_graph(g) as (ctx, tree, _):
         P = gpu.make_params(sigma2, r, t, rounds, 8, cap, gpu.GRASS_FP64, inner_tol, inner_maxit)
@@ -305,8 +321,11 @@ def _densify_parity(gpu, g, sigma2, r, t, rounds, cap, inner_tol=1e-13, inner_ma
                 assert d["lmax_est"][k] == pytest.approx(res.lmax[k], rel=1e-8)
                 assert d["lmin_est"][k] == pytest.approx(res.lmin[k], rel=1e-13)
             diff = np.flatnonzero(got != res.in_s)
-            # only edges within rounding of the threshold may differ
-            assert diff.shape[0] <= max(2, 1e-4 * og.m), diff.shape
+            # several results are correct only for edges within rounding of a
+            # decision: the threshold theta * heat_max of some round, or the
+            # heat of the last edge a cap kept (a near tie in heat rank)
+            for e in diff:
+                assert _near_decision(res.trace, int(e)), (int(e), diff.shape)
             return d, res
         finally:
             gpu.grass_sparsifier_destroy(S)

@@ -72,3 +72,45 @@ def test_noalloc_rejects_what_it_cannot_serve(gpu):
         gpu.grass_tree_solve_noalloc(ctx, tree, 0, 4, gpu.GRASS_FP64, B, X)
         ref = host(X_ref)
         assert np.abs(host(X) - ref).max() <= SOLVE_TOL * np.abs(ref).max()
+
+
+def test_noalloc_leaves_device_memory_unchanged(gpu):
+    """Once the kernels are loaded (the first call) and the L_T + D factor
+    exists, further calls take no device memory: the free memory the driver
+    reports is the same before and after them."""
+    import torch
+    g = graphs.grid3d_loguniform(40, 40, 40, seed=6)
+    with gpu_graph(g) as (ctx, tree, _):
+        B = dev(rng.gaussian_block(60, 1, g.n, 8))
+        X = torch.empty_like(B)
+        gpu.grass_tree_solve(ctx, tree, 1, 8, gpu.GRASS_FP64, B, X)      # builds L_T + D
+        for with_D in (0, 1):
+            gpu.grass_tree_solve_noalloc(ctx, tree, with_D, 8, gpu.GRASS_FP64, B, X)   # warm
+        torch.cuda.synchronize()
+        free0, _ = torch.cuda.mem_get_info()
+        for with_D in (0, 1, 0, 1):
+            gpu.grass_tree_solve_noalloc(ctx, tree, with_D, 8, gpu.GRASS_FP64, B, X)
+        torch.cuda.synchronize()
+        free1, _ = torch.cuda.mem_get_info()
+        assert free1 == free0
+
+
+def test_noalloc_bounded_wait_runs_out_and_recovers(gpu):
+    """The barrier waits of the no-allocation solve are bounded like those of
+    grass_tree_solve: with the context's test hold on, every wait runs out,
+    the call returns GRASS_ERR_TIMEOUT, and the next normal call is right."""
+    import torch
+    g = graphs.grid2d_uniform(120, 100, seed=5)
+    with gpu_graph(g) as (ctx, tree, _):
+        B = dev(rng.gaussian_block(61, 1, g.n, 4))
+        X_ref = torch.empty_like(B)
+        gpu.grass_tree_solve(ctx, tree, 0, 4, gpu.GRASS_FP64, B, X_ref)
+        X = torch.empty_like(B)
+        gpu.grass_ctx_set_wait_limit(ctx, 2000, 1)
+        with pytest.raises(gpu.GrassError) as e:
+            gpu.grass_tree_solve_noalloc(ctx, tree, 0, 4, gpu.GRASS_FP64, B, X)
+        assert e.value.status == gpu.GRASS_ERR_TIMEOUT
+        gpu.grass_ctx_set_wait_limit(ctx, 0, 0)
+        gpu.grass_tree_solve_noalloc(ctx, tree, 0, 4, gpu.GRASS_FP64, B, X)
+        ref = host(X_ref)
+        assert np.abs(host(X) - ref).max() <= SOLVE_TOL * np.abs(ref).max()
