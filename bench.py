@@ -56,7 +56,7 @@ WORKLOADS = {
                       pcg_inner_maxit=1, pcg_maxit=4000),
 }
 
-FAMILIES = {"spmm_g": 1, "spmm_s": 2, "heat": 3, "tree": 4, "cg": 5, "pcg": 6}
+FAMILIES = {"spmm_g": 1, "spmm_s": 2, "heat": 3, "tree": 4, "cg": 5, "pcg": 6, "spmm_blk": 7}
 
 
 def make_inputs(w: dict):

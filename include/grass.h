@@ -151,6 +151,9 @@ grass_status grass_ctx_set_wait_limit(grass_ctx_t ctx, int64_t polls, int hold_b
  *                         the inner CG and the power steps, whose vectors
  *                         are then kept in preorder); 0: the elimination
  *                         rounds
+ *   "similarity_check"    0 (default) or 1: grass_densify filters each
+ *                         round's edges with the similarity check of
+ *                         grass_filter_similar (Sec. IV-D step 6)
  *   "euler_max_n"         trees built on this context with more vertices
  *                         than this (default 4,000,000) get no Euler tour
  *                         and keep the elimination rounds (the tour's FP64
@@ -165,6 +168,8 @@ grass_status grass_ctx_set_param(grass_ctx_t ctx, const char *name, int64_t valu
  * algorithmic bytes the launch must move (each array counted once per
  * phase that touches it):
  *   GRASS_KF_SPMM_G  Y = L_G X:  4(n+1) + 2m(4+s) + 2nrs
+ *   GRASS_KF_SPMM_BLK  the launches of GRASS_KF_SPMM_G with r > 1 columns
+ *                    (the embedding's power steps), same bytes
  *   GRASS_KF_SPMM_S  the same over the sparsifier's adjacency (+ns with D)
  *   GRASS_KF_HEAT    m_off(8+s) + nrs + m_off s
  *   GRASS_KF_TREE    one whole tree solve:
@@ -191,7 +196,8 @@ typedef enum {
     GRASS_KF_HEAT = 3,
     GRASS_KF_TREE = 4,
     GRASS_KF_CG = 5,
-    GRASS_KF_PCG = 6
+    GRASS_KF_PCG = 6,
+    GRASS_KF_SPMM_BLK = 7
 } grass_kernel_family;
 grass_status grass_kernel_timing_enable(grass_ctx_t ctx, int family);
 grass_status grass_kernel_timing_read(grass_ctx_t ctx, double *ms, int64_t *launches, double *bytes);
@@ -210,6 +216,17 @@ grass_status grass_kernel_timing_read(grass_ctx_t ctx, double *ms, int64_t *laun
 grass_status grass_build_tree(grass_ctx_t ctx, const grass_csr_t *A, int32_t ground,
                               grass_tree_t *out);
 void grass_tree_destroy(grass_tree_t tree);
+
+/* The same as grass_build_tree with the caller's spanning tree in place of
+ * the maximum-weight one: tree_eids (device, n-1 edge ids in any order) are
+ * the tree's edges, e.g. the "hair-comb" tree of a 2D mesh (Sec. V-C) or a
+ * low-stretch tree (Sec. III-B).  The ids are checked to lie in [0, m), to
+ * be distinct and to form a spanning tree (no cycle); the graph must be
+ * connected.  Everything after the tree (schedule, factors, sparsifiers,
+ * solves) is as for grass_build_tree.  Errors: INVALID (bad CSR, ids out of
+ * range, repeated, or containing a cycle), NOT_SDD, DISCONNECTED, OOM, CUDA. */
+grass_status grass_tree_from_edges(grass_ctx_t ctx, const grass_csr_t *A, const int64_t *tree_eids,
+                                   int32_t ground, grass_tree_t *out);
 
 /* Sizes: n, m (edges), factor_rounds (contraction rounds of the tree
  * elimination schedule).  Any pointer may be NULL.  Host outputs. */
@@ -281,6 +298,14 @@ grass_status grass_sparsifier_add(grass_ctx_t ctx, grass_sparsifier_t S, const i
 grass_status grass_sparsifier_info(grass_sparsifier_t S, int64_t *n_edges, int64_t *m_off);
 /* in_s[e] = 1 if edge e is in S (device, m bytes). */
 grass_status grass_sparsifier_mask(grass_ctx_t ctx, grass_sparsifier_t S, uint8_t *in_s);
+/* Host export of the sparsifier's edge set (Sec. IV-D: the sparsifier that
+ * densification returns, the preconditioner of Sec. V-A): the ids of the
+ * edges in S in increasing order.  eids_host: host, room for cap ids (may be
+ * NULL when cap = 0); the first min(cap, count) ids are written.  *count
+ * (host) = the number of edges in S.  Uses S's context and stream;
+ * synchronises.  Errors: INVALID (null S or count, cap < 0), CUDA. */
+grass_status grass_sparsifier_edges(grass_sparsifier_t S, int64_t *eids_host, int64_t cap,
+                                    int64_t *count);
 /* Ids of the edges outside S, increasing (device, m_off entries): the order
  * of the heat array of grass_embed. */
 grass_status grass_sparsifier_offtree(grass_ctx_t ctx, grass_sparsifier_t S, int64_t *eids);
@@ -324,13 +349,28 @@ grass_status grass_filter(grass_ctx_t ctx, grass_sparsifier_t S, const void *hea
                           double sigma2, double lmin, double lmax, int t, int64_t cap,
                           int64_t *accepted, int64_t *n_accepted, double *theta);
 
+/* Edge filter with the similarity check of Sec. IV-D step 6 ("only add
+ * dissimilar edges"), which the paper leaves undefined; read here as an
+ * endpoint conflict: of the off-S edges grass_filter would keep without a
+ * cap (heat >= theta * max(heat)), take them in order of heat descending,
+ * smaller id first among equal heats, and reject every edge with an
+ * endpoint on an edge kept before it; then cap > 0 keeps the first cap of
+ * the kept ones in that order.  The kept edges form a matching.  Arguments,
+ * outputs and errors as grass_filter.  grass_densify applies the same check
+ * after grass_ctx_set_param(ctx, "similarity_check", 1). */
+grass_status grass_filter_similar(grass_ctx_t ctx, grass_sparsifier_t S, const void *heat,
+                                  grass_prec prec, double sigma2, double lmin, double lmax, int t,
+                                  int64_t cap, int64_t *accepted, int64_t *n_accepted,
+                                  double *theta);
+
 /* ---------------------------------------------------------------- densify / solve */
 
 /* Iterative densification (Sec. IV-D).  Per round k < max_rounds:
  * (2) lambda estimates on the current S, (3) stop if lmax/lmin <= sigma2,
  * (4) embed with h0 + k*n*r (device, max_rounds*n*r doubles) and the
  * lambda_max start v0 + k*n (device, max_rounds*n doubles), (5) filter,
- * add the kept edges.  The paper's step (6) similarity check is not applied.
+ * add the kept edges.  The paper's step (6) similarity check is applied when
+ * the context's "similarity_check" parameter is 1 (grass_filter_similar).
  * out: a new sparsifier (tree + added edges).  stats: host, optional. */
 grass_status grass_densify(grass_ctx_t ctx, grass_tree_t tree, const grass_params_t *params,
                            const double *h0, const double *v0, grass_sparsifier_t *out,

@@ -368,13 +368,44 @@ def filter_edges(heat_vals: np.ndarray, off_eids: np.ndarray, theta: float, cap:
     return off_eids[keep].astype(np.int64)
 
 
+def similarity_check(og: OGraph, heat_vals: np.ndarray, off_eids: np.ndarray, theta: float,
+                     cap: int = 0) -> np.ndarray:
+    """Section IV-D step 6, "only add dissimilar edges", read as endpoint
+    conflicts (the paper does not define similarity): the edges that pass
+    the threshold theta * heat_max are visited in order of heat descending,
+    smaller edge id first among equal heats; an edge is kept unless one of
+    its endpoints is an endpoint of an edge kept before it; with cap > 0 the
+    visit stops after cap kept edges.  Returns the kept ids in increasing
+    order."""
+    if heat_vals.shape[0] == 0:
+        return np.zeros(0, np.int64)
+    thr = theta * float(np.max(heat_vals))
+    sel = np.flatnonzero(heat_vals >= thr)
+    order = sel[np.lexsort((off_eids[sel], -heat_vals[sel]))]
+    used = set()
+    kept = []
+    for i in order:
+        e = int(off_eids[i])
+        a, b = int(og.eu[e]), int(og.ev[e])
+        if a in used or b in used:
+            continue
+        used.add(a)
+        used.add(b)
+        kept.append(e)
+        if cap > 0 and len(kept) == cap:
+            break
+    return np.array(sorted(kept), dtype=np.int64)
+
+
 def densify(og: OGraph, tree: OTree, h0s, v0s, sigma2: float, t: int, max_rounds: int,
             lmax_iters: int = 8, cap: int = 0, inner_tol: float = 1e-12,
-            inner_maxit: int = 1000, record: bool = False) -> DensifyResult:
+            inner_maxit: int = 1000, record: bool = False,
+            similarity: bool = False) -> DensifyResult:
     """Section IV-D: per round, (1) S updated, (2) lambda estimates,
     (3) stop when lmax/lmin <= sigma^2, (4) t-step power iteration with the
-    round's r start vectors, (5) filter by theta_sigma, add the kept edges.
-    Step (6)'s similarity check is not applied (the paper leaves it undefined)."""
+    round's r start vectors, (5) filter by theta_sigma, (6) with
+    similarity=True keep only the edges similarity_check keeps (the paper
+    leaves step 6 undefined; off by default), add the kept edges."""
     in_s = tree.in_tree.copy()
     res = DensifyResult(in_s)
     for rd in range(max_rounds):
@@ -389,7 +420,10 @@ def densify(og: OGraph, tree: OTree, h0s, v0s, sigma2: float, t: int, max_rounds
         hv, off = heat(og, in_s, H)
         th = theta_sigma(sigma2, lmin, lmax, t)
         res.theta.append(th)
-        acc = filter_edges(hv, off, th, cap)
+        if similarity:
+            acc = similarity_check(og, hv, off, th, cap)
+        else:
+            acc = filter_edges(hv, off, th, cap)
         if record:
             thr = th * float(np.max(hv)) if hv.shape[0] else 0.0
             kth = None

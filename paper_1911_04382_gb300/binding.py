@@ -124,6 +124,8 @@ def lib():
                                              C.POINTER(_i64), _i64],
                 "grass_kernel_timing_read": [_vp, C.POINTER(_d), C.POINTER(_i64), C.POINTER(_d)],
                 "grass_build_tree": [_vp, C.POINTER(grass_csr_t), _i32, C.POINTER(_vp)],
+                "grass_tree_from_edges": [_vp, C.POINTER(grass_csr_t), _vp, _i32, C.POINTER(_vp)],
+                "grass_sparsifier_edges": [_vp, C.POINTER(_i64), _i64, C.POINTER(_i64)],
                 "grass_tree_info": [_vp, C.POINTER(_i64), C.POINTER(_i64), C.POINTER(_i64)],
                 "grass_tree_graph": [_vp, _vp, _vp, _vp, _vp, _vp],
                 "grass_tree_edges": [_vp, _vp, _vp],
@@ -141,6 +143,8 @@ def lib():
                 "grass_lambda_max": [_vp, _vp, _vp, C.c_int, C.c_int, _d, C.c_int, C.POINTER(_d)],
                 "grass_filter": [_vp, _vp, _vp, C.c_int, _d, _d, _d, C.c_int, _i64, _vp,
                                  C.POINTER(_i64), C.POINTER(_d)],
+                "grass_filter_similar": [_vp, _vp, _vp, C.c_int, _d, _d, _d, C.c_int, _i64, _vp,
+                                         C.POINTER(_i64), C.POINTER(_d)],
                 "grass_densify": [_vp, _vp, C.POINTER(grass_params_t), _vp, _vp, C.POINTER(_vp),
                                   C.POINTER(grass_sparsify_stats_t)],
                 "grass_pcg_solve": [_vp, _vp, _vp, _vp, _d, C.c_int, C.c_int, _d, _d, C.c_int,
@@ -251,7 +255,7 @@ def grass_ctx_set_wait_limit(ctx: int, polls: int = 0, hold_barriers: int = 0) -
 
 
 GRASS_KF_NONE, GRASS_KF_SPMM_G, GRASS_KF_SPMM_S, GRASS_KF_HEAT, GRASS_KF_TREE, GRASS_KF_CG = 0, 1, 2, 3, 4, 5
-GRASS_KF_PCG = 6
+GRASS_KF_PCG, GRASS_KF_SPMM_BLK = 6, 7
 
 
 def grass_kernel_timing_enable(ctx: int, family: int) -> None:
@@ -278,6 +282,19 @@ def grass_build_tree(ctx: int, rowptr, col, val, ground: int = 0, n: int | None 
     out = _vp()
     _check(ctx, lib().grass_build_tree(ctx, C.byref(A), int(ground), C.byref(out)),
            "grass_build_tree")
+    return out.value
+
+
+def grass_tree_from_edges(ctx: int, rowptr, col, val, tree_eids, ground: int = 0) -> int:
+    """grass_build_tree with the caller's spanning tree: tree_eids (device
+    int64, n-1 edge ids)."""
+    A = grass_csr_t()
+    A.n = int(rowptr.numel() - 1)
+    A.nnz = int(col.numel())
+    A.rowptr, A.col, A.val = _p(rowptr), _p(col), _p(val)
+    out = _vp()
+    _check(ctx, lib().grass_tree_from_edges(ctx, C.byref(A), _p(tree_eids), int(ground),
+                                            C.byref(out)), "grass_tree_from_edges")
     return out.value
 
 
@@ -342,6 +359,20 @@ def grass_sparsifier_mask(ctx, S, in_s) -> None:
     _check(ctx, lib().grass_sparsifier_mask(ctx, S, _p(in_s)), "grass_sparsifier_mask")
 
 
+def grass_sparsifier_edges(S, cap: int | None = None):
+    """Host export: (ids of the edges in S in increasing order as a numpy
+    int64 array of min(cap, count) entries, count).  cap None: all."""
+    import numpy as np
+    if cap is None:
+        ne, _ = grass_sparsifier_info(S)
+        cap = ne
+    out = np.empty(max(int(cap), 1), dtype=np.int64)
+    cnt = _i64(0)
+    _check(None, lib().grass_sparsifier_edges(S, out.ctypes.data_as(C.POINTER(_i64)), int(cap),
+                                              C.byref(cnt)), "grass_sparsifier_edges")
+    return out[:min(int(cap), cnt.value)].copy(), cnt.value
+
+
 def grass_sparsifier_offtree(ctx, S, eids) -> None:
     _check(ctx, lib().grass_sparsifier_offtree(ctx, S, _p(eids)), "grass_sparsifier_offtree")
 
@@ -375,6 +406,15 @@ def grass_filter(ctx, S, heat, prec: int, sigma2: float, lmin: float, lmax: floa
     na, th = _i64(0), _d(0.0)
     _check(ctx, lib().grass_filter(ctx, S, _p(heat), prec, sigma2, lmin, lmax, t, int(cap),
                                    _p(accepted), C.byref(na), C.byref(th)), "grass_filter")
+    return na.value, th.value
+
+
+def grass_filter_similar(ctx, S, heat, prec: int, sigma2: float, lmin: float, lmax: float,
+                         t: int, cap: int, accepted) -> tuple[int, float]:
+    na, th = _i64(0), _d(0.0)
+    _check(ctx, lib().grass_filter_similar(ctx, S, _p(heat), prec, sigma2, lmin, lmax, t, int(cap),
+                                           _p(accepted), C.byref(na), C.byref(th)),
+           "grass_filter_similar")
     return na.value, th.value
 
 

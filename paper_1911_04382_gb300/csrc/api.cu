@@ -175,10 +175,86 @@ __global__ void k_mark_roots(int64_t nroots, const int32_t *roots, uint8_t *isro
     if (q < nroots) isroot[roots[q]] = 1;
 }
 
+// ---------------------------------------------------------------- a caller's tree
+
+__global__ void k_user_mark(int64_t cnt, const int64_t *eids, int64_t m, uint8_t *in_tree,
+                            int *bad) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= cnt) return;
+    const int64_t e = eids[i];
+    if (e < 0 || e >= m) {
+        atomicOr(bad, 1);
+        return;
+    }
+    in_tree[e] = 1;
+}
+
+// w[e] = 2 for the caller's edges, 1 for the others: the maximum spanning
+// tree under these weights contains every caller edge unless they close a
+// cycle
+__global__ void k_indicator_w(int64_t m, const uint8_t *mark, double *w) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < m) w[e] = mark[e] ? 2.0 : 1.0;
+}
+
+// counts[0] += #{e : a[e] != 0}, counts[1] += #{e : a[e] != b[e]}
+__global__ void k_mask_counts(int64_t m, const uint8_t *a, const uint8_t *b,
+                              unsigned long long *counts) {
+    unsigned long long ones = 0, diff = 0;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        ones += a[e] != 0;
+        diff += (a[e] != 0) != (b[e] != 0);
+    }
+    for (int d = 16; d > 0; d >>= 1) {
+        ones += __shfl_xor_sync(0xffffffffu, ones, d);
+        diff += __shfl_xor_sync(0xffffffffu, diff, d);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (ones) atomicAdd(counts, ones);
+        if (diff) atomicAdd(counts + 1, diff);
+    }
+}
+
+// in_tree = the caller's n-1 edge ids, after checking that they are a
+// spanning tree of the graph: ids in range and distinct, and equal to the
+// maximum spanning tree under weights that prefer them (which holds iff
+// they contain no cycle; n-1 acyclic edges of a connected graph span it).
+void user_tree(grass_ctx_t ctx, const GraphData &g, const int64_t *eids, uint8_t *in_tree) {
+    const int64_t n = g.n, m = g.m;
+    memset_d(ctx, in_tree, 0, (size_t)m);
+    memset_d(ctx, ctx->flags.p, 0, sizeof(int));
+    launch(ctx, k_user_mark, cdiv(n - 1, kBlock), kBlock, 0, n - 1, eids, m, in_tree,
+           ctx->flags.p);
+    int bad = 0;
+    d2h(ctx, &bad, ctx->flags.p, sizeof(int));
+    if (bad) fail(GRASS_ERR_INVALID, "tree edge id out of range");
+    DBuf<double> w;
+    w.alloc(m);
+    DBuf<uint8_t> chk;
+    chk.alloc(m);
+    DBuf<unsigned long long> cnt;
+    cnt.alloc(2);
+    launch(ctx, k_indicator_w, cdiv(m, kBlock), kBlock, 0, m, (const uint8_t *)in_tree, w.p);
+    mst_boruvka_w(ctx, g, w.p, chk.p);
+    memset_d(ctx, cnt.p, 0, 2 * sizeof(unsigned long long));
+    launch(ctx, k_mask_counts, std::min<int64_t>(kRedBlocks, std::max<int64_t>(1, cdiv(m, kBlock))),
+           kBlock, 0, m, (const uint8_t *)in_tree, (const uint8_t *)chk.p, cnt.p);
+    unsigned long long c[2] = {0, 0};
+    d2h(ctx, c, cnt.p, sizeof(c));
+    if ((int64_t)c[0] != n - 1)
+        fail(GRASS_ERR_INVALID, "tree edge ids are not distinct (" + std::to_string(c[0]) +
+                                    " distinct edges for n - 1 = " + std::to_string(n - 1) + ")");
+    if (c[1] != 0) fail(GRASS_ERR_INVALID, "the tree edges contain a cycle (they do not span the graph)");
+}
+
 // Spanning tree (one root) or spanning forest of a batch (one root per graph,
 // the graph's first vertex), its elimination schedule and the L_T factor.
+// user_eids (device, n-1 edge ids) replaces the maximum spanning tree by the
+// caller's tree (single graph only).
 grass_tree_t build_tree_impl(grass_ctx_t ctx, const grass_csr_t *A,
-                             const std::vector<int64_t> &voff, const std::vector<int32_t> &roots) {
+                             const std::vector<int64_t> &voff, const std::vector<int32_t> &roots,
+                             const int64_t *user_eids = nullptr) {
     auto *T = new grass_tree_s();
     T->ctx = ctx;
     T->nroots = (int64_t)roots.size();
@@ -196,7 +272,8 @@ grass_tree_t build_tree_impl(grass_ctx_t ctx, const grass_csr_t *A,
         launch(ctx, k_mark_roots, cdiv(T->nroots, kBlock), kBlock, 0, T->nroots,
                (const int32_t *)T->roots.p, T->isroot.p);
         T->in_tree.alloc(T->g.m);
-        mst_boruvka(ctx, T->g, T->in_tree.p);
+        if (user_eids) user_tree(ctx, T->g, user_eids, T->in_tree.p);
+        else mst_boruvka(ctx, T->g, T->in_tree.p);
         tree_schedule(ctx, T);
         tree_factor(ctx, T, false, T->lap);
         ctx->sync();
@@ -300,6 +377,9 @@ grass_status grass_ctx_set_param(grass_ctx_t ctx, const char *name, int64_t valu
     } else if (k == "euler_solve") {
         need(value == 0 || value == 1, "euler_solve must be 0 or 1");
         ctx->euler_solve = (int)value;
+    } else if (k == "similarity_check") {
+        need(value == 0 || value == 1, "similarity_check must be 0 or 1");
+        ctx->similarity_check = (int)value;
     } else if (k == "euler_max_n") {
         need(value >= 0, "euler_max_n must be >= 0");
         ctx->euler_max_n = value;
@@ -335,7 +415,7 @@ grass_status grass_tree_schedule_info(grass_tree_t T, int64_t *eliminated, int64
 grass_status grass_kernel_timing_enable(grass_ctx_t ctx, int family) {
     if (!ctx) return GRASS_ERR_INVALID;
     API_BEGIN(ctx)
-    need(family >= GRASS_KF_NONE && family <= GRASS_KF_PCG, "unknown kernel family");
+    need(family >= GRASS_KF_NONE && family <= GRASS_KF_SPMM_BLK, "unknown kernel family");
     ctx->sync();
     ctx->tfam = family;
     ctx->ev_used = 0;
@@ -379,6 +459,17 @@ grass_status grass_build_tree(grass_ctx_t ctx, const grass_csr_t *A, int32_t gro
     *out = nullptr;
     need(ground >= 0 && ground < A->n, "ground must be in [0, n)");
     *out = build_tree_impl(ctx, A, {0, A->n}, {ground});
+    API_END
+}
+
+grass_status grass_tree_from_edges(grass_ctx_t ctx, const grass_csr_t *A, const int64_t *tree_eids,
+                                   int32_t ground, grass_tree_t *out) {
+    if (!ctx) return GRASS_ERR_INVALID;
+    API_BEGIN(ctx)
+    need(A && out && tree_eids, "null argument");
+    *out = nullptr;
+    need(ground >= 0 && ground < A->n, "ground must be in [0, n)");
+    *out = build_tree_impl(ctx, A, {0, A->n}, {ground}, tree_eids);
     API_END
 }
 
@@ -523,6 +614,37 @@ __global__ void k_i32_to_i64(int64_t n, const int32_t *a, int64_t *b) {
     if (i < n) b[i] = a[i];
 }
 
+__global__ void k_s_flag(int64_t m, const uint8_t *in_s, int64_t *flag) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < m) flag[e] = in_s[e] ? 1 : 0;
+}
+
+__global__ void k_s_ids(int64_t m, const uint8_t *in_s, const int64_t *pos, int64_t *ids) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < m && in_s[e]) ids[pos[e]] = e;
+}
+
+grass_status grass_sparsifier_edges(grass_sparsifier_t S, int64_t *eids_host, int64_t cap,
+                                    int64_t *count) {
+    if (!S || !count || cap < 0 || (cap > 0 && !eids_host)) return GRASS_ERR_INVALID;
+    grass_ctx_t ctx = S->ctx;
+    API_BEGIN(ctx)
+    const int64_t m = S->tree->g.m;
+    int64_t *flag = ctx->scr<int64_t>(SCR_TMP0, m + 1);
+    int64_t *pos = ctx->scr<int64_t>(SCR_TMP1, m + 1);
+    int64_t *ids = ctx->scr<int64_t>(SCR_TMP2, m + 1);
+    launch(ctx, k_s_flag, cdiv(m, kBlock), kBlock, 0, m, (const uint8_t *)S->in_s.p, flag);
+    int64_t ns = 0;
+    scan_i64(ctx, flag, pos, m, &ns);
+    launch(ctx, k_s_ids, cdiv(m, kBlock), kBlock, 0, m, (const uint8_t *)S->in_s.p,
+           (const int64_t *)pos, ids);
+    const int64_t k = std::min(cap, ns);
+    if (k > 0) d2h(ctx, eids_host, ids, (size_t)k * sizeof(int64_t));
+    ctx->sync();
+    *count = ns;
+    API_END
+}
+
 grass_status grass_sparsifier_offtree(grass_ctx_t ctx, grass_sparsifier_t S, int64_t *eids) {
     if (!ctx || !S) return GRASS_ERR_INVALID;
     API_BEGIN(ctx)
@@ -602,6 +724,32 @@ grass_status grass_filter(grass_ctx_t ctx, grass_sparsifier_t S, const void *hea
     API_END
 }
 
+grass_status grass_filter_similar(grass_ctx_t ctx, grass_sparsifier_t S, const void *heat,
+                                  grass_prec prec, double sigma2, double lmin, double lmax, int t,
+                                  int64_t cap, int64_t *accepted, int64_t *n_accepted,
+                                  double *theta) {
+    if (!ctx || !S || !n_accepted) return GRASS_ERR_INVALID;
+    API_BEGIN(ctx)
+    need(S->tree->g.nseg == 1, "a batch of graphs: use grass_densify_batch");
+    need(heat || S->m_off == 0, "null heat");
+    need(accepted || S->m_off == 0, "null output");
+    need_prec(prec);
+    need(sigma2 > 0 && lmin > 0 && lmax > 0 && t >= 1, "sigma2, lmin, lmax must be > 0, t >= 1");
+    double th = theta_sigma(sigma2, lmin, lmax, t);
+    if (theta) *theta = th;
+    *n_accepted = 0;
+    if (S->m_off > 0) {
+        unsigned long long *hm = maxslot(ctx, 3);
+        memset_d(ctx, hm, 0, sizeof(unsigned long long));
+        max_abs_bits(ctx, prec, S->m_off, heat, hm);
+        unsigned long long b = 0;
+        d2h(ctx, &b, hm, sizeof(b));
+        *n_accepted = filter_similar(ctx, S, heat, prec, th * bits_to_double(b), cap, accepted);
+        ctx->sync();
+    }
+    API_END
+}
+
 // ---------------------------------------------------------------- densify / solve
 
 grass_status grass_densify(grass_ctx_t ctx, grass_tree_t T, const grass_params_t *P,
@@ -658,8 +806,11 @@ grass_status grass_densify(grass_ctx_t ctx, grass_tree_t T, const grass_params_t
             st.heat_max[k] = eo.heat_max;
             st.embedded_round[k] = moff;
             st.offtree_embedded += moff;
-            int64_t na = filter_heat(ctx, S, heat, P->embed_prec, th * eo.heat_max,
-                                     P->max_add_per_round, acc);
+            int64_t na = ctx->similarity_check
+                             ? filter_similar(ctx, S, heat, P->embed_prec, th * eo.heat_max,
+                                              P->max_add_per_round, acc)
+                             : filter_heat(ctx, S, heat, P->embed_prec, th * eo.heat_max,
+                                           P->max_add_per_round, acc);
             double td = now_ms();
             st.ms_filter += td - tc;
             st.rounds = k + 1;

@@ -9,53 +9,146 @@ __device__ inline double scale_of(const unsigned long long *scale_from) {
     return scale_from ? pow2_scale_from_bits(*scale_from) : 1.0;
 }
 
-// Y = s * (L X + D .* X), (L X)_i = sum_j w_ij (X_i - X_j) (Eq. formula_laplacian).
-template <typename T, int R>
-__global__ void k_lapmm(int64_t n, const int32_t *__restrict__ ptr, const int32_t *__restrict__ col,
-                        const T *__restrict__ w, const T *__restrict__ D, const T *__restrict__ X,
-                        T *__restrict__ Y, const unsigned long long *scale_from) {
-    constexpr int TPR = Lay<R>::TPR, EPT = Lay<R>::EPT;
-    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int64_t i = t / TPR;
-    if (i >= n) return;
-    int c = (int)(t % TPR);
-    const T s = (T)scale_of(scale_from);
-    const T *xi = X + i * R + c * EPT;
-    T x0[EPT], acc[EPT];
-#pragma unroll
-    for (int e = 0; e < EPT; ++e) {
-        x0[e] = xi[e];
-        acc[e] = (T)0;
+// ---------------------------------------------------------------- row chunks
+// The r values of a vertex are one contiguous row of r*sizeof(T) bytes.
+// When that is a multiple of 16 bytes the row kernels move it in 16-byte
+// chunks (float4 / double2), L consecutive lanes per row, CPL chunks a lane;
+// otherwise (or when the block is not 16-byte aligned: ALIGNED = false) in
+// single elements.  L divides 32, so a row never straddles a warp.
+template <typename T, int R, bool ALIGNED = true>
+struct RowLay {
+    static constexpr bool VEC = ALIGNED && (R * sizeof(T)) % 16 == 0;
+    static constexpr int EL = VEC ? int(16 / sizeof(T)) : 1;   // elements per chunk
+    static constexpr int C = R / EL;                          // chunks per row
+    static constexpr int L = (C % 8 == 0) ? 8 : (C % 4 == 0) ? 4 : (C % 2 == 0) ? 2 : 1;
+    static constexpr int CPL = C / L;                         // chunks per lane
+};
+
+template <typename T, int EL>
+struct RowChunk {
+    T v[EL];
+};
+
+template <typename T, int EL>
+__device__ __forceinline__ RowChunk<T, EL> ld_row_chunk(const T *p) {
+    RowChunk<T, EL> c;
+    if constexpr (EL == 4) {
+        const float4 q = __ldg(reinterpret_cast<const float4 *>(p));
+        c.v[0] = q.x; c.v[1] = q.y; c.v[2] = q.z; c.v[3] = q.w;
+    } else if constexpr (EL == 2) {
+        const double2 q = __ldg(reinterpret_cast<const double2 *>(p));
+        c.v[0] = q.x; c.v[1] = q.y;
+    } else {
+        c.v[0] = __ldg(p);
     }
-    int32_t j1 = ptr[i + 1];
-    for (int32_t j = ptr[i]; j < j1; ++j) {
-        const T *xq = X + (int64_t)col[j] * R + c * EPT;
-        T wj = w[j];
+    return c;
+}
+
+template <typename T, int EL>
+__device__ __forceinline__ void st_row_chunk(T *p, const RowChunk<T, EL> &c) {
+    if constexpr (EL == 4) {
+        *reinterpret_cast<float4 *>(p) = make_float4(c.v[0], c.v[1], c.v[2], c.v[3]);
+    } else if constexpr (EL == 2) {
+        *reinterpret_cast<double2 *>(p) = make_double2(c.v[0], c.v[1]);
+    } else {
+        *p = c.v[0];
+    }
+}
+
+// Y = s * (L X + D .* X), (L X)_i = sum_j w_ij (X_i - X_j) (Eq. formula_laplacian).
+// L lanes per row; each lane owns CPL chunks of the row and walks the row's
+// entries in batches of B = 4 (indices and weights first, then the four
+// gathers, then the sums), so a lane has several gathers in flight (larger
+// batches cost registers, and the occupancy lost outweighed the gain).
+template <typename T, int R, bool ALIGNED>
+__global__ void __launch_bounds__(256) k_lapmm(int64_t n, const int32_t *__restrict__ ptr,
+                                               const int32_t *__restrict__ col,
+                                               const T *__restrict__ w, const T *__restrict__ D,
+                                               const T *__restrict__ X, T *__restrict__ Y,
+                                               const unsigned long long *scale_from) {
+    using RL = RowLay<T, R, ALIGNED>;
+    constexpr int EL = RL::EL, L = RL::L, CPL = RL::CPL;
+    constexpr int B = 4;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t i = t / L;
+    if (i >= n) return;
+    const int lane = (int)(t % L);
+    const T s = (T)scale_of(scale_from);
+    const int64_t off = lane * CPL * EL;   // first element of this lane in a row
+    RowChunk<T, EL> x0[CPL], acc[CPL];
 #pragma unroll
-        for (int e = 0; e < EPT; ++e) acc[e] += wj * (x0[e] - xq[e]);
+    for (int c = 0; c < CPL; ++c) {
+        x0[c] = ld_row_chunk<T, EL>(X + i * R + off + c * EL);
+#pragma unroll
+        for (int e = 0; e < EL; ++e) acc[c].v[e] = (T)0;
+    }
+    const int32_t j0 = __ldg(ptr + i), j1 = __ldg(ptr + i + 1);
+    for (int32_t j = j0; j < j1; j += B) {
+        int32_t cj[B];
+        T wj[B];
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+            // past the row's end: reload its last entry (every address stays
+            // inside the arrays) and mark the slot unused
+            const int32_t jb = j + b < j1 ? j + b : j1 - 1;
+            cj[b] = __ldg(col + jb);
+            wj[b] = __ldg(w + jb);
+            if (j + b >= j1) cj[b] = -1;
+        }
+        RowChunk<T, EL> xq[B][CPL];
+#pragma unroll
+        for (int b = 0; b < B; ++b)
+#pragma unroll
+            for (int c = 0; c < CPL; ++c)
+                if (cj[b] >= 0) xq[b][c] = ld_row_chunk<T, EL>(X + (int64_t)cj[b] * R + off + c * EL);
+#pragma unroll
+        for (int b = 0; b < B; ++b)
+            if (cj[b] >= 0)
+#pragma unroll
+                for (int c = 0; c < CPL; ++c)
+#pragma unroll
+                    for (int e = 0; e < EL; ++e) acc[c].v[e] += wj[b] * (x0[c].v[e] - xq[b][c].v[e]);
     }
     if (D) {
-        T d = D[i];
+        const T d = __ldg(D + i);
 #pragma unroll
-        for (int e = 0; e < EPT; ++e) acc[e] += d * x0[e];
+        for (int c = 0; c < CPL; ++c)
+#pragma unroll
+            for (int e = 0; e < EL; ++e) acc[c].v[e] += d * x0[c].v[e];
     }
-    T *yi = Y + i * R + c * EPT;
 #pragma unroll
-    for (int e = 0; e < EPT; ++e) yi[e] = acc[e] * s;
+    for (int c = 0; c < CPL; ++c) {
+#pragma unroll
+        for (int e = 0; e < EL; ++e) acc[c].v[e] *= s;
+        st_row_chunk<T, EL>(Y + i * R + off + c * EL, acc[c]);
+    }
+}
+
+inline bool aligned16(const void *p) { return p == nullptr || ((uintptr_t)p & 15u) == 0; }
+
+template <typename T, int R, bool ALIGNED>
+static void lapmm_T(grass_ctx_t ctx, int64_t n, const int32_t *ptr, const int32_t *col,
+                    const void *w, const void *D, const void *X, void *Y,
+                    const unsigned long long *sf) {
+    constexpr int L = RowLay<T, R, ALIGNED>::L;
+    launch(ctx, k_lapmm<T, R, ALIGNED>, cdiv(n * L, 256), 256, 0, n, ptr, col, (const T *)w,
+           (const T *)D, (const T *)X, (T *)Y, sf);
 }
 
 template <int R>
 static void lapmm_R(grass_ctx_t ctx, grass_prec prec, int64_t n, const int32_t *ptr,
                     const int32_t *col, const void *w, const void *D, const void *X, void *Y,
                     const unsigned long long *sf) {
-    constexpr int TPR = Lay<R>::TPR;
-    int64_t grid = cdiv(n * TPR, kBlock);
-    if (prec == GRASS_FP64)
-        launch(ctx, k_lapmm<double, R>, grid, kBlock, 0, n, ptr, col, (const double *)w,
-               (const double *)D, (const double *)X, (double *)Y, sf);
-    else
-        launch(ctx, k_lapmm<float, R>, grid, kBlock, 0, n, ptr, col, (const float *)w,
-               (const float *)D, (const float *)X, (float *)Y, sf);
+    // 16-byte chunks need 16-byte aligned blocks (library scratch always is;
+    // a caller's block or a slice of one may not be)
+    const bool al = aligned16(X) && aligned16(Y);
+    if (prec == GRASS_FP64) {
+        if (al) lapmm_T<double, R, true>(ctx, n, ptr, col, w, D, X, Y, sf);
+        else lapmm_T<double, R, false>(ctx, n, ptr, col, w, D, X, Y, sf);
+    } else {
+        if (al) lapmm_T<float, R, true>(ctx, n, ptr, col, w, D, X, Y, sf);
+        else lapmm_T<float, R, false>(ctx, n, ptr, col, w, D, X, Y, sf);
+    }
 }
 
 void lap_mm(grass_ctx_t ctx, int r, grass_prec prec, int64_t n, int64_t nnz, const int32_t *ptr,
@@ -63,6 +156,8 @@ void lap_mm(grass_ctx_t ctx, int r, grass_prec prec, int64_t n, int64_t nnz, con
             const unsigned long long *scale_from, int fam) {
     const double s = prec == GRASS_FP64 ? 8.0 : 4.0;
     const double bytes = 4.0 * (n + 1) + nnz * (4.0 + s) + 2.0 * n * r * s + (Dopt ? n * s : 0.0);
+    // products with L_G over r > 1 columns are also a family of their own
+    if (fam == GRASS_KF_SPMM_G && r > 1 && ctx->tfam == GRASS_KF_SPMM_BLK) fam = GRASS_KF_SPMM_BLK;
     bool timed = ctx->t_begin(fam, bytes);
     GRASS_DISPATCH_R(r, lapmm_R, ctx, prec, n, ptr, col, w, Dopt, X, Y, scale_from);
     ctx->t_end(timed);
@@ -123,52 +218,93 @@ void max_abs_bits(grass_ctx_t ctx, grass_prec prec, int64_t count, const void *X
 // heat_i = w_i * sum_j (H[u][j] - H[v][j])^2 for the i-th off-S edge
 // (Eqs. formula_Joule, formula_pwr_iter5new, formula_pwr_iter6), with H
 // multiplied by the pending power of two s (exact): heat = w s^2 sum(...).
-
-template <typename T, int R>
-__global__ void k_heat(int64_t moff, const int32_t *__restrict__ ou, const int32_t *__restrict__ ov,
-                       const T *__restrict__ ow, const T *__restrict__ H,
-                       const unsigned long long *scale_from, T *__restrict__ heat,
-                       unsigned long long *heatmax) {
-    constexpr int TPR = Lay<R>::TPR, EPT = Lay<R>::EPT;
-    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int64_t i = t / TPR;
-    int c = (int)(t % TPR);
-    T part = (T)0;
+// One edge per thread (no shuffles: the edge lists and the heats are read and
+// written coalesced); a fixed grid walks the edges, each thread loading its
+// next edge's endpoints and weight before it consumes this edge's row
+// gathers, which it issues G chunks of 16 bytes per endpoint at a time.
+// Every block ends with one atomicMax of its largest heat.
+template <typename T, int R, bool ALIGNED>
+__global__ void __launch_bounds__(256) k_heat(int64_t moff, const int32_t *__restrict__ ou,
+                                              const int32_t *__restrict__ ov,
+                                              const T *__restrict__ ow, const T *__restrict__ H,
+                                              const unsigned long long *scale_from,
+                                              T *__restrict__ heat, unsigned long long *heatmax) {
+    using RL = RowLay<T, R, ALIGNED>;
+    constexpr int EL = RL::EL, C = R / EL;
+    // chunks per endpoint in flight together: at most four, dividing the row
+    constexpr int G = C % 4 == 0 ? 4 : C % 3 == 0 ? 3 : C % 2 == 0 ? 2 : 1;
+    static_assert(C % G == 0, "chunk groups must tile the row");
+    const T s = (T)scale_of(scale_from);
+    const T s2 = s * s;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double mx = 0.0;
+    int32_t eu = 0, ev = 0;
+    T ew = (T)0;
     if (i < moff) {
-        const T *hu = H + (int64_t)ou[i] * R + c * EPT;
-        const T *hv = H + (int64_t)ov[i] * R + c * EPT;
+        eu = __ldg(ou + i);
+        ev = __ldg(ov + i);
+        ew = __ldg(ow + i);
+    }
+    for (; i < moff; i += stride) {
+        // the next edge of this thread (its last one reloads itself, so
+        // every address stays inside the arrays)
+        const int64_t inx = i + stride < moff ? i + stride : i;
+        const int32_t nu = __ldg(ou + inx), nv = __ldg(ov + inx);
+        const T nw = __ldg(ow + inx);
+        const T *hu = H + (int64_t)eu * R;
+        const T *hv = H + (int64_t)ev * R;
+        T part = (T)0;
 #pragma unroll
-        for (int e = 0; e < EPT; ++e) {
-            T d = hu[e] - hv[e];
-            part += d * d;
+        for (int c0 = 0; c0 < C; c0 += G) {
+            RowChunk<T, EL> a[G], b[G];
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+                a[g] = ld_row_chunk<T, EL>(hu + (c0 + g) * EL);
+                b[g] = ld_row_chunk<T, EL>(hv + (c0 + g) * EL);
+            }
+#pragma unroll
+            for (int g = 0; g < G; ++g)
+#pragma unroll
+                for (int e = 0; e < EL; ++e) {
+                    const T d = a[g].v[e] - b[g].v[e];
+                    part += d * d;
+                }
         }
-    }
-#pragma unroll
-    for (int d = TPR / 2; d > 0; d >>= 1) part += __shfl_xor_sync(0xffffffffu, part, d);
-    double hval = 0.0;
-    if (i < moff && c == 0) {
-        T s = (T)scale_of(scale_from);
-        T h = ow[i] * (part * (s * s));
+        const T h = ew * (part * s2);
         heat[i] = h;
-        hval = (double)h;
+        mx = fmax(mx, (double)h);
+        eu = nu;
+        ev = nv;
+        ew = nw;
     }
-    block_atomic_max(heatmax, hval);
+    block_atomic_max(heatmax, mx);
+}
+
+template <typename T, int R, bool ALIGNED>
+static void heat_T(grass_ctx_t ctx, grass_sparsifier_t S, const void *H,
+                   const unsigned long long *sf, void *heat, unsigned long long *hm) {
+    const int64_t moff = S->m_off;
+    const int sms = ctx->num_sms > 0 ? ctx->num_sms : 152;
+    int nb = 0;
+    GCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_heat<T, R, ALIGNED>, 256, 0));
+    const int64_t grid = std::min<int64_t>(cdiv(moff, 256), (int64_t)sms * std::max(nb, 1));
+    const T *ow = sizeof(T) == 8 ? (const T *)S->off_w64.p : (const T *)S->off_w32.p;
+    launch(ctx, k_heat<T, R, ALIGNED>, grid, 256, 0, moff, (const int32_t *)S->off_u.p,
+           (const int32_t *)S->off_v.p, ow, (const T *)H, sf, (T *)heat, hm);
 }
 
 template <int R>
 static void heat_R(grass_ctx_t ctx, grass_prec prec, grass_sparsifier_t S, const void *H,
                    const unsigned long long *sf, void *heat, unsigned long long *hm) {
-    constexpr int TPR = Lay<R>::TPR;
-    int64_t moff = S->m_off;
-    int64_t grid = cdiv(moff * TPR, kBlock);
-    if (prec == GRASS_FP64)
-        launch(ctx, k_heat<double, R>, grid, kBlock, 0, moff, (const int32_t *)S->off_u.p,
-               (const int32_t *)S->off_v.p, (const double *)S->off_w64.p, (const double *)H, sf,
-               (double *)heat, hm);
-    else
-        launch(ctx, k_heat<float, R>, grid, kBlock, 0, moff, (const int32_t *)S->off_u.p,
-               (const int32_t *)S->off_v.p, (const float *)S->off_w32.p, (const float *)H, sf,
-               (float *)heat, hm);
+    const bool al = aligned16(H);
+    if (prec == GRASS_FP64) {
+        if (al) heat_T<double, R, true>(ctx, S, H, sf, heat, hm);
+        else heat_T<double, R, false>(ctx, S, H, sf, heat, hm);
+    } else {
+        if (al) heat_T<float, R, true>(ctx, S, H, sf, heat, hm);
+        else heat_T<float, R, false>(ctx, S, H, sf, heat, hm);
+    }
 }
 
 void heat_offs(grass_ctx_t ctx, int r, grass_prec prec, grass_sparsifier_t S, const void *H,

@@ -71,6 +71,7 @@ enum ScratchSlot {
     SCR_PCG_X, SCR_PCG_R, SCR_PCG_Z, SCR_PCG_P, SCR_PCG_Q, SCR_PCG_ZOLD, SCR_PCG_E,
     SCR_FILTER, SCR_FILTER2, SCR_HEAT, SCR_LMAX_V, SCR_LMAX_Y, SCR_PART2,
     SCR_EU_S, SCR_EU_C, SCR_EU_P, SCR_EU_A, SCR_CG_XP,
+    SCR_SIM_V, SCR_SIM_E, SCR_SIM_C,
     SCR_COUNT
 };
 
@@ -106,6 +107,7 @@ struct grass_ctx_s {
     int tree_threads = 1024;
     int64_t tree_tail_items = 2048;
     int euler_solve = 1;   // scan form for grounded r = 1 solves without D
+    int similarity_check = 0;   // 1: Sec. IV-D step 6 in grass_densify (endpoint conflicts)
     int64_t euler_max_n = 4000000;   // trees larger than this keep the elimination rounds
     // co-resident grid of each cooperative kernel shape, per context (no
     // process-wide state: contexts may run on different host threads)
@@ -407,6 +409,7 @@ void copy_d(grass_ctx_t ctx, void *dst, const void *src, size_t bytes);
 
 void graph_extract(grass_ctx_t ctx, const grass_csr_t *A, GraphData &g);
 void mst_boruvka(grass_ctx_t ctx, const GraphData &g, uint8_t *in_tree);
+void mst_boruvka_w(grass_ctx_t ctx, const GraphData &g, const double *ew, uint8_t *in_tree);
 void tree_schedule(grass_ctx_t ctx, grass_tree_t T);
 // Euler tour from the tree adjacency (slot lists tptr/tocc, tree edge id of
 // every slot in tsrc; L slots), before the contraction rounds modify it.
@@ -471,6 +474,13 @@ void sparsifier_add(grass_ctx_t ctx, grass_sparsifier_t S, const int64_t *eids, 
 void lambda_min(grass_ctx_t ctx, grass_sparsifier_t S, double *out_host);
 int64_t filter_heat(grass_ctx_t ctx, grass_sparsifier_t S, const void *heat, grass_prec prec,
                     double thr, int64_t cap, int64_t *accepted);
+// Sec. IV-D step 6 (similarity check), endpoint-conflict reading: of the
+// off-S edges with heat >= thr, keep those that the greedy pass in (heat
+// descending, id ascending) order accepts when it rejects every edge with an
+// endpoint on an edge accepted before it, then at most cap (> 0) of them, the
+// first ones in that order.  Writes the kept ids (increasing) to accepted.
+int64_t filter_similar(grass_ctx_t ctx, grass_sparsifier_t S, const void *heat, grass_prec prec,
+                       double thr, int64_t cap, int64_t *accepted);
 
 // A thread's dot-product accumulator.  Double vectors: an FP64 sum, as in
 // the plain definition.  Float vectors: a pair of floats, the running sum and

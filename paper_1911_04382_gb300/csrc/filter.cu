@@ -255,4 +255,137 @@ int64_t filter_heat(grass_ctx_t ctx, grass_sparsifier_t S, const void *heat, gra
     return filter_T<float>(ctx, S, (const float *)heat, thr, cap, accepted);
 }
 
+// ---------------------------------------------------------------- similarity check (Sec. IV-D step 6)
+// The greedy pass over the selected edges in priority order (heat
+// descending, id ascending) that keeps an edge unless an endpoint already
+// carries a kept edge is a greedy matching under a strict total order.  It
+// equals the result of rounds that keep, at once, every remaining edge that
+// has the highest priority at both of its endpoints among the remaining
+// edges there, then drop the remaining edges that touch a kept one: the
+// highest-priority remaining edge is always kept, so the rounds end, and no
+// round keeps an edge that the sequential pass would reject.  Per vertex the
+// highest priority is an atomicMax on the heat's bit pattern (non-negative
+// floats order like their bits) followed by an atomicMin on the id among
+// edges of that heat; the result does not depend on timing.
+
+enum : uint8_t { SIM_ALIVE = 0, SIM_KEPT = 1, SIM_DROPPED = 2 };
+
+// candidates: off-S positions i with heat[i] >= thr (flag from k_thr_flag)
+__global__ void k_sim_init(int64_t moff, const int64_t *flag, const int32_t *ou, const int32_t *ov,
+                           uint8_t *state, unsigned long long *vbest, int32_t *vid, uint8_t *vmatched) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= moff) return;
+    state[i] = flag[i] ? SIM_ALIVE : SIM_DROPPED;
+    if (!flag[i]) return;
+    const int32_t u = ou[i], v = ov[i];
+    vbest[u] = 0ULL;
+    vbest[v] = 0ULL;
+    vid[u] = 0x7FFFFFFF;
+    vid[v] = 0x7FFFFFFF;
+    vmatched[u] = 0;
+    vmatched[v] = 0;
+}
+
+template <typename T>
+__global__ void k_sim_max(int64_t moff, const uint8_t *state, const T *heat, const int32_t *ou,
+                          const int32_t *ov, unsigned long long *vbest) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= moff || state[i] != SIM_ALIVE) return;
+    const unsigned long long k = key_of<T>(heat[i]);
+    atomicMax(vbest + ou[i], k);
+    atomicMax(vbest + ov[i], k);
+}
+
+template <typename T>
+__global__ void k_sim_min(int64_t moff, const uint8_t *state, const T *heat, const int32_t *ou,
+                          const int32_t *ov, const int32_t *oe, const unsigned long long *vbest,
+                          int32_t *vid) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= moff || state[i] != SIM_ALIVE) return;
+    const unsigned long long k = key_of<T>(heat[i]);
+    if (vbest[ou[i]] == k) atomicMin(vid + ou[i], oe[i]);
+    if (vbest[ov[i]] == k) atomicMin(vid + ov[i], oe[i]);
+}
+
+__global__ void k_sim_keep(int64_t moff, uint8_t *state, const int32_t *ou, const int32_t *ov,
+                           const int32_t *oe, const int32_t *vid, uint8_t *vmatched) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= moff || state[i] != SIM_ALIVE) return;
+    if (vid[ou[i]] == oe[i] && vid[ov[i]] == oe[i]) {
+        state[i] = SIM_KEPT;
+        vmatched[ou[i]] = 1;
+        vmatched[ov[i]] = 1;
+    }
+}
+
+// drop the remaining edges at a kept edge's endpoint, reset the per-vertex
+// best for the next round and count the edges still remaining
+__global__ void k_sim_prune(int64_t moff, uint8_t *state, const int32_t *ou, const int32_t *ov,
+                            const uint8_t *vmatched, unsigned long long *vbest, int32_t *vid,
+                            unsigned long long *alive) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool a = false;
+    if (i < moff && state[i] == SIM_ALIVE) {
+        const int32_t u = ou[i], v = ov[i];
+        if (vmatched[u] || vmatched[v]) state[i] = SIM_DROPPED;
+        else a = true;
+        vbest[u] = 0ULL;
+        vbest[v] = 0ULL;
+        vid[u] = 0x7FFFFFFF;
+        vid[v] = 0x7FFFFFFF;
+    }
+    const unsigned int cnt = __popc(__ballot_sync(0xffffffffu, a));
+    if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(alive, (unsigned long long)cnt);
+}
+
+// heat of the kept edges, -1 (below any threshold) for the others
+template <typename T>
+__global__ void k_sim_heat(int64_t moff, const uint8_t *state, const T *heat, T *out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < moff) out[i] = state[i] == SIM_KEPT ? heat[i] : (T)-1;
+}
+
+template <typename T>
+static int64_t similar_T(grass_ctx_t ctx, grass_sparsifier_t S, const T *heat, double thr,
+                         int64_t cap, int64_t *accepted) {
+    const int64_t moff = S->m_off, n = S->tree->g.n;
+    if (moff == 0) return 0;
+    const int64_t g = cdiv(moff, kBlock);
+    int64_t *flag = ctx->scr<int64_t>(SCR_FILTER, moff + 1);
+    uint8_t *state = ctx->scr<uint8_t>(SCR_SIM_C, moff + 1);
+    // per vertex: best key, best id, matched flag; one round's live count
+    char *vb = ctx->scr<char>(SCR_SIM_V, (size_t)n * (8 + 4 + 1) + 64);
+    unsigned long long *vbest = reinterpret_cast<unsigned long long *>(vb);
+    int32_t *vid = reinterpret_cast<int32_t *>(vb + (size_t)n * 8);
+    uint8_t *vmatched = reinterpret_cast<uint8_t *>(vb + (size_t)n * 12);
+    unsigned long long *alive = reinterpret_cast<unsigned long long *>(ctx->scal.p + DS_MAX + 10);
+    const int32_t *ou = S->off_u.p, *ov = S->off_v.p, *oe = S->off_eid.p;
+    launch(ctx, k_thr_flag<T>, g, kBlock, 0, moff, heat, thr, flag);
+    launch(ctx, k_sim_init, g, kBlock, 0, moff, (const int64_t *)flag, ou, ov, state, vbest, vid,
+           vmatched);
+    for (int64_t round = 0;; ++round) {
+        if (round > moff) fail(GRASS_ERR_CUDA, "similarity check did not finish");
+        launch(ctx, k_sim_max<T>, g, kBlock, 0, moff, (const uint8_t *)state, heat, ou, ov, vbest);
+        launch(ctx, k_sim_min<T>, g, kBlock, 0, moff, (const uint8_t *)state, heat, ou, ov, oe,
+               (const unsigned long long *)vbest, vid);
+        launch(ctx, k_sim_keep, g, kBlock, 0, moff, state, ou, ov, oe, (const int32_t *)vid,
+               vmatched);
+        memset_d(ctx, alive, 0, sizeof(unsigned long long));
+        launch(ctx, k_sim_prune, g, kBlock, 0, moff, state, ou, ov, (const uint8_t *)vmatched,
+               vbest, vid, alive);
+        unsigned long long left = 0;
+        d2h(ctx, &left, alive, sizeof(left));
+        if (left == 0) break;
+    }
+    T *kept_heat = reinterpret_cast<T *>(ctx->scr<char>(SCR_SIM_E, (size_t)(moff + 1) * sizeof(T)));
+    launch(ctx, k_sim_heat<T>, g, kBlock, 0, moff, (const uint8_t *)state, heat, kept_heat);
+    return filter_T<T>(ctx, S, kept_heat, thr, cap, accepted);
+}
+
+int64_t filter_similar(grass_ctx_t ctx, grass_sparsifier_t S, const void *heat, grass_prec prec,
+                       double thr, int64_t cap, int64_t *accepted) {
+    if (prec == GRASS_FP64) return similar_T<double>(ctx, S, (const double *)heat, thr, cap, accepted);
+    return similar_T<float>(ctx, S, (const float *)heat, thr, cap, accepted);
+}
+
 }  // namespace grass

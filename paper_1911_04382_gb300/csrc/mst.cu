@@ -111,6 +111,12 @@ __global__ void k_bor_compact(int64_t na, const int32_t *act, const int64_t *fla
 }
 
 void mst_boruvka(grass_ctx_t ctx, const GraphData &g, uint8_t *in_tree) {
+    mst_boruvka_w(ctx, g, g.ew64.p, in_tree);
+}
+
+// The same over the graph's edges with weights ew (device, m positive
+// doubles) in place of the graph's own.
+void mst_boruvka_w(grass_ctx_t ctx, const GraphData &g, const double *ew, uint8_t *in_tree) {
     const int64_t n = g.n, m = g.m;
     DBuf<int32_t> comp, hook, nh, be, act0, act1;
     DBuf<unsigned long long> bw;
@@ -136,9 +142,9 @@ void mst_boruvka(grass_ctx_t ctx, const GraphData &g, uint8_t *in_tree) {
         memset_d(ctx, bw.p, 0, n * sizeof(unsigned long long));
         memset_d(ctx, be.p, 0x7F, n * sizeof(int32_t));     // kNoEdge
         launch(ctx, k_bor_max, cdiv(na, kBlock), kBlock, 0, na, (const int32_t *)act, g.eu.p,
-               g.ev.p, g.ew64.p, (const int32_t *)comp.p, bw.p);
+               g.ev.p, ew, (const int32_t *)comp.p, bw.p);
         launch(ctx, k_bor_min, cdiv(na, kBlock), kBlock, 0, na, (const int32_t *)act, g.eu.p,
-               g.ev.p, g.ew64.p, (const int32_t *)comp.p, (const unsigned long long *)bw.p, be.p);
+               g.ev.p, ew, (const int32_t *)comp.p, (const unsigned long long *)bw.p, be.p);
         launch(ctx, k_bor_hook, cdiv(n, kBlock), kBlock, 0, n, (const int32_t *)comp.p,
                (const int32_t *)be.p, g.eu.p, g.ev.p, hook.p);
         memset_d(ctx, nhooked, 0, sizeof(unsigned int));

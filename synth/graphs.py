@@ -306,3 +306,15 @@ def config_batch(count: int = 256, seed: int = 7, side_lo: int = 32, side_hi: in
             n = int(round(ring_lo * (ring_hi / ring_lo) ** u[k]))
             gs.append(ring_chords(n, seed + k))
     return gs
+
+
+def hair_comb_edges(nx: int, ny: int) -> tuple[np.ndarray, np.ndarray]:
+    """Vertex pairs (u < v) of the "hair-comb" spanning tree of the nx x ny
+    grid (vertex id x + nx*y): the spine is row y = 0 and every column x is
+    a tooth from y = 0 to y = ny - 1."""
+    x = np.arange(nx - 1, dtype=np.int64)
+    su, sv = x, x + 1
+    xx, yy = np.meshgrid(np.arange(nx, dtype=np.int64), np.arange(ny - 1, dtype=np.int64),
+                         indexing="xy")
+    tu = (xx + nx * yy).ravel()
+    return np.concatenate([su, tu]), np.concatenate([sv, tu + nx])

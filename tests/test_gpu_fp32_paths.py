@@ -37,7 +37,7 @@ def _with_extra(og, ot, every):
 
 
 # the scan form applies to one column only: r = 1 runs with it and without
-@pytest.mark.parametrize("r,euler", [(1, 1), (1, 0), (4, 1), (8, 1), (16, 1), (32, 1)])
+@pytest.mark.parametrize("r,euler", [(1, 1), (1, 0), (2, 1), (4, 1), (8, 1), (16, 1), (24, 1), (32, 1)])
 def test_fp32_embedding_through_inner_cg(gpu, r, euler):
     import torch
     g = graphs.grid2d_uniform(37, 29, seed=11)          # n = 1073

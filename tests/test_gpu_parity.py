@@ -101,20 +101,34 @@ def test_invalid_inputs_are_rejected(gpu):
         G.grass_ctx_destroy(ctx)
 
 
-@pytest.mark.parametrize("r", [1, 8, 16, 24])
-def test_spmm_matches_oracle(gpu, r):
+def _at_offset(a, offset, dtype):
+    """A device copy of a whose first element sits `offset` elements past a
+    256-byte aligned allocation (offset 1: not 16-byte aligned)."""
+    import torch
+    flat = torch.zeros(a.size + offset + 64, dtype=dtype, device="cuda")
+    v = flat[offset:offset + a.size].view(a.shape)
+    v.copy_(torch.from_numpy(np.ascontiguousarray(a)).to(dtype))
+    return v
+
+
+@pytest.mark.parametrize("offset", [0, 1])
+@pytest.mark.parametrize("r", [1, 2, 4, 8, 16, 24, 32])
+def test_spmm_matches_oracle(gpu, r, offset):
+    """Every supported r, rows in 16-byte chunks (aligned blocks) or single
+    elements (a block that is not 16-byte aligned); the 3D grid's rows have
+    up to six entries, so the batches of four leave remainders."""
     import torch
     g = graphs.grid3d_loguniform(15, 13, 11, seed=21)
     og = oracle.from_graph(g)
     X = rng.gaussian_block(21, 5, g.n, r)
     ref = oracle.lap_apply(og, X)
     with gpu_graph(g) as (ctx, tree, _):
-        Xd = dev(X)
-        Y = torch.empty_like(Xd)
+        Xd = _at_offset(X, offset, torch.float64)
+        Y = _at_offset(np.zeros_like(X), offset, torch.float64)
         gpu.grass_spmm(ctx, tree, r, gpu.GRASS_FP64, Xd, Y)
         assert np.abs(host(Y) - ref).max() <= 1e-12 * np.abs(ref).max()
-        X32 = Xd.float()
-        Y32 = torch.empty_like(X32)
+        X32 = _at_offset(X, offset, torch.float32)
+        Y32 = _at_offset(np.zeros_like(X), offset, torch.float32)
         gpu.grass_spmm(ctx, tree, r, gpu.GRASS_FP32, X32, Y32)
         assert np.abs(host(Y32) - ref).max() <= 1e-4 * np.abs(ref).max()
 
@@ -197,7 +211,7 @@ def test_embed_heat_tree_matches_oracle(gpu, gi):
     _heat_parity(gpu, g, t=2, r=8)
 
 
-@pytest.mark.parametrize("t,r", [(1, 1), (3, 16), (2, 24)])
+@pytest.mark.parametrize("t,r", [(1, 1), (2, 2), (2, 4), (3, 16), (2, 24), (1, 32)])
 def test_embed_heat_shapes(gpu, t, r):
     _heat_parity(gpu, graphs.grid2d_uniform(40, 33, seed=31), t=t, r=r, rho=17)
 
