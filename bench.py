@@ -545,6 +545,244 @@ def run_batch(G, w=BATCH) -> dict:
     return out
 
 
+# ---------------------------------------------------------------- extras (outside the timed region)
+
+def round_bytes(n: int, m: int, nnz: int, moff: int, r: int, t: int, s: int) -> float:
+    """Algorithmic bytes of one embedding round by the formulas of the scope
+    table (each array once, perfect reuse of gathered rows): t (SpMM + tree
+    solve) + heat, SpMM = 8(n+1) + nnz(4+s) + 2nrs, tree = 2n(4+2s) + 6nrs,
+    heat = moff(8+s) + nrs + moff s."""
+    spmm = 8 * (n + 1) + nnz * (4 + s) + 2 * n * r * s
+    tree = 2 * n * (4 + 2 * s) + 6 * n * r * s
+    heat = moff * (8 + s) + n * r * s + moff * s
+    return t * (spmm + tree) + heat
+
+
+def per_round(st: dict, g, w: dict, peak: float) -> list:
+    """Off-tree edges embedded per second of each round's embedding (power
+    steps + heat, host wall time of a call that ends synchronised), and for
+    round 1 (tree solves, no inner CG) its fraction of the HBM roofline."""
+    s = 4 if w["embed"] == "fp32" else 8
+    out = []
+    for k in range(st["rounds"]):
+        ms = st["ms_embed_round"][k]
+        moff = st["embedded_round"][k]
+        row = {"round": k + 1, "offtree_edges": moff, "ms": ms,
+               "edges_per_s": moff / (ms / 1e3) if ms > 0 else None}
+        if k == 0:
+            by = round_bytes(g.n, g.m, g.nnz, moff, w["r"], w["t"], s)
+            row.update(algorithmic_bytes=by, GBps=by / (ms / 1e3) / 1e9,
+                       frac_of_measured_hbm=by / (ms / 1e3) / 1e9 / peak)
+        else:
+            row["note"] = "sparsifier solves by inner CG (t x inner iterations tree solves)"
+        out.append(row)
+    return out
+
+
+def c2_extras(G, ctx, w: dict, g, rp, col, val, h0d, v0d, bd, P, peak: float) -> dict:
+    """On the step's sparsifier: the lambda estimates with tight inner solves
+    (certifying the stop decision), the plain FP64 method at the same 1e-8
+    accuracy, and the PCG iteration count and time for inner budgets 0 (tree
+    preconditioner) .. 8 (one-step FP32 PCG passes, FP64 refinement)."""
+    import torch
+    out = {}
+    tree = G.grass_build_tree(ctx, rp, col, val, 0)
+    S, st = G.grass_densify(ctx, tree, P, h0d, v0d)
+    try:
+        d = st.as_dict()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        lmin = G.grass_lambda_min(ctx, S)
+        vk = torch.randn(g.n, dtype=torch.float64, device="cuda",
+                         generator=torch.Generator(device="cuda").manual_seed(11))
+        lmax = G.grass_lambda_max(ctx, S, vk, 30, G.GRASS_FP64, 1e-10, 3000)
+        out["kappa_check"] = {
+            "lambda_min_est": lmin, "lambda_max_tight": lmax, "kappa_tight": lmax / lmin,
+            "sigma2": w["sigma2"], "bench_lambda_max_est": d["lmax_est"][-1],
+            "bench_stopped_similar": d["stopped_similar"],
+            "method": "30 generalized power steps from a fresh vector, FP64, inner CG to "
+                      "1e-10 (Rayleigh quotient: a lower bound of the true lambda_max)",
+            "s": time.perf_counter() - t0}
+        sweep = []
+        x = torch.zeros(g.n, dtype=torch.float64, device="cuda")
+        for inner in (0, 1, 2, 4, 8):
+            x.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            stt, ps = G.grass_pcg_solve(ctx, S, bd, x, w["pcg_tol"], w["pcg_maxit"], G.GRASS_FP32,
+                                        w["refine_tol"], w["pcg_inner_tol"], inner)
+            torch.cuda.synchronize()
+            sweep.append({"inner_maxit": inner, "iters": ps.iters, "ms": 1e3 * (time.perf_counter() - t0),
+                          "rel_resid_fp64": ps.rel_resid_fp64, "status": stt})
+        out["pcg_inner_sweep"] = sweep
+    finally:
+        G.grass_sparsifier_destroy(S)
+        G.grass_tree_destroy(tree)
+    # the plain FP64 method: FP64 embedding and FP64 PCG to the same tolerance
+    P64 = G.make_params(w["sigma2"], w["r"], w["t"], w["rounds"], w["lmax_iters"],
+                        int(w["cap_frac"] * g.n), G.GRASS_FP64, w["inner_tol"], w["inner_maxit"])
+    x = torch.zeros(g.n, dtype=torch.float64, device="cuda")
+
+    def fp64_step():
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        tr = G.grass_build_tree(ctx, rp, col, val, 0)
+        t1 = time.perf_counter()
+        S2, st2 = G.grass_densify(ctx, tr, P64, h0d, v0d)
+        t2 = time.perf_counter()
+        x.zero_()
+        s2, ps2 = G.grass_pcg_solve(ctx, S2, bd, x, w["pcg_tol"], w["pcg_maxit"], G.GRASS_FP64,
+                                    w["refine_tol"], w["pcg_inner_tol"], w["pcg_inner_maxit"])
+        torch.cuda.synchronize()
+        t3 = time.perf_counter()
+        G.grass_sparsifier_destroy(S2)
+        G.grass_tree_destroy(tr)
+        return {"ms_per_step": 1e3 * (t3 - t0),
+                "phase_ms": {"tree": 1e3 * (t1 - t0), "densify": 1e3 * (t2 - t1), "pcg": 1e3 * (t3 - t2)},
+                "edges_embedded": st2.offtree_embedded, "rounds": st2.rounds, "added": st2.added,
+                "pcg_iters": ps2.iters, "rel_resid_fp64": ps2.rel_resid_fp64, "status": s2}
+    fp64_step()
+    out["fp64_path"] = fp64_step()
+    out["fp64_path"]["edges_per_s"] = out["fp64_path"]["edges_embedded"] / (
+        out["fp64_path"]["ms_per_step"] / 1e3)
+    return out
+
+
+def c1_latency(G, reps: int = 10) -> dict:
+    """The 64 x 64 grid, plain FP64 method (tree, one round r=8 t=2
+    sigma^2=100, PCG to 1e-3): latency of the whole path from the device CSR."""
+    import torch
+    w = WORKLOADS["grid2d_64"]
+    g, h0, v0, b = make_inputs(w)
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    rp, col, val, h0d, v0d, bd = d(g.rowptr), d(g.col), d(g.val), d(h0), d(v0), d(b)
+    x = torch.zeros(g.n, dtype=torch.float64, device="cuda")
+    ctx = G.grass_ctx_create()
+    P = G.make_params(w["sigma2"], w["r"], w["t"], w["rounds"], w["lmax_iters"], 0, G.GRASS_FP64,
+                      w["inner_tol"], w["inner_maxit"])
+    times, last = [], None
+    try:
+        for k in range(reps + 3):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            tree = G.grass_build_tree(ctx, rp, col, val, 0)
+            S, st = G.grass_densify(ctx, tree, P, h0d, v0d)
+            x.zero_()
+            s, ps = G.grass_pcg_solve(ctx, S, bd, x, w["pcg_tol"], w["pcg_maxit"], G.GRASS_FP64,
+                                      w["refine_tol"], w["pcg_inner_tol"], w["pcg_inner_maxit"])
+            torch.cuda.synchronize()
+            if k >= 3:
+                times.append(1e6 * (time.perf_counter() - t0))
+            last = (st, ps)
+            G.grass_sparsifier_destroy(S)
+            G.grass_tree_destroy(tree)
+    finally:
+        G.grass_ctx_destroy(ctx)
+    st, ps = last
+    return {"workload": describe(w, g), "latency_us_median": float(np.median(times)),
+            "latency_us_min": float(np.min(times)), "reps": reps, "added": st.added,
+            "pcg_iters": ps.iters, "rel_resid_fp64": ps.rel_resid_fp64,
+            "edges_embedded_per_s": st.offtree_embedded / (np.median(times) / 1e6)}
+
+
+C3 = dict(n=4_000_000, seed=3, r=24, t=3, sigma2=500.0, rounds=3, lmax_iters=8, cap_frac=0.02,
+          embed="fp32", inner_tol=1e-2, inner_maxit=30)
+
+
+def c3_powerlaw(G, peak: float, w=C3) -> dict:
+    """Chung-Lu power-law graph (4M sampled nodes, mean degree 10, exponent
+    2.1, unit weights, largest component), r=24, t=3, sigma^2=500, FP32
+    embedding, <= 3 densification rounds with a 2 % per-round cap: spanning
+    tree + densification from the device CSR (one warm run, one timed)."""
+    import torch
+    from synth import graphs, rng
+    t0 = time.perf_counter()
+    g = graphs.chung_lu(w["n"], w["seed"])
+    gen_s = time.perf_counter() - t0
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    rp, col, val = d(g.rowptr), d(g.col), d(g.val)
+    gen = torch.Generator(device="cuda").manual_seed(w["seed"])
+    h0 = torch.randn(w["rounds"] * g.n * w["r"], generator=gen, device="cuda", dtype=torch.float64)
+    v0 = torch.randn(w["rounds"] * g.n, generator=gen, device="cuda", dtype=torch.float64)
+    P = G.make_params(w["sigma2"], w["r"], w["t"], w["rounds"], w["lmax_iters"],
+                      int(w["cap_frac"] * g.n), G.GRASS_FP32, w["inner_tol"], w["inner_maxit"])
+    ctx = G.grass_ctx_create()
+    try:
+        def run():
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            tree = G.grass_build_tree(ctx, rp, col, val, 0)
+            t1 = time.perf_counter()
+            S, st = G.grass_densify(ctx, tree, P, h0, v0)
+            torch.cuda.synchronize()
+            t2 = time.perf_counter()
+            n_s, _ = G.grass_sparsifier_info(S)
+            rounds = G.grass_tree_info(tree)[2]
+            G.grass_sparsifier_destroy(S)
+            G.grass_tree_destroy(tree)
+            return st.as_dict(), 1e3 * (t1 - t0), 1e3 * (t2 - t1), n_s, rounds
+        run()
+        st, tree_ms, dens_ms, n_s, frounds = run()
+    finally:
+        G.grass_ctx_destroy(ctx)
+    deg = np.diff(g.rowptr) - 1
+    wdesc = dict(embed="fp32", r=w["r"], t=w["t"])
+    return {"workload": f"Chung-Lu power law ({w['n']} sampled nodes, LCC {g.n} nodes, {g.m} edges, "
+                        f"max degree {int(deg.max())}, unit weights); r={w['r']}, t={w['t']}, "
+                        f"sigma^2={w['sigma2']:g}, <= {w['rounds']} rounds, cap 2 % of n; FP32",
+            "n": g.n, "m": g.m, "tree_ms": tree_ms, "densify_ms": dens_ms,
+            "edges_embedded": st["offtree_embedded"],
+            "edges_embedded_per_s": st["offtree_embedded"] / ((tree_ms + dens_ms) / 1e3),
+            "per_round": per_round(st, g, wdesc, peak), "densify": st,
+            "sparsifier_edges": n_s, "tree_factor_rounds": frounds, "host_generation_s": gen_s}
+
+
+def hair_comb(G, k: int = 200, add: int = 400) -> dict:
+    """The hair-comb spanning tree of the k x k unit mesh (a caller's tree):
+    lambda_max estimate of the tree (eight power steps), then one random
+    vector, one power step, the `add` hottest off-tree edges added, and the
+    estimate again (30 steps, inner CG to 1e-10)."""
+    import torch
+    from synth import graphs, rng
+    g = graphs.grid((k, k), None, 0.0)
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    rp, col, val = d(g.rowptr), d(g.col), d(g.val)
+    u, v = graphs.hair_comb_edges(k, k)
+    ctx = G.grass_ctx_create()
+    tree = S = None
+    try:
+        eu = torch.empty(g.m, dtype=torch.int32, device="cuda")
+        ev = torch.empty_like(eu)
+        t0 = G.grass_build_tree(ctx, rp, col, val, 0)          # for its edge list only
+        G.grass_tree_graph(ctx, t0, eu, ev, None, None)
+        G.grass_tree_destroy(t0)
+        key = eu.cpu().numpy().astype(np.int64) * g.n + ev.cpu().numpy()
+        ids = np.searchsorted(key, u * g.n + v).astype(np.int64)
+        tree = G.grass_tree_from_edges(ctx, rp, col, val, d(ids), 0)
+        S = G.grass_sparsifier_create(ctx, tree)
+        v0 = d(rng.normal(3, rng.STREAM_V0, g.n))
+        before = G.grass_lambda_max(ctx, S, v0, 8, G.GRASS_FP64, 1e-12, 100)
+        _, moff = G.grass_sparsifier_info(S)
+        heat = torch.empty(moff, dtype=torch.float64, device="cuda")
+        G.grass_embed(ctx, S, d(rng.gaussian_block(3, rng.STREAM_H0, g.n, 1)), 1, 1, G.GRASS_FP64,
+                      1e-12, 100, None, heat)
+        acc = torch.empty(moff, dtype=torch.int64, device="cuda")
+        na, _ = G.grass_filter(ctx, S, heat, G.GRASS_FP64, 1e-30, 1.0, 1.0, 1, add, acc)
+        G.grass_sparsifier_add(ctx, S, acc[:na].contiguous())
+        after = G.grass_lambda_max(ctx, S, v0, 30, G.GRASS_FP64, 1e-10, 3000)
+    finally:
+        if S:
+            G.grass_sparsifier_destroy(S)
+        if tree:
+            G.grass_tree_destroy(tree)
+        G.grass_ctx_destroy(ctx)
+    return {"workload": f"{k}x{k} unit mesh, hair-comb spanning tree (spine y=0, one tooth per "
+                        f"column); t=1, one random vector, top {add} by heat added",
+            "lambda_max_tree": before, "lambda_max_after": after, "added": na,
+            "paper_context": "Sec. V-C: about 64,000 for the tree, about 100 after adding the top "
+                             "400 edges (figure not reproduced by this reading; see DESIGN)"}
+
+
 # ---------------------------------------------------------------- replicas
 
 def replica_max(dist, v: float, device: str = "cuda") -> float:
@@ -587,6 +825,10 @@ def main() -> int:
     ap.add_argument("--solve40m-only", action="store_true")
     ap.add_argument("--batch", action="store_true",
                     help="run the 256-graph batch benchmark instead and print its line")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the keys measured outside the timed region (per-round rates, "
+                         "kappa check, FP64 path, PCG inner sweep, 64x64 latency, power-law "
+                         "workload, hair comb)")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     if args.impl == "reference":
@@ -763,6 +1005,23 @@ def main() -> int:
                "sample": f"{reps} x (oracle extraction + Kruskal tree + round-1 lambda estimates "
                          f"+ FP64 embedding/heat/filter of all {e} off-tree edges), single thread"}
 
+    extras = {}
+    if rank == 0 and not args.no_extras and args.workload == "grid3d_100":
+        for name, fn in (("c2", lambda: c2_extras(G, ctx, w, g, rp, col, val, h0d, v0d, bd, P, peak)),
+                         ("c1_latency", lambda: c1_latency(G)),
+                         ("c3_powerlaw", lambda: c3_powerlaw(G, peak)),
+                         ("hair_comb", lambda: hair_comb(G))):
+            try:
+                r_ = fn()
+                if name == "c2":
+                    extras.update(r_)
+                else:
+                    extras[name] = r_
+            except Exception as ex:          # reported, never fatal for the line
+                extras[name] = {"error": f"{type(ex).__name__}: {ex}"[:300]}
+        if last.get("st"):
+            extras["per_round"] = per_round(last["st"], g, w, peak)
+
     s40 = None
     if rank == 0 and not args.no_solve40m and args.workload == "grid3d_100":
         try:
@@ -787,6 +1046,7 @@ def main() -> int:
             "sparsifier_edges": last.get("n_s"), "tree_factor_rounds": last.get("tree_rounds"),
             "kernels": breakdown, "solve_40m": s40,
         }
+        line.update(extras)
         print(json.dumps(line), flush=True)
     G.grass_ctx_destroy(ctx)
     if dist is not None:

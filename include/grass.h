@@ -95,6 +95,9 @@ typedef struct {
     double heat_max[GRASS_MAX_ROUNDS];
     int64_t inner_iters;                     /* inner CG iterations, all solves       */
     double ms_estimate, ms_embed, ms_filter, ms_update, ms_total;
+    double ms_embed_round[GRASS_MAX_ROUNDS]; /* each round's power steps + heat (ms)  */
+    int64_t lmax_capped[GRASS_MAX_ROUNDS];   /* inner solves of round k's lambda_max
+                                                estimate that reached inner_maxit      */
 } grass_sparsify_stats_t;
 
 typedef struct {
@@ -366,7 +369,10 @@ grass_status grass_filter_similar(grass_ctx_t ctx, grass_sparsifier_t S, const v
 /* ---------------------------------------------------------------- densify / solve */
 
 /* Iterative densification (Sec. IV-D).  Per round k < max_rounds:
- * (2) lambda estimates on the current S, (3) stop if lmax/lmin <= sigma2,
+ * (2) lambda estimates on the current S, (3) stop if lmax/lmin <= sigma2
+ * and every inner CG solve of the lambda_max estimate met inner_tol before
+ * inner_maxit (a Rayleigh quotient after inexact solves can fall far below
+ * lambda_max; stats->lmax_capped[k] counts the solves that did not),
  * (4) embed with h0 + k*n*r (device, max_rounds*n*r doubles) and the
  * lambda_max start v0 + k*n (device, max_rounds*n doubles), (5) filter,
  * add the kept edges.  The paper's step (6) similarity check is applied when

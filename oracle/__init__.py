@@ -338,15 +338,25 @@ def lambda_max_est(og: OGraph, tree: OTree, in_s: np.ndarray, v0: np.ndarray, it
                    inner_tol: float = 1e-12, inner_maxit: int = 1000) -> float:
     """Section IV-C-1: `iters` generalized power iterations from v0 (made
     orthogonal to 1), then the Rayleigh quotient v^T L_G v / v^T L_S v."""
+    return lambda_max_est_checked(og, tree, in_s, v0, iters, inner_tol, inner_maxit)[0]
+
+
+def lambda_max_est_checked(og: OGraph, tree: OTree, in_s: np.ndarray, v0: np.ndarray, iters: int,
+                           inner_tol: float = 1e-12, inner_maxit: int = 1000):
+    """lambda_max_est and the number of its inner CG solves that reached
+    inner_maxit (0 when S is the tree: those solves are direct)."""
     v = np.asarray(v0, dtype=np.float64).reshape(-1, 1)
     v = v - v.mean()
     mask = _s_mask(tree, in_s)
+    capped = 0
     for _ in range(iters):
         y = lap_apply(og, v)
-        v, _ = s_solve(og, tree, mask, y, None, inner_tol, inner_maxit)
+        v, it = s_solve(og, tree, mask, y, None, inner_tol, inner_maxit)
+        if mask is not None and int(np.max(it)) >= inner_maxit:
+            capped += 1
         v = pow2_rescale(v)
     qG, qS = quad_forms(og, in_s, v)
-    return float(qG[0] / qS[0])
+    return float(qG[0] / qS[0]), capped
 
 
 def theta_sigma(sigma2: float, lmin: float, lmax: float, t: int) -> float:
@@ -410,10 +420,14 @@ def densify(og: OGraph, tree: OTree, h0s, v0s, sigma2: float, t: int, max_rounds
     res = DensifyResult(in_s)
     for rd in range(max_rounds):
         lmin = lambda_min_est(og, in_s)
-        lmax = lambda_max_est(og, tree, in_s, v0s[rd], lmax_iters, inner_tol, inner_maxit)
+        lmax, capped = lambda_max_est_checked(og, tree, in_s, v0s[rd], lmax_iters, inner_tol,
+                                              inner_maxit)
         res.lmin.append(lmin)
         res.lmax.append(lmax)
-        if lmax / lmin <= sigma2:
+        # (3) a Rayleigh quotient bounds lambda_max from below only; one taken
+        # after inner solves that stopped at their cap is not evidence of
+        # similarity, so the stop test needs every solve to meet inner_tol
+        if capped == 0 and lmax / lmin <= sigma2:
             res.stopped_similar = True
             break
         H = embed(og, tree, in_s, h0s[rd], t, inner_tol, inner_maxit)

@@ -56,7 +56,8 @@ class grass_sparsify_stats_t(C.Structure):
                 ("lmax_est", C.c_double * _R), ("theta", C.c_double * _R),
                 ("heat_max", C.c_double * _R), ("inner_iters", C.c_int64),
                 ("ms_estimate", C.c_double), ("ms_embed", C.c_double), ("ms_filter", C.c_double),
-                ("ms_update", C.c_double), ("ms_total", C.c_double)]
+                ("ms_update", C.c_double), ("ms_total", C.c_double),
+                ("ms_embed_round", C.c_double * _R), ("lmax_capped", C.c_int64 * _R)]
 
     def as_dict(self) -> dict:
         k = max(self.rounds, 1 if self.stopped_similar else 0)
@@ -70,7 +71,8 @@ class grass_sparsify_stats_t(C.Structure):
             "theta": list(self.theta[:self.rounds]), "heat_max": list(self.heat_max[:self.rounds]),
             "inner_iters": self.inner_iters, "ms_estimate": self.ms_estimate,
             "ms_embed": self.ms_embed, "ms_filter": self.ms_filter, "ms_update": self.ms_update,
-            "ms_total": self.ms_total,
+            "ms_total": self.ms_total, "ms_embed_round": list(self.ms_embed_round[:self.rounds]),
+            "lmax_capped": list(self.lmax_capped[:k]),
         }
 
 

@@ -783,13 +783,21 @@ grass_status grass_densify(grass_ctx_t ctx, grass_tree_t T, const grass_params_t
             double lmin = 0.0;
             lambda_min(ctx, S, &lmin);
             int64_t inner = 0;
+            memset_d(ctx, ctx->scal.p + DS_RED + DS_CAPPED, 0, sizeof(double));
             double lmax = lambda_max_impl(ctx, S, v0 + (int64_t)k * n, P->lmax_iters,
                                           P->embed_prec, P->inner_tol, P->inner_maxit, &inner);
+            double capped = 0.0;
+            d2h(ctx, &capped, ctx->scal.p + DS_RED + DS_CAPPED, sizeof(double));
             st.lmin_est[k] = lmin;
             st.lmax_est[k] = lmax;
+            st.lmax_capped[k] = (int64_t)capped;
             double tb = now_ms();
             st.ms_estimate += tb - ta;
-            if (lmax / lmin <= P->sigma2) {
+            // step 3: a Rayleigh quotient only bounds lambda_max from below,
+            // and one taken after inexact inner solves can fall far below it;
+            // the stop test trusts an estimate whose inner solves all met
+            // inner_tol before inner_maxit
+            if (capped == 0.0 && lmax / lmin <= P->sigma2) {
                 st.stopped_similar = 1;
                 st.inner_iters += inner;
                 break;
@@ -801,6 +809,7 @@ grass_status grass_densify(grass_ctx_t ctx, grass_tree_t T, const grass_params_t
             st.inner_iters += inner;
             double tc = now_ms();
             st.ms_embed += tc - tb;
+            st.ms_embed_round[k] = tc - tb;
             double th = theta_sigma(P->sigma2, lmin, lmax, P->t);
             st.theta[k] = th;
             st.heat_max[k] = eo.heat_max;

@@ -779,6 +779,7 @@ extern "C" grass_status grass_densify_batch(grass_ctx_t ctx, grass_tree_t T, con
             d2h(ctx, hmax.data(), bits.p, G * sizeof(double));
             const double tc = now_ms();
             st.ms_embed = tc - tb;
+            st.ms_embed_round[0] = tc - tb;
             // filter (Eq. heatratio_final) with each graph's own threshold
             for (int64_t k = 0; k < G; ++k) {
                 thr[k] = std::isinf(theta[k]) ? INFINITY : theta[k] * hmax[k];

@@ -78,6 +78,7 @@ enum ScratchSlot {
 // device scalar area layout (doubles)
 enum {
     DS_ITER = 40,        // inside DS_RED: inner-CG iteration accumulator
+    DS_CAPPED = 41,      // inside DS_RED: inner-CG solves that reached their iteration cap
     DS_PCG = 42,         // inside DS_RED: fused PCG iterations and final r.r
     DS_RED = 0,          // 64 doubles: reduction outputs (PCG scalars)
     DS_CG = 64,          // 12 x 32 doubles: per-column CG scalars

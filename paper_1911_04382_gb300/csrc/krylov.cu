@@ -108,7 +108,8 @@ struct CGArgs {
     double tol;
     int maxit;
     double *part;                // [2][gridDim.x][32]
-    double *iter_acc;            // += max over columns of the iterations
+    double *iter_acc;            // += max over columns of the iterations; iter_acc[1] += 1
+                                 // when a column reached the iteration cap
     unsigned long long *maxbits; // optional max |X|
     EulerKArgs eu;               // scan-form tree solve (r = 1, no D)
     // one column, scan form: perm != nullptr when the solve runs in another
@@ -619,6 +620,7 @@ __device__ __forceinline__ bool cg_dev(const CGArgs<T> &g, const TreeKArgs<T> &t
         int mxit = 0;
         for (int j = 0; j < R; ++j) mxit = max(mxit, s_it[j]);
         *g.iter_acc += (double)mxit;
+        if (mxit >= g.maxit) g.iter_acc[1] += 1.0;
     }
     return true;
 }
