@@ -396,6 +396,34 @@ grass_status grass_pcg_solve(grass_ctx_t ctx, grass_sparsifier_t S, const double
                              double tol, int maxit, grass_prec prec, double refine_tol,
                              double inner_tol, int inner_maxit, grass_solve_stats_t *stats);
 
+/* ---------------------------------------------------------------- partitioning */
+
+typedef struct {
+    int iters_done;          /* inverse power iterations run                    */
+    int64_t pcg_iters;       /* PCG iterations over all of them                 */
+    double worst_rel_resid;  /* largest FP64 relative residual of a solve       */
+    int64_t n_pos, n_neg;    /* vertices on each side of the sign cut           */
+    double rayleigh;         /* u^T L_G u of the returned unit vector u         */
+    double ms;
+} grass_fiedler_stats_t;
+
+/* Spectral graph partitioning (Sec. V-F, Table VI): an approximate Fiedler
+ * vector by `iters` inverse power iterations on A = L_G + D of S's tree
+ * (u <- A^{-1} u, each solve by grass_pcg_solve's PCG preconditioned by the
+ * sparsifier, to ||b - A y|| <= tol ||b|| within maxit iterations, prec and
+ * inner_maxit as there), with u made orthogonal to the all-ones vector and
+ * normalised to unit length before and after every solve (for a graph
+ * Laplacian, D = 0, this keeps the singular system consistent), then the
+ * sign cut side[i] = 1 iff u[i] >= 0.
+ *   x0: device, n doubles (the start vector; need not be orthogonal to 1).
+ *   u_out: device, n doubles (the final unit vector), optional.
+ *   side_out: device, n bytes, optional.  stats: host, optional.
+ * Errors: INVALID, NOT_CONVERGED (some solve missed tol; outputs and stats
+ * still written), TIMEOUT, CUDA. */
+grass_status grass_fiedler(grass_ctx_t ctx, grass_sparsifier_t S, const double *x0, int iters,
+                           double tol, int maxit, grass_prec prec, int inner_maxit, double *u_out,
+                           uint8_t *side_out, grass_fiedler_stats_t *stats);
+
 /* ---------------------------------------------------------------- batching */
 
 /* Batched form (no counterpart in the paper, which handles one graph at a

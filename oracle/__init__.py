@@ -464,9 +464,35 @@ def pcg(og: OGraph, tree: OTree, in_s: np.ndarray | None, b: np.ndarray, tol: fl
     it = C.c_int32(0)
     rel = C.c_double(0.0)
     mask = _s_mask(tree, in_s)
+    # With D identically zero, L_S + D is a graph Laplacian: its solve is the
+    # one grounded at the tree's root (the limit of Sec. III-F), not a division
+    # by the root pivot, which elimination by subtraction leaves as a
+    # rounding residue instead of zero.
+    Dp = og.D if np.any(og.D != 0.0) else None
     st = lib().ora_pcg(og.n, _p(og.rowptr, _i64), _p(og.col, _i32), _p(og.val, _f64), og.m,
                        _p(og.eu, _i32), _p(og.ev, _i32), _p(og.ew, _f64), _p(mask, _u8),
                        _p(tree.parent, _i32), _p(tree.pw, _f64), _p(tree.order, _i32),
-                       _p(og.D, _f64), _p(b, _f64), _p(x, _f64), float(tol), int(maxit),
+                       _p(Dp, _f64), _p(b, _f64), _p(x, _f64), float(tol), int(maxit),
                        float(inner_tol), int(inner_maxit), C.byref(it), C.byref(rel))
     return x, it.value, rel.value, st
+
+
+def fiedler(og: OGraph, tree: OTree, in_s: np.ndarray | None, x0: np.ndarray, iters: int,
+            tol: float, maxit: int = 5000, inner_tol: float = 1e-6, inner_maxit: int = 50):
+    """Section V-F: spectral partitioning by a few inverse power iterations
+    u <- A^{-1} u with A = L_G + D (for a graph Laplacian, D = 0: the
+    Fiedler vector), u made orthogonal to the all-ones vector and of unit
+    length before and after each solve, every solve by PCG preconditioned by
+    the sparsifier (pcg); then the sign cut side = (u >= 0).  Returns
+    (u, side, u^T L_G u, PCG iterations)."""
+    x = np.asarray(x0, dtype=np.float64).copy()
+    x -= x.mean()
+    x /= np.linalg.norm(x)
+    total = 0
+    for _ in range(iters):
+        y, it, rel, st = pcg(og, tree, in_s, x, tol, maxit, inner_tol, inner_maxit)
+        total += it
+        y -= y.mean()
+        x = y / np.linalg.norm(y)
+    qG, _ = quad_forms(og, np.ones(og.m, np.uint8), x)
+    return x, (x >= 0).astype(np.uint8), float(qG[0]), total

@@ -333,7 +333,17 @@ void ora_s_solve(int64_t n, int64_t m, const int32_t *eu, const int32_t *ev, con
     double *p = malloc((size_t)n * sizeof(double));
     double *q = malloc((size_t)n * sizeof(double));
     for (int j = 0; j < r; ++j) {
-        for (int64_t i = 0; i < n; ++i) { y[i] = Y[i * r + j]; x[i] = 0.0; res[i] = y[i]; }
+        for (int64_t i = 0; i < n; ++i) { y[i] = Y[i * r + j]; x[i] = 0.0; }
+        if (!D) {
+            /* L_S alone is singular: L_S^+ acts on the complement of the
+             * all-ones vector, so the right-hand side is projected there
+             * (its component along 1 is rounding, which CG cannot remove) */
+            double mean = 0.0;
+            for (int64_t i = 0; i < n; ++i) mean += y[i];
+            mean /= (double)n;
+            for (int64_t i = 0; i < n; ++i) y[i] -= mean;
+        }
+        for (int64_t i = 0; i < n; ++i) res[i] = y[i];
         double ynorm = sqrt(dot(n, y, y));
         ora_tree_solve(n, parent, pw, order, D, 1, res, z);
         memcpy(p, z, (size_t)n * sizeof(double));

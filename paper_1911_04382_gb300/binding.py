@@ -86,6 +86,15 @@ class grass_solve_stats_t(C.Structure):
                 "ms": self.ms}
 
 
+class grass_fiedler_stats_t(C.Structure):
+    _fields_ = [("iters_done", C.c_int), ("pcg_iters", C.c_int64), ("worst_rel_resid", C.c_double),
+                ("n_pos", C.c_int64), ("n_neg", C.c_int64), ("rayleigh", C.c_double),
+                ("ms", C.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class grass_request_t(C.Structure):
     _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("rowptr", C.c_void_p), ("col", C.c_void_p),
                 ("val", C.c_void_p), ("h0", C.c_void_p), ("v0", C.c_void_p), ("b", C.c_void_p),
@@ -151,6 +160,8 @@ def lib():
                                   C.POINTER(grass_sparsify_stats_t)],
                 "grass_pcg_solve": [_vp, _vp, _vp, _vp, _d, C.c_int, C.c_int, _d, _d, C.c_int,
                                     C.POINTER(grass_solve_stats_t)],
+                "grass_fiedler": [_vp, _vp, _vp, C.c_int, _d, C.c_int, C.c_int, C.c_int, _vp, _vp,
+                                  C.POINTER(grass_fiedler_stats_t)],
                 "grass_build_forest": [_vp, C.POINTER(grass_csr_t), _i64, C.POINTER(_i64),
                                        C.POINTER(_vp)],
                 "grass_tree_segments": [_vp, C.POINTER(_i64), C.POINTER(_i64), C.POINTER(_i64)],
@@ -418,6 +429,16 @@ def grass_filter_similar(ctx, S, heat, prec: int, sigma2: float, lmin: float, lm
                                            _p(accepted), C.byref(na), C.byref(th)),
            "grass_filter_similar")
     return na.value, th.value
+
+
+def grass_fiedler(ctx, S, x0, iters: int, tol: float, maxit: int, prec: int = GRASS_FP64,
+                  inner_maxit: int = 1, u_out=None, side_out=None):
+    """(status, grass_fiedler_stats_t); NOT_CONVERGED is returned, not raised."""
+    st = grass_fiedler_stats_t()
+    s = _check(ctx, lib().grass_fiedler(ctx, S, _p(x0), int(iters), float(tol), int(maxit), prec,
+                                        int(inner_maxit), _p(u_out), _p(side_out), C.byref(st)),
+               "grass_fiedler", allow=(GRASS_ERR_NOT_CONVERGED,))
+    return s, st
 
 
 # ---------------------------------------------------------------- densify / solve

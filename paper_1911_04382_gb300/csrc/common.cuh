@@ -72,6 +72,7 @@ enum ScratchSlot {
     SCR_FILTER, SCR_FILTER2, SCR_HEAT, SCR_LMAX_V, SCR_LMAX_Y, SCR_PART2,
     SCR_EU_S, SCR_EU_C, SCR_EU_P, SCR_EU_A, SCR_CG_XP,
     SCR_SIM_V, SCR_SIM_E, SCR_SIM_C,
+    SCR_PART_X, SCR_PART_Y, SCR_PART_1,
     SCR_COUNT
 };
 
