@@ -1,0 +1,615 @@
+// amg.cu -- aggregation multigrid for the sparsifier's matrix M = L_S + D
+// (or L_S alone), the sparsifier solver of Sec. IV-C-1 / IV-D step 1 (the
+// paper factorises or multigrids the sparsifier), used as the PCG
+// preconditioner of A = L_G + D (Sec. V-A) and for the lambda_max
+// estimate's solves with L_S.
+//
+// Setup, level by level until at most kCoarse vertices remain:
+//  1. heavy-edge matching: rounds in which every unmatched vertex names its
+//     heaviest unmatched neighbour (weight descending, smaller id on ties)
+//     and mutual choices are matched -- each matched edge is the heaviest at
+//     both its ends among the remaining ones (a locally dominant matching;
+//     the result does not depend on timing);
+//  2. an unmatched vertex joins the pair of its heaviest matched neighbour
+//     (its anchor); a vertex with no matched neighbour stays alone;
+//  3. aggregates are numbered in order of their smallest vertex; members
+//     are listed as: the pair's smaller id, the other, the joiners anchored
+//     at the smaller in the order of its adjacency row, then those of the
+//     other -- a fixed order, so every sum below is deterministic;
+//  4. the coarse matrix P^T M P of the piecewise-constant P: coarse row c is
+//     the members' rows in member order, entries to other aggregates only
+//     (a pair joined by several fine edges keeps them as separate entries),
+//     coarse D = the members' summed D, diagonal = coarse D + row weights.
+// The coarsest matrix is inverted densely (Gauss-Jordan, one block); for a
+// Laplacian (D = 0 on the whole level) its last vertex is grounded first,
+// which changes the coarse solution by a constant only.
+//
+// V-cycle from zero: nu weighted-Jacobi sweeps (omega = 2/3; the first one is
+// x = omega D^-1 b), residual restricted to the coarse level (one kernel over
+// the members), recursion, prolongation x += x_c[agg], nu sweeps.  The cycle
+// is symmetric, so it is a fixed SPD (on the complement of 1 for a
+// Laplacian) preconditioner for CG.
+#include <cmath>
+
+#include "common.cuh"
+
+namespace grass {
+
+constexpr int64_t kCoarse = 256;        // the coarsest level has at most this many vertices
+constexpr int kMaxLevels = 40;
+constexpr int kMatchRounds = 8;
+constexpr double kOmega = 2.0 / 3.0;
+
+// ---------------------------------------------------------------- setup kernels
+
+// heavier (w, smaller id) than the current best?
+__device__ __forceinline__ bool better(double w, int32_t u, double bw, int32_t bu) {
+    return w > bw || (w == bw && u < bu);
+}
+
+__global__ void k_amg_diag(int64_t n, const int32_t *ptr, const double *w, const double *D,
+                           double *diag) {
+    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    double s = D ? D[v] : 0.0;
+    for (int32_t j = ptr[v]; j < ptr[v + 1]; ++j) s += w[j];
+    diag[v] = s;
+}
+
+__global__ void k_amg_cand(int64_t n, const int32_t *ptr, const int32_t *col, const double *w,
+                           const int32_t *mate, int32_t *cand) {
+    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    if (mate[v] >= 0) {
+        cand[v] = -1;
+        return;
+    }
+    double bw = -1.0;
+    int32_t bu = -1;
+    for (int32_t j = ptr[v]; j < ptr[v + 1]; ++j) {
+        const int32_t u = col[j];
+        if (u == v || mate[u] >= 0) continue;
+        if (bu < 0 || better(w[j], u, bw, bu)) {
+            bw = w[j];
+            bu = u;
+        }
+    }
+    cand[v] = bu;
+}
+
+__global__ void k_amg_pair(int64_t n, const int32_t *cand, int32_t *mate, int *changed) {
+    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n || mate[v] >= 0) return;
+    const int32_t u = cand[v];
+    if (u >= 0 && cand[u] == (int32_t)v) {
+        mate[v] = u;
+        *changed = 1;
+    }
+}
+
+// anchor[v]: for an unmatched v, its heaviest matched neighbour (-1: none);
+// -2 for matched vertices.  leader[v]: smallest id of v's aggregate.
+__global__ void k_amg_join(int64_t n, const int32_t *ptr, const int32_t *col, const double *w,
+                           const int32_t *mate, int32_t *anchor, int32_t *leader) {
+    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    if (mate[v] >= 0) {
+        anchor[v] = -2;
+        leader[v] = min((int32_t)v, mate[v]);
+        return;
+    }
+    double bw = -1.0;
+    int32_t bu = -1;
+    for (int32_t j = ptr[v]; j < ptr[v + 1]; ++j) {
+        const int32_t u = col[j];
+        if (u == v || mate[u] < 0) continue;
+        if (bu < 0 || better(w[j], u, bw, bu)) {
+            bw = w[j];
+            bu = u;
+        }
+    }
+    anchor[v] = bu;
+    leader[v] = bu >= 0 ? min(bu, mate[bu]) : (int32_t)v;
+}
+
+// jslot[v]: rank of joiner v among the joiners anchored at its anchor, in the
+// order of the anchor's row (first occurrence); jcount[u]: their number
+__global__ void k_amg_slots(int64_t n, const int32_t *ptr, const int32_t *col, const int32_t *mate,
+                            const int32_t *anchor, int32_t *jslot, int32_t *jcount) {
+    int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= n) return;
+    int32_t c = 0;
+    if (mate[u] >= 0) {
+        for (int32_t j = ptr[u]; j < ptr[u + 1]; ++j) {
+            const int32_t v = col[j];
+            if (anchor[v] == (int32_t)u && jslot[v] < 0) jslot[v] = c++;
+        }
+    }
+    jcount[u] = c;
+}
+
+__global__ void k_amg_leadflag(int64_t n, const int32_t *leader, int64_t *flag) {
+    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v < n) flag[v] = leader[v] == (int32_t)v ? 1 : 0;
+}
+
+// agg[v] = number of the aggregate (pos of its leader); member counts
+__global__ void k_amg_agg(int64_t n, const int32_t *leader, const int64_t *pos, const int32_t *mate,
+                          const int32_t *jcount, int32_t *agg, int64_t *mcnt) {
+    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    agg[v] = (int32_t)pos[leader[v]];
+    if (leader[v] == (int32_t)v) {
+        const int32_t m = mate[v];
+        mcnt[pos[v]] = 1 + (m >= 0 ? 1 + jcount[m] : 0) + jcount[v];
+    }
+}
+
+__global__ void k_amg_members(int64_t n, const int32_t *leader, const int32_t *mate,
+                              const int32_t *anchor, const int32_t *jslot, const int32_t *jcount,
+                              const int32_t *agg, const int64_t *moff, int32_t *mem) {
+    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    const int64_t base = moff[agg[v]];
+    const int32_t l = leader[v];
+    const int32_t lm = mate[l];                       // the leader's mate (or -1)
+    const int64_t pairs = lm >= 0 ? 2 : 1;
+    if (anchor[v] == -2 || anchor[v] == -1) {         // matched, or alone
+        mem[base + ((int32_t)v == l ? 0 : 1)] = (int32_t)v;
+        return;
+    }
+    const int32_t a = anchor[v];
+    mem[base + pairs + (a == l ? 0 : jcount[l]) + jslot[v]] = (int32_t)v;
+}
+
+// coarse row sizes: entries of the members' rows to other aggregates
+__global__ void k_amg_ccount(int64_t nc, const int32_t *mptr, const int32_t *mem, const int32_t *ptr,
+                             const int32_t *col, const int32_t *agg, int64_t *ccnt) {
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nc) return;
+    int64_t k = 0;
+    for (int32_t q = mptr[c]; q < mptr[c + 1]; ++q) {
+        const int32_t v = mem[q];
+        for (int32_t j = ptr[v]; j < ptr[v + 1]; ++j) k += agg[col[j]] != (int32_t)c;
+    }
+    ccnt[c] = k;
+}
+
+__global__ void k_amg_cfill(int64_t nc, const int32_t *mptr, const int32_t *mem, const int32_t *ptr,
+                            const int32_t *col, const double *w, const double *D,
+                            const int32_t *agg, const int64_t *coff, int32_t *cptr, int32_t *ccol,
+                            double *cw, double *cD, double *cdiag) {
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nc) return;
+    int64_t k = coff[c];
+    cptr[c] = (int32_t)k;
+    if (c == nc - 1) cptr[nc] = (int32_t)coff[nc];
+    double dsum = 0.0, wsum = 0.0;
+    for (int32_t q = mptr[c]; q < mptr[c + 1]; ++q) {
+        const int32_t v = mem[q];
+        dsum += D[v];
+        for (int32_t j = ptr[v]; j < ptr[v + 1]; ++j) {
+            const int32_t a = agg[col[j]];
+            if (a == (int32_t)c) continue;
+            ccol[k] = a;
+            cw[k] = w[j];
+            wsum += w[j];
+            ++k;
+        }
+    }
+    cD[c] = dsum;
+    cdiag[c] = dsum + wsum;
+}
+
+__global__ void k_i64_to_i32(int64_t n, const int64_t *a, int32_t *b) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = (int32_t)a[i];
+}
+
+__global__ void k_amg_f32(int64_t n, const double *a, float *b) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = (float)a[i];
+}
+
+// dense coarsest matrix (row i by thread i, its entries added in row order)
+__global__ void k_amg_dense(int64_t nc, const int32_t *ptr, const int32_t *col, const double *w,
+                            const double *diag, int ground, double *M) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nc) return;
+    double *row = M + i * nc;
+    for (int64_t j = 0; j < nc; ++j) row[j] = 0.0;
+    if (ground && i == nc - 1) {
+        row[i] = 1.0;
+        return;
+    }
+    row[i] = diag[i];
+    for (int32_t j = ptr[i]; j < ptr[i + 1]; ++j) {
+        const int32_t c = col[j];
+        if (ground && c == nc - 1) continue;
+        row[c] -= w[j];
+    }
+}
+
+// In-place Gauss-Jordan inverse of the SPD matrix M (nc x nc, one block; no
+// pivoting: the pivots of an SPD matrix stay positive).  With `ground`, the
+// grounded vertex's row and column of the inverse are then zeroed.
+__global__ void k_amg_gauss_jordan(int64_t nc, double *M, int ground) {
+    __shared__ double s_piv;
+    for (int64_t p = 0; p < nc; ++p) {
+        if (threadIdx.x == 0) s_piv = M[p * nc + p];
+        __syncthreads();
+        const double inv = 1.0 / s_piv;
+        // row p: a_pj /= piv (j != p), a_pp = 1 / piv
+        for (int64_t j = threadIdx.x; j < nc; j += blockDim.x)
+            M[p * nc + j] = j == p ? inv : M[p * nc + j] * inv;
+        __syncthreads();
+        // other rows: a_ij -= a_ip a_pj (j != p); a_ip = -a_ip / piv
+        for (int64_t e = threadIdx.x; e < nc * nc; e += blockDim.x) {
+            const int64_t i = e / nc, j = e % nc;
+            if (i == p || j == p) continue;
+            M[e] -= M[i * nc + p] * M[p * nc + j];
+        }
+        __syncthreads();
+        for (int64_t i = threadIdx.x; i < nc; i += blockDim.x)
+            if (i != p) M[i * nc + p] = -M[i * nc + p] * inv;
+        __syncthreads();
+    }
+    if (ground) {
+        for (int64_t j = threadIdx.x; j < nc; j += blockDim.x) {
+            M[(nc - 1) * nc + j] = 0.0;
+            M[j * nc + (nc - 1)] = 0.0;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- V-cycle kernels
+
+template <typename T>
+__global__ void k_jac0(int64_t n, const T *b, const T *diag, T *x) {
+    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v < n) x[v] = diag[v] > (T)0 ? (T)kOmega * b[v] / diag[v] : (T)0;
+}
+
+// xo = x + omega (b - M x) / diag,  (M x)_v = diag_v x_v - sum_j w_vj x_j
+template <typename T>
+__global__ void k_jac(int64_t n, const int32_t *ptr, const int32_t *col, const T *w, const T *diag,
+                      const T *b, const T *x, T *xo) {
+    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    T s = (T)0;
+    for (int32_t j = ptr[v]; j < ptr[v + 1]; ++j) s += w[j] * x[col[j]];
+    const T d = diag[v];
+    xo[v] = d > (T)0 ? x[v] + (T)kOmega * (b[v] - (d * x[v] - s)) / d : x[v];
+}
+
+// bc[c] = sum over members v (in member order) of (b - M x)_v
+template <typename T>
+__global__ void k_res_restrict(int64_t nc, const int32_t *mptr, const int32_t *mem,
+                               const int32_t *ptr, const int32_t *col, const T *w, const T *diag,
+                               const T *b, const T *x, T *bc) {
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nc) return;
+    T acc = (T)0;
+    for (int32_t q = mptr[c]; q < mptr[c + 1]; ++q) {
+        const int32_t v = mem[q];
+        T s = (T)0;
+        for (int32_t j = ptr[v]; j < ptr[v + 1]; ++j) s += w[j] * x[col[j]];
+        acc += b[v] - (diag[v] * x[v] - s);
+    }
+    bc[c] = acc;
+}
+
+template <typename T>
+__global__ void k_prolong(int64_t n, const int32_t *agg, const T *xc, T *x) {
+    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v < n) x[v] += xc[agg[v]];
+}
+
+// x = Cinv b for the coarsest level (one block; b staged in shared memory)
+template <typename T>
+__global__ void k_coarse_apply(int64_t nc, const T *Cinv, const T *b, T *x) {
+    __shared__ T sb[kCoarse];
+    for (int64_t j = threadIdx.x; j < nc; j += blockDim.x) sb[j] = b[j];
+    __syncthreads();
+    for (int64_t i = threadIdx.x; i < nc; i += blockDim.x) {
+        T s = (T)0;
+        for (int64_t j = 0; j < nc; ++j) s += Cinv[i * nc + j] * sb[j];
+        x[i] = s;
+    }
+}
+
+// ---------------------------------------------------------------- setup
+
+namespace {
+
+template <typename T>
+T *lvl_w(AmgLevel &L) {
+    if constexpr (sizeof(T) == 8) return L.w64.p;
+    else return L.w32.p;
+}
+template <typename T>
+T *lvl_diag(AmgLevel &L) {
+    if constexpr (sizeof(T) == 8) return L.diag64.p;
+    else return L.diag32.p;
+}
+
+// level 0 from the sparsifier's adjacency (a copy: the hierarchy owns it)
+std::unique_ptr<AmgLevel> level0(grass_ctx_t ctx, grass_sparsifier_t S, bool with_D) {
+    const GraphData &g = S->tree->g;
+    auto L = std::make_unique<AmgLevel>();
+    L->n = g.n;
+    L->nnz = S->s_nnz;
+    L->ptr.alloc(g.n + 1);
+    L->col.alloc(S->s_nnz);
+    L->w64.alloc(S->s_nnz);
+    copy_d(ctx, L->ptr.p, S->s_ptr.p, (g.n + 1) * sizeof(int32_t));
+    copy_d(ctx, L->col.p, S->s_col.p, S->s_nnz * sizeof(int32_t));
+    copy_d(ctx, L->w64.p, S->s_w64.p, S->s_nnz * sizeof(double));
+    L->D64.alloc(g.n);
+    if (with_D) copy_d(ctx, L->D64.p, g.D64.p, g.n * sizeof(double));
+    else memset_d(ctx, L->D64.p, 0, g.n * sizeof(double));
+    L->diag64.alloc(g.n);
+    launch(ctx, k_amg_diag, cdiv(g.n, kBlock), kBlock, 0, g.n, (const int32_t *)L->ptr.p,
+           (const double *)L->w64.p, (const double *)L->D64.p, L->diag64.p);
+    return L;
+}
+
+// aggregate level L into a new coarse level
+std::unique_ptr<AmgLevel> coarsen(grass_ctx_t ctx, AmgLevel &L) {
+    const int64_t n = L.n;
+    DBuf<int32_t> mate, cand, anchor, leader, jslot, jcount;
+    mate.alloc(n);
+    cand.alloc(n);
+    anchor.alloc(n);
+    leader.alloc(n);
+    jslot.alloc(n);
+    jcount.alloc(n);
+    memset_d(ctx, mate.p, 0xFF, n * sizeof(int32_t));     // -1
+    memset_d(ctx, jslot.p, 0xFF, n * sizeof(int32_t));
+    int *changed = ctx->flags.p + 4;
+    const int64_t g = cdiv(n, kBlock);
+    for (int round = 0; round < kMatchRounds; ++round) {
+        memset_d(ctx, changed, 0, sizeof(int));
+        launch(ctx, k_amg_cand, g, kBlock, 0, n, (const int32_t *)L.ptr.p, (const int32_t *)L.col.p,
+               (const double *)L.w64.p, (const int32_t *)mate.p, cand.p);
+        launch(ctx, k_amg_pair, g, kBlock, 0, n, (const int32_t *)cand.p, mate.p, changed);
+        int ch = 0;
+        d2h(ctx, &ch, changed, sizeof(int));
+        if (!ch) break;
+    }
+    launch(ctx, k_amg_join, g, kBlock, 0, n, (const int32_t *)L.ptr.p, (const int32_t *)L.col.p,
+           (const double *)L.w64.p, (const int32_t *)mate.p, anchor.p, leader.p);
+    launch(ctx, k_amg_slots, g, kBlock, 0, n, (const int32_t *)L.ptr.p, (const int32_t *)L.col.p,
+           (const int32_t *)mate.p, (const int32_t *)anchor.p, jslot.p, jcount.p);
+    DBuf<int64_t> flag, pos;
+    flag.alloc(n + 1);
+    pos.alloc(n + 1);
+    launch(ctx, k_amg_leadflag, g, kBlock, 0, n, (const int32_t *)leader.p, flag.p);
+    int64_t nc = 0;
+    scan_i64(ctx, flag.p, pos.p, n, &nc);
+    auto C = std::make_unique<AmgLevel>();
+    C->n = nc;
+    L.agg.alloc(n);
+    DBuf<int64_t> mcnt, moff;
+    mcnt.alloc(nc + 1);
+    moff.alloc(nc + 1);
+    launch(ctx, k_amg_agg, g, kBlock, 0, n, (const int32_t *)leader.p, (const int64_t *)pos.p,
+           (const int32_t *)mate.p, (const int32_t *)jcount.p, L.agg.p, mcnt.p);
+    int64_t nm = 0;
+    scan_i64(ctx, mcnt.p, moff.p, nc, &nm);
+    if (nm != n) fail(GRASS_ERR_CUDA, "multigrid aggregation lost vertices");
+    L.mem.alloc(n);
+    L.mptr.alloc(nc + 1);
+    launch(ctx, k_amg_members, g, kBlock, 0, n, (const int32_t *)leader.p, (const int32_t *)mate.p,
+           (const int32_t *)anchor.p, (const int32_t *)jslot.p, (const int32_t *)jcount.p,
+           (const int32_t *)L.agg.p, (const int64_t *)moff.p, L.mem.p);
+    launch(ctx, k_i64_to_i32, cdiv(nc + 1, kBlock), kBlock, 0, nc + 1, (const int64_t *)moff.p,
+           L.mptr.p);
+    // coarse matrix
+    const int64_t gc = cdiv(nc, kBlock);
+    DBuf<int64_t> ccnt, coff;
+    ccnt.alloc(nc + 1);
+    coff.alloc(nc + 1);
+    launch(ctx, k_amg_ccount, gc, kBlock, 0, nc, (const int32_t *)L.mptr.p, (const int32_t *)L.mem.p,
+           (const int32_t *)L.ptr.p, (const int32_t *)L.col.p, (const int32_t *)L.agg.p, ccnt.p);
+    int64_t cnnz = 0;
+    scan_i64(ctx, ccnt.p, coff.p, nc, &cnnz);
+    C->nnz = cnnz;
+    C->ptr.alloc(nc + 1);
+    C->col.alloc(cnnz);
+    C->w64.alloc(cnnz);
+    C->D64.alloc(nc);
+    C->diag64.alloc(nc);
+    launch(ctx, k_amg_cfill, gc, kBlock, 0, nc, (const int32_t *)L.mptr.p, (const int32_t *)L.mem.p,
+           (const int32_t *)L.ptr.p, (const int32_t *)L.col.p, (const double *)L.w64.p,
+           (const double *)L.D64.p, (const int32_t *)L.agg.p, (const int64_t *)coff.p, C->ptr.p,
+           C->col.p, C->w64.p, C->D64.p, C->diag64.p);
+    return C;
+}
+
+__global__ void k_sum_d(int64_t n, const double *D, double *out) {
+    // one block: deterministic sum of a small vector
+    __shared__ double sh[kBlock];
+    double s = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += D[i];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+        if (threadIdx.x < k) sh[threadIdx.x] += sh[threadIdx.x + k];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = sh[0];
+}
+
+}  // namespace
+
+AmgHier &amg_get(grass_ctx_t ctx, grass_sparsifier_t S, bool with_D) {
+    auto &slot = S->amg[with_D ? 1 : 0];
+    if (slot) return *slot;
+    if (S->is_tree || S->s_nnz == 0) fail(GRASS_ERR_INVALID, "multigrid needs a sparsifier with off-tree edges");
+    auto H = std::make_unique<AmgHier>();
+    H->lv.push_back(level0(ctx, S, with_D));
+    while (H->lv.back()->n > kCoarse) {
+        if ((int)H->lv.size() >= kMaxLevels) fail(GRASS_ERR_CUDA, "multigrid: too many levels");
+        auto C = coarsen(ctx, *H->lv.back());
+        if (C->n > H->lv.back()->n * 95 / 100)
+            fail(GRASS_ERR_CUDA, "multigrid coarsening stalled at " + std::to_string(C->n) + " vertices");
+        H->lv.push_back(std::move(C));
+    }
+    // FP32 copies and V-cycle vectors
+    for (size_t l = 0; l < H->lv.size(); ++l) {
+        AmgLevel &L = *H->lv[l];
+        L.w32.alloc(std::max<int64_t>(L.nnz, 1));
+        L.diag32.alloc(L.n);
+        launch(ctx, k_amg_f32, cdiv(L.nnz, kBlock), kBlock, 0, L.nnz, (const double *)L.w64.p, L.w32.p);
+        launch(ctx, k_amg_f32, cdiv(L.n, kBlock), kBlock, 0, L.n, (const double *)L.diag64.p,
+               L.diag32.p);
+        if (l > 0) {
+            L.vb.alloc(L.n * sizeof(double) + 256);
+            L.vx.alloc(L.n * sizeof(double) + 256);
+        }
+        L.vt.alloc(L.n * sizeof(double) + 256);
+    }
+    // coarsest: dense (grounded) inverse
+    AmgLevel &Lc = *H->lv.back();
+    H->nc = Lc.n;
+    double *dsum = ctx->scal.p + DS_RED + 51;
+    launch(ctx, k_sum_d, 1, kBlock, 0, Lc.n, (const double *)Lc.D64.p, dsum);
+    double ds = 0.0;
+    d2h(ctx, &ds, dsum, sizeof(double));
+    H->singular = !(ds > 0.0);
+    H->cinv64.alloc(Lc.n * Lc.n);
+    H->cinv32.alloc(Lc.n * Lc.n);
+    launch(ctx, k_amg_dense, cdiv(Lc.n, kBlock), kBlock, 0, Lc.n, (const int32_t *)Lc.ptr.p,
+           (const int32_t *)Lc.col.p, (const double *)Lc.w64.p, (const double *)Lc.diag64.p,
+           H->singular ? 1 : 0, H->cinv64.p);
+    launch(ctx, k_amg_gauss_jordan, 1, 1024, 0, Lc.n, H->cinv64.p, H->singular ? 1 : 0);
+    launch(ctx, k_amg_f32, cdiv(Lc.n * Lc.n, kBlock), kBlock, 0, Lc.n * Lc.n,
+           (const double *)H->cinv64.p, H->cinv32.p);
+    ctx->sync();
+    slot = std::move(H);
+    return *slot;
+}
+
+// ---------------------------------------------------------------- V-cycle
+
+template <typename T>
+static void vcycle_T(grass_ctx_t ctx, AmgHier &H, size_t l, const T *b, T *x, int nu) {
+    AmgLevel &L = *H.lv[l];
+    const int64_t n = L.n;
+    const int64_t g = cdiv(n, kBlock);
+    if (l + 1 == H.lv.size()) {
+        const T *ci;
+        if constexpr (sizeof(T) == 8) ci = H.cinv64.p;
+        else ci = H.cinv32.p;
+        launch(ctx, k_coarse_apply<T>, 1, kBlock, 0, n, ci, b, x);
+        return;
+    }
+    const int32_t *ptr = L.ptr.p, *col = L.col.p;
+    const T *w = lvl_w<T>(L), *diag = lvl_diag<T>(L);
+    // the sweeps alternate between x and t; `cur` holds the iterate.  With
+    // nu sweeps before and nu after (2 nu in all, an even count) the last
+    // one ends in x.
+    T *t = reinterpret_cast<T *>(L.vt.p);
+    T *cur = x, *nxt = t;
+    launch(ctx, k_jac0<T>, g, kBlock, 0, n, b, diag, cur);           // pre-smoothing from 0
+    for (int s = 1; s < nu; ++s) {
+        launch(ctx, k_jac<T>, g, kBlock, 0, n, ptr, col, w, diag, b, (const T *)cur, nxt);
+        std::swap(cur, nxt);
+    }
+    AmgLevel &C = *H.lv[l + 1];
+    T *bc = reinterpret_cast<T *>(C.vb.p), *xc = reinterpret_cast<T *>(C.vx.p);
+    launch(ctx, k_res_restrict<T>, cdiv(C.n, kBlock), kBlock, 0, C.n, (const int32_t *)L.mptr.p,
+           (const int32_t *)L.mem.p, ptr, col, w, diag, b, (const T *)cur, bc);
+    vcycle_T<T>(ctx, H, l + 1, bc, xc, nu);
+    launch(ctx, k_prolong<T>, g, kBlock, 0, n, (const int32_t *)L.agg.p, (const T *)xc, cur);
+    for (int s = 0; s < nu; ++s) {
+        launch(ctx, k_jac<T>, g, kBlock, 0, n, ptr, col, w, diag, b, (const T *)cur, nxt);
+        std::swap(cur, nxt);
+    }
+    if (cur != x) copy_d(ctx, x, cur, n * sizeof(T));
+}
+
+void amg_vcycle(grass_ctx_t ctx, grass_sparsifier_t S, bool with_D, grass_prec prec, const void *r,
+                void *z) {
+    AmgHier &H = amg_get(ctx, S, with_D);
+    if (prec == GRASS_FP64) vcycle_T<double>(ctx, H, 0, (const double *)r, (double *)z, ctx->amg_sweeps);
+    else vcycle_T<float>(ctx, H, 0, (const float *)r, (float *)z, ctx->amg_sweeps);
+}
+
+// ---------------------------------------------------------------- CG on L_S
+
+__global__ void k_amg_center(int64_t n, double *y, const double *sum) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[i] -= *sum / (double)n;
+}
+
+__global__ void k_amg_ones(int64_t n, double *o) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) o[i] = 1.0;
+}
+
+// x += a p, r -= a q (a = num / den)
+__global__ void k_amg_axpy(int64_t n, const double *num, const double *den, double *x, double *r,
+                           const double *p, const double *q) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double a = *num / *den;
+    x[i] += a * p[i];
+    r[i] -= a * q[i];
+}
+
+// p = z + (num / den) p
+__global__ void k_amg_p(int64_t n, const double *num, const double *den, const double *z, double *p) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = z[i] + (*num / *den) * p[i];
+}
+
+int amg_cg_lap(grass_ctx_t ctx, grass_sparsifier_t S, const double *y, double *x, double tol,
+               int maxit) {
+    const int64_t n = S->tree->g.n;
+    const int64_t g = cdiv(n, kBlock);
+    amg_get(ctx, S, false);
+    double *r = ctx->scr<double>(SCR_PART_X, n);
+    double *z = ctx->scr<double>(SCR_PART_Y, n);
+    double *p = ctx->scr<double>(SCR_PART_1, n);
+    double *q = ctx->scr<double>(SCR_SIM_E, n);
+    double *ones = ctx->scr<double>(SCR_TMP3, n);
+    double *sc = ctx->scal.p + DS_RED + 52;     // [52..57] scalars of this solve
+    launch(ctx, k_amg_ones, g, kBlock, 0, n, ones);
+    copy_d(ctx, r, y, n * sizeof(double));
+    dot_cols(ctx, 1, GRASS_FP64, n, r, ones, sc);
+    launch(ctx, k_amg_center, g, kBlock, 0, n, r, (const double *)sc);
+    memset_d(ctx, x, 0, n * sizeof(double));
+    dot_cols(ctx, 1, GRASS_FP64, n, r, r, sc + 1);       // ||y||^2
+    double yy = 0.0;
+    d2h(ctx, &yy, sc + 1, sizeof(double));
+    if (!(yy > 0.0)) return 0;
+    amg_vcycle(ctx, S, false, GRASS_FP64, r, z);
+    copy_d(ctx, p, z, n * sizeof(double));
+    dot_cols(ctx, 1, GRASS_FP64, n, r, z, sc + 2);       // r.z
+    const void *w = S->s_w64.p;
+    int k = 0;
+    for (; k < maxit; ++k) {
+        lap_mm(ctx, 1, GRASS_FP64, n, S->s_nnz, S->s_ptr.p, S->s_col.p, w, nullptr, p, q, nullptr,
+               GRASS_KF_SPMM_S);
+        dot_cols(ctx, 1, GRASS_FP64, n, p, q, sc + 3);
+        launch(ctx, k_amg_axpy, g, kBlock, 0, n, (const double *)(sc + 2), (const double *)(sc + 3),
+               x, r, (const double *)p, (const double *)q);
+        dot_cols(ctx, 1, GRASS_FP64, n, r, r, sc + 4);
+        double rr = 0.0;
+        d2h(ctx, &rr, sc + 4, sizeof(double));
+        if (std::sqrt(rr) <= tol * std::sqrt(yy)) {
+            ++k;
+            break;
+        }
+        amg_vcycle(ctx, S, false, GRASS_FP64, r, z);
+        dot_cols(ctx, 1, GRASS_FP64, n, r, z, sc + 5);
+        launch(ctx, k_amg_p, g, kBlock, 0, n, (const double *)(sc + 5), (const double *)(sc + 2),
+               (const double *)z, p);
+        copy_d(ctx, sc + 2, sc + 5, sizeof(double));
+    }
+    return k;
+}
+
+}  // namespace grass

@@ -380,6 +380,15 @@ grass_status grass_ctx_set_param(grass_ctx_t ctx, const char *name, int64_t valu
     } else if (k == "similarity_check") {
         need(value == 0 || value == 1, "similarity_check must be 0 or 1");
         ctx->similarity_check = (int)value;
+    } else if (k == "pcg_precond") {
+        need(value == 0 || value == 1, "pcg_precond must be 0 or 1");
+        ctx->pcg_precond = (int)value;
+    } else if (k == "amg_sweeps") {
+        need(value >= 1 && value <= 8, "amg_sweeps must be in [1, 8]");
+        ctx->amg_sweeps = (int)value;
+    } else if (k == "lmax_amg") {
+        need(value == 0 || value == 1, "lmax_amg must be 0 or 1");
+        ctx->lmax_amg = (int)value;
     } else if (k == "euler_max_n") {
         need(value >= 0, "euler_max_n must be >= 0");
         ctx->euler_max_n = value;

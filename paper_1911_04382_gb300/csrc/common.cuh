@@ -8,6 +8,7 @@
 #include <algorithm>
 #include <cstdint>
 #include <cstring>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -72,7 +73,7 @@ enum ScratchSlot {
     SCR_FILTER, SCR_FILTER2, SCR_HEAT, SCR_LMAX_V, SCR_LMAX_Y, SCR_PART2,
     SCR_EU_S, SCR_EU_C, SCR_EU_P, SCR_EU_A, SCR_CG_XP,
     SCR_SIM_V, SCR_SIM_E, SCR_SIM_C,
-    SCR_PART_X, SCR_PART_Y, SCR_PART_1,
+    SCR_PART_X, SCR_PART_Y, SCR_PART_1, SCR_AMG_Y, SCR_AMG_X, SCR_ONES,
     SCR_COUNT
 };
 
@@ -110,6 +111,9 @@ struct grass_ctx_s {
     int64_t tree_tail_items = 2048;
     int euler_solve = 1;   // scan form for grounded r = 1 solves without D
     int similarity_check = 0;   // 1: Sec. IV-D step 6 in grass_densify (endpoint conflicts)
+    int pcg_precond = 0;        // 1: the sparsifier's multigrid V-cycle preconditions PCG
+    int amg_sweeps = 2;         // Jacobi sweeps before and after each coarse correction
+    int lmax_amg = 0;           // 1: lambda_max estimates solve L_S by multigrid-preconditioned CG
     int64_t euler_max_n = 4000000;   // trees larger than this keep the elimination rounds
     // co-resident grid of each cooperative kernel shape, per context (no
     // process-wide state: contexts may run on different host threads)
@@ -262,6 +266,7 @@ struct GraphData {
     DBuf<double> D64;                 // [n] diagonal load
     DBuf<float> D32;
     DBuf<double> degG;                // [n] weighted degree (Laplacian diagonal)
+    bool lap_only = false;            // D = 0 everywhere: A is a graph Laplacian (singular)
     // a batch of independent graphs stored as one block-diagonal matrix:
     // graph k owns vertices [seg_voff[k], seg_voff[k+1]) and edge ids
     // [seg_eoff[k], seg_eoff[k+1]); one segment for a single graph
@@ -341,6 +346,30 @@ struct EulerTour {
     DBuf<float> ipw32_pre;
 };
 
+// Aggregation multigrid hierarchy of the sparsifier's matrix L_S (+ D)
+// (amg.cu).  Level 0 is S itself; each coarser level is the exact Galerkin
+// product P^T M P for the piecewise-constant aggregation P: the contracted
+// graph (edges between different aggregates kept, repeated pairs kept as
+// separate entries) with the aggregates' summed diagonal loads.
+struct AmgLevel {
+    int64_t n = 0, nnz = 0;
+    DBuf<int32_t> ptr, col;           // off-diagonal adjacency (a column may repeat)
+    DBuf<double> w64, diag64, D64;    // weights, diagonal = weighted degree + D, D
+    DBuf<float> w32, diag32;
+    DBuf<int32_t> agg;                // [n] coarse vertex of each vertex (not on the coarsest)
+    DBuf<int32_t> mptr, mem;          // members of coarse vertex c: mem[mptr[c] .. mptr[c+1])
+    DBuf<char> vb, vx, vt;            // V-cycle vectors of this level (coarse levels)
+};
+
+struct AmgHier {
+    std::vector<std::unique_ptr<AmgLevel>> lv;
+    bool singular = false;            // D = 0: the coarsest solve is grounded
+    int64_t nc = 0;                   // coarsest size
+    DBuf<double> cinv64;              // coarsest (grounded) inverse, dense row-major
+    DBuf<float> cinv32;
+    DBuf<char> t0;                    // level-0 scratch vector
+};
+
 }  // namespace grass
 
 struct grass_tree_s {
@@ -382,6 +411,9 @@ struct grass_sparsifier_s {
     grass::DBuf<int32_t> p_ptr, p_col;
     grass::DBuf<double> p_w64;
     grass::DBuf<float> p_w32;
+    // multigrid hierarchies of L_S ([0]) and L_S + D ([1]), built on first
+    // use after each change of S
+    std::unique_ptr<grass::AmgHier> amg[2];
 };
 
 namespace grass {
@@ -405,6 +437,9 @@ void dot_cols(grass_ctx_t ctx, int r, grass_prec prec, int64_t n, const void *A,
 void d2h(grass_ctx_t ctx, void *dst, const void *src, size_t bytes);
 void h2d(grass_ctx_t ctx, void *dst, const void *src, size_t bytes);
 void memset_d(grass_ctx_t ctx, void *p, int v, size_t bytes);
+// v -= mean(v) (FP64, deterministic sum): the projection on the complement
+// of the all-ones vector, the range of a graph Laplacian
+void project_ones(grass_ctx_t ctx, int64_t n, double *v);
 void copy_d(grass_ctx_t ctx, void *dst, const void *src, size_t bytes);
 
 // ---------------------------------------------------------------- per-module entry points
@@ -454,6 +489,21 @@ int64_t s_solve(grass_ctx_t ctx, grass_sparsifier_t S, bool with_D, int r, grass
 void pcg_solve(grass_ctx_t ctx, grass_sparsifier_t S, const double *b, double *x, double tol,
                int maxit, grass_prec prec, double refine_tol, double inner_tol, int inner_maxit,
                grass_solve_stats_t *st);
+
+// ---------------------------------------------------------------- amg.cu
+
+// The hierarchy of L_S (+ D with with_D), built on first use (S must not be
+// the tree alone).
+grass::AmgHier &amg_get(grass_ctx_t ctx, grass_sparsifier_t S, bool with_D);
+// z = V-cycle(r): one multigrid V-cycle on L_S (+ D) from zero, r and z
+// device vectors of n elements in prec (may not alias).
+void amg_vcycle(grass_ctx_t ctx, grass_sparsifier_t S, bool with_D, grass_prec prec, const void *r,
+                void *z);
+// x = L_S^+ y (D = 0; y projected on the complement of 1) by CG
+// preconditioned by the V-cycle, until ||r|| <= tol ||y||; FP64; returns
+// iterations (maxit when the cap was reached).
+int amg_cg_lap(grass_ctx_t ctx, grass_sparsifier_t S, const double *y, double *x, double tol,
+               int maxit);
 
 // ---------------------------------------------------------------- api.cu helpers
 

@@ -95,6 +95,8 @@ void sparsifier_rebuild(grass_ctx_t ctx, grass_sparsifier_t S) {
                S->s_col.p, S->s_w64.p, S->s_w32.p);
     }
     S->pre_ok = false;
+    S->amg[0].reset();
+    S->amg[1].reset();
 }
 
 __global__ void k_mark(int64_t cnt, const int64_t *eids, int64_t m, uint8_t *in_s, int *flags) {

@@ -211,6 +211,13 @@ void graph_extract(grass_ctx_t ctx, const grass_csr_t *A, GraphData &g) {
         g.seg_voff = {0, n};
         g.seg_eoff = {0, m};
     }
+    // a pure graph Laplacian (no diagonal load anywhere)?
+    unsigned long long *mb = (unsigned long long *)(ctx->scal.p + DS_MAX + 12);
+    memset_d(ctx, mb, 0, sizeof(unsigned long long));
+    max_abs_bits(ctx, GRASS_FP64, n, g.D64.p, mb);
+    unsigned long long bits = 0;
+    d2h(ctx, &bits, mb, sizeof(bits));
+    g.lap_only = bits == 0;
 }
 
 }  // namespace grass

@@ -797,6 +797,22 @@ __global__ void k_acc_iters(int r, const double *cg_it, double *acc) {
     *acc += m;
 }
 
+__global__ void k_f2d(int64_t n, const float *a, double *b) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = (double)a[i];
+}
+
+__global__ void k_d2f(int64_t n, const double *a, float *b) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = (float)a[i];
+}
+
+// the inner-solve accumulators: iterations, and solves that reached the cap
+__global__ void k_note_solve(double *acc, double its, double capped) {
+    acc[0] += its;
+    acc[1] += capped;
+}
+
 int64_t s_solve(grass_ctx_t ctx, grass_sparsifier_t S, bool with_D, int r, grass_prec prec,
                 const void *Y, void *X, double tol, int maxit, unsigned long long *maxbits) {
     grass_tree_t T = S->tree;
@@ -807,6 +823,23 @@ int64_t s_solve(grass_ctx_t ctx, grass_sparsifier_t S, bool with_D, int r, grass
     if (S->is_tree) {
         copy_d(ctx, X, Y, total * es);
         tree_solve_inplace(ctx, T, f, r, prec, X, maxbits);
+        return 0;
+    }
+    if (ctx->lmax_amg && !with_D && r == 1) {
+        // one column of L_S^+ by multigrid-preconditioned CG in FP64
+        const double *y64 = (const double *)Y;
+        double *x64 = (double *)X;
+        if (prec == GRASS_FP32) {
+            double *yb = ctx->scr<double>(SCR_AMG_Y, n);
+            launch(ctx, k_f2d, cdiv(n, kBlock), kBlock, 0, n, (const float *)Y, yb);
+            y64 = yb;
+            x64 = ctx->scr<double>(SCR_AMG_X, n);
+        }
+        const int its = amg_cg_lap(ctx, S, y64, x64, tol, maxit);
+        if (prec == GRASS_FP32) launch(ctx, k_d2f, cdiv(n, kBlock), kBlock, 0, n, (const double *)x64, (float *)X);
+        if (maxbits) max_abs_bits(ctx, prec, n, X, maxbits);
+        launch(ctx, k_note_solve, 1, 1, 0, ctx->scal.p + DS_RED + DS_ITER, (double)its,
+               its >= maxit ? 1.0 : 0.0);
         return 0;
     }
     if (ctx->num_sms > 0) {
@@ -1354,20 +1387,27 @@ static int pcg_core(grass_ctx_t ctx, grass_sparsifier_t S, grass_prec prec, cons
     grass_tree_t Tr = S->tree;
     const GraphData &g = Tr->g;
     const int64_t n = g.n;
-    const bool flexible = !S->is_tree && inner_maxit > 0;
+    // the sparsifier's multigrid V-cycle: a fixed SPD preconditioner (plain
+    // PCG update); else the tree solve or the inner CG (flexible update)
+    const bool amg = ctx->pcg_precond == 1 && !S->is_tree;
+    const bool flexible = !amg && !S->is_tree && inner_maxit > 0;
     double *sc = ctx->scal.p + DS_RED;
     T *r = ctx->scr<T>(SCR_PCG_R, n);
     T *z = ctx->scr<T>(SCR_PCG_Z, n);
     T *p = ctx->scr<T>(SCR_PCG_P, n);
     T *q = ctx->scr<T>(SCR_PCG_Q, n);
     T *zold = ctx->scr<T>(SCR_PCG_ZOLD, n);
-    if (ctx->num_sms > 0) return pcg_fused<T>(ctx, S, rhs, e, r, z, p, q, zold, tol_abs, maxit,
-                                               inner_tol, inner_maxit);
+    if (ctx->num_sms > 0 && !amg) return pcg_fused<T>(ctx, S, rhs, e, r, z, p, q, zold, tol_abs, maxit,
+                                                       inner_tol, inner_maxit);
     const void *wA = prec == GRASS_FP64 ? (const void *)g.adj_w64.p : (const void *)g.adj_w32.p;
     const void *DA = prec == GRASS_FP64 ? (const void *)g.D64.p : (const void *)g.D32.p;
     int64_t grid = cdiv(n, kBlock);
     // inner_maxit = 0: the tree solve alone
     auto precond = [&]() -> int64_t {
+        if (amg) {
+            amg_vcycle(ctx, S, true, prec, r, z);
+            return 0;
+        }
         if (inner_maxit > 0) return s_solve(ctx, S, true, 1, prec, r, z, inner_tol, inner_maxit, nullptr);
         copy_d(ctx, z, r, n * sizeof(T));
         tree_solve_inplace(ctx, Tr, Tr->sdd, 1, prec, z, nullptr);
@@ -1450,6 +1490,10 @@ void pcg_solve(grass_ctx_t ctx, grass_sparsifier_t S, const double *b, double *x
         while (true) {
             if (rel <= tol || iters >= maxit || passes >= 64) break;
             double rnorm = rel * bnorm;
+            // a singular A (graph Laplacian): keep the pass's right-hand side in
+            // A's range, the complement of 1 (rounding puts a component along 1
+            // into r, which no correction can cancel)
+            if (g.lap_only) project_ones(ctx, n, r64);
             convert_block(ctx, GRASS_FP32, n, r64, r32);
             int it = pcg_core<float>(ctx, S, GRASS_FP32, r32, e32, refine_tol * rnorm,
                                      maxit - iters, inner_tol, inner_maxit, &inner);

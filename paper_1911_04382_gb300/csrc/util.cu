@@ -214,4 +214,22 @@ void dot_cols(grass_ctx_t ctx, int r, grass_prec prec, int64_t n, const void *A,
                (const float *)B, ctx->partials.p, ctx->counters.p + 1, out);
 }
 
+__global__ void k_ones64(int64_t n, double *o) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) o[i] = 1.0;
+}
+
+__global__ void k_sub_mean(int64_t n, double *v, const double *sum) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) v[i] -= *sum / (double)n;
+}
+
+void project_ones(grass_ctx_t ctx, int64_t n, double *v) {
+    double *ones = ctx->scr<double>(SCR_ONES, n);
+    double *sum = ctx->scal.p + DS_RED + 60;
+    launch(ctx, k_ones64, cdiv(n, kBlock), kBlock, 0, n, ones);
+    dot_cols(ctx, 1, GRASS_FP64, n, v, ones, sum);
+    launch(ctx, k_sub_mean, cdiv(n, kBlock), kBlock, 0, n, v, (const double *)sum);
+}
+
 }  // namespace grass
