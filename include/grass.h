@@ -157,6 +157,19 @@ grass_status grass_ctx_set_wait_limit(grass_ctx_t ctx, int64_t polls, int hold_b
  *   "similarity_check"    0 (default) or 1: grass_densify filters each
  *                         round's edges with the similarity check of
  *                         grass_filter_similar (Sec. IV-D step 6)
+ *   "pcg_precond"         0 (default): grass_pcg_solve's preconditioner is the
+ *                         tree solve / inner CG of inner_maxit; 1: one V-cycle
+ *                         of the sparsifier's aggregation multigrid for
+ *                         L_S + D (the sparsifier's solver; Sec. IV-C-1 and
+ *                         IV-D step 1 name multigrid for it), a fixed SPD
+ *                         preconditioner (plain PCG update), hierarchy built
+ *                         on first use after each change of S; also used by
+ *                         grass_fiedler's solves
+ *   "amg_sweeps"          weighted-Jacobi sweeps before and after each
+ *                         coarse correction of the V-cycle (1-8, default 1)
+ *   "lmax_amg"            0 (default) or 1: the lambda_max estimate's solves
+ *                         with L_S (one column) are CG preconditioned by the
+ *                         multigrid V-cycle of L_S, in FP64, to inner_tol
  *   "euler_max_n"         trees built on this context with more vertices
  *                         than this (default 4,000,000) get no Euler tour
  *                         and keep the elimination rounds (the tour's FP64

@@ -282,20 +282,33 @@ __global__ void k_jac(int64_t n, const int32_t *ptr, const int32_t *col, const T
     xo[v] = d > (T)0 ? x[v] + (T)kOmega * (b[v] - (d * x[v] - s)) / d : x[v];
 }
 
-// bc[c] = sum over members v (in member order) of (b - M x)_v
+// res = b - M x, one row per thread
 template <typename T>
-__global__ void k_res_restrict(int64_t nc, const int32_t *mptr, const int32_t *mem,
-                               const int32_t *ptr, const int32_t *col, const T *w, const T *diag,
-                               const T *b, const T *x, T *bc) {
+__global__ void k_residual(int64_t n, const int32_t *ptr, const int32_t *col, const T *w,
+                           const T *diag, const T *b, const T *x, T *res) {
+    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    T s = (T)0;
+    for (int32_t j = ptr[v]; j < ptr[v + 1]; ++j) s += w[j] * x[col[j]];
+    res[v] = b[v] - (diag[v] * x[v] - s);
+}
+
+// bc[c] = sum of res over the members of c, in member order (the first four
+// gathers issued together)
+template <typename T>
+__global__ void k_restrict(int64_t nc, const int32_t *mptr, const int32_t *mem, const T *res,
+                           T *bc) {
     int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= nc) return;
-    T acc = (T)0;
-    for (int32_t q = mptr[c]; q < mptr[c + 1]; ++q) {
-        const int32_t v = mem[q];
-        T s = (T)0;
-        for (int32_t j = ptr[v]; j < ptr[v + 1]; ++j) s += w[j] * x[col[j]];
-        acc += b[v] - (diag[v] * x[v] - s);
-    }
+    const int32_t q0 = mptr[c], q1 = mptr[c + 1];
+    T v[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] = q0 + k < q1 ? res[mem[q0 + k]] : (T)0;
+    T acc = v[0];
+#pragma unroll
+    for (int k = 1; k < 4; ++k)
+        if (q0 + k < q1) acc += v[k];
+    for (int32_t q = q0 + 4; q < q1; ++q) acc += res[mem[q]];
     bc[c] = acc;
 }
 
@@ -519,8 +532,9 @@ static void vcycle_T(grass_ctx_t ctx, AmgHier &H, size_t l, const T *b, T *x, in
     }
     AmgLevel &C = *H.lv[l + 1];
     T *bc = reinterpret_cast<T *>(C.vb.p), *xc = reinterpret_cast<T *>(C.vx.p);
-    launch(ctx, k_res_restrict<T>, cdiv(C.n, kBlock), kBlock, 0, C.n, (const int32_t *)L.mptr.p,
-           (const int32_t *)L.mem.p, ptr, col, w, diag, b, (const T *)cur, bc);
+    launch(ctx, k_residual<T>, g, kBlock, 0, n, ptr, col, w, diag, b, (const T *)cur, nxt);
+    launch(ctx, k_restrict<T>, cdiv(C.n, kBlock), kBlock, 0, C.n, (const int32_t *)L.mptr.p,
+           (const int32_t *)L.mem.p, (const T *)nxt, bc);
     vcycle_T<T>(ctx, H, l + 1, bc, xc, nu);
     launch(ctx, k_prolong<T>, g, kBlock, 0, n, (const int32_t *)L.agg.p, (const T *)xc, cur);
     for (int s = 0; s < nu; ++s) {
@@ -536,6 +550,155 @@ void amg_vcycle(grass_ctx_t ctx, grass_sparsifier_t S, bool with_D, grass_prec p
     if (prec == GRASS_FP64) vcycle_T<double>(ctx, H, 0, (const double *)r, (double *)z, ctx->amg_sweeps);
     else vcycle_T<float>(ctx, H, 0, (const float *)r, (float *)z, ctx->amg_sweeps);
 }
+
+// ---------------------------------------------------------------- PCG on A with the V-cycle
+// Device scalars s: [0] r.z, [1] p.q, [2] r.r, [3] new r.z, [4] go (1 while
+// the iteration goes on), [5] iterations done.  Every kernel of an
+// iteration reads `go`, so iterations replayed after convergence change
+// nothing.
+
+template <typename T>
+__global__ void k_ap_axpy(int64_t n, const double *s, T *x, T *r, const T *p, const T *q) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || s[4] == 0.0) return;
+    const T a = (T)(s[0] / s[1]);
+    x[i] += a * p[i];
+    r[i] -= a * q[i];
+}
+
+// one thread: count the iteration just done and decide whether to go on
+__global__ void k_ap_check(double *s, double tol2, double maxit) {
+    if (s[4] == 0.0) return;
+    s[5] += 1.0;
+    if (!(s[2] > tol2) || s[5] >= maxit) s[4] = 0.0;
+}
+
+template <typename T>
+__global__ void k_ap_p(int64_t n, const double *s, const T *z, T *p) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || s[4] == 0.0) return;
+    p[i] = z[i] + (T)(s[3] / s[0]) * p[i];
+}
+
+__global__ void k_ap_shift(double *s) {
+    if (s[4] != 0.0) s[0] = s[3];
+}
+
+__global__ void k_ap_init(double *s, double tol2) {
+    s[4] = s[2] > tol2 ? 1.0 : 0.0;
+    s[5] = 0.0;
+}
+
+template <typename T>
+int amg_pcg(grass_ctx_t ctx, grass_sparsifier_t S, const T *rhs, T *e, double tol_abs, int maxit) {
+    const GraphData &g = S->tree->g;
+    const int64_t n = g.n, gn = cdiv(n, kBlock);
+    const grass_prec prec = sizeof(T) == 8 ? GRASS_FP64 : GRASS_FP32;
+    amg_get(ctx, S, true);
+    T *r = ctx->scr<T>(SCR_PCG_R, n);
+    T *z = ctx->scr<T>(SCR_PCG_Z, n);
+    T *p = ctx->scr<T>(SCR_PCG_P, n);
+    T *q = ctx->scr<T>(SCR_PCG_Q, n);
+    double *s = ctx->scal.p + DS_RED + 24;        // [24 .. 29]
+    const void *wA = prec == GRASS_FP64 ? (const void *)g.adj_w64.p : (const void *)g.adj_w32.p;
+    const void *DA = prec == GRASS_FP64 ? (const void *)g.D64.p : (const void *)g.D32.p;
+    const double tol2 = tol_abs * tol_abs;
+    // the work runs on the context's capture stream, after the caller's work
+    if (!ctx->cap_stream) {
+        GCK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+        GCK(cudaEventCreateWithFlags(&ctx->cap_ev[0], cudaEventDisableTiming));
+        GCK(cudaEventCreateWithFlags(&ctx->cap_ev[1], cudaEventDisableTiming));
+    }
+    cudaStream_t user = ctx->stream;
+    const bool own = ctx->tfam == 0;              // kernel timing records events on the caller's stream
+    if (own) {
+        GCK(cudaEventRecord(ctx->cap_ev[0], user));
+        GCK(cudaStreamWaitEvent(ctx->cap_stream, ctx->cap_ev[0], 0));
+        ctx->stream = ctx->cap_stream;
+    }
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    auto iteration = [&]() {
+        lap_mm(ctx, 1, prec, n, 2 * g.m, g.adj_ptr.p, g.adj_col.p, wA, DA, p, q, nullptr,
+               GRASS_KF_SPMM_G);
+        dot_cols(ctx, 1, prec, n, p, q, s + 1);
+        launch(ctx, k_ap_axpy<T>, gn, kBlock, 0, n, (const double *)s, e, r, (const T *)p, (const T *)q);
+        dot_cols(ctx, 1, prec, n, r, r, s + 2);
+        launch(ctx, k_ap_check, 1, 1, 0, s, tol2, (double)maxit);
+        amg_vcycle(ctx, S, true, prec, r, z);
+        dot_cols(ctx, 1, prec, n, r, z, s + 3);
+        launch(ctx, k_ap_p<T>, gn, kBlock, 0, n, (const double *)s, (const T *)z, p);
+        launch(ctx, k_ap_shift, 1, 1, 0, s);
+    };
+    double st[2] = {0.0, 0.0};
+    try {
+        memset_d(ctx, e, 0, n * sizeof(T));
+        copy_d(ctx, r, rhs, n * sizeof(T));
+        dot_cols(ctx, 1, prec, n, r, r, s + 2);
+        launch(ctx, k_ap_init, 1, 1, 0, s, tol2);
+        amg_vcycle(ctx, S, true, prec, r, z);
+        copy_d(ctx, p, z, n * sizeof(T));
+        dot_cols(ctx, 1, prec, n, r, z, s);
+        d2h(ctx, st, s + 4, sizeof(st));
+        if (st[0] != 0.0 && maxit > 0) {
+            iteration();                          // plain: fills the shape caches
+            bool captured = false;
+            int64_t per = 0;
+            if (own) {
+                const int64_t l0 = ctx->launches;
+                if (cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+                    bool ok = true;
+                    try {
+                        iteration();
+                    } catch (...) {
+                        ok = false;
+                    }
+                    cudaError_t ce = cudaStreamEndCapture(ctx->stream, &graph);
+                    captured = ok && ce == cudaSuccess && graph &&
+                               cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
+                    if (!captured) cudaGetLastError();
+                } else {
+                    cudaGetLastError();
+                }
+                per = ctx->launches - l0;
+                ctx->launches = l0;
+            }
+            constexpr int kCheck = 8;
+            d2h(ctx, st, s + 4, sizeof(st));
+            while (st[0] != 0.0) {
+                for (int j = 0; j < kCheck; ++j) {
+                    if (captured) {
+                        GCK(cudaGraphLaunch(exec, ctx->stream));
+                        ctx->launches += per;
+                    } else {
+                        iteration();
+                    }
+                }
+                d2h(ctx, st, s + 4, sizeof(st));
+            }
+        }
+    } catch (...) {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        if (own) {
+            ctx->stream = user;
+            cudaEventRecord(ctx->cap_ev[1], ctx->cap_stream);
+            cudaStreamWaitEvent(user, ctx->cap_ev[1], 0);
+        }
+        throw;
+    }
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (own) {
+        ctx->stream = user;
+        GCK(cudaEventRecord(ctx->cap_ev[1], ctx->cap_stream));
+        GCK(cudaStreamWaitEvent(user, ctx->cap_ev[1], 0));
+    }
+    return (int)st[1];
+}
+
+template int amg_pcg<double>(grass_ctx_t, grass_sparsifier_t, const double *, double *, double, int);
+template int amg_pcg<float>(grass_ctx_t, grass_sparsifier_t, const float *, float *, double, int);
 
 // ---------------------------------------------------------------- CG on L_S
 

@@ -112,8 +112,13 @@ struct grass_ctx_s {
     int euler_solve = 1;   // scan form for grounded r = 1 solves without D
     int similarity_check = 0;   // 1: Sec. IV-D step 6 in grass_densify (endpoint conflicts)
     int pcg_precond = 0;        // 1: the sparsifier's multigrid V-cycle preconditions PCG
-    int amg_sweeps = 2;         // Jacobi sweeps before and after each coarse correction
+    int amg_sweeps = 1;         // Jacobi sweeps before and after each coarse correction
     int lmax_amg = 0;           // 1: lambda_max estimates solve L_S by multigrid-preconditioned CG
+    // a non-blocking stream of the context's own, on which multi-kernel
+    // iterations are captured into CUDA graphs and replayed (ordered with the
+    // caller's stream by events); created on first use
+    cudaStream_t cap_stream = nullptr;
+    cudaEvent_t cap_ev[2] = {nullptr, nullptr};
     int64_t euler_max_n = 4000000;   // trees larger than this keep the elimination rounds
     // co-resident grid of each cooperative kernel shape, per context (no
     // process-wide state: contexts may run on different host threads)
@@ -175,6 +180,9 @@ struct grass_ctx_s {
     }
     ~grass_ctx_s() {
         for (auto e : events) cudaEventDestroy(e);
+        for (auto e : cap_ev)
+            if (e) cudaEventDestroy(e);
+        if (cap_stream) cudaStreamDestroy(cap_stream);
     }
 
     template <typename T>
@@ -499,6 +507,11 @@ grass::AmgHier &amg_get(grass_ctx_t ctx, grass_sparsifier_t S, bool with_D);
 // device vectors of n elements in prec (may not alias).
 void amg_vcycle(grass_ctx_t ctx, grass_sparsifier_t S, bool with_D, grass_prec prec, const void *r,
                 void *z);
+// PCG on A = L_G + D with the V-cycle of L_S + D as the preconditioner, from
+// e = 0, until ||rhs - A e|| <= tol_abs (maxit iterations at most); one
+// iteration is captured into a CUDA graph and replayed.  Returns iterations.
+template <typename T>
+int amg_pcg(grass_ctx_t ctx, grass_sparsifier_t S, const T *rhs, T *e, double tol_abs, int maxit);
 // x = L_S^+ y (D = 0; y projected on the complement of 1) by CG
 // preconditioned by the V-cycle, until ||r|| <= tol ||y||; FP64; returns
 // iterations (maxit when the cap was reached).

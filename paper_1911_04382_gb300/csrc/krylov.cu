@@ -1397,8 +1397,9 @@ static int pcg_core(grass_ctx_t ctx, grass_sparsifier_t S, grass_prec prec, cons
     T *p = ctx->scr<T>(SCR_PCG_P, n);
     T *q = ctx->scr<T>(SCR_PCG_Q, n);
     T *zold = ctx->scr<T>(SCR_PCG_ZOLD, n);
-    if (ctx->num_sms > 0 && !amg) return pcg_fused<T>(ctx, S, rhs, e, r, z, p, q, zold, tol_abs, maxit,
-                                                       inner_tol, inner_maxit);
+    if (amg) return amg_pcg<T>(ctx, S, rhs, e, tol_abs, maxit);
+    if (ctx->num_sms > 0) return pcg_fused<T>(ctx, S, rhs, e, r, z, p, q, zold, tol_abs, maxit,
+                                               inner_tol, inner_maxit);
     const void *wA = prec == GRASS_FP64 ? (const void *)g.adj_w64.p : (const void *)g.adj_w32.p;
     const void *DA = prec == GRASS_FP64 ? (const void *)g.D64.p : (const void *)g.D32.p;
     int64_t grid = cdiv(n, kBlock);
