@@ -10,15 +10,16 @@ __device__ inline double scale_of(const unsigned long long *scale_from) {
 }
 
 // ---------------------------------------------------------------- row chunks
-// The r values of a vertex are one contiguous row of r*sizeof(T) bytes.
-// When that is a multiple of 16 bytes the row kernels move it in 16-byte
-// chunks (float4 / double2), L consecutive lanes per row, CPL chunks a lane;
-// otherwise (or when the block is not 16-byte aligned: ALIGNED = false) in
-// single elements.  L divides 32, so a row never straddles a warp.
-template <typename T, int R, bool ALIGNED = true>
+// The r values of a vertex are one contiguous row of r*sizeof(T) bytes.  The
+// row kernels move it in chunks of VB bytes: 32 (256-bit loads of sm_100
+// and later), 16 (float4 / double2), or single elements (VB = 0) -- the
+// widest that divides the row and that the block's alignment allows; L
+// consecutive lanes per row, CPL chunks a lane.  L divides 32, so a row
+// never straddles a warp.
+template <typename T, int R, int VB>
 struct RowLay {
-    static constexpr bool VEC = ALIGNED && (R * sizeof(T)) % 16 == 0;
-    static constexpr int EL = VEC ? int(16 / sizeof(T)) : 1;   // elements per chunk
+    static constexpr bool VEC = VB > 0 && (R * sizeof(T)) % VB == 0;
+    static constexpr int EL = VEC ? int(VB / sizeof(T)) : 1;   // elements per chunk
     static constexpr int C = R / EL;                          // chunks per row
     static constexpr int L = (C % 8 == 0) ? 8 : (C % 4 == 0) ? 4 : (C % 2 == 0) ? 2 : 1;
     static constexpr int CPL = C / L;                         // chunks per lane
@@ -32,13 +33,23 @@ struct RowChunk {
 template <typename T, int EL>
 __device__ __forceinline__ RowChunk<T, EL> ld_row_chunk(const T *p) {
     RowChunk<T, EL> c;
-    if constexpr (EL == 4) {
+    if constexpr (sizeof(T) == 4 && EL == 8) {
+        asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+            : "=f"(c.v[0]), "=f"(c.v[1]), "=f"(c.v[2]), "=f"(c.v[3]), "=f"(c.v[4]), "=f"(c.v[5]),
+              "=f"(c.v[6]), "=f"(c.v[7])
+            : "l"(p));
+    } else if constexpr (sizeof(T) == 8 && EL == 4) {
+        asm("ld.global.nc.v4.f64 {%0, %1, %2, %3}, [%4];"
+            : "=d"(c.v[0]), "=d"(c.v[1]), "=d"(c.v[2]), "=d"(c.v[3])
+            : "l"(p));
+    } else if constexpr (sizeof(T) == 4 && EL == 4) {
         const float4 q = __ldg(reinterpret_cast<const float4 *>(p));
         c.v[0] = q.x; c.v[1] = q.y; c.v[2] = q.z; c.v[3] = q.w;
-    } else if constexpr (EL == 2) {
+    } else if constexpr (sizeof(T) == 8 && EL == 2) {
         const double2 q = __ldg(reinterpret_cast<const double2 *>(p));
         c.v[0] = q.x; c.v[1] = q.y;
     } else {
+        static_assert(EL == 1, "chunk shape");
         c.v[0] = __ldg(p);
     }
     return c;
@@ -46,29 +57,54 @@ __device__ __forceinline__ RowChunk<T, EL> ld_row_chunk(const T *p) {
 
 template <typename T, int EL>
 __device__ __forceinline__ void st_row_chunk(T *p, const RowChunk<T, EL> &c) {
-    if constexpr (EL == 4) {
+    if constexpr (sizeof(T) == 4 && EL == 8) {
+        asm volatile("st.global.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p),
+                     "f"(c.v[0]), "f"(c.v[1]), "f"(c.v[2]), "f"(c.v[3]), "f"(c.v[4]), "f"(c.v[5]),
+                     "f"(c.v[6]), "f"(c.v[7])
+                     : "memory");
+    } else if constexpr (sizeof(T) == 8 && EL == 4) {
+        asm volatile("st.global.v4.f64 [%0], {%1, %2, %3, %4};" ::"l"(p), "d"(c.v[0]), "d"(c.v[1]),
+                     "d"(c.v[2]), "d"(c.v[3])
+                     : "memory");
+    } else if constexpr (sizeof(T) == 4 && EL == 4) {
         *reinterpret_cast<float4 *>(p) = make_float4(c.v[0], c.v[1], c.v[2], c.v[3]);
-    } else if constexpr (EL == 2) {
+    } else if constexpr (sizeof(T) == 8 && EL == 2) {
         *reinterpret_cast<double2 *>(p) = make_double2(c.v[0], c.v[1]);
     } else {
+        static_assert(EL == 1, "chunk shape");
         *p = c.v[0];
     }
 }
 
+inline bool aligned_to(const void *p, uintptr_t a) { return p == nullptr || ((uintptr_t)p & (a - 1)) == 0; }
+
+// chunk width for r columns of `es`-byte elements over the given blocks
+inline int chunk_bytes(int r, size_t es, std::initializer_list<const void *> blocks) {
+    for (int vb : {32, 16}) {
+        if ((r * es) % vb) continue;
+        bool ok = true;
+        for (const void *b : blocks) ok = ok && aligned_to(b, vb);
+        if (ok) return vb;
+    }
+    return 0;
+}
+
 // Y = s * (L X + D .* X), (L X)_i = sum_j w_ij (X_i - X_j) (Eq. formula_laplacian).
 // L lanes per row; each lane owns CPL chunks of the row and walks the row's
-// entries in batches of B = 4 (indices and weights first, then the four
-// gathers, then the sums), so a lane has several gathers in flight (larger
-// batches cost registers, and the occupancy lost outweighed the gain).
-template <typename T, int R, bool ALIGNED>
+// entries in batches of B (indices and weights first, then the B gathers,
+// then the sums), B chosen so that a lane has about 64 bytes of gathers in
+// flight (more cost registers, and the occupancy lost outweighed the gain).
+template <typename T, int R, int VB>
 __global__ void __launch_bounds__(256) k_lapmm(int64_t n, const int32_t *__restrict__ ptr,
                                                const int32_t *__restrict__ col,
                                                const T *__restrict__ w, const T *__restrict__ D,
                                                const T *__restrict__ X, T *__restrict__ Y,
                                                const unsigned long long *scale_from) {
-    using RL = RowLay<T, R, ALIGNED>;
+    using RL = RowLay<T, R, VB>;
     constexpr int EL = RL::EL, L = RL::L, CPL = RL::CPL;
-    constexpr int B = 4;
+    // neighbours per batch: about 64 bytes of gathers in flight per lane
+    constexpr int LB = CPL * EL * (int)sizeof(T);
+    constexpr int B = LB >= 64 ? 1 : LB >= 32 ? 2 : 4;
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t i = t / L;
     if (i >= n) return;
@@ -124,31 +160,34 @@ __global__ void __launch_bounds__(256) k_lapmm(int64_t n, const int32_t *__restr
     }
 }
 
-inline bool aligned16(const void *p) { return p == nullptr || ((uintptr_t)p & 15u) == 0; }
-
-template <typename T, int R, bool ALIGNED>
+template <typename T, int R, int VB>
 static void lapmm_T(grass_ctx_t ctx, int64_t n, const int32_t *ptr, const int32_t *col,
                     const void *w, const void *D, const void *X, void *Y,
                     const unsigned long long *sf) {
-    constexpr int L = RowLay<T, R, ALIGNED>::L;
-    launch(ctx, k_lapmm<T, R, ALIGNED>, cdiv(n * L, 256), 256, 0, n, ptr, col, (const T *)w,
+    constexpr int L = RowLay<T, R, VB>::L;
+    launch(ctx, k_lapmm<T, R, VB>, cdiv(n * L, 256), 256, 0, n, ptr, col, (const T *)w,
            (const T *)D, (const T *)X, (T *)Y, sf);
+}
+
+template <typename T, int R>
+static void lapmm_P(grass_ctx_t ctx, int64_t n, const int32_t *ptr, const int32_t *col,
+                    const void *w, const void *D, const void *X, void *Y,
+                    const unsigned long long *sf) {
+    // widest chunks that the row size and both blocks' alignment allow (a
+    // caller's block or a slice of one may be only element-aligned)
+    switch (chunk_bytes(R, sizeof(T), {X, Y})) {
+        case 32: lapmm_T<T, R, 32>(ctx, n, ptr, col, w, D, X, Y, sf); break;
+        case 16: lapmm_T<T, R, 16>(ctx, n, ptr, col, w, D, X, Y, sf); break;
+        default: lapmm_T<T, R, 0>(ctx, n, ptr, col, w, D, X, Y, sf); break;
+    }
 }
 
 template <int R>
 static void lapmm_R(grass_ctx_t ctx, grass_prec prec, int64_t n, const int32_t *ptr,
                     const int32_t *col, const void *w, const void *D, const void *X, void *Y,
                     const unsigned long long *sf) {
-    // 16-byte chunks need 16-byte aligned blocks (library scratch always is;
-    // a caller's block or a slice of one may not be)
-    const bool al = aligned16(X) && aligned16(Y);
-    if (prec == GRASS_FP64) {
-        if (al) lapmm_T<double, R, true>(ctx, n, ptr, col, w, D, X, Y, sf);
-        else lapmm_T<double, R, false>(ctx, n, ptr, col, w, D, X, Y, sf);
-    } else {
-        if (al) lapmm_T<float, R, true>(ctx, n, ptr, col, w, D, X, Y, sf);
-        else lapmm_T<float, R, false>(ctx, n, ptr, col, w, D, X, Y, sf);
-    }
+    if (prec == GRASS_FP64) lapmm_P<double, R>(ctx, n, ptr, col, w, D, X, Y, sf);
+    else lapmm_P<float, R>(ctx, n, ptr, col, w, D, X, Y, sf);
 }
 
 void lap_mm(grass_ctx_t ctx, int r, grass_prec prec, int64_t n, int64_t nnz, const int32_t *ptr,
@@ -223,13 +262,13 @@ void max_abs_bits(grass_ctx_t ctx, grass_prec prec, int64_t count, const void *X
 // next edge's endpoints and weight before it consumes this edge's row
 // gathers, which it issues G chunks of 16 bytes per endpoint at a time.
 // Every block ends with one atomicMax of its largest heat.
-template <typename T, int R, bool ALIGNED>
+template <typename T, int R, int VB>
 __global__ void __launch_bounds__(256) k_heat(int64_t moff, const int32_t *__restrict__ ou,
                                               const int32_t *__restrict__ ov,
                                               const T *__restrict__ ow, const T *__restrict__ H,
                                               const unsigned long long *scale_from,
                                               T *__restrict__ heat, unsigned long long *heatmax) {
-    using RL = RowLay<T, R, ALIGNED>;
+    using RL = RowLay<T, R, VB>;
     constexpr int EL = RL::EL, C = R / EL;
     // chunks per endpoint in flight together: at most four, dividing the row
     constexpr int G = C % 4 == 0 ? 4 : C % 3 == 0 ? 3 : C % 2 == 0 ? 2 : 1;
@@ -281,30 +320,34 @@ __global__ void __launch_bounds__(256) k_heat(int64_t moff, const int32_t *__res
     block_atomic_max(heatmax, mx);
 }
 
-template <typename T, int R, bool ALIGNED>
+template <typename T, int R, int VB>
 static void heat_T(grass_ctx_t ctx, grass_sparsifier_t S, const void *H,
                    const unsigned long long *sf, void *heat, unsigned long long *hm) {
     const int64_t moff = S->m_off;
     const int sms = ctx->num_sms > 0 ? ctx->num_sms : 152;
     int nb = 0;
-    GCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_heat<T, R, ALIGNED>, 256, 0));
+    GCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_heat<T, R, VB>, 256, 0));
     const int64_t grid = std::min<int64_t>(cdiv(moff, 256), (int64_t)sms * std::max(nb, 1));
     const T *ow = sizeof(T) == 8 ? (const T *)S->off_w64.p : (const T *)S->off_w32.p;
-    launch(ctx, k_heat<T, R, ALIGNED>, grid, 256, 0, moff, (const int32_t *)S->off_u.p,
+    launch(ctx, k_heat<T, R, VB>, grid, 256, 0, moff, (const int32_t *)S->off_u.p,
            (const int32_t *)S->off_v.p, ow, (const T *)H, sf, (T *)heat, hm);
+}
+
+template <typename T, int R>
+static void heat_P(grass_ctx_t ctx, grass_sparsifier_t S, const void *H,
+                   const unsigned long long *sf, void *heat, unsigned long long *hm) {
+    switch (chunk_bytes(R, sizeof(T), {H})) {
+        case 32: heat_T<T, R, 32>(ctx, S, H, sf, heat, hm); break;
+        case 16: heat_T<T, R, 16>(ctx, S, H, sf, heat, hm); break;
+        default: heat_T<T, R, 0>(ctx, S, H, sf, heat, hm); break;
+    }
 }
 
 template <int R>
 static void heat_R(grass_ctx_t ctx, grass_prec prec, grass_sparsifier_t S, const void *H,
                    const unsigned long long *sf, void *heat, unsigned long long *hm) {
-    const bool al = aligned16(H);
-    if (prec == GRASS_FP64) {
-        if (al) heat_T<double, R, true>(ctx, S, H, sf, heat, hm);
-        else heat_T<double, R, false>(ctx, S, H, sf, heat, hm);
-    } else {
-        if (al) heat_T<float, R, true>(ctx, S, H, sf, heat, hm);
-        else heat_T<float, R, false>(ctx, S, H, sf, heat, hm);
-    }
+    if (prec == GRASS_FP64) heat_P<double, R>(ctx, S, H, sf, heat, hm);
+    else heat_P<float, R>(ctx, S, H, sf, heat, hm);
 }
 
 void heat_offs(grass_ctx_t ctx, int r, grass_prec prec, grass_sparsifier_t S, const void *H,
