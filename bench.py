@@ -905,6 +905,9 @@ def main() -> int:
     ap.add_argument("--no-breakdown", action="store_true")
     ap.add_argument("--profile-step", action="store_true",
                     help="run exactly one step and exit (for ncu launch lists)")
+    ap.add_argument("--profile-amg", action="store_true",
+                    help="one warm and one NVTX-ranged ('amgpcg') multigrid-preconditioned PCG solve "
+                         "(FP32 + FP64 refinement, 1e-8) on the step's sparsifier, for ncu launch lists")
     ap.add_argument("--profile-kernel", choices=["cg", "tree", "pcg"], default=None,
                     help="one warm launch, then one timed launch of the kernel (for ncu captures)")
     ap.add_argument("--no-solve40m", action="store_true",
@@ -984,6 +987,26 @@ def main() -> int:
 
     if args.profile_kernel:
         return profile_kernel(G, ctx, args.profile_kernel, g, rp, col, val, v0d, w)
+
+    if args.profile_amg:
+        tree = G.grass_build_tree(ctx, rp, col, val, 0)
+        S, _ = G.grass_densify(ctx, tree, P, h0d, v0d)
+        G.grass_ctx_set_param(ctx, "pcg_precond", 1)
+        G.grass_pcg_solve(ctx, S, bd, x, w["pcg_tol"], w["pcg_maxit"], pcg_prec, w["refine_tol"],
+                          w["pcg_inner_tol"], 0)                       # warm: builds the hierarchy
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("amgpcg")
+        t0 = time.perf_counter()
+        s_, ps = G.grass_pcg_solve(ctx, S, bd, x, w["pcg_tol"], w["pcg_maxit"], pcg_prec,
+                                   w["refine_tol"], w["pcg_inner_tol"], 0)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        print(json.dumps({"profile_amg": True, "iters": ps.iters, "rel_resid_fp64": ps.rel_resid_fp64,
+                          "ms": 1e3 * (time.perf_counter() - t0)}), flush=True)
+        G.grass_sparsifier_destroy(S)
+        G.grass_tree_destroy(tree)
+        G.grass_ctx_destroy(ctx)
+        return 0
 
     if args.profile_step:
         e = step(rp, col, val, h0d, v0d, bd, x)
