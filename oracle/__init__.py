@@ -22,6 +22,9 @@ orchestration below follows the paper's steps in the paper's order:
 * Eq. (formula_heatratio_final): threshold theta_sigma = (sigma^2 lmin/lmax)^(2t+1).
 * Section IV-D: iterative densification.
 * Section V-A: PCG on L_G + D preconditioned by the sparsifier.
+* Section III-B: a low-stretch spanning tree (weight classes, shifted
+  low-diameter decompositions with SplitMix64 shifts) and the total stretch
+  st_T(G); pinned by ``tests/test_oracle_lsst.py``.
 
 Pinned by ``tests/test_oracle_pins.py`` against dense linear algebra,
 brute force and closed forms.  Unpinned parts (see the tests): the absolute
@@ -496,3 +499,159 @@ def fiedler(og: OGraph, tree: OTree, in_s: np.ndarray | None, x0: np.ndarray, it
         x = y / np.linalg.norm(y)
     qG, _ = quad_forms(og, np.ones(og.m, np.uint8), x)
     return x, (x >= 0).astype(np.uint8), float(qG[0]), total
+
+
+
+# --------------------------------------------------------------------------
+# Low-stretch spanning tree (Section III-B: the backbone the paper prefers to
+# a maximum-weight tree).  Construction in the manner of Alon, Karp, Peleg
+# and West: the edges fall into weight classes, heaviest first; within the
+# edges of classes <= c the clusters are repeatedly split by a low-diameter
+# decomposition (shifted breadth-first growth from cluster centres, after
+# Miller, Peng and Xu) and contracted, the growth edges forming the tree.
+# --------------------------------------------------------------------------
+
+_M64 = (1 << 64) - 1
+_GOLDEN = 0x9E3779B97F4A7C15
+_LEVEL_MUL = 0xD1B54A32D192ED03
+LSST_SHIFT_SCALE = 3    # shift = 3 x (leading zeros of a 64-bit draw)
+LSST_SHIFT_CAP = 20     # on the leading zeros
+
+
+def splitmix64(x: int) -> int:
+    """Output of the SplitMix64 generator (Steele, Lea and Flood, 2014)
+    whose state before the step is x: the state advances by the golden
+    gamma 0x9E3779B97F4A7C15, then two xor-shift-multiply rounds and a
+    final xor-shift mix it."""
+    z = (x + _GOLDEN) & _M64
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _M64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _M64
+    return z ^ (z >> 31)
+
+
+def lsst_shift(seed: int, cls: int, level: int, x: int) -> int:
+    """Integer shift of cluster x at (class, level): 3 times the number of
+    leading zero bits (at most 20) of the SplitMix64 output for the state
+    seed + (x + 1) G + (1000003 cls + level) H (mod 2^64), G the golden
+    gamma and H = 0xD1B54A32D192ED03.  P(shift >= 3k) = 2^-k: a geometric
+    stand-in for the exponential shifts of the decomposition."""
+    st = (seed + (x + 1) * _GOLDEN + (cls * 1000003 + level) * _LEVEL_MUL) & _M64
+    h = splitmix64(st)
+    lz = 64 - h.bit_length()
+    return LSST_SHIFT_SCALE * min(lz, LSST_SHIFT_CAP)
+
+
+def lsst_classes(ew: np.ndarray) -> np.ndarray:
+    """Weight class of each edge: emax - e, with e the binary exponent of w
+    (w = f 2^e, 1/2 <= f < 1) and emax the largest; class 0 holds the
+    heaviest edges and each class spans a factor of 2."""
+    _, e = np.frexp(np.asarray(ew, dtype=np.float64))
+    return (int(e.max()) - e).astype(np.int64)
+
+
+def lsst_ldd(X, A, B, E, ew, start):
+    """One low-diameter decomposition of the cluster graph whose vertices are
+    the cluster ids X and whose edges are (A[k], B[k]) with graph edge ids
+    E[k] (repeated pairs allowed).  start[x] is the round at which x would
+    start its own cluster.  Rounds t = 0, 1, ...:
+      1. an unclaimed cluster x adjacent to clusters claimed in round t-1
+         joins, among their centres, the one with the smallest
+         (start, centre id); it joins through the heaviest edge (smallest id
+         on equal weight) to a neighbour claimed in round t-1 by that centre;
+      2. every cluster still unclaimed whose start is t becomes a centre.
+    Returns (centre, when, via): dicts over X of the centre, the round of
+    the claim, and (non-centres only) the edge id it joined through."""
+    nbr = {int(x): [] for x in X}
+    for a, b, e in zip(A, B, E):
+        nbr[int(a)].append((int(b), int(e)))
+        nbr[int(b)].append((int(a), int(e)))
+    centre = {int(x): -1 for x in X}
+    when = {int(x): -1 for x in X}
+    via = {}
+    left = len(nbr)
+    t = 0
+    while left > 0:
+        joins = {}
+        for x, adj in nbr.items():
+            if centre[x] >= 0:
+                continue
+            best = None
+            for y, e in adj:
+                if centre[y] < 0 or when[y] != t - 1:
+                    continue
+                c = centre[y]
+                key = (start[c], c, -float(ew[e]), e)
+                if best is None or key < best:
+                    best = key
+            if best is not None:
+                joins[x] = best
+        for x, key in joins.items():
+            centre[x] = key[1]
+            when[x] = t
+            via[x] = key[3]
+            left -= 1
+        for x in nbr:
+            if centre[x] < 0 and start[x] == t:
+                centre[x] = x
+                when[x] = t
+                left -= 1
+        t += 1
+    return centre, when, via
+
+
+def low_stretch_tree(og: OGraph, seed: int = 1) -> np.ndarray:
+    """A low-stretch spanning tree of G (returns in_tree, uint8[m]).  For each
+    weight class c = 0, 1, ... (lsst_classes) and level = 0, 1, ...: take
+    the edges of classes <= c whose endpoints lie in different clusters
+    (every vertex starts as its own cluster, named by its id); stop the
+    class when there are none; else give each cluster x touched by them the
+    shift s_x = lsst_shift(seed, c, level, x) and the start S - s_x (S the
+    largest shift of the level), decompose (lsst_ldd), add every join edge
+    to the tree and rename every cluster by its centre."""
+    n, m = og.n, og.m
+    cls = lsst_classes(og.ew)
+    label = np.arange(n, dtype=np.int64)
+    in_tree = np.zeros(m, np.uint8)
+    for c in range(int(cls.max()) + 1):
+        level = 0
+        while True:
+            a = label[og.eu]
+            b = label[og.ev]
+            act = np.flatnonzero((cls <= c) & (a != b))
+            if act.shape[0] == 0:
+                break
+            X = np.unique(np.concatenate([a[act], b[act]]))
+            shift = {int(x): lsst_shift(seed, c, level, int(x)) for x in X}
+            S = max(shift.values())
+            start = {x: S - s for x, s in shift.items()}
+            centre, _, via = lsst_ldd(X, a[act], b[act], act, og.ew, start)
+            for e in via.values():
+                in_tree[e] = 1
+            label = np.array([centre.get(int(l), int(l)) for l in label], dtype=np.int64)
+            level += 1
+    return in_tree
+
+
+def total_stretch(og: OGraph, in_tree: np.ndarray) -> tuple[float, np.ndarray]:
+    """Stretch of every edge, w_e times the resistance of the tree path
+    between its endpoints (Section III-B; 1 for a tree edge), and their
+    sum st_T(G), by walking the paths of the tree oriented from vertex 0."""
+    tr = orient(og, in_tree, 0)
+    depth = np.zeros(og.n, np.int64)
+    dist = np.zeros(og.n)
+    for v in tr.order[1:]:
+        depth[v] = depth[tr.parent[v]] + 1
+        dist[v] = dist[tr.parent[v]] + 1.0 / tr.pw[v]
+    st = np.empty(og.m)
+    for e in range(og.m):
+        p, q = int(og.eu[e]), int(og.ev[e])
+        a, b = p, q
+        while depth[a] > depth[b]:
+            a = tr.parent[a]
+        while depth[b] > depth[a]:
+            b = tr.parent[b]
+        while a != b:
+            a = tr.parent[a]
+            b = tr.parent[b]
+        st[e] = og.ew[e] * (dist[p] + dist[q] - 2.0 * dist[a])
+    return float(st.sum()), st
