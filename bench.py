@@ -59,6 +59,19 @@ WORKLOADS = {
 FAMILIES = {"spmm_g": 1, "spmm_s": 2, "heat": 3, "tree": 4, "cg": 5, "pcg": 6, "spmm_blk": 7}
 
 
+def measured_peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def peak_hbm() -> float:
+    """Measured copy bandwidth (GB/s), else the 6800 GB/s fallback."""
+    return float(measured_peaks().get("hbm_gbs", 6800.0))
+
+
 def make_inputs(w: dict):
     from synth import graphs, rng
     if w["kind"] == "grid3d":
@@ -337,7 +350,7 @@ def solve_40m(G, w=SOLVE40M) -> dict:
 SERVE = dict(n_lo=1e4, n_hi=4.0e7, pool=12, seed=9, r=8, t=2, sigma2=100.0, rounds=1,
              lmax_iters=8, cap_frac=0.05, inner_tol=1e-2, inner_maxit=30, tol=1e-3,
              refine_tol=1e-3, pcg_inner_tol=1e-2, pcg_inner_maxit=1, maxit=5000,
-             requests=200, loads=(0.5, 0.8, 0.95), slots=4, capacity_requests=60)
+             requests=1000, loads=(0.5, 0.8, 0.95), slots=4, capacity_requests=60)
 
 
 def run_serve(G, args, w=SERVE) -> dict:
@@ -365,6 +378,9 @@ def run_serve(G, args, w=SERVE) -> dict:
                                 w["inner_maxit"])
     rs = np.random.default_rng(w["seed"])
     srv = G.Server(0, w["slots"], 0)
+    grid_sms = getattr(args, "serve_grid_sms", 0) or 0
+    srv.set_param("grid_sms", grid_sms)
+    n_req = getattr(args, "serve_requests", None) or w["requests"]
 
     def submit(j):
         e = pool[j]
@@ -388,10 +404,10 @@ def run_serve(G, args, w=SERVE) -> dict:
         res, bad, lat, span = collect([submit(int(j)) for j in picks], picks)
         capacity = len(res) / span
         loads = []
-        for f in w["loads"]:
+        for f in (w["loads"] if not getattr(args, "serve_capacity_only", False) else ()):
             rate = f * capacity
-            picks = rs.integers(0, len(pool), w["requests"])
-            gaps = rs.exponential(1.0 / rate, w["requests"])
+            picks = rs.integers(0, len(pool), n_req)
+            gaps = rs.exponential(1.0 / rate, n_req)
             t0 = time.perf_counter()
             due = t0 + np.cumsum(gaps)
             tickets = []
@@ -413,11 +429,18 @@ def run_serve(G, args, w=SERVE) -> dict:
         st = srv.stats()
     finally:
         srv.close()
+    if not loads:
+        return {"metric": "serve capacity", "value": capacity, "unit": "requests/s",
+                "higher_is_better": True, "grid_sms": grid_sms, "slots": w["slots"],
+                "n_errors": len(bad), "errors": bad[:5],
+                "capacity_latency_ms": {"p50": float(np.percentile(lat, 50)),
+                                        "max": float(lat.max())}}
     mid = loads[len(loads) // 2]
     return {"metric": "serve p50/p99 latency", "value": mid["p99_ms"], "unit": "ms (p99)",
             "higher_is_better": False, "p50_ms": mid["p50_ms"], "load_of_value": mid["load"],
             "capacity_rps": capacity, "loads": loads, "errors": bad[:5], "n_errors": len(bad),
-            "slots": w["slots"], "max_running": st["max_running"],
+            "slots": w["slots"], "max_running": st["max_running"], "grid_sms": grid_sms,
+            "requests_per_load": n_req,
             "pool_sizes": [p["g"].n for p in pool],
             "workload": "Poisson stream of sparsify+PCG requests, power-grid meshes (U[0.1,10] "
                         "wires, 1% vias of weight 100, pads U[1e-4,1e-2]), sizes log-uniform in "
@@ -872,6 +895,86 @@ def hair_comb(G, k: int = 200, add: int = 400) -> dict:
                              "400 edges (figure not reproduced by this reading; see DESIGN)"}
 
 
+def lsst_vs_mst(G, w: dict, P, g=None, h0d=None, v0d=None, bd=None, label: str = "") -> dict:
+    """The maximum-weight tree against the low-stretch tree (Sec. III-B) on
+    one workload: construction time, total stretch st_T(G), PCG with the
+    tree alone as preconditioner, and the densified sparsifier (rounds,
+    edges, lambda_max estimates) with its PCG, both under the step's
+    parameters."""
+    import torch
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    rp, col, val = d(g.rowptr), d(g.col), d(g.val)
+    pcg_prec = G.GRASS_FP32 if w["pcg"] == "fp32" else G.GRASS_FP64
+    out = {"workload": label}
+    ctx = G.grass_ctx_create(torch.cuda.current_stream())
+    try:
+        for kind in ("mst", "lsst"):
+            r_ = {}
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            if kind == "mst":
+                tree = G.grass_build_tree(ctx, rp, col, val, 0)
+            else:
+                tree, ls = G.grass_build_lsst(ctx, rp, col, val, 1, 0)
+                r_["construction"] = ls
+            torch.cuda.synchronize()
+            r_["build_ms"] = 1e3 * (time.perf_counter() - t0)
+            S = None
+            try:
+                t0 = time.perf_counter()
+                r_["total_stretch"] = G.grass_tree_stretch(ctx, tree)
+                r_["stretch_ms"] = 1e3 * (time.perf_counter() - t0)
+                r_["mean_stretch"] = r_["total_stretch"] / g.m
+                S = G.grass_sparsifier_create(ctx, tree)
+                x = torch.zeros(g.n, dtype=torch.float64, device="cuda")
+                t0 = time.perf_counter()
+                st_, ps = G.grass_pcg_solve(ctx, S, bd, x, w["pcg_tol"], w["pcg_maxit"], pcg_prec,
+                                            w["refine_tol"], w["pcg_inner_tol"], 0)
+                r_["pcg_tree_only"] = {"iters": ps.iters, "ms": 1e3 * (time.perf_counter() - t0),
+                                       "rel_resid_fp64": ps.rel_resid_fp64, "status": st_}
+                G.grass_sparsifier_destroy(S)
+                S = None
+                if h0d is not None:
+                    t0 = time.perf_counter()
+                    S, dst = G.grass_densify(ctx, tree, P, h0d, v0d)
+                    dd = dst.as_dict()
+                    r_["densify"] = {"ms": 1e3 * (time.perf_counter() - t0), "rounds": dd["rounds"],
+                                     "added": dd["added"], "lmax_est": dd["lmax_est"],
+                                     "lmax_capped": dd.get("lmax_capped"),
+                                     "stopped_similar": dd["stopped_similar"]}
+                    x.zero_()
+                    t0 = time.perf_counter()
+                    st_, ps = G.grass_pcg_solve(ctx, S, bd, x, w["pcg_tol"], w["pcg_maxit"],
+                                                pcg_prec, w["refine_tol"], w["pcg_inner_tol"],
+                                                w["pcg_inner_maxit"])
+                    r_["pcg_sparsifier"] = {"iters": ps.iters,
+                                            "ms": 1e3 * (time.perf_counter() - t0),
+                                            "rel_resid_fp64": ps.rel_resid_fp64, "status": st_}
+            finally:
+                if S:
+                    G.grass_sparsifier_destroy(S)
+                G.grass_tree_destroy(tree)
+            out[kind] = r_
+    finally:
+        G.grass_ctx_destroy(ctx)
+    return out
+
+
+def lsst_extras(G, w: dict, P, g, h0d, v0d, bd) -> dict:
+    """lsst_vs_mst on the step's workload (with densification) and on a
+    1000 x 1000 unit mesh with D = 1e-3 I (tree-only PCG to 1e-3)."""
+    import torch
+    from synth import graphs, rng
+    res = {"grid3d": lsst_vs_mst(G, w, P, g, h0d, v0d, bd, describe(w, g))}
+    gm = graphs.grid((1000, 1000), None, 1e-3)
+    wm = dict(w, pcg_tol=1e-3, pcg="fp32")
+    bm = torch.from_numpy(rng.normal(4, rng.STREAM_RHS, gm.n)).cuda()
+    res["unit_mesh_1000"] = lsst_vs_mst(G, wm, P, gm, None, None, bm,
+                                        "1000x1000 unit mesh, D = 1e-3 I; tree-only PCG to 1e-3 "
+                                        "(FP32 + FP64 refinement)")
+    return res
+
+
 # ---------------------------------------------------------------- replicas
 
 def replica_max(dist, v: float, device: str = "cuda") -> float:
@@ -915,8 +1018,16 @@ def main() -> int:
     ap.add_argument("--serve", action="store_true",
                     help="run the serving benchmark instead and print its line")
     ap.add_argument("--solve40m-only", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=None,
+                    help="arrivals per load level of --serve (default 1000)")
+    ap.add_argument("--serve-grid-sms", type=int, default=0,
+                    help="SMs of each request's cooperative kernels in --serve (0: all)")
+    ap.add_argument("--serve-capacity-only", action="store_true",
+                    help="--serve: measure the closed-burst capacity only")
     ap.add_argument("--batch", action="store_true",
                     help="run the 256-graph batch benchmark instead and print its line")
+    ap.add_argument("--only-extra", default=None, choices=["lsst_vs_mst", "c3_powerlaw"],
+                    help="run only the named measurement (outside any timed region) and print it")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the keys measured outside the timed region (per-round rates, "
                          "kappa check, FP64 path, PCG inner sweep, 64x64 latency, power-law "
@@ -987,6 +1098,13 @@ def main() -> int:
 
     if args.profile_kernel:
         return profile_kernel(G, ctx, args.profile_kernel, g, rp, col, val, v0d, w)
+
+    if args.only_extra:
+        fn = {"lsst_vs_mst": lambda: lsst_extras(G, w, P, g, h0d, v0d, bd),
+              "c3_powerlaw": lambda: c3_powerlaw(G, peak_hbm())}[args.only_extra]
+        print(json.dumps({args.only_extra: fn()}), flush=True)
+        G.grass_ctx_destroy(ctx)
+        return 0
 
     if args.profile_amg:
         tree = G.grass_build_tree(ctx, rp, col, val, 0)
@@ -1079,12 +1197,8 @@ def main() -> int:
                                "GBps": (fb / (fms / 1e3) / 1e9) if fms > 0 else None}
         G.grass_kernel_timing_enable(ctx, 0)
 
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except Exception:
-        pass
-    peak = float(peaks.get("hbm_gbs", 6800.0))
+    peaks = measured_peaks()
+    peak = peak_hbm()
     achieved = (kbytes / kl) / ((kms / kl) / 1e3) / 1e9 if kl and kms > 0 else None
     # DRAM traffic per launch from the committed ncu capture (dram bytes /
     # algorithmic bytes of the captured launch, times this run's algorithmic
@@ -1123,6 +1237,7 @@ def main() -> int:
                          ("c1_latency", lambda: c1_latency(G)),
                          ("c3_powerlaw", lambda: c3_powerlaw(G, peak)),
                          ("hair_comb", lambda: hair_comb(G)),
+                         ("lsst_vs_mst", lambda: lsst_extras(G, w, P, g, h0d, v0d, bd)),
                          ("partition_mesh_1m", lambda: partition_mesh(G))):
             try:
                 r_ = fn()

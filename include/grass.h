@@ -175,6 +175,10 @@ grass_status grass_ctx_set_wait_limit(grass_ctx_t ctx, int64_t polls, int hold_b
  *                         and keep the elimination rounds (the tour's FP64
  *                         arrays then no longer fit the L2 cache and its
  *                         gathers are slower than the rounds)
+ *   "grid_sms"            cooperative kernels (tree solves, fused CG and
+ *                         PCG) use at most this many SMs (0, the default:
+ *                         all); results depend on the grid, so a fixed
+ *                         value gives fixed results
  * Errors: INVALID for an unknown name or a value out of range. */
 grass_status grass_ctx_set_param(grass_ctx_t ctx, const char *name, int64_t value);
 
@@ -243,6 +247,41 @@ void grass_tree_destroy(grass_tree_t tree);
  * range, repeated, or containing a cycle), NOT_SDD, DISCONNECTED, OOM, CUDA. */
 grass_status grass_tree_from_edges(grass_ctx_t ctx, const grass_csr_t *A, const int64_t *tree_eids,
                                    int32_t ground, grass_tree_t *out);
+
+/* Low-stretch spanning tree in place of the maximum-weight one (Sec. III-B:
+ * the backbone the paper starts from is a tree of low total stretch
+ * st_T(G) = sum_e w_e R_T(e) = Tr(L_T^+ L_G)).  The construction clusters
+ * by weight classes, heaviest first (class = the binade of w_e), and within
+ * the edges of classes <= c repeats shifted low-diameter decompositions of
+ * the cluster graph until every component is one cluster:
+ *   shift(x) = 3 min(20, leading zeros of SplitMix64(seed + (x+1) G +
+ *   (1000003 c + level) H)), G = 0x9E3779B97F4A7C15, H = 0xD1B54A32D192ED03;
+ *   a cluster starts growing at round S - shift(x) (S the largest shift);
+ *   an unclaimed cluster next to clusters claimed in the previous round
+ *   joins the centre with the smallest (start, centre id) through the
+ *   heaviest edge (smallest id on equal weight) to such a neighbour; that
+ *   edge joins the tree; clusters are then renamed by their centres.
+ * The result is a function of (graph, seed) alone: runs and devices agree
+ * bit for bit.  Everything after the tree is as for grass_build_tree.
+ * stats (host, may be NULL): classes, decompositions ("levels") and growth
+ * rounds run, and the construction's device time in ms (CUDA events).
+ * Errors: as grass_build_tree. */
+typedef struct {
+    int32_t classes;
+    int64_t levels;
+    int64_t rounds;
+    double ms;
+} grass_lsst_stats_t;
+grass_status grass_build_lsst(grass_ctx_t ctx, const grass_csr_t *A, uint64_t seed, int32_t ground,
+                              grass_tree_t *out, grass_lsst_stats_t *stats);
+
+/* Stretch of every edge of the tree's graph, w_e times the resistance of
+ * the tree path between its endpoints (tree edges: 1), into stretch
+ * (device, m doubles, may be NULL), and their sum st_T(G) (host, may be
+ * NULL; a deterministic FP64 sum).  Single trees only, of at most
+ * euler_max_n vertices (the tree's Euler tour orients it).  Errors: INVALID
+ * (a forest, or no Euler tour), OOM, CUDA. */
+grass_status grass_tree_stretch(grass_ctx_t ctx, grass_tree_t tree, double *stretch, double *total);
 
 /* Sizes: n, m (edges), factor_rounds (contraction rounds of the tree
  * elimination schedule).  Any pointer may be NULL.  Host outputs. */
@@ -561,6 +600,11 @@ typedef struct {
 grass_status grass_server_create(int device, int slots, int64_t hbm_budget, grass_server_t *out);
 /* The budget in bytes (-1 for a null server). */
 int64_t grass_server_budget(grass_server_t srv);
+/* Server-wide knob applied to every request admitted after the call:
+ * "grid_sms" = the context knob of that name on each worker (0: all SMs;
+ * a share such as SMs / slots lets admitted requests' cooperative kernels
+ * run side by side).  Errors: INVALID (unknown name, value out of range). */
+grass_status grass_server_set_param(grass_server_t srv, const char *name, int64_t value);
 /* Queue a request (copied; its host arrays are read when it is admitted).
  * *ticket identifies it for grass_server_wait.  Errors: INVALID (bad
  * request, or the server is stopping), OOM (footprint above the budget). */

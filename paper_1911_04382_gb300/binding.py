@@ -95,6 +95,14 @@ class grass_fiedler_stats_t(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class grass_lsst_stats_t(C.Structure):
+    _fields_ = [("classes", C.c_int32), ("levels", C.c_int64), ("rounds", C.c_int64),
+                ("ms", C.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class grass_request_t(C.Structure):
     _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("rowptr", C.c_void_p), ("col", C.c_void_p),
                 ("val", C.c_void_p), ("h0", C.c_void_p), ("v0", C.c_void_p), ("b", C.c_void_p),
@@ -136,6 +144,9 @@ def lib():
                 "grass_kernel_timing_read": [_vp, C.POINTER(_d), C.POINTER(_i64), C.POINTER(_d)],
                 "grass_build_tree": [_vp, C.POINTER(grass_csr_t), _i32, C.POINTER(_vp)],
                 "grass_tree_from_edges": [_vp, C.POINTER(grass_csr_t), _vp, _i32, C.POINTER(_vp)],
+                "grass_build_lsst": [_vp, C.POINTER(grass_csr_t), C.c_uint64, _i32, C.POINTER(_vp),
+                                     C.POINTER(grass_lsst_stats_t)],
+                "grass_tree_stretch": [_vp, _vp, _vp, C.POINTER(_d)],
                 "grass_sparsifier_edges": [_vp, C.POINTER(_i64), _i64, C.POINTER(_i64)],
                 "grass_tree_info": [_vp, C.POINTER(_i64), C.POINTER(_i64), C.POINTER(_i64)],
                 "grass_tree_graph": [_vp, _vp, _vp, _vp, _vp, _vp],
@@ -173,6 +184,7 @@ def lib():
                                           C.POINTER(_d)],
                 "grass_autotune": [_vp, _vp, C.c_int, C.c_int, C.POINTER(_i64), C.POINTER(_d)],
                 "grass_server_create": [C.c_int, C.c_int, _i64, C.POINTER(_vp)],
+                "grass_server_set_param": [_vp, C.c_char_p, _i64],
                 "grass_server_submit": [_vp, C.POINTER(grass_request_t), C.POINTER(_i64)],
                 "grass_server_wait": [_vp, _i64, C.POINTER(grass_result_t)],
                 "grass_server_stats": [_vp, C.POINTER(_i64), C.POINTER(_i64), C.POINTER(_i64),
@@ -309,6 +321,29 @@ def grass_tree_from_edges(ctx: int, rowptr, col, val, tree_eids, ground: int = 0
     _check(ctx, lib().grass_tree_from_edges(ctx, C.byref(A), _p(tree_eids), int(ground),
                                             C.byref(out)), "grass_tree_from_edges")
     return out.value
+
+
+def grass_build_lsst(ctx: int, rowptr, col, val, seed: int = 1, ground: int = 0) -> tuple[int, dict]:
+    """grass_build_tree with the low-stretch tree of the given seed; returns
+    (tree handle, stats dict)."""
+    A = grass_csr_t()
+    A.n = int(rowptr.numel() - 1)
+    A.nnz = int(col.numel())
+    A.rowptr, A.col, A.val = _p(rowptr), _p(col), _p(val)
+    out = _vp()
+    st = grass_lsst_stats_t()
+    _check(ctx, lib().grass_build_lsst(ctx, C.byref(A), C.c_uint64(int(seed) & (2**64 - 1)),
+                                       int(ground), C.byref(out), C.byref(st)), "grass_build_lsst")
+    return out.value, st.as_dict()
+
+
+def grass_tree_stretch(ctx: int, tree: int, stretch=None) -> float:
+    """Per-edge stretch into stretch (device float64 [m], optional); returns
+    the total stretch st_T(G)."""
+    tot = _d(0.0)
+    _check(ctx, lib().grass_tree_stretch(ctx, tree, _p(stretch), C.byref(tot)),
+           "grass_tree_stretch")
+    return tot.value
 
 
 def grass_tree_destroy(tree: int) -> None:
@@ -499,6 +534,11 @@ def grass_server_stats(srv) -> dict:
     return dict(zip(("in_use", "queued", "running", "max_running"), (a.value for a in v)))
 
 
+def grass_server_set_param(srv, name: str, value: int) -> None:
+    _check(None, lib().grass_server_set_param(srv, name.encode(), int(value)),
+           "grass_server_set_param")
+
+
 class Server:
     """grass_server_* with the host arrays of each request kept alive until
     its result has been collected (the library reads them on admission)."""
@@ -535,6 +575,9 @@ class Server:
 
     def stats(self) -> dict:
         return grass_server_stats(self.handle)
+
+    def set_param(self, name: str, value: int) -> None:
+        grass_server_set_param(self.handle, name, value)
 
     def budget(self) -> int:
         return grass_server_budget(self.handle)

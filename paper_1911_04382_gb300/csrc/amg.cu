@@ -620,7 +620,7 @@ int amg_pcg(grass_ctx_t ctx, grass_sparsifier_t S, const T *rhs, T *e, double to
     cudaGraphExec_t exec = nullptr;
     auto iteration = [&]() {
         lap_mm(ctx, 1, prec, n, 2 * g.m, g.adj_ptr.p, g.adj_col.p, wA, DA, p, q, nullptr,
-               GRASS_KF_SPMM_G);
+               GRASS_KF_SPMM_G, &g.heavy);
         dot_cols(ctx, 1, prec, n, p, q, s + 1);
         launch(ctx, k_ap_axpy<T>, gn, kBlock, 0, n, (const double *)s, e, r, (const T *)p, (const T *)q);
         dot_cols(ctx, 1, prec, n, r, r, s + 2);
@@ -755,7 +755,7 @@ int amg_cg_lap(grass_ctx_t ctx, grass_sparsifier_t S, const double *y, double *x
     int k = 0;
     for (; k < maxit; ++k) {
         lap_mm(ctx, 1, GRASS_FP64, n, S->s_nnz, S->s_ptr.p, S->s_col.p, w, nullptr, p, q, nullptr,
-               GRASS_KF_SPMM_S);
+               GRASS_KF_SPMM_S, &S->s_heavy);
         dot_cols(ctx, 1, GRASS_FP64, n, p, q, sc + 3);
         launch(ctx, k_amg_axpy, g, kBlock, 0, n, (const double *)(sc + 2), (const double *)(sc + 3),
                x, r, (const double *)p, (const double *)q);

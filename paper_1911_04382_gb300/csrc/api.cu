@@ -93,7 +93,7 @@ int64_t power_steps(grass_ctx_t ctx, grass_sparsifier_t S, const double *h0, int
     int64_t inner = 0;
     for (int s = 0; s < t; ++s) {
         lap_mm(ctx, r, prec, n, 2 * g.m, g.adj_ptr.p, g.adj_col.p, w, nullptr, H, Y,
-               prev >= 0 ? maxslot(ctx, prev) : nullptr, GRASS_KF_SPMM_G);
+               prev >= 0 ? maxslot(ctx, prev) : nullptr, GRASS_KF_SPMM_G, &g.heavy);
         memset_d(ctx, maxslot(ctx, cur), 0, sizeof(unsigned long long));
         inner += s_solve(ctx, S, false, r, prec, Y, H, inner_tol, inner_maxit, maxslot(ctx, cur));
         prev = cur;
@@ -251,10 +251,12 @@ void user_tree(grass_ctx_t ctx, const GraphData &g, const int64_t *eids, uint8_t
 // Spanning tree (one root) or spanning forest of a batch (one root per graph,
 // the graph's first vertex), its elimination schedule and the L_T factor.
 // user_eids (device, n-1 edge ids) replaces the maximum spanning tree by the
-// caller's tree (single graph only).
+// caller's tree, lsst_seed by the low-stretch tree of that seed (single graph
+// only).
 grass_tree_t build_tree_impl(grass_ctx_t ctx, const grass_csr_t *A,
                              const std::vector<int64_t> &voff, const std::vector<int32_t> &roots,
-                             const int64_t *user_eids = nullptr) {
+                             const int64_t *user_eids = nullptr, const uint64_t *lsst_seed = nullptr,
+                             LsstStats *lsst_stats = nullptr) {
     auto *T = new grass_tree_s();
     T->ctx = ctx;
     T->nroots = (int64_t)roots.size();
@@ -273,6 +275,7 @@ grass_tree_t build_tree_impl(grass_ctx_t ctx, const grass_csr_t *A,
                (const int32_t *)T->roots.p, T->isroot.p);
         T->in_tree.alloc(T->g.m);
         if (user_eids) user_tree(ctx, T->g, user_eids, T->in_tree.p);
+        else if (lsst_seed) lsst_build(ctx, T->g, *lsst_seed, T->in_tree.p, lsst_stats);
         else mst_boruvka(ctx, T->g, T->in_tree.p);
         tree_schedule(ctx, T);
         tree_factor(ctx, T, false, T->lap);
@@ -389,6 +392,9 @@ grass_status grass_ctx_set_param(grass_ctx_t ctx, const char *name, int64_t valu
     } else if (k == "lmax_amg") {
         need(value == 0 || value == 1, "lmax_amg must be 0 or 1");
         ctx->lmax_amg = (int)value;
+    } else if (k == "grid_sms") {
+        need(value >= 0, "grid_sms must be >= 0");
+        ctx->grid_sms = (int)value;
     } else if (k == "euler_max_n") {
         need(value >= 0, "euler_max_n must be >= 0");
         ctx->euler_max_n = value;
@@ -482,6 +488,49 @@ grass_status grass_tree_from_edges(grass_ctx_t ctx, const grass_csr_t *A, const 
     API_END
 }
 
+grass_status grass_build_lsst(grass_ctx_t ctx, const grass_csr_t *A, uint64_t seed, int32_t ground,
+                              grass_tree_t *out, grass_lsst_stats_t *stats) {
+    if (!ctx) return GRASS_ERR_INVALID;
+    API_BEGIN(ctx)
+    need(A && out, "null argument");
+    *out = nullptr;
+    need(ground >= 0 && ground < A->n, "ground must be in [0, n)");
+    LsstStats ls;
+    cudaEvent_t ev[2];
+    GCK(cudaEventCreate(&ev[0]));
+    GCK(cudaEventCreate(&ev[1]));
+    GCK(cudaEventRecord(ev[0], ctx->stream));
+    try {
+        *out = build_tree_impl(ctx, A, {0, A->n}, {ground}, nullptr, &seed, &ls);
+    } catch (...) {
+        cudaEventDestroy(ev[0]);
+        cudaEventDestroy(ev[1]);
+        throw;
+    }
+    GCK(cudaEventRecord(ev[1], ctx->stream));
+    GCK(cudaEventSynchronize(ev[1]));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ev[0], ev[1]);
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    if (stats) {
+        stats->classes = ls.classes;
+        stats->levels = ls.levels;
+        stats->rounds = ls.rounds;
+        stats->ms = ms;
+    }
+    API_END
+}
+
+grass_status grass_tree_stretch(grass_ctx_t ctx, grass_tree_t tree, double *stretch, double *total) {
+    if (!ctx || !tree) return GRASS_ERR_INVALID;
+    API_BEGIN(ctx)
+    need(tree->ctx == ctx, "tree belongs to another context");
+    need(tree->nroots == 1, "stretch is defined here for a single spanning tree");
+    tree_stretch(ctx, tree, stretch, total);
+    API_END
+}
+
 grass_status grass_build_forest(grass_ctx_t ctx, const grass_csr_t *A, int64_t nseg,
                                 const int64_t *seg_off, grass_tree_t *out) {
     if (!ctx) return GRASS_ERR_INVALID;
@@ -571,7 +620,7 @@ grass_status grass_spmm(grass_ctx_t ctx, grass_tree_t T, int r, grass_prec prec,
     const GraphData &g = T->g;
     lap_mm(ctx, r, prec, g.n, 2 * g.m, g.adj_ptr.p, g.adj_col.p,
            prec == GRASS_FP64 ? (const void *)g.adj_w64.p : (const void *)g.adj_w32.p, nullptr, X,
-           Y, nullptr, GRASS_KF_SPMM_G);
+           Y, nullptr, GRASS_KF_SPMM_G, &g.heavy);
     API_END
 }
 

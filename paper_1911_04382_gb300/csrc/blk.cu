@@ -99,7 +99,8 @@ __global__ void __launch_bounds__(256) k_lapmm(int64_t n, const int32_t *__restr
                                                const int32_t *__restrict__ col,
                                                const T *__restrict__ w, const T *__restrict__ D,
                                                const T *__restrict__ X, T *__restrict__ Y,
-                                               const unsigned long long *scale_from) {
+                                               const unsigned long long *scale_from,
+                                               int32_t heavy_deg) {
     using RL = RowLay<T, R, VB>;
     constexpr int EL = RL::EL, L = RL::L, CPL = RL::CPL;
     // neighbours per batch: about 64 bytes of gathers in flight per lane
@@ -108,6 +109,8 @@ __global__ void __launch_bounds__(256) k_lapmm(int64_t n, const int32_t *__restr
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t i = t / L;
     if (i >= n) return;
+    const int32_t j0 = __ldg(ptr + i), j1 = __ldg(ptr + i + 1);
+    if (j1 - j0 > heavy_deg) return;      // a hub row: k_lapmm_heavy
     const int lane = (int)(t % L);
     const T s = (T)scale_of(scale_from);
     const int64_t off = lane * CPL * EL;   // first element of this lane in a row
@@ -118,7 +121,6 @@ __global__ void __launch_bounds__(256) k_lapmm(int64_t n, const int32_t *__restr
 #pragma unroll
         for (int e = 0; e < EL; ++e) acc[c].v[e] = (T)0;
     }
-    const int32_t j0 = __ldg(ptr + i), j1 = __ldg(ptr + i + 1);
     for (int32_t j = j0; j < j1; j += B) {
         int32_t cj[B];
         T wj[B];
@@ -160,46 +162,122 @@ __global__ void __launch_bounds__(256) k_lapmm(int64_t n, const int32_t *__restr
     }
 }
 
+// The same product for the hub rows: one block of 256 threads per row, G =
+// 256 / L groups of L lanes, group g taking the row's entries g, g + G, ...;
+// the groups' partial sums meet in shared memory and are added in group
+// order (deterministic), then D and the scale.
+template <typename T, int R, int VB>
+__global__ void __launch_bounds__(256) k_lapmm_heavy(const int32_t *__restrict__ rows,
+                                                     const int32_t *__restrict__ ptr,
+                                                     const int32_t *__restrict__ col,
+                                                     const T *__restrict__ w,
+                                                     const T *__restrict__ D,
+                                                     const T *__restrict__ X, T *__restrict__ Y,
+                                                     const unsigned long long *scale_from) {
+    using RL = RowLay<T, R, VB>;
+    constexpr int EL = RL::EL, L = RL::L, CPL = RL::CPL;
+    constexpr int G = 256 / L;
+    __shared__ T part[G * R];
+    const int64_t i = rows[blockIdx.x];
+    const int g = (int)threadIdx.x / L, lane = (int)threadIdx.x % L;
+    const int64_t off = lane * CPL * EL;
+    RowChunk<T, EL> x0[CPL], acc[CPL];
+#pragma unroll
+    for (int c = 0; c < CPL; ++c) {
+        x0[c] = ld_row_chunk<T, EL>(X + i * R + off + c * EL);
+#pragma unroll
+        for (int e = 0; e < EL; ++e) acc[c].v[e] = (T)0;
+    }
+    const int32_t j0 = __ldg(ptr + i), j1 = __ldg(ptr + i + 1);
+    for (int32_t j = j0 + g; j < j1; j += G) {
+        const int32_t cj = __ldg(col + j);
+        const T wj = __ldg(w + j);
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) {
+            const RowChunk<T, EL> xq = ld_row_chunk<T, EL>(X + (int64_t)cj * R + off + c * EL);
+#pragma unroll
+            for (int e = 0; e < EL; ++e) acc[c].v[e] += wj * (x0[c].v[e] - xq.v[e]);
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < CPL; ++c)
+#pragma unroll
+        for (int e = 0; e < EL; ++e) part[g * R + off + c * EL + e] = acc[c].v[e];
+    __syncthreads();
+    const T s = (T)scale_of(scale_from);
+    for (int q = (int)threadIdx.x; q < R; q += 256) {
+        T y = (T)0;
+        for (int k = 0; k < G; ++k) y += part[k * R + q];
+        if (D) y += __ldg(D + i) * X[i * R + q];
+        Y[i * R + q] = y * s;
+    }
+}
+
 template <typename T, int R, int VB>
 static void lapmm_T(grass_ctx_t ctx, int64_t n, const int32_t *ptr, const int32_t *col,
                     const void *w, const void *D, const void *X, void *Y,
-                    const unsigned long long *sf) {
+                    const unsigned long long *sf, const HeavyRows *hv) {
     constexpr int L = RowLay<T, R, VB>::L;
+    const bool split = hv && hv->count > 0;
     launch(ctx, k_lapmm<T, R, VB>, cdiv(n * L, 256), 256, 0, n, ptr, col, (const T *)w,
-           (const T *)D, (const T *)X, (T *)Y, sf);
+           (const T *)D, (const T *)X, (T *)Y, sf, split ? (int32_t)kHeavyDeg : INT32_MAX);
+    if (split)
+        launch(ctx, k_lapmm_heavy<T, R, VB>, hv->count, 256, 0, (const int32_t *)hv->rows.p, ptr,
+               col, (const T *)w, (const T *)D, (const T *)X, (T *)Y, sf);
 }
 
 template <typename T, int R>
 static void lapmm_P(grass_ctx_t ctx, int64_t n, const int32_t *ptr, const int32_t *col,
                     const void *w, const void *D, const void *X, void *Y,
-                    const unsigned long long *sf) {
+                    const unsigned long long *sf, const HeavyRows *hv) {
     // widest chunks that the row size and both blocks' alignment allow (a
     // caller's block or a slice of one may be only element-aligned)
     switch (chunk_bytes(R, sizeof(T), {X, Y})) {
-        case 32: lapmm_T<T, R, 32>(ctx, n, ptr, col, w, D, X, Y, sf); break;
-        case 16: lapmm_T<T, R, 16>(ctx, n, ptr, col, w, D, X, Y, sf); break;
-        default: lapmm_T<T, R, 0>(ctx, n, ptr, col, w, D, X, Y, sf); break;
+        case 32: lapmm_T<T, R, 32>(ctx, n, ptr, col, w, D, X, Y, sf, hv); break;
+        case 16: lapmm_T<T, R, 16>(ctx, n, ptr, col, w, D, X, Y, sf, hv); break;
+        default: lapmm_T<T, R, 0>(ctx, n, ptr, col, w, D, X, Y, sf, hv); break;
     }
 }
 
 template <int R>
 static void lapmm_R(grass_ctx_t ctx, grass_prec prec, int64_t n, const int32_t *ptr,
                     const int32_t *col, const void *w, const void *D, const void *X, void *Y,
-                    const unsigned long long *sf) {
-    if (prec == GRASS_FP64) lapmm_P<double, R>(ctx, n, ptr, col, w, D, X, Y, sf);
-    else lapmm_P<float, R>(ctx, n, ptr, col, w, D, X, Y, sf);
+                    const unsigned long long *sf, const HeavyRows *hv) {
+    if (prec == GRASS_FP64) lapmm_P<double, R>(ctx, n, ptr, col, w, D, X, Y, sf, hv);
+    else lapmm_P<float, R>(ctx, n, ptr, col, w, D, X, Y, sf, hv);
 }
 
 void lap_mm(grass_ctx_t ctx, int r, grass_prec prec, int64_t n, int64_t nnz, const int32_t *ptr,
             const int32_t *col, const void *w, const void *Dopt, const void *X, void *Y,
-            const unsigned long long *scale_from, int fam) {
+            const unsigned long long *scale_from, int fam, const HeavyRows *hv) {
     const double s = prec == GRASS_FP64 ? 8.0 : 4.0;
     const double bytes = 4.0 * (n + 1) + nnz * (4.0 + s) + 2.0 * n * r * s + (Dopt ? n * s : 0.0);
     // products with L_G over r > 1 columns are also a family of their own
     if (fam == GRASS_KF_SPMM_G && r > 1 && ctx->tfam == GRASS_KF_SPMM_BLK) fam = GRASS_KF_SPMM_BLK;
     bool timed = ctx->t_begin(fam, bytes);
-    GRASS_DISPATCH_R(r, lapmm_R, ctx, prec, n, ptr, col, w, Dopt, X, Y, scale_from);
+    GRASS_DISPATCH_R(r, lapmm_R, ctx, prec, n, ptr, col, w, Dopt, X, Y, scale_from, hv);
     ctx->t_end(timed);
+}
+
+__global__ void k_heavy_list(int64_t n, const int32_t *ptr, int32_t deg, int64_t cap,
+                             int32_t *rows, unsigned int *cnt) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || ptr[i + 1] - ptr[i] <= deg) return;
+    const unsigned int k = atomicAdd(cnt, 1u);
+    if ((int64_t)k < cap) rows[k] = (int32_t)i;
+}
+
+void heavy_rows(grass_ctx_t ctx, int64_t n, int64_t nnz, const int32_t *ptr, HeavyRows &hv) {
+    // at most nnz / (kHeavyDeg + 1) rows have more than kHeavyDeg entries
+    const int64_t cap = nnz / (kHeavyDeg + 1) + 1;
+    hv.rows.reserve(cap);
+    hv.cnt.reserve(1);
+    memset_d(ctx, hv.cnt.p, 0, sizeof(unsigned int));
+    launch(ctx, k_heavy_list, cdiv(n, kBlock), kBlock, 0, n, ptr, (int32_t)kHeavyDeg, cap,
+           hv.rows.p, hv.cnt.p);
+    unsigned int c = 0;
+    d2h(ctx, &c, hv.cnt.p, sizeof(c));
+    hv.count = std::min<int64_t>(c, cap);
 }
 
 // ---------------------------------------------------------------- conversions, scaling

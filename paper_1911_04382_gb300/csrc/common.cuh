@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 #include <cstdint>
 #include <cstring>
 #include <memory>
@@ -107,6 +108,7 @@ struct grass_ctx_s {
     int num_sms = 0;
     // launch-shape knobs (grass_ctx_set_param)
     int tree_bpsm = 1;
+    int grid_sms = 0;      // cooperative grids on at most this many SMs (0: all)
     int tree_threads = 1024;
     int64_t tree_tail_items = 2048;
     int euler_solve = 1;   // scan form for grounded r = 1 solves without D
@@ -127,7 +129,7 @@ struct grass_ctx_s {
         int threads;
         size_t smem;
         int bpsm;
-        int grid;
+        int grid;   // co-resident blocks per SM
     };
     std::vector<CoopEntry> coop_cache;
     // kernel-family timing (grass_kernel_timing_*)
@@ -261,6 +263,17 @@ inline bool r_supported(int r) {
 
 // ---------------------------------------------------------------- graph / tree data
 
+// Rows of an adjacency with more than kHeavyDeg entries (the hubs of a
+// power-law graph): the r-column products give each one a whole block
+// instead of the few lanes of an ordinary row (list order is arbitrary; every
+// row's result is order-independent).
+constexpr int kHeavyDeg = 256;
+struct HeavyRows {
+    int64_t count = 0;
+    DBuf<int32_t> rows;
+    DBuf<unsigned int> cnt;
+};
+
 struct GraphData {
     int64_t n = 0, m = 0;
     DBuf<int32_t> adj_ptr;            // [n+1] off-diagonal adjacency in CSR order
@@ -274,6 +287,7 @@ struct GraphData {
     DBuf<double> D64;                 // [n] diagonal load
     DBuf<float> D32;
     DBuf<double> degG;                // [n] weighted degree (Laplacian diagonal)
+    HeavyRows heavy;                  // rows of adj_ptr above kHeavyDeg entries
     bool lap_only = false;            // D = 0 everywhere: A is a graph Laplacian (singular)
     // a batch of independent graphs stored as one block-diagonal matrix:
     // graph k owns vertices [seg_voff[k], seg_voff[k+1]) and edge ids
@@ -409,6 +423,7 @@ struct grass_sparsifier_s {
     grass::DBuf<float> off_w32;
     grass::DBuf<int32_t> s_ptr, s_col;            // S adjacency (when !is_tree)
     int64_t s_nnz = 0;
+    grass::HeavyRows s_heavy;                     // rows of s_ptr above kHeavyDeg entries
     grass::DBuf<double> s_w64;
     grass::DBuf<float> s_w32;
     grass::DBuf<double> degS;         // [n]
@@ -455,6 +470,18 @@ void copy_d(grass_ctx_t ctx, void *dst, const void *src, size_t bytes);
 void graph_extract(grass_ctx_t ctx, const grass_csr_t *A, GraphData &g);
 void mst_boruvka(grass_ctx_t ctx, const GraphData &g, uint8_t *in_tree);
 void mst_boruvka_w(grass_ctx_t ctx, const GraphData &g, const double *ew, uint8_t *in_tree);
+// Low-stretch spanning tree (lsst.cu): in_tree (device, m bytes) of the
+// deterministic class-by-class shifted-decomposition construction; stats
+// may be null.
+struct LsstStats {
+    int classes = 0;
+    int64_t levels = 0, rounds = 0, edge_passes = 0;
+};
+void lsst_build(grass_ctx_t ctx, const GraphData &g, uint64_t seed, uint8_t *in_tree,
+                LsstStats *stats);
+// Per-edge stretch w_e R_T(u_e, v_e) (device, m doubles, may be null) and
+// its sum (host, may be null); needs the tree's Euler tour.
+void tree_stretch(grass_ctx_t ctx, grass_tree_t T, double *st, double *total);
 void tree_schedule(grass_ctx_t ctx, grass_tree_t T);
 // Euler tour from the tree adjacency (slot lists tptr/tocc, tree edge id of
 // every slot in tsrc; L slots), before the contraction rounds modify it.
@@ -470,7 +497,9 @@ void tree_solve_inplace(grass_ctx_t ctx, grass_tree_t T, const TreeFactor &f, in
 // come from a device max-bits word (pow2 rescale) when scale_from != nullptr.
 void lap_mm(grass_ctx_t ctx, int r, grass_prec prec, int64_t n, int64_t nnz, const int32_t *ptr,
             const int32_t *col, const void *w, const void *Dopt, const void *X, void *Y,
-            const unsigned long long *scale_from, int fam);
+            const unsigned long long *scale_from, int fam, const HeavyRows *hv);
+// hv.rows / hv.count for an adjacency (n rows, nnz entries); synchronises.
+void heavy_rows(grass_ctx_t ctx, int64_t n, int64_t nnz, const int32_t *ptr, HeavyRows &hv);
 // Convert an n x r double block to prec (copy or float conversion).
 void convert_block(grass_ctx_t ctx, grass_prec prec, int64_t count, const double *src, void *dst);
 // Multiply an n x r block in place by the pow2 factor derived from maxbits.

@@ -93,6 +93,9 @@ void sparsifier_rebuild(grass_ctx_t ctx, grass_sparsifier_t S) {
         launch(ctx, k_s_fill, cdiv(n, kBlock), kBlock, 0, n, g.adj_ptr.p, g.adj_col.p, g.adj_eid.p,
                g.adj_w64.p, (const uint8_t *)S->in_s.p, (const int64_t *)off, S->s_ptr.p,
                S->s_col.p, S->s_w64.p, S->s_w32.p);
+        heavy_rows(ctx, n, ns, S->s_ptr.p, S->s_heavy);
+    } else {
+        S->s_heavy.count = 0;
     }
     S->pre_ok = false;
     S->amg[0].reset();

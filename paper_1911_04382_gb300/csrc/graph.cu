@@ -218,6 +218,7 @@ void graph_extract(grass_ctx_t ctx, const grass_csr_t *A, GraphData &g) {
     unsigned long long bits = 0;
     d2h(ctx, &bits, mb, sizeof(bits));
     g.lap_only = bits == 0;
+    heavy_rows(ctx, n, 2 * m, g.adj_ptr.p, g.heavy);
 }
 
 }  // namespace grass

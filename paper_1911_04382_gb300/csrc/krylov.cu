@@ -19,8 +19,9 @@ __global__ void k_cg_init_scalars(int r, double *cg) {
     }
 }
 
-// alpha_j for columns still iterating; the test at the top of the oracle's
-// loop (||r|| <= tol ||y||) and its pq <= 0 exit, per column.
+// alpha_j for columns still iterating: the inner CG's stop test at the top
+// of each iteration (a column stops once ||r|| <= tol ||y||, the inner
+// solve's relative residual) and its exit on pq <= 0, per column.
 __global__ void k_cg_alpha(int r, double tol, double *cg) {
     int j = threadIdx.x;
     if (j >= r) return;
@@ -332,7 +333,7 @@ __device__ __forceinline__ bool cg_dev(const CGArgs<T> &g, const TreeKArgs<T> &t
     }
     // Iteration `it` starts with Z = M^{-1} R (the only call site of the
     // tree solve), then P (it = 0: P = Z; else P = Z + beta P), then the
-    // oracle's loop test ||r|| > tol ||y|| per column, the product and the
+    // stop test (a column goes on while ||r|| > tol ||y||), the product and the
     // updates.  After the updates the test is looked at once more, so no
     // solve is spent when no column goes on.
     for (int it = 0;; ++it) {
@@ -425,7 +426,7 @@ __device__ __forceinline__ bool cg_dev(const CGArgs<T> &g, const TreeKArgs<T> &t
             if (!grid_sync(tk.bar, tk.budget, tk.err, epoch)) return false;
         }
         if (it >= g.maxit) break;
-        // the oracle's loop test, per column: ||r|| > tol ||y||
+        // stop test per column: a column goes on while ||r|| > tol ||y||
         if (threadIdx.x == 0) s_nact = 0;
         __syncthreads();
         if (threadIdx.x < R) {
@@ -873,7 +874,7 @@ int64_t s_solve(grass_ctx_t ctx, grass_sparsifier_t S, bool with_D, int r, grass
             if (nact == 0) break;
         }
         lap_mm(ctx, r, prec, n, S->s_nnz, S->s_ptr.p, S->s_col.p, w, D, P, Q, nullptr,
-               GRASS_KF_SPMM_S);
+               GRASS_KF_SPMM_S, &S->s_heavy);
         dot_cols(ctx, r, prec, n, P, Q, cg + CG_PQ * 32);
         launch(ctx, k_cg_alpha, 1, 32, 0, r, tol, cg);
         if (prec == GRASS_FP64)
@@ -1427,7 +1428,7 @@ static int pcg_core(grass_ctx_t ctx, grass_sparsifier_t S, grass_prec prec, cons
         d2h(ctx, &rr, sc + P_RR, sizeof(double));
         if (std::sqrt(rr) <= tol_abs) break;
         lap_mm(ctx, 1, prec, n, 2 * g.m, g.adj_ptr.p, g.adj_col.p, wA, DA, p, q, nullptr,
-               GRASS_KF_SPMM_G);
+               GRASS_KF_SPMM_G, &g.heavy);
         dot_cols(ctx, 1, prec, n, p, q, sc + P_PQ);
         launch(ctx, k_pcg_axpy<T>, grid, kBlock, 0, n, (const double *)(sc + P_RZ0 + cur),
                (const double *)(sc + P_PQ), e, r, (const T *)p, (const T *)q);
@@ -1450,7 +1451,7 @@ static double true_relres(grass_ctx_t ctx, const GraphData &g, const double *b, 
     const int64_t n = g.n;
     double *Ax = ctx->scr<double>(SCR_PCG_E, n);
     lap_mm(ctx, 1, GRASS_FP64, n, 2 * g.m, g.adj_ptr.p, g.adj_col.p, g.adj_w64.p, g.D64.p, x, Ax,
-           nullptr, GRASS_KF_SPMM_G);
+           nullptr, GRASS_KF_SPMM_G, &g.heavy);
     launch(ctx, k_residual64, cdiv(n, kBlock), kBlock, 0, n, b, (const double *)Ax, rvec);
     double *sc = ctx->scal.p + DS_RED;
     dot_cols(ctx, 1, GRASS_FP64, n, rvec, rvec, sc + P_EE);

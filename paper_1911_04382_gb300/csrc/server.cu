@@ -12,6 +12,7 @@
 // requests in flight overlaps on the device.  Every launch shape depends on
 // the request alone, never on what else runs, so a result is the same alone
 // and in the mix.
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -66,6 +67,7 @@ struct grass_server_s {
     bool stop = false;
     int64_t next_id = 1;
     int64_t running = 0, max_running = 0;
+    std::atomic<int> grid_sms{0};   // cooperative grids of every request (0: all SMs)
     grass::Clock::time_point t0;
 
     double now() const {
@@ -173,6 +175,8 @@ void grass_server_s::worker(int slot) {
             set_error(t->res, GRASS_ERR_CUDA, "worker could not create its context");
         } else {
             try {
+                if (grass_ctx_set_param(ctx, "grid_sms", grid_sms.load()) != GRASS_OK)
+                    fail(GRASS_ERR_INVALID, "grid_sms rejected");
                 run(slot, ctx, *t);
             } catch (const Error &e) {
                 set_error(t->res, e.st, e.msg.c_str());
@@ -193,6 +197,16 @@ void grass_server_s::worker(int slot) {
     }
     if (ctx) grass_ctx_destroy(ctx);
     if (s) cudaStreamDestroy(s);
+}
+
+extern "C" grass_status grass_server_set_param(grass_server_t srv, const char *name, int64_t value) {
+    if (!srv || !name) return GRASS_ERR_INVALID;
+    if (std::string(name) == "grid_sms") {
+        if (value < 0 || value > (1 << 20)) return GRASS_ERR_INVALID;
+        srv->grid_sms.store((int)value);
+        return GRASS_OK;
+    }
+    return GRASS_ERR_INVALID;
 }
 
 extern "C" grass_status grass_server_create(int device, int slots, int64_t hbm_budget,

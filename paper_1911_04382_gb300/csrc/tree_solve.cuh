@@ -961,24 +961,28 @@ inline void euler_kargs(grass_ctx_t ctx, const grass_tree_s *Tr, int grid, Euler
 // Grid of a cooperative kernel with `threads` threads and `smem` dynamic
 // shared memory: co-resident blocks per SM, capped by tree_blocks_per_sm, and
 // no more blocks than `work_threads` threads of work fill (small graphs leave
-// the other SMs free and their grid barriers have fewer arrivals).  The grid
-// is a function of the shape and the work only, so a result does not depend
-// on what else runs on the device.
+// the other SMs free and their grid barriers have fewer arrivals), on at
+// most grid_sms SMs when that knob is set.  The grid is a function of the
+// shape, the work and the knobs only, so a result does not depend on what
+// else runs on the device.
 template <typename K>
 inline int coop_grid(grass_ctx_t ctx, K kernel, int threads, size_t smem, int64_t work_threads) {
     const void *k = (const void *)kernel;
-    int full = 0;
+    int per_sm = 0;
     for (const auto &e : ctx->coop_cache)
         if (e.kernel == k && e.threads == threads && e.smem == smem && e.bpsm == ctx->tree_bpsm)
-            full = e.grid;
-    if (full == 0) {
+            per_sm = e.grid;
+    if (per_sm == 0) {
         GCK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTailSmem));
         int nb = 0;
         GCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, threads, smem));
         if (nb < 1) fail(GRASS_ERR_CUDA, "cooperative kernel does not fit on an SM");
-        full = ctx->num_sms * std::min(nb, ctx->tree_bpsm);
-        ctx->coop_cache.push_back({k, threads, smem, ctx->tree_bpsm, full});
+        per_sm = std::min(nb, ctx->tree_bpsm);
+        ctx->coop_cache.push_back({k, threads, smem, ctx->tree_bpsm, per_sm});
     }
+    // grid_sms: a share of the device (requests served side by side)
+    const int sms = ctx->grid_sms > 0 ? std::min(ctx->grid_sms, ctx->num_sms) : ctx->num_sms;
+    const int64_t full = (int64_t)sms * per_sm;
     const int64_t need = std::max<int64_t>(1, (work_threads + threads - 1) / threads);
     return (int)std::min<int64_t>(full, need);
 }

@@ -240,3 +240,39 @@ def test_hair_comb_200(gpu):
         if tree:
             gpu.grass_tree_destroy(tree)
         gpu.grass_ctx_destroy(ctx)
+
+
+# ---------------------------------------------------------------- grid share
+
+@pytest.mark.parametrize("grid_sms", [8, 37])
+def test_grid_sms_share_keeps_results(gpu, grid_sms):
+    """Cooperative kernels on a share of the SMs (the serving knob): the tree
+    solve matches the oracle, the fused PCG reaches its tolerance (checked
+    with the oracle's product), and repeated runs under the same share are
+    bit-identical."""
+    import torch
+    g = graphs.grid3d_loguniform(22, 19, 17, seed=90)
+    og = oracle.from_graph(g)
+    ot = oracle.build_tree(og, 0)
+    B = rng.gaussian_block(90, 6, g.n, 8)
+    ref = oracle.tree_solve(og, ot, B, og.D)
+    b = rng.normal(90, rng.STREAM_RHS, g.n)
+    with gpu_graph(g) as (ctx, tree, (rp, col, val)):
+        gpu.grass_ctx_set_param(ctx, "grid_sms", grid_sms)
+        X = torch.empty(g.n, 8, dtype=torch.float64, device="cuda")
+        gpu.grass_tree_solve(ctx, tree, 1, 8, gpu.GRASS_FP64, dev(B), X)
+        assert np.abs(host(X) - ref).max() <= 1e-10 * np.abs(ref).max()
+        S = gpu.grass_sparsifier_create(ctx, tree)
+        try:
+            xs = []
+            for _ in range(2):
+                x = torch.zeros(g.n, dtype=torch.float64, device="cuda")
+                st, ps = gpu.grass_pcg_solve(ctx, S, dev(b), x, 1e-8, 4000, gpu.GRASS_FP32, 1e-2,
+                                             1e-2, 1)
+                assert st == 0 and ps.rel_resid_fp64 <= 1e-8
+                xs.append(host(x))
+            assert np.array_equal(xs[0], xs[1])
+            A = oracle.lap_apply(og, xs[0]) + og.D * xs[0]
+            assert np.linalg.norm(b - A) <= 1.01e-8 * np.linalg.norm(b)
+        finally:
+            gpu.grass_sparsifier_destroy(S)

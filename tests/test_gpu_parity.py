@@ -133,6 +133,51 @@ def test_spmm_matches_oracle(gpu, r, offset):
         assert np.abs(host(Y32) - ref).max() <= 1e-4 * np.abs(ref).max()
 
 
+def _hub_graph():
+    """A star of 3000 leaves around vertex 0 (a row of 3001 entries), a
+    second hub (302 entries, above the 256-entry split), a row of exactly 256
+    entries (not split), and a path through the leaves so the graph has
+    ordinary rows too; weights 2^U(-3, 3), D = 1e-3 I."""
+    n = 3400
+    u = [0] * 3000 + [1] * 300 + [2] * 255 + list(range(3, n - 1))
+    v = list(range(3, 3003)) + list(range(1000, 1300)) + list(range(2000, 2255)) + \
+        list(range(4, n))
+    pairs = sorted({(min(a, b), max(a, b)) for a, b in zip(u, v)} | {(0, 1), (1, 2)})
+    uu = np.array([p[0] for p in pairs]); vv = np.array([p[1] for p in pairs])
+    w = 2.0 ** (6.0 * rng.uniform(44, 1, len(pairs)) - 3.0)
+    rowptr, col, val = graphs.csr_from_edges(n, uu, vv, w, 1e-3)
+    return graphs.Graph("hubs", n, rowptr, col, val)
+
+
+@pytest.mark.parametrize("r", [1, 2, 8, 24, 32])
+@pytest.mark.parametrize("which", ["hubs", "chung_lu"])
+def test_spmm_hub_rows_match_oracle(gpu, r, which):
+    """Rows above 256 entries go to one block each (groups of lanes over the
+    row, partial sums added in group order): every r, both precisions, a
+    constructed hub graph and a power-law graph, aligned and element-aligned
+    blocks."""
+    import torch
+    g = _hub_graph() if which == "hubs" else graphs.chung_lu(30000, 5)
+    og = oracle.from_graph(g)
+    deg = np.diff(g.rowptr) - 1
+    assert deg.max() > 256
+    X = rng.gaussian_block(45, 5, g.n, r)
+    ref = oracle.lap_apply(og, X)
+    with gpu_graph(g) as (ctx, tree, _):
+        for offset in (0, 1):
+            Xd = _at_offset(X, offset, torch.float64)
+            Y = _at_offset(np.zeros_like(X), offset, torch.float64)
+            gpu.grass_spmm(ctx, tree, r, gpu.GRASS_FP64, Xd, Y)
+            assert np.abs(host(Y) - ref).max() <= 1e-12 * np.abs(ref).max()
+            X32 = _at_offset(X, offset, torch.float32)
+            Y32 = _at_offset(np.zeros_like(X), offset, torch.float32)
+            gpu.grass_spmm(ctx, tree, r, gpu.GRASS_FP32, X32, Y32)
+            assert np.abs(host(Y32) - ref).max() <= 1e-4 * np.abs(ref).max()
+            Y2 = _at_offset(np.zeros_like(X), offset, torch.float32)
+            gpu.grass_spmm(ctx, tree, r, gpu.GRASS_FP32, X32, Y2)
+            assert torch.equal(Y2, Y32)          # deterministic
+
+
 @pytest.mark.parametrize("gi", range(6))
 @pytest.mark.parametrize("ground", [0, -1])
 def test_tree_solve_matches_oracle(gpu, gi, ground):
