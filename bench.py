@@ -486,6 +486,7 @@ def run_batch(G, w=BATCH) -> dict:
         try:
             tree = G.grass_build_forest(ctx, rp, col, val, off)
             best, best_ms = G.grass_autotune(ctx, tree, w["r"], G.GRASS_FP32)
+            row_best, row_ms = G.grass_autotune_rows(ctx, tree, w["r"], G.GRASS_FP32)
             G.grass_tree_destroy(tree)
 
             def one(prec):
@@ -559,7 +560,10 @@ def run_batch(G, w=BATCH) -> dict:
            "sequential_plain_fp64_s": seq_s, "sequential_rel_resid_max": seq_worst,
            "speedup_vs_sequential_fp64": seq_s / best_run["total"],
            "autotune": {"tree_threads": best[0], "tree_blocks_per_sm": best[1],
-                        "tree_tail_items": best[2], "forest_solve_ms_r8": best_ms},
+                        "tree_tail_items": best[2], "forest_solve_ms_r8": best_ms,
+                        "spmm_chunk_cap": row_best[0], "spmm_variant": row_best[1],
+                        "heat_form": row_best[2], "spmm_ms_r8": row_ms[0],
+                        "heat_ms_r8": row_ms[1]},
            "workload": f"{nseg} graphs ({u.n} nodes, {n_edges} edges): 2D grids side "
                        "log-uniform in [32,512] and rings of log-uniform [1e3,2e5] nodes with n/4 "
                        "chords, w ~ U[1,10), D = 1e-3 I; r=8, t=2, sigma^2=100, one round; PCG to "
@@ -1134,6 +1138,15 @@ def main() -> int:
         G.grass_ctx_destroy(ctx)
         return 0
 
+    # row-kernel autotuner (SpMM launch variant and chunk width, heat form)
+    # on this graph for the step's r and precision, before the warm-up
+    t_tune = G.grass_build_tree(ctx, rp, col, val, 0)
+    row_best, row_ms = G.grass_autotune_rows(ctx, t_tune, w["r"], embed_prec)
+    G.grass_tree_destroy(t_tune)
+    row_tune = {"spmm_chunk_cap": row_best[0], "spmm_variant": row_best[1],
+                "heat_form": row_best[2], "spmm_ms": row_ms[0], "heat_ms": row_ms[1],
+                "what": "grass_autotune_rows on the step's graph, r and precision, before the warm-up"}
+
     for _ in range(max(args.warmup, 0)):
         step(rp, col, val, h0d, v0d, bd, x)
 
@@ -1272,7 +1285,7 @@ def main() -> int:
             "clocks": clk, "edges_embedded_per_step": edges_per_step,
             "phase_ms": last.get("phase_ms"), "densify": last.get("st"), "pcg": last.get("sst"),
             "sparsifier_edges": last.get("n_s"), "tree_factor_rounds": last.get("tree_rounds"),
-            "kernels": breakdown, "solve_40m": s40,
+            "kernels": breakdown, "solve_40m": s40, "row_autotune": row_tune,
         }
         line.update(extras)
         print(json.dumps(line), flush=True)

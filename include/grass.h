@@ -175,6 +175,17 @@ grass_status grass_ctx_set_wait_limit(grass_ctx_t ctx, int64_t polls, int hold_b
  *                         and keep the elimination rounds (the tour's FP64
  *                         arrays then no longer fit the L2 cache and its
  *                         gathers are slower than the rounds)
+ *   "spmm_variant"        -1 (default: the autotuner's choice, else 0) or
+ *                         0-7: the r-column SpMM's launch variant, see
+ *                         grass_autotune_rows
+ *   "spmm_chunk"          -1 (default: the autotuner's choice, else the
+ *                         widest), 0 (widest chunk the row and alignment
+ *                         allow) or 16 (at most 16-byte chunks)
+ *   "heat_lanes"          heat kernel form: 0 (default: several lanes per
+ *                         edge when the row splits into 2 or 4 chunks), 1
+ *                         (one lane per edge), 2 / 3 (forms 0 / 1 with two
+ *                         edges in flight per lane); set by
+ *                         grass_autotune_rows
  *   "grid_sms"            cooperative kernels (tree solves, fused CG and
  *                         PCG) use at most this many SMs (0, the default:
  *                         all); results depend on the grid, so a fixed
@@ -542,6 +553,20 @@ grass_status grass_pcg_solve_batch(grass_ctx_t ctx, grass_sparsifier_t S, const 
  * solve.  Results of every solve are the same under any shape. */
 grass_status grass_autotune(grass_ctx_t ctx, grass_tree_t tree, int r, grass_prec prec,
                             int64_t *best, double *best_ms);
+/* Row-kernel autotuner (no counterpart in the paper): on the tree's graph,
+ * time the r-column SpMM (Y = L_G X) under each launch variant -- neighbour
+ * batch {by row size, 1, 2, 4} x register cap {none, 6 blocks per SM}, and
+ * each block on a contiguous range of rows (batch by row size or 1) -- and
+ * each chunk width {widest, 16 bytes}, and the Joule-heat kernel of the
+ * tree's off-tree edges in each of its forms ("heat_lanes"); keep the
+ * fastest on ctx: the SpMM choice for (prec, r) (the "spmm_variant" and
+ * "spmm_chunk" knobs, when set, still take precedence), the heat form as
+ * the "heat_lanes" knob.  best: host [3] = chunk cap (0 = widest, 16),
+ * variant (0-7), heat form (0-3); best_ms: host [2] = SpMM and heat time
+ * per launch.  Results are the same up to rounding order under any choice.
+ * Errors: INVALID, OOM, CUDA. */
+grass_status grass_autotune_rows(grass_ctx_t ctx, grass_tree_t tree, int r, grass_prec prec,
+                                 int32_t *best, double *best_ms);
 
 /* ---------------------------------------------------------------- serving */
 

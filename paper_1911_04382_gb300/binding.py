@@ -147,6 +147,7 @@ def lib():
                 "grass_build_lsst": [_vp, C.POINTER(grass_csr_t), C.c_uint64, _i32, C.POINTER(_vp),
                                      C.POINTER(grass_lsst_stats_t)],
                 "grass_tree_stretch": [_vp, _vp, _vp, C.POINTER(_d)],
+                "grass_autotune_rows": [_vp, _vp, C.c_int, C.c_int, C.POINTER(_i32), C.POINTER(_d)],
                 "grass_sparsifier_edges": [_vp, C.POINTER(_i64), _i64, C.POINTER(_i64)],
                 "grass_tree_info": [_vp, C.POINTER(_i64), C.POINTER(_i64), C.POINTER(_i64)],
                 "grass_tree_graph": [_vp, _vp, _vp, _vp, _vp, _vp],
@@ -344,6 +345,16 @@ def grass_tree_stretch(ctx: int, tree: int, stretch=None) -> float:
     _check(ctx, lib().grass_tree_stretch(ctx, tree, _p(stretch), C.byref(tot)),
            "grass_tree_stretch")
     return tot.value
+
+
+def grass_autotune_rows(ctx: int, tree: int, r: int, prec: int) -> tuple[list, list]:
+    """Row-kernel autotuner: returns ([chunk cap, SpMM variant, heat form],
+    [SpMM ms, heat ms])."""
+    best = (_i32 * 3)()
+    ms = (_d * 2)()
+    _check(ctx, lib().grass_autotune_rows(ctx, tree, int(r), int(prec), best, ms),
+           "grass_autotune_rows")
+    return list(best), list(ms)
 
 
 def grass_tree_destroy(tree: int) -> None:

@@ -392,6 +392,15 @@ grass_status grass_ctx_set_param(grass_ctx_t ctx, const char *name, int64_t valu
     } else if (k == "lmax_amg") {
         need(value == 0 || value == 1, "lmax_amg must be 0 or 1");
         ctx->lmax_amg = (int)value;
+    } else if (k == "spmm_variant") {
+        need(value >= -1 && value <= 7, "spmm_variant must be in [-1, 7]");
+        ctx->spmm_variant = (int)value;
+    } else if (k == "spmm_chunk") {
+        need(value == -1 || value == 0 || value == 16, "spmm_chunk must be -1, 0 or 16");
+        ctx->spmm_chunk = (int)value;
+    } else if (k == "heat_lanes") {
+        need(value >= 0 && value <= 3, "heat_lanes must be in [0, 3]");
+        ctx->heat_lanes = (int)value;
     } else if (k == "grid_sms") {
         need(value >= 0, "grid_sms must be >= 0");
         ctx->grid_sms = (int)value;
@@ -519,6 +528,16 @@ grass_status grass_build_lsst(grass_ctx_t ctx, const grass_csr_t *A, uint64_t se
         stats->rounds = ls.rounds;
         stats->ms = ms;
     }
+    API_END
+}
+
+grass_status grass_autotune_rows(grass_ctx_t ctx, grass_tree_t tree, int r, grass_prec prec,
+                                 int32_t *best, double *best_ms) {
+    if (!ctx || !tree) return GRASS_ERR_INVALID;
+    API_BEGIN(ctx)
+    need(r_supported(r), "r must be 1, 2, 4, 8, 16, 24 or 32");
+    need_prec(prec);
+    autotune_rows(ctx, tree, r, prec, best, best_ms);
     API_END
 }
 

@@ -89,76 +89,105 @@ inline int chunk_bytes(int r, size_t es, std::initializer_list<const void *> blo
     return 0;
 }
 
+// The SpMM launch variant and chunk cap for (precision, r): the
+// spmm_variant / spmm_chunk knobs when set (>= 0), else what the row-kernel
+// autotuner kept (variant 0 and the widest chunk until it runs).
+inline int r_slot(int r) {
+    switch (r) {
+        case 1: return 0;
+        case 2: return 1;
+        case 4: return 2;
+        case 8: return 3;
+        case 16: return 4;
+        case 24: return 5;
+        default: return 6;
+    }
+}
+inline int spmm_variant_of(grass_ctx_t ctx, bool fp64, int r) {
+    return ctx->spmm_variant >= 0 ? ctx->spmm_variant : ctx->spmm_tuned[fp64][r_slot(r)][1];
+}
+inline int spmm_chunk_of(grass_ctx_t ctx, bool fp64, int r) {
+    return ctx->spmm_chunk >= 0 ? ctx->spmm_chunk : ctx->spmm_tuned[fp64][r_slot(r)][0];
+}
+
 // Y = s * (L X + D .* X), (L X)_i = sum_j w_ij (X_i - X_j) (Eq. formula_laplacian).
 // L lanes per row; each lane owns CPL chunks of the row and walks the row's
 // entries in batches of B (indices and weights first, then the B gathers,
-// then the sums), B chosen so that a lane has about 64 bytes of gathers in
-// flight (more cost registers, and the occupancy lost outweighed the gain).
-template <typename T, int R, int VB>
-__global__ void __launch_bounds__(256) k_lapmm(int64_t n, const int32_t *__restrict__ ptr,
-                                               const int32_t *__restrict__ col,
-                                               const T *__restrict__ w, const T *__restrict__ D,
-                                               const T *__restrict__ X, T *__restrict__ Y,
-                                               const unsigned long long *scale_from,
-                                               int32_t heavy_deg) {
+// then the sums).  Launch variants (picked by the row-kernel autotuner, or
+// the spmm_variant knob): B = BB, or by default sized so that a lane has
+// about 64 bytes of gathers in flight; MB = the minimum resident blocks
+// per SM asked of the compiler (a register cap); BLK = each block walks its
+// own contiguous range of rows, 256 / L rows a step (the neighbour rows that
+// earlier steps loaded are still in L1), else one row per L lanes of the
+// grid.
+template <typename T, int R, int VB, int BB, int MB, bool BLK>
+__global__ void __launch_bounds__(256, MB) k_lapmm(int64_t n, const int32_t *__restrict__ ptr,
+                                                   const int32_t *__restrict__ col,
+                                                   const T *__restrict__ w, const T *__restrict__ D,
+                                                   const T *__restrict__ X, T *__restrict__ Y,
+                                                   const unsigned long long *scale_from,
+                                                   int32_t heavy_deg) {
     using RL = RowLay<T, R, VB>;
     constexpr int EL = RL::EL, L = RL::L, CPL = RL::CPL;
-    // neighbours per batch: about 64 bytes of gathers in flight per lane
     constexpr int LB = CPL * EL * (int)sizeof(T);
-    constexpr int B = LB >= 64 ? 1 : LB >= 32 ? 2 : 4;
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t i = t / L;
-    if (i >= n) return;
-    const int32_t j0 = __ldg(ptr + i), j1 = __ldg(ptr + i + 1);
-    if (j1 - j0 > heavy_deg) return;      // a hub row: k_lapmm_heavy
-    const int lane = (int)(t % L);
+    constexpr int B = BB > 0 ? BB : LB >= 64 ? 1 : LB >= 32 ? 2 : 4;
+    const int64_t per = BLK ? (n + gridDim.x - 1) / gridDim.x : 0;
+    const int64_t lo = BLK ? min(n, (int64_t)blockIdx.x * per) : 0;
+    const int64_t hi = BLK ? min(n, lo + per) : n;
+    const int lane = (int)(threadIdx.x % L);
     const T s = (T)scale_of(scale_from);
     const int64_t off = lane * CPL * EL;   // first element of this lane in a row
-    RowChunk<T, EL> x0[CPL], acc[CPL];
+    const int64_t step = BLK ? (int64_t)blockDim.x / L : n;
+    for (int64_t i = BLK ? lo + threadIdx.x / L : ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / L;
+         i < hi; i += step) {
+        const int32_t j0 = __ldg(ptr + i), j1 = __ldg(ptr + i + 1);
+        if (j1 - j0 > heavy_deg) continue;      // a hub row: k_lapmm_heavy
+        RowChunk<T, EL> x0[CPL], acc[CPL];
 #pragma unroll
-    for (int c = 0; c < CPL; ++c) {
-        x0[c] = ld_row_chunk<T, EL>(X + i * R + off + c * EL);
+        for (int c = 0; c < CPL; ++c) {
+            x0[c] = ld_row_chunk<T, EL>(X + i * R + off + c * EL);
 #pragma unroll
-        for (int e = 0; e < EL; ++e) acc[c].v[e] = (T)0;
-    }
-    for (int32_t j = j0; j < j1; j += B) {
-        int32_t cj[B];
-        T wj[B];
-#pragma unroll
-        for (int b = 0; b < B; ++b) {
-            // past the row's end: reload its last entry (every address stays
-            // inside the arrays) and mark the slot unused
-            const int32_t jb = j + b < j1 ? j + b : j1 - 1;
-            cj[b] = __ldg(col + jb);
-            wj[b] = __ldg(w + jb);
-            if (j + b >= j1) cj[b] = -1;
+            for (int e = 0; e < EL; ++e) acc[c].v[e] = (T)0;
         }
-        RowChunk<T, EL> xq[B][CPL];
+        for (int32_t j = j0; j < j1; j += B) {
+            int32_t cj[B];
+            T wj[B];
 #pragma unroll
-        for (int b = 0; b < B; ++b)
+            for (int b = 0; b < B; ++b) {
+                // past the row's end: reload its last entry (every address
+                // stays inside the arrays) and mark the slot unused
+                const int32_t jb = j + b < j1 ? j + b : j1 - 1;
+                cj[b] = __ldg(col + jb);
+                wj[b] = __ldg(w + jb);
+                if (j + b >= j1) cj[b] = -1;
+            }
+            RowChunk<T, EL> xq[B][CPL];
 #pragma unroll
-            for (int c = 0; c < CPL; ++c)
-                if (cj[b] >= 0) xq[b][c] = ld_row_chunk<T, EL>(X + (int64_t)cj[b] * R + off + c * EL);
-#pragma unroll
-        for (int b = 0; b < B; ++b)
-            if (cj[b] >= 0)
+            for (int b = 0; b < B; ++b)
 #pragma unroll
                 for (int c = 0; c < CPL; ++c)
+                    if (cj[b] >= 0) xq[b][c] = ld_row_chunk<T, EL>(X + (int64_t)cj[b] * R + off + c * EL);
 #pragma unroll
-                    for (int e = 0; e < EL; ++e) acc[c].v[e] += wj[b] * (x0[c].v[e] - xq[b][c].v[e]);
-    }
-    if (D) {
-        const T d = __ldg(D + i);
+            for (int b = 0; b < B; ++b)
+                if (cj[b] >= 0)
 #pragma unroll
-        for (int c = 0; c < CPL; ++c)
+                    for (int c = 0; c < CPL; ++c)
 #pragma unroll
-            for (int e = 0; e < EL; ++e) acc[c].v[e] += d * x0[c].v[e];
-    }
+                        for (int e = 0; e < EL; ++e) acc[c].v[e] += wj[b] * (x0[c].v[e] - xq[b][c].v[e]);
+        }
+        if (D) {
+            const T d = __ldg(D + i);
 #pragma unroll
-    for (int c = 0; c < CPL; ++c) {
+            for (int c = 0; c < CPL; ++c)
 #pragma unroll
-        for (int e = 0; e < EL; ++e) acc[c].v[e] *= s;
-        st_row_chunk<T, EL>(Y + i * R + off + c * EL, acc[c]);
+                for (int e = 0; e < EL; ++e) acc[c].v[e] += d * x0[c].v[e];
+        }
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) {
+#pragma unroll
+            for (int e = 0; e < EL; ++e) acc[c].v[e] *= s;
+            st_row_chunk<T, EL>(Y + i * R + off + c * EL, acc[c]);
+        }
     }
 }
 
@@ -213,14 +242,45 @@ __global__ void __launch_bounds__(256) k_lapmm_heavy(const int32_t *__restrict__
     }
 }
 
+template <typename T, int R, int VB, int BB, int MB, bool BLK = false>
+static void lapmm_V(grass_ctx_t ctx, int64_t n, const int32_t *ptr, const int32_t *col,
+                    const void *w, const void *D, const void *X, void *Y,
+                    const unsigned long long *sf, int32_t heavy_deg) {
+    constexpr int L = RowLay<T, R, VB>::L;
+    int64_t grid = cdiv(n * L, 256);
+    if (BLK) {
+        int nb = 0;
+        GCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_lapmm<T, R, VB, BB, MB, BLK>, 256, 0));
+        const int sms = ctx->num_sms > 0 ? ctx->num_sms : 152;
+        grid = std::min<int64_t>(grid, (int64_t)sms * std::max(nb, 1));
+    }
+    launch(ctx, k_lapmm<T, R, VB, BB, MB, BLK>, grid, 256, 0, n, ptr, col, (const T *)w,
+           (const T *)D, (const T *)X, (T *)Y, sf, heavy_deg);
+}
+
+// The autotuned launch variants of the SpMM: (batch, minimum blocks per SM)
+// = (rule, 1), (1, 1), (2, 1), (4, 1), (1, 6), (2, 6), and 6 / 7 = (rule, 1)
+// / (1, 1) with each block on a contiguous range of rows.  Element-chunk
+// layouts and r < 4 keep variant 0.
+constexpr int kSpmmVariants = 8;
+
 template <typename T, int R, int VB>
 static void lapmm_T(grass_ctx_t ctx, int64_t n, const int32_t *ptr, const int32_t *col,
                     const void *w, const void *D, const void *X, void *Y,
                     const unsigned long long *sf, const HeavyRows *hv) {
-    constexpr int L = RowLay<T, R, VB>::L;
     const bool split = hv && hv->count > 0;
-    launch(ctx, k_lapmm<T, R, VB>, cdiv(n * L, 256), 256, 0, n, ptr, col, (const T *)w,
-           (const T *)D, (const T *)X, (T *)Y, sf, split ? (int32_t)kHeavyDeg : INT32_MAX);
+    const int32_t hd = split ? (int32_t)kHeavyDeg : INT32_MAX;
+    const int v = (VB == 0 || R < 4) ? 0 : spmm_variant_of(ctx, sizeof(T) == 8, R);
+    switch (v) {
+        case 1: lapmm_V<T, R, VB, 1, 1>(ctx, n, ptr, col, w, D, X, Y, sf, hd); break;
+        case 2: lapmm_V<T, R, VB, 2, 1>(ctx, n, ptr, col, w, D, X, Y, sf, hd); break;
+        case 3: lapmm_V<T, R, VB, 4, 1>(ctx, n, ptr, col, w, D, X, Y, sf, hd); break;
+        case 4: lapmm_V<T, R, VB, 1, 6>(ctx, n, ptr, col, w, D, X, Y, sf, hd); break;
+        case 5: lapmm_V<T, R, VB, 2, 6>(ctx, n, ptr, col, w, D, X, Y, sf, hd); break;
+        case 6: lapmm_V<T, R, VB, 0, 1, true>(ctx, n, ptr, col, w, D, X, Y, sf, hd); break;
+        case 7: lapmm_V<T, R, VB, 1, 1, true>(ctx, n, ptr, col, w, D, X, Y, sf, hd); break;
+        default: lapmm_V<T, R, VB, 0, 1>(ctx, n, ptr, col, w, D, X, Y, sf, hd); break;
+    }
     if (split)
         launch(ctx, k_lapmm_heavy<T, R, VB>, hv->count, 256, 0, (const int32_t *)hv->rows.p, ptr,
                col, (const T *)w, (const T *)D, (const T *)X, (T *)Y, sf);
@@ -232,7 +292,9 @@ static void lapmm_P(grass_ctx_t ctx, int64_t n, const int32_t *ptr, const int32_
                     const unsigned long long *sf, const HeavyRows *hv) {
     // widest chunks that the row size and both blocks' alignment allow (a
     // caller's block or a slice of one may be only element-aligned)
-    switch (chunk_bytes(R, sizeof(T), {X, Y})) {
+    int vb = chunk_bytes(R, sizeof(T), {X, Y});
+    if (vb == 32 && spmm_chunk_of(ctx, sizeof(T) == 8, R) == 16) vb = 16;
+    switch (vb) {
         case 32: lapmm_T<T, R, 32>(ctx, n, ptr, col, w, D, X, Y, sf, hv); break;
         case 16: lapmm_T<T, R, 16>(ctx, n, ptr, col, w, D, X, Y, sf, hv); break;
         default: lapmm_T<T, R, 0>(ctx, n, ptr, col, w, D, X, Y, sf, hv); break;
@@ -335,12 +397,14 @@ void max_abs_bits(grass_ctx_t ctx, grass_prec prec, int64_t count, const void *X
 // heat_i = w_i * sum_j (H[u][j] - H[v][j])^2 for the i-th off-S edge
 // (Eqs. formula_Joule, formula_pwr_iter5new, formula_pwr_iter6), with H
 // multiplied by the pending power of two s (exact): heat = w s^2 sum(...).
-// One edge per thread (no shuffles: the edge lists and the heats are read and
-// written coalesced); a fixed grid walks the edges, each thread loading its
-// next edge's endpoints and weight before it consumes this edge's row
-// gathers, which it issues G chunks of 16 bytes per endpoint at a time.
+// P consecutive lanes per edge, each with C/P of the row's C
+// chunks (P > 1: the P chunks of a row that one load instruction fetches
+// lie in one cache line; partial sums meet by xor shuffles), E edges in
+// flight per lane.  The edge lists and the heats are read and written in
+// order; a fixed grid walks the edges, each lane loading its next edges'
+// endpoints and weights before it consumes this step's row gathers.
 // Every block ends with one atomicMax of its largest heat.
-template <typename T, int R, int VB>
+template <typename T, int R, int VB, int P, int E>
 __global__ void __launch_bounds__(256) k_heat(int64_t moff, const int32_t *__restrict__ ou,
                                               const int32_t *__restrict__ ov,
                                               const T *__restrict__ ow, const T *__restrict__ H,
@@ -348,67 +412,125 @@ __global__ void __launch_bounds__(256) k_heat(int64_t moff, const int32_t *__res
                                               T *__restrict__ heat, unsigned long long *heatmax) {
     using RL = RowLay<T, R, VB>;
     constexpr int EL = RL::EL, C = R / EL;
-    // chunks per endpoint in flight together: at most four, dividing the row
-    constexpr int G = C % 4 == 0 ? 4 : C % 3 == 0 ? 3 : C % 2 == 0 ? 2 : 1;
-    static_assert(C % G == 0, "chunk groups must tile the row");
+    static_assert(P >= 1 && C % P == 0 && 32 % P == 0, "lanes must split the row");
+    constexpr int CP = C / P;                 // chunks per lane
+    // chunks per endpoint in flight together: at most four (two with two
+    // edges in flight), dividing CP
+    constexpr int GM = E == 1 ? 4 : 2;
+    constexpr int G = CP % GM == 0 ? GM : (CP % 3 == 0 && GM >= 3) ? 3 : CP % 2 == 0 ? 2 : 1;
+    static_assert(CP % G == 0, "chunk groups must tile the lane's share");
     const T s = (T)scale_of(scale_from);
     const T s2 = s * s;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = (int)(gt % P);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x / P;
+    const int off = lane * CP * EL;
     double mx = 0.0;
-    int32_t eu = 0, ev = 0;
-    T ew = (T)0;
-    if (i < moff) {
-        eu = __ldg(ou + i);
-        ev = __ldg(ov + i);
-        ew = __ldg(ow + i);
-    }
-    for (; i < moff; i += stride) {
-        // the next edge of this thread (its last one reloads itself, so
-        // every address stays inside the arrays)
-        const int64_t inx = i + stride < moff ? i + stride : i;
-        const int32_t nu = __ldg(ou + inx), nv = __ldg(ov + inx);
-        const T nw = __ldg(ow + inx);
-        const T *hu = H + (int64_t)eu * R;
-        const T *hv = H + (int64_t)ev * R;
-        T part = (T)0;
+    // E edges per lane and step: i, i + stride, ..., i + (E-1) stride; the
+    // lane's edges beyond moff reload the last edge (every address stays
+    // inside the arrays) and are not written
+    int64_t i = gt / P;
+    int32_t eu[E], ev[E];
+    T ew[E];
+    auto load_edges = [&](int64_t i0, int32_t (&u)[E], int32_t (&v)[E], T (&w)[E]) {
 #pragma unroll
-        for (int c0 = 0; c0 < C; c0 += G) {
-            RowChunk<T, EL> a[G], b[G];
-#pragma unroll
-            for (int g = 0; g < G; ++g) {
-                a[g] = ld_row_chunk<T, EL>(hu + (c0 + g) * EL);
-                b[g] = ld_row_chunk<T, EL>(hv + (c0 + g) * EL);
-            }
-#pragma unroll
-            for (int g = 0; g < G; ++g)
-#pragma unroll
-                for (int e = 0; e < EL; ++e) {
-                    const T d = a[g].v[e] - b[g].v[e];
-                    part += d * d;
-                }
+        for (int q = 0; q < E; ++q) {
+            int64_t k = i0 + q * stride;
+            if (k >= moff) k = moff - 1;
+            u[q] = __ldg(ou + k);
+            v[q] = __ldg(ov + k);
+            w[q] = __ldg(ow + k);
         }
-        const T h = ew * (part * s2);
-        heat[i] = h;
-        mx = fmax(mx, (double)h);
-        eu = nu;
-        ev = nv;
-        ew = nw;
+    };
+    if (i < moff) load_edges(i, eu, ev, ew);
+    // every lane of a group runs the same trip count (same i), so the
+    // shuffles below see the whole group
+    for (; i < moff; i += E * stride) {
+        int32_t nu[E], nv[E];
+        T nw[E];
+        load_edges(i + E * stride < moff ? i + E * stride : i, nu, nv, nw);
+        T part[E];
+#pragma unroll
+        for (int q = 0; q < E; ++q) part[q] = (T)0;
+#pragma unroll
+        for (int c0 = 0; c0 < CP; c0 += G) {
+            RowChunk<T, EL> a[E][G], b[E][G];
+#pragma unroll
+            for (int q = 0; q < E; ++q)
+#pragma unroll
+                for (int g = 0; g < G; ++g) {
+                    a[q][g] = ld_row_chunk<T, EL>(H + (int64_t)eu[q] * R + off + (c0 + g) * EL);
+                    b[q][g] = ld_row_chunk<T, EL>(H + (int64_t)ev[q] * R + off + (c0 + g) * EL);
+                }
+#pragma unroll
+            for (int q = 0; q < E; ++q)
+#pragma unroll
+                for (int g = 0; g < G; ++g)
+#pragma unroll
+                    for (int e = 0; e < EL; ++e) {
+                        const T d = a[q][g].v[e] - b[q][g].v[e];
+                        part[q] += d * d;
+                    }
+        }
+#pragma unroll
+        for (int q = 0; q < E; ++q) {
+            if constexpr (P > 1) {
+                const unsigned gm = ((1u << P) - 1u) << (((int)threadIdx.x & 31) & ~(P - 1));
+#pragma unroll
+                for (int d = P / 2; d > 0; d >>= 1) part[q] += __shfl_xor_sync(gm, part[q], d, P);
+            }
+            const int64_t k = i + q * stride;
+            if (k < moff) {
+                const T h = ew[q] * (part[q] * s2);
+                if (lane == 0) heat[k] = h;
+                mx = fmax(mx, (double)h);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < E; ++q) {
+            eu[q] = nu[q];
+            ev[q] = nv[q];
+            ew[q] = nw[q];
+        }
     }
     block_atomic_max(heatmax, mx);
 }
 
+// lanes per edge: the largest power of two (at most 4) dividing the row's
+// chunks
 template <typename T, int R, int VB>
-static void heat_T(grass_ctx_t ctx, grass_sparsifier_t S, const void *H,
+struct HeatLanes {
+    static constexpr int C = R / RowLay<T, R, VB>::EL;
+    static constexpr int P = C % 4 == 0 ? 4 : C % 2 == 0 ? 2 : 1;
+};
+
+template <typename T, int R, int VB, int P, int E>
+static void heat_L(grass_ctx_t ctx, grass_sparsifier_t S, const void *H,
                    const unsigned long long *sf, void *heat, unsigned long long *hm) {
     const int64_t moff = S->m_off;
     const int sms = ctx->num_sms > 0 ? ctx->num_sms : 152;
     int nb = 0;
-    GCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_heat<T, R, VB>, 256, 0));
-    const int64_t grid = std::min<int64_t>(cdiv(moff, 256), (int64_t)sms * std::max(nb, 1));
+    GCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_heat<T, R, VB, P, E>, 256, 0));
+    const int64_t grid =
+        std::min<int64_t>(cdiv(cdiv(moff, E) * P, 256), (int64_t)sms * std::max(nb, 1));
     const T *ow = sizeof(T) == 8 ? (const T *)S->off_w64.p : (const T *)S->off_w32.p;
-    launch(ctx, k_heat<T, R, VB>, grid, 256, 0, moff, (const int32_t *)S->off_u.p,
+    launch(ctx, k_heat<T, R, VB, P, E>, grid, 256, 0, moff, (const int32_t *)S->off_u.p,
            (const int32_t *)S->off_v.p, ow, (const T *)H, sf, (T *)heat, hm);
+}
+
+// heat_lanes knob / autotuner choice: 0 = P lanes per edge (by row size),
+// one edge in flight; 1 = one lane per edge; 2 = P lanes, two edges in
+// flight per lane; 3 = one lane, two edges
+template <typename T, int R, int VB>
+static void heat_T(grass_ctx_t ctx, grass_sparsifier_t S, const void *H,
+                   const unsigned long long *sf, void *heat, unsigned long long *hm) {
+    constexpr int P = HeatLanes<T, R, VB>::P;
+    switch (ctx->heat_lanes) {
+        case 1: heat_L<T, R, VB, 1, 1>(ctx, S, H, sf, heat, hm); break;
+        case 2: heat_L<T, R, VB, P, 2>(ctx, S, H, sf, heat, hm); break;
+        case 3: heat_L<T, R, VB, 1, 2>(ctx, S, H, sf, heat, hm); break;
+        default: heat_L<T, R, VB, P, 1>(ctx, S, H, sf, heat, hm); break;
+    }
 }
 
 template <typename T, int R>
@@ -498,6 +620,105 @@ void quad_forms(grass_ctx_t ctx, grass_prec prec, grass_sparsifier_t S, const vo
         launch(ctx, k_quad<float>, grid, kBlock, 0, g.m, (const int32_t *)g.eu.p,
                (const int32_t *)g.ev.p, (const double *)g.ew64.p, (const uint8_t *)S->in_s.p,
                (const float *)x, ctx->partials.p, ctx->counters.p + 2, out);
+}
+
+}  // namespace grass
+
+// ---------------------------------------------------------------- row-kernel autotuner
+
+namespace grass {
+
+// Times the r-column SpMM over the tree's graph under every launch variant
+// and chunk width, and the heat kernel of the tree's off-tree edges in each
+// of its forms; keeps the fastest on the context.  Results of either kernel
+// are the same up to rounding order under any choice.
+void autotune_rows(grass_ctx_t ctx, grass_tree_t T, int r, grass_prec prec, int32_t *best,
+                   double *best_ms) {
+    const GraphData &g = T->g;
+    const int64_t n = g.n;
+    const bool f64 = prec == GRASS_FP64;
+    const size_t es = f64 ? 8 : 4;
+    DBuf<char> X, Y;
+    X.alloc(n * r * es);
+    Y.alloc(n * r * es);
+    memset_d(ctx, X.p, 0, n * r * es);
+    const void *w = f64 ? (const void *)g.adj_w64.p : (const void *)g.adj_w32.p;
+    cudaEvent_t e0, e1;
+    GCK(cudaEventCreate(&e0));
+    GCK(cudaEventCreate(&e1));
+    const int keep_v = ctx->spmm_variant, keep_c = ctx->spmm_chunk, keep_h = ctx->heat_lanes;
+    auto timed = [&](auto &&fn) {
+        fn();   // warm
+        GCK(cudaEventRecord(e0, ctx->stream));
+        for (int k = 0; k < 5; ++k) fn();
+        GCK(cudaEventRecord(e1, ctx->stream));
+        GCK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        GCK(cudaEventElapsedTime(&ms, e0, e1));
+        return ms / 5.0;
+    };
+    int bc = 0, bv = 0, bh = 0;
+    double bms = 1e300, hms = 1e300;
+    grass_sparsifier_t S = nullptr;
+    try {
+        const int widest = chunk_bytes(r, es, {X.p, Y.p});
+        for (int cap : {0, 16}) {
+            if (cap == 16 && widest != 32) continue;
+            for (int v = 0; v < kSpmmVariants; ++v) {
+                if (v > 0 && r < 4) break;
+                ctx->spmm_chunk = cap;
+                ctx->spmm_variant = v;
+                const double ms = timed([&] {
+                    lap_mm(ctx, r, prec, n, 2 * g.m, g.adj_ptr.p, g.adj_col.p, w, nullptr, X.p,
+                           Y.p, nullptr, GRASS_KF_NONE, &g.heavy);
+                });
+                if (ms < bms) {
+                    bms = ms;
+                    bc = cap;
+                    bv = v;
+                }
+            }
+        }
+        if (grass_sparsifier_create(ctx, T, &S) != GRASS_OK) fail(GRASS_ERR_CUDA, "autotune sparsifier");
+        if (S->m_off > 0) {
+            DBuf<char> heat;
+            heat.alloc(S->m_off * es);
+            unsigned long long *hm = (unsigned long long *)(ctx->scal.p + DS_MAX + 13);
+            for (int h = 0; h <= 3; ++h) {
+                ctx->heat_lanes = h;
+                const double ms = timed([&] { heat_offs(ctx, r, prec, S, X.p, nullptr, heat.p, hm); });
+                if (ms < hms) {
+                    hms = ms;
+                    bh = h;
+                }
+            }
+        }
+    } catch (...) {
+        if (S) grass_sparsifier_destroy(S);
+        ctx->spmm_variant = keep_v;
+        ctx->spmm_chunk = keep_c;
+        ctx->heat_lanes = keep_h;
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        throw;
+    }
+    if (S) grass_sparsifier_destroy(S);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->spmm_variant = keep_v;
+    ctx->spmm_chunk = keep_c;
+    ctx->spmm_tuned[f64][r_slot(r)][0] = bc;
+    ctx->spmm_tuned[f64][r_slot(r)][1] = bv;
+    ctx->heat_lanes = bh;
+    if (best) {
+        best[0] = bc;
+        best[1] = bv;
+        best[2] = bh;
+    }
+    if (best_ms) {
+        best_ms[0] = bms;
+        best_ms[1] = hms < 1e299 ? hms : 0.0;
+    }
 }
 
 }  // namespace grass

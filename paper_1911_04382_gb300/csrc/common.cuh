@@ -109,6 +109,11 @@ struct grass_ctx_s {
     // launch-shape knobs (grass_ctx_set_param)
     int tree_bpsm = 1;
     int grid_sms = 0;      // cooperative grids on at most this many SMs (0: all)
+    int heat_lanes = 0;    // heat kernel form (0-3), see blk.cu heat_T
+    // SpMM launch variant (0..7) and chunk cap (0 = widest, 16) when >= 0;
+    // else spmm_tuned[fp64][r slot] = {chunk cap, variant} from the autotuner
+    int spmm_variant = -1, spmm_chunk = -1;
+    int spmm_tuned[2][7][2] = {};
     int tree_threads = 1024;
     int64_t tree_tail_items = 2048;
     int euler_solve = 1;   // scan form for grounded r = 1 solves without D
@@ -498,6 +503,11 @@ void tree_solve_inplace(grass_ctx_t ctx, grass_tree_t T, const TreeFactor &f, in
 void lap_mm(grass_ctx_t ctx, int r, grass_prec prec, int64_t n, int64_t nnz, const int32_t *ptr,
             const int32_t *col, const void *w, const void *Dopt, const void *X, void *Y,
             const unsigned long long *scale_from, int fam, const HeavyRows *hv);
+// Row-kernel autotuner (blk.cu): SpMM launch variant and chunk width, heat
+// kernel form, timed on the tree's graph; kept on ctx.  best: [3] chunk cap,
+// variant, heat form; best_ms: [2] SpMM and heat ms per launch.
+void autotune_rows(grass_ctx_t ctx, grass_tree_t T, int r, grass_prec prec, int32_t *best,
+                   double *best_ms);
 // hv.rows / hv.count for an adjacency (n rows, nnz entries); synchronises.
 void heavy_rows(grass_ctx_t ctx, int64_t n, int64_t nnz, const int32_t *ptr, HeavyRows &hv);
 // Convert an n x r double block to prec (copy or float conversion).

@@ -220,6 +220,64 @@ __global__ void k_ls_commit(int64_t nx, const int32_t *xl, int t, const unsigned
     }
 }
 
+// A whole level (rounds 0..S, the same four passes) in one block, for the
+// many small levels: __syncthreads between the passes in place of launches.
+constexpr int kLevelBlock = 1024;
+constexpr int64_t kSmallLevel = 32768;   // active edges
+
+__global__ void __launch_bounds__(kLevelBlock) k_ls_level(
+    int64_t na, int64_t nx, const int32_t *act, const int32_t *ca, const int32_t *cb,
+    const int32_t *xl, const int *smax, const int32_t *start, const double *ew, int32_t *ctr,
+    int32_t *when, unsigned long long *key, unsigned long long *wb, int32_t *eb,
+    uint8_t *in_tree) {
+    const int S = *smax;
+    for (int t = 0; t <= S; ++t) {
+        for (int64_t k = threadIdx.x; k < na; k += blockDim.x) {
+            const int32_t x = ca[k], y = cb[k];
+            const int32_t cx = ctr[x], cy = ctr[y];
+            if (cx < 0 && cy >= 0 && when[y] == t - 1) atomicMin(key + x, ls_key(start, cy));
+            else if (cy < 0 && cx >= 0 && when[x] == t - 1) atomicMin(key + y, ls_key(start, cx));
+        }
+        __syncthreads();
+        for (int64_t k = threadIdx.x; k < na; k += blockDim.x) {
+            const int32_t x = ca[k], y = cb[k];
+            const int32_t cx = ctr[x], cy = ctr[y];
+            if (cx < 0 && cy >= 0 && when[y] == t - 1) {
+                if (ls_key(start, cy) == key[x]) atomicMax(wb + x, wbits(ew[act[k]]));
+            } else if (cy < 0 && cx >= 0 && when[x] == t - 1) {
+                if (ls_key(start, cx) == key[y]) atomicMax(wb + y, wbits(ew[act[k]]));
+            }
+        }
+        __syncthreads();
+        for (int64_t k = threadIdx.x; k < na; k += blockDim.x) {
+            const int32_t x = ca[k], y = cb[k];
+            const int32_t cx = ctr[x], cy = ctr[y];
+            const int32_t e = act[k];
+            if (cx < 0 && cy >= 0 && when[y] == t - 1) {
+                if (ls_key(start, cy) == key[x] && wbits(ew[e]) == wb[x]) atomicMin(eb + x, e);
+            } else if (cy < 0 && cx >= 0 && when[x] == t - 1) {
+                if (ls_key(start, cx) == key[y] && wbits(ew[e]) == wb[y]) atomicMin(eb + y, e);
+            }
+        }
+        __syncthreads();
+        for (int64_t i = threadIdx.x; i < nx; i += blockDim.x) {
+            const int32_t x = xl[i];
+            if (ctr[x] >= 0) continue;
+            const unsigned long long kk = key[x];
+            if (kk != kNoKey) {
+                ctr[x] = (int32_t)(uint32_t)(kk & 0xFFFFFFFFull);
+                when[x] = t;
+                const int32_t e = eb[x];
+                if (e != kNoEdgeId) in_tree[e] = 1;
+            } else if (start[x] == t) {
+                ctr[x] = x;
+                when[x] = t;
+            }
+        }
+        __syncthreads();
+    }
+}
+
 __global__ void k_ls_relabel(int64_t n, const int32_t *ctr, int32_t *label) {
     int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= n) return;
@@ -426,7 +484,14 @@ void lsst_build(grass_ctx_t ctx, const GraphData &g, uint64_t seed, uint8_t *in_
             launch(ctx, k_ls_xinit, cdiv(nx, kBlock), kBlock, 0, nx, (const int32_t *)xl.p,
                    (const int *)(small.p + 2), (unsigned long long)seed, c, level, ctr.p, when.p,
                    start.p, key.p, wb.p, eb.p);
-            for (int t = 0; t <= S; ++t) {
+            if (na <= kSmallLevel) {
+                launch(ctx, k_ls_level, 1, kLevelBlock, 0, na, nx, (const int32_t *)act[cur].p,
+                       (const int32_t *)ca[cur].p, (const int32_t *)cb[cur].p,
+                       (const int32_t *)xl.p, (const int *)(small.p + 2), (const int32_t *)start.p,
+                       (const double *)g.ew64.p, ctr.p, when.p, key.p, wb.p, eb.p, in_tree);
+                edge_passes += 3 * (S + 1);
+            }
+            for (int t = 0; t <= S && na > kSmallLevel; ++t) {
                 launch(ctx, k_ls_offer, cdiv(na, kBlock), kBlock, 0, na, (const int32_t *)ca[cur].p,
                        (const int32_t *)cb[cur].p, (const int32_t *)ctr.p, (const int32_t *)when.p,
                        (const int32_t *)start.p, t, key.p);

@@ -178,6 +178,50 @@ def test_spmm_hub_rows_match_oracle(gpu, r, which):
             assert torch.equal(Y2, Y32)          # deterministic
 
 
+@pytest.mark.parametrize("variant", range(8))
+@pytest.mark.parametrize("chunk", [0, 16])
+@pytest.mark.parametrize("r", [4, 8, 16, 24, 32])
+def test_spmm_variants_match_oracle(gpu, variant, chunk, r):
+    """Every SpMM launch variant the row-kernel autotuner picks from (batch
+    by row size / 1 / 2 / 4, register cap, per-block contiguous rows), at
+    the widest and at 16-byte chunks, both precisions."""
+    import torch
+    g = graphs.grid3d_loguniform(15, 13, 11, seed=23)
+    og = oracle.from_graph(g)
+    X = rng.gaussian_block(23, 5, g.n, r)
+    ref = oracle.lap_apply(og, X)
+    with gpu_graph(g) as (ctx, tree, _):
+        gpu.grass_ctx_set_param(ctx, "spmm_variant", variant)
+        gpu.grass_ctx_set_param(ctx, "spmm_chunk", chunk)
+        Y = torch.zeros(g.n, r, dtype=torch.float64, device="cuda")
+        gpu.grass_spmm(ctx, tree, r, gpu.GRASS_FP64, dev(X), Y)
+        assert np.abs(host(Y) - ref).max() <= 1e-12 * np.abs(ref).max()
+        Y32 = torch.zeros(g.n, r, dtype=torch.float32, device="cuda")
+        gpu.grass_spmm(ctx, tree, r, gpu.GRASS_FP32, dev(X, torch.float32), Y32)
+        assert np.abs(host(Y32) - ref).max() <= 1e-4 * np.abs(ref).max()
+
+
+def test_row_autotuner_keeps_results(gpu):
+    """grass_autotune_rows picks a variant, a chunk width and a heat form
+    (each within its range), and the products after it still match."""
+    import torch
+    g = graphs.grid3d_loguniform(30, 30, 30, seed=24)
+    og = oracle.from_graph(g)
+    X = rng.gaussian_block(24, 5, g.n, 16)
+    ref = oracle.lap_apply(og, X)
+    with gpu_graph(g) as (ctx, tree, _):
+        for prec in (gpu.GRASS_FP32, gpu.GRASS_FP64):
+            best, ms = gpu.grass_autotune_rows(ctx, tree, 16, prec)
+            assert best[0] in (0, 16) and 0 <= best[1] <= 7 and 0 <= best[2] <= 3
+            assert ms[0] > 0 and ms[1] > 0
+        Y = torch.zeros(g.n, 16, dtype=torch.float64, device="cuda")
+        gpu.grass_spmm(ctx, tree, 16, gpu.GRASS_FP64, dev(X), Y)
+        assert np.abs(host(Y) - ref).max() <= 1e-12 * np.abs(ref).max()
+        Y32 = torch.zeros(g.n, 16, dtype=torch.float32, device="cuda")
+        gpu.grass_spmm(ctx, tree, 16, gpu.GRASS_FP32, dev(X, torch.float32), Y32)
+        assert np.abs(host(Y32) - ref).max() <= 1e-4 * np.abs(ref).max()
+
+
 @pytest.mark.parametrize("gi", range(6))
 @pytest.mark.parametrize("ground", [0, -1])
 def test_tree_solve_matches_oracle(gpu, gi, ground):
@@ -212,7 +256,8 @@ def test_tree_solve_matches_oracle(gpu, gi, ground):
         assert np.abs(host(X32) - ref0).max() <= 1e-3 * np.abs(ref0).max()
 
 
-def _heat_parity(gpu, g, t, r, extra_every=0, inner_tol=1e-13, inner_maxit=2000, rho=0):
+def _heat_parity(gpu, g, t, r, extra_every=0, inner_tol=1e-13, inner_maxit=2000, rho=0,
+                 knobs=None):
     import torch
     og = oracle.from_graph(g)
     ot = oracle.build_tree(og, rho)
@@ -224,6 +269,8 @@ def _heat_parity(gpu, g, t, r, extra_every=0, inner_tol=1e-13, inner_maxit=2000,
     H_ref = oracle.embed(og, ot, in_s, h0, t, inner_tol, inner_maxit)
     hv_ref, off_ref = oracle.heat(og, in_s, H_ref)
     with gpu_graph(g, rho) as (ctx, tree, _):
+        for k, v in (knobs or {}).items():
+            gpu.grass_ctx_set_param(ctx, k, v)
         S = gpu.grass_sparsifier_create(ctx, tree)
         try:
             if extra_every:
@@ -259,6 +306,31 @@ def test_embed_heat_tree_matches_oracle(gpu, gi):
 @pytest.mark.parametrize("t,r", [(1, 1), (2, 2), (2, 4), (3, 16), (2, 24), (1, 32)])
 def test_embed_heat_shapes(gpu, t, r):
     _heat_parity(gpu, graphs.grid2d_uniform(40, 33, seed=31), t=t, r=r, rho=17)
+
+
+@pytest.mark.parametrize("form", [0, 1, 2, 3])
+@pytest.mark.parametrize("t,r", [(2, 2), (2, 8), (3, 16), (2, 24), (1, 32)])
+def test_heat_forms_match_oracle(gpu, form, t, r):
+    """Heat in each of its forms (the heat_lanes knob: several or one lane
+    per edge, one or two edges in flight per lane); an odd off-tree edge count
+    (37 x 29 of them) gives the two-edge forms a ragged end.  FP64 against
+    the oracle, and FP32 against the oracle's heats at the FP32 tolerance."""
+    import torch
+    g = graphs.grid2d_uniform(38, 30, seed=33)
+    hv, hv_ref, off_ref, _, _, _ = _heat_parity(gpu, g, t=t, r=r, rho=5,
+                                                knobs={"heat_lanes": form})
+    og = oracle.from_graph(g)
+    h0 = rng.gaussian_block(7, rng.STREAM_H0, g.n, r)
+    with gpu_graph(g, 5) as (ctx, tree, _):
+        gpu.grass_ctx_set_param(ctx, "heat_lanes", form)
+        S = gpu.grass_sparsifier_create(ctx, tree)
+        try:
+            heat = torch.empty(off_ref.shape[0], dtype=torch.float32, device="cuda")
+            gpu.grass_embed(ctx, S, dev(h0), r, t, gpu.GRASS_FP32, 1e-13, 2000, None, heat)
+            h32 = host(heat).astype(np.float64)
+            assert np.abs(h32 / h32.max() - hv_ref / hv_ref.max()).max() <= 1e-3
+        finally:
+            gpu.grass_sparsifier_destroy(S)
 
 
 @pytest.mark.parametrize("gi", [0, 2, 4])
