@@ -313,12 +313,21 @@ def solve_40m(G, w=SOLVE40M) -> dict:
         G.grass_tree_destroy(tree)
         return dict(total=t5 - t0, tree=t2 - t1, densify=t3 - t2, pcg=t4 - t3, status=s,
                     iters=ps.iters, rel=ps.rel_resid_fp64, rounds=st.rounds, added=st.added,
-                    lmax=list(st.lmax_est[:st.rounds + 1]), n_s=n_s)
+                    lmax=list(st.lmax_est[:st.rounds + 1]), n_s=n_s,
+                    capped=list(st.lmax_capped[:st.rounds + 1]),
+                    stopped=bool(st.stopped_similar))
 
     try:
         once(False)                                  # warm (allocations, first launches)
         a = once(False)
         e = once(True)
+        # the same solve with the lambda_max estimate's solves by
+        # multigrid-preconditioned CG (lmax_amg): a converged estimate may
+        # let the stop test end densification early
+        G.grass_ctx_set_param(ctx, "lmax_amg", 1)
+        once(False)
+        m = once(False)
+        G.grass_ctx_set_param(ctx, "lmax_amg", 0)
         out = {"metric": "40M-unknown SDD solve s to 1e-3", "value": a["total"], "unit": "s",
                "higher_is_better": False,
                "workload": f"power-grid mesh {w['k']}x{w['k']} ({g.n} unknowns, {g.nnz} stored "
@@ -333,6 +342,14 @@ def solve_40m(G, w=SOLVE40M) -> dict:
                "e2e": {"value": e["total"], "unit": "s",
                        "h2d_bytes": sum(t.numel() * t.element_size() for t in hp),
                        "d2h_bytes": xh.numel() * 8},
+               "lmax_capped": a["capped"], "stopped_similar": a["stopped"],
+               "lmax_multigrid": {"value": m["total"], "unit": "s",
+                                  "phase_s": {"tree": m["tree"], "densify": m["densify"],
+                                              "pcg": m["pcg"]},
+                                  "rounds": m["rounds"], "added": m["added"],
+                                  "lmax_est": m["lmax"], "lmax_capped": m["capped"],
+                                  "stopped_similar": m["stopped"], "pcg_iters": m["iters"],
+                                  "rel_resid_fp64": m["rel"], "status": m["status"]},
                "host_generation_s": gen_s,
                "paper_context": "110 s, 34 PCG iterations: thupg8 (4.0e7 unknowns, 1.8e8 "
                                 "nonzeros), one 2.67 GHz CPU core, Cholmod-factored sparsifier"}
@@ -1131,8 +1148,16 @@ def main() -> int:
         return 0
 
     if args.profile_step:
+        # the autotuner's choice first (as in the timed run), then one step
+        # inside the NVTX range "step" (ncu --nvtx --nvtx-include "step/")
+        t_tune = G.grass_build_tree(ctx, rp, col, val, 0)
+        G.grass_autotune_rows(ctx, t_tune, w["r"], embed_prec)
+        G.grass_tree_destroy(t_tune)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("step")
         e = step(rp, col, val, h0d, v0d, bd, x)
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
         print(json.dumps({"profile_step": True, "edges": e, "launches": G.grass_launch_count(ctx),
                           "phase_ms": last.get("phase_ms")}), flush=True)
         G.grass_ctx_destroy(ctx)

@@ -76,7 +76,6 @@ void sparsifier_rebuild(grass_ctx_t ctx, grass_sparsifier_t S) {
            S->off_w64.p, S->off_w32.p);
     S->m_off = moff;
     S->n_edges = m - moff;
-
     S->is_tree = S->n_edges == n - S->tree->nroots;
     S->degS.reserve(n);
     int64_t *cnt = ctx->scr<int64_t>(SCR_TMP2, n + 1);
