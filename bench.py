@@ -222,11 +222,12 @@ def kernel_sources_hash(read=None) -> str:
 
 def profile_kernel(G, ctx, which, g, rp, col, val, v0d, w) -> int:
     """One warm and one timed launch of the fused inner CG (exactly 30
-    iterations, r = 1, FP32, sparsifier = tree + every 197th off-tree edge)
-    or of the tree solve (r = 16, FP32); prints its algorithmic bytes."""
+    iterations, r = 1 -- "cg" -- or r = 16 -- "cg16", one embedding step --,
+    FP32, sparsifier = tree + every 197th off-tree edge), of the fused PCG, or
+    of the tree solve (r = 16, FP32); prints its algorithmic bytes."""
     import torch
     tree = G.grass_build_tree(ctx, rp, col, val, 0)
-    if which in ("cg", "pcg"):
+    if which in ("cg", "pcg", "cg16"):
         S = G.grass_sparsifier_create(ctx, tree)
         _, moff = G.grass_sparsifier_info(S)
         ids = torch.empty(moff, dtype=torch.int64, device="cuda")
@@ -235,6 +236,11 @@ def profile_kernel(G, ctx, which, g, rp, col, val, v0d, w) -> int:
         if which == "cg":
             run = lambda: G.grass_lambda_max(ctx, S, v0d[:g.n], 1, G.GRASS_FP32, 0.0, 30)
             fam, units = G.GRASS_KF_CG, "30 iterations, r=1"
+        elif which == "cg16":
+            from synth import rng as _rng
+            h16 = torch.from_numpy(_rng.gaussian_block(w["seed"], _rng.STREAM_H0, g.n, 16)).cuda()
+            run = lambda: G.grass_embed(ctx, S, h16, 16, 1, G.GRASS_FP32, 0.0, 30)
+            fam, units = G.GRASS_KF_CG, "30 iterations, r=16 (one embedding step)"
         else:
             bq = v0d[:g.n].contiguous()
             xq = torch.zeros(g.n, dtype=torch.float64, device="cuda")
@@ -1032,7 +1038,7 @@ def main() -> int:
     ap.add_argument("--profile-amg", action="store_true",
                     help="one warm and one NVTX-ranged ('amgpcg') multigrid-preconditioned PCG solve "
                          "(FP32 + FP64 refinement, 1e-8) on the step's sparsifier, for ncu launch lists")
-    ap.add_argument("--profile-kernel", choices=["cg", "tree", "pcg"], default=None,
+    ap.add_argument("--profile-kernel", choices=["cg", "cg16", "tree", "pcg"], default=None,
                     help="one warm launch, then one timed launch of the kernel (for ncu captures)")
     ap.add_argument("--no-solve40m", action="store_true",
                     help="skip the 40M-unknown solve (solve_40m key of the line)")
