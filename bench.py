@@ -996,9 +996,18 @@ def lsst_extras(G, w: dict, P, g, h0d, v0d, bd) -> dict:
     gm = graphs.grid((1000, 1000), None, 1e-3)
     wm = dict(w, pcg_tol=1e-3, pcg="fp32")
     bm = torch.from_numpy(rng.normal(4, rng.STREAM_RHS, gm.n)).cuda()
-    res["unit_mesh_1000"] = lsst_vs_mst(G, wm, P, gm, None, None, bm,
-                                        "1000x1000 unit mesh, D = 1e-3 I; tree-only PCG to 1e-3 "
-                                        "(FP32 + FP64 refinement)")
+    R = w["rounds"]
+    hm = torch.from_numpy(np.concatenate([rng.gaussian_block(4, rng.STREAM_H0 + k, gm.n, w["r"])
+                                          for k in range(R)])).cuda()
+    vm = torch.from_numpy(np.concatenate([rng.normal(4, rng.STREAM_V0 + k, gm.n)
+                                          for k in range(R)])).cuda()
+    Pm = G.make_params(w["sigma2"], w["r"], w["t"], R, w["lmax_iters"], int(w["cap_frac"] * gm.n),
+                       G.GRASS_FP32 if w["embed"] == "fp32" else G.GRASS_FP64, w["inner_tol"],
+                       w["inner_maxit"])
+    res["unit_mesh_1000"] = lsst_vs_mst(G, wm, Pm, gm, hm, vm, bm,
+                                        "1000x1000 unit mesh, D = 1e-3 I; the step's densification "
+                                        "parameters; PCG to 1e-3 (FP32 + FP64 refinement), tree "
+                                        "only and with the sparsifier")
     return res
 
 
