@@ -977,6 +977,22 @@ def lsst_vs_mst(G, w: dict, P, g=None, h0d=None, v0d=None, bd=None, label: str =
                     r_["pcg_sparsifier"] = {"iters": ps.iters,
                                             "ms": 1e3 * (time.perf_counter() - t0),
                                             "rel_resid_fp64": ps.rel_resid_fp64, "status": st_}
+                    # the same sparsifier applied by its multigrid V-cycle
+                    # (pcg_precond = 1; the first call builds the hierarchy)
+                    G.grass_ctx_set_param(ctx, "pcg_precond", 1)
+                    try:
+                        x.zero_()
+                        G.grass_pcg_solve(ctx, S, bd, x, w["pcg_tol"], w["pcg_maxit"], pcg_prec,
+                                          w["refine_tol"], w["pcg_inner_tol"], 0)
+                        x.zero_()
+                        t0 = time.perf_counter()
+                        st_, ps = G.grass_pcg_solve(ctx, S, bd, x, w["pcg_tol"], w["pcg_maxit"],
+                                                    pcg_prec, w["refine_tol"], w["pcg_inner_tol"], 0)
+                        r_["pcg_sparsifier_multigrid"] = {
+                            "iters": ps.iters, "ms": 1e3 * (time.perf_counter() - t0),
+                            "rel_resid_fp64": ps.rel_resid_fp64, "status": st_}
+                    finally:
+                        G.grass_ctx_set_param(ctx, "pcg_precond", 0)
             finally:
                 if S:
                     G.grass_sparsifier_destroy(S)

@@ -6,12 +6,14 @@
 //
 // Setup, level by level until at most kCoarse vertices remain:
 //  1. heavy-edge matching: rounds in which every unmatched vertex names its
-//     heaviest unmatched neighbour (weight descending, smaller id on ties)
-//     and mutual choices are matched -- each matched edge is the heaviest at
+//     heaviest unmatched neighbour (weight descending, equal weights by a
+//     fixed hash of the edge's end pair) and mutual choices are matched --
+//     each matched edge is the heaviest at
 //     both its ends among the remaining ones (a locally dominant matching;
 //     the result does not depend on timing);
 //  2. an unmatched vertex joins the pair of its heaviest matched neighbour
-//     (its anchor); a vertex with no matched neighbour stays alone;
+//     (its anchor; the same tie-break); a vertex with no matched neighbour
+//     stays alone;
 //  3. aggregates are numbered in order of their smallest vertex; members
 //     are listed as: the pair's smaller id, the other, the joiners anchored
 //     at the smaller in the order of its adjacency row, then those of the
@@ -42,9 +44,24 @@ constexpr double kOmega = 2.0 / 3.0;
 
 // ---------------------------------------------------------------- setup kernels
 
-// heavier (w, smaller id) than the current best?
-__device__ __forceinline__ bool better(double w, int32_t u, double bw, int32_t bu) {
-    return w > bw || (w == bw && u < bu);
+// Tie-break key of the edge {a, b}: the SplitMix64 output mix (Steele, Lea
+// and Flood) of the ordered pair, the same from both ends.  Equal weights
+// then rank the edges in a scattered but fixed order, so a round of
+// locally dominant edges matches a share of every chain instead of only
+// the pair at its smaller end (which a plain smaller-id rule gives on
+// unit-weight meshes, stalling the coarsening).
+__device__ __forceinline__ unsigned long long pair_key(int32_t a, int32_t b) {
+    unsigned long long z = ((unsigned long long)(uint32_t)min(a, b) << 32) | (uint32_t)max(a, b);
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// heavier (w, then the larger pair key) than the current best?
+__device__ __forceinline__ bool better(double w, unsigned long long k, double bw,
+                                       unsigned long long bk) {
+    return w > bw || (w == bw && k > bk);
 }
 
 __global__ void k_amg_diag(int64_t n, const int32_t *ptr, const double *w, const double *D,
@@ -66,12 +83,15 @@ __global__ void k_amg_cand(int64_t n, const int32_t *ptr, const int32_t *col, co
     }
     double bw = -1.0;
     int32_t bu = -1;
+    unsigned long long bk = 0;
     for (int32_t j = ptr[v]; j < ptr[v + 1]; ++j) {
         const int32_t u = col[j];
         if (u == v || mate[u] >= 0) continue;
-        if (bu < 0 || better(w[j], u, bw, bu)) {
+        const unsigned long long k = pair_key((int32_t)v, u);
+        if (bu < 0 || better(w[j], k, bw, bk)) {
             bw = w[j];
             bu = u;
+            bk = k;
         }
     }
     cand[v] = bu;
@@ -100,12 +120,15 @@ __global__ void k_amg_join(int64_t n, const int32_t *ptr, const int32_t *col, co
     }
     double bw = -1.0;
     int32_t bu = -1;
+    unsigned long long bk = 0;
     for (int32_t j = ptr[v]; j < ptr[v + 1]; ++j) {
         const int32_t u = col[j];
         if (u == v || mate[u] < 0) continue;
-        if (bu < 0 || better(w[j], u, bw, bu)) {
+        const unsigned long long k = pair_key((int32_t)v, u);
+        if (bu < 0 || better(w[j], k, bw, bk)) {
             bw = w[j];
             bu = u;
+            bk = k;
         }
     }
     anchor[v] = bu;

@@ -4,7 +4,8 @@ and for the lambda_max estimate's solves with L_S.
 
 * PCG with the V-cycle of L_S + D reaches the tolerance, judged by an
   independent FP64 residual, in FP64 and in FP32 with FP64 refinement, in
-  fewer iterations than the tree preconditioner;
+  fewer iterations than the tree preconditioner (including a unit-weight
+  mesh, where every matching choice is a tie);
 * the lambda_max estimate with multigrid-CG solves equals the oracle's
   (tight inner solves on both sides) to 1e-9;
 * a pure Laplacian (D = 0, singular): the partitioner's solves converge.
@@ -29,13 +30,15 @@ def _with_extra(gpu, ctx, tree, og, ot, every):
     return S, in_s
 
 
-@pytest.mark.parametrize("which", ["grid3d", "powergrid", "powerlaw"])
+@pytest.mark.parametrize("which", ["grid3d", "powergrid", "powerlaw", "unitmesh"])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_amg_preconditioned_pcg(gpu, which, prec):
     import torch
     g = {"grid3d": lambda: graphs.grid3d_loguniform(30, 27, 25, seed=101),
          "powergrid": lambda: graphs.power_grid(150, seed=102),
-         "powerlaw": lambda: graphs.chung_lu(30000, seed=103)}[which]()
+         "powerlaw": lambda: graphs.chung_lu(30000, seed=103),
+         # all weights equal: the matching's ties decide every choice
+         "unitmesh": lambda: graphs.grid((170, 160), None, 1e-3)}[which]()
     og = oracle.from_graph(g)
     ot = oracle.build_tree(og)
     if not np.any(og.D > 0):
