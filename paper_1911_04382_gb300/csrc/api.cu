@@ -398,6 +398,9 @@ grass_status grass_ctx_set_param(grass_ctx_t ctx, const char *name, int64_t valu
     } else if (k == "spmm_chunk") {
         need(value == -1 || value == 0 || value == 16, "spmm_chunk must be -1, 0 or 16");
         ctx->spmm_chunk = (int)value;
+    } else if (k == "lsst_small_level") {
+        need(value >= 0, "lsst_small_level must be >= 0");
+        ctx->lsst_small_level = value;
     } else if (k == "heat_lanes") {
         need(value >= 0 && value <= 3, "heat_lanes must be in [0, 3]");
         ctx->heat_lanes = (int)value;

@@ -110,6 +110,7 @@ struct grass_ctx_s {
     int tree_bpsm = 1;
     int grid_sms = 0;      // cooperative grids on at most this many SMs (0: all)
     int heat_lanes = 0;    // heat kernel form (0-3), see blk.cu heat_T
+    int64_t lsst_small_level = 4096;   // low-stretch levels run in one block up to this many edges
     // SpMM launch variant (0..7) and chunk cap (0 = widest, 16) when >= 0;
     // else spmm_tuned[fp64][r slot] = {chunk cap, variant} from the autotuner
     int spmm_variant = -1, spmm_chunk = -1;

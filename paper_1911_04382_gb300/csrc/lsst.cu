@@ -221,9 +221,9 @@ __global__ void k_ls_commit(int64_t nx, const int32_t *xl, int t, const unsigned
 }
 
 // A whole level (rounds 0..S, the same four passes) in one block, for the
-// many small levels: __syncthreads between the passes in place of launches.
+// many small levels (at most ctx->lsst_small_level active edges):
+// __syncthreads between the passes in place of launches.
 constexpr int kLevelBlock = 1024;
-constexpr int64_t kSmallLevel = 32768;   // active edges
 
 __global__ void __launch_bounds__(kLevelBlock) k_ls_level(
     int64_t na, int64_t nx, const int32_t *act, const int32_t *ca, const int32_t *cb,
@@ -484,14 +484,14 @@ void lsst_build(grass_ctx_t ctx, const GraphData &g, uint64_t seed, uint8_t *in_
             launch(ctx, k_ls_xinit, cdiv(nx, kBlock), kBlock, 0, nx, (const int32_t *)xl.p,
                    (const int *)(small.p + 2), (unsigned long long)seed, c, level, ctr.p, when.p,
                    start.p, key.p, wb.p, eb.p);
-            if (na <= kSmallLevel) {
+            if (na <= ctx->lsst_small_level) {
                 launch(ctx, k_ls_level, 1, kLevelBlock, 0, na, nx, (const int32_t *)act[cur].p,
                        (const int32_t *)ca[cur].p, (const int32_t *)cb[cur].p,
                        (const int32_t *)xl.p, (const int *)(small.p + 2), (const int32_t *)start.p,
                        (const double *)g.ew64.p, ctr.p, when.p, key.p, wb.p, eb.p, in_tree);
                 edge_passes += 3 * (S + 1);
             }
-            for (int t = 0; t <= S && na > kSmallLevel; ++t) {
+            for (int t = 0; t <= S && na > ctx->lsst_small_level; ++t) {
                 launch(ctx, k_ls_offer, cdiv(na, kBlock), kBlock, 0, na, (const int32_t *)ca[cur].p,
                        (const int32_t *)cb[cur].p, (const int32_t *)ctr.p, (const int32_t *)when.p,
                        (const int32_t *)start.p, t, key.p);
