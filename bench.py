@@ -922,6 +922,77 @@ def hair_comb(G, k: int = 200, add: int = 400) -> dict:
                              "400 edges (figure not reproduced by this reading; see DESIGN)"}
 
 
+def densify_budget(G, w: dict, g, rp, col, val, bd, rounds=(3, 6, 16)) -> dict:
+    """The 100^3 step's densification with more rounds at the same per-round
+    cap, lambda_max by the step's tree-preconditioned inner CG and by
+    multigrid-CG solves: sparsifier edges, the lambda_max estimates, the
+    edges each round added, and the PCG iterations and time with the
+    sparsifier applied as in the step (one inner step) and by its multigrid
+    V-cycle.  The paper's 36-40 iterations at sigma^2 = 200 (Table V) need a
+    sparsifier whose kappa reaches sigma^2; this shows how the count moves
+    with the densification budget."""
+    import torch
+    from synth import rng
+    ctx = G.grass_ctx_create(torch.cuda.current_stream())
+    out = {"rounds_cap": f"{w['cap_frac']:.0%} of n per round", "runs": []}
+    pcg_prec = G.GRASS_FP32 if w["pcg"] == "fp32" else G.GRASS_FP64
+    try:
+        for amg in (0, 1):
+            G.grass_ctx_set_param(ctx, "lmax_amg", amg)
+            for R in rounds:
+                h0 = torch.from_numpy(np.concatenate(
+                    [rng.gaussian_block(w["seed"], rng.STREAM_H0 + k, g.n, w["r"])
+                     for k in range(R)])).cuda()
+                v0 = torch.from_numpy(np.concatenate(
+                    [rng.normal(w["seed"], rng.STREAM_V0 + k, g.n) for k in range(R)])).cuda()
+                P = G.make_params(w["sigma2"], w["r"], w["t"], R, w["lmax_iters"],
+                                  int(w["cap_frac"] * g.n),
+                                  G.GRASS_FP32 if w["embed"] == "fp32" else G.GRASS_FP64,
+                                  w["inner_tol"], w["inner_maxit"])
+                tree = G.grass_build_tree(ctx, rp, col, val, 0)
+                S = None
+                try:
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    S, st = G.grass_densify(ctx, tree, P, h0, v0)
+                    torch.cuda.synchronize()
+                    dd = st.as_dict()
+                    r_ = {"lambda_max": "multigrid-CG" if amg else "tree-CG (the step's)",
+                          "rounds_max": R, "rounds": dd["rounds"],
+                          "densify_ms": 1e3 * (time.perf_counter() - t0),
+                          "sparsifier_edges": G.grass_sparsifier_info(S)[0],
+                          "lmax_est": dd["lmax_est"], "lmax_capped": dd["lmax_capped"],
+                          "added_round": dd["added_round"],
+                          "stopped_similar": dd["stopped_similar"]}
+                    x = torch.zeros(g.n, dtype=torch.float64, device="cuda")
+                    for name, pre, inner in (("pcg_one_inner_step", 0, w["pcg_inner_maxit"]),
+                                             ("pcg_multigrid", 1, 0)):
+                        G.grass_ctx_set_param(ctx, "pcg_precond", pre)
+                        if pre:
+                            x.zero_()
+                            G.grass_pcg_solve(ctx, S, bd, x, w["pcg_tol"], w["pcg_maxit"],
+                                              pcg_prec, w["refine_tol"], w["pcg_inner_tol"],
+                                              inner)
+                        x.zero_()
+                        torch.cuda.synchronize()
+                        t0 = time.perf_counter()
+                        s_, ps = G.grass_pcg_solve(ctx, S, bd, x, w["pcg_tol"], w["pcg_maxit"],
+                                                   pcg_prec, w["refine_tol"], w["pcg_inner_tol"],
+                                                   inner)
+                        torch.cuda.synchronize()
+                        r_[name] = {"iters": ps.iters,
+                                    "ms": 1e3 * (time.perf_counter() - t0), "status": s_}
+                    G.grass_ctx_set_param(ctx, "pcg_precond", 0)
+                    out["runs"].append(r_)
+                finally:
+                    if S:
+                        G.grass_sparsifier_destroy(S)
+                    G.grass_tree_destroy(tree)
+    finally:
+        G.grass_ctx_destroy(ctx)
+    return out
+
+
 def lsst_vs_mst(G, w: dict, P, g=None, h0d=None, v0d=None, bd=None, label: str = "") -> dict:
     """The maximum-weight tree against the low-stretch tree (Sec. III-B) on
     one workload: construction time, total stretch st_T(G), PCG with the
@@ -1078,7 +1149,8 @@ def main() -> int:
                     help="--serve: measure the closed-burst capacity only")
     ap.add_argument("--batch", action="store_true",
                     help="run the 256-graph batch benchmark instead and print its line")
-    ap.add_argument("--only-extra", default=None, choices=["lsst_vs_mst", "c3_powerlaw"],
+    ap.add_argument("--only-extra", default=None,
+                    choices=["lsst_vs_mst", "c3_powerlaw", "densify_budget"],
                     help="run only the named measurement (outside any timed region) and print it")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the keys measured outside the timed region (per-round rates, "
@@ -1153,7 +1225,8 @@ def main() -> int:
 
     if args.only_extra:
         fn = {"lsst_vs_mst": lambda: lsst_extras(G, w, P, g, h0d, v0d, bd),
-              "c3_powerlaw": lambda: c3_powerlaw(G, peak_hbm())}[args.only_extra]
+              "c3_powerlaw": lambda: c3_powerlaw(G, peak_hbm()),
+              "densify_budget": lambda: densify_budget(G, w, g, rp, col, val, bd)}[args.only_extra]
         print(json.dumps({args.only_extra: fn()}), flush=True)
         G.grass_ctx_destroy(ctx)
         return 0
@@ -1307,6 +1380,7 @@ def main() -> int:
                          ("c3_powerlaw", lambda: c3_powerlaw(G, peak)),
                          ("hair_comb", lambda: hair_comb(G)),
                          ("lsst_vs_mst", lambda: lsst_extras(G, w, P, g, h0d, v0d, bd)),
+                         ("densify_budget", lambda: densify_budget(G, w, g, rp, col, val, bd)),
                          ("partition_mesh_1m", lambda: partition_mesh(G))):
             try:
                 r_ = fn()

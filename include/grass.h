@@ -441,8 +441,12 @@ grass_status grass_filter_similar(grass_ctx_t ctx, grass_sparsifier_t S, const v
  * inner_maxit (a Rayleigh quotient after inexact solves can fall far below
  * lambda_max; stats->lmax_capped[k] counts the solves that did not),
  * (4) embed with h0 + k*n*r (device, max_rounds*n*r doubles) and the
- * lambda_max start v0 + k*n (device, max_rounds*n doubles), (5) filter,
- * add the kept edges.  The paper's step (6) similarity check is applied when
+ * lambda_max start v0 + k*n (device, max_rounds*n doubles), (5) filter by
+ * theta_sigma, add the kept edges.  theta_sigma takes the round's
+ * lambda_max estimate when its solves converged, else the last estimate
+ * whose solves did (round 1's are direct tree solves): lambda_max can only
+ * fall as edges are added.  stats->lmax_est[k] is the round's own estimate,
+ * stats->theta[k] the theta_sigma used.  The paper's step (6) similarity check is applied when
  * the context's "similarity_check" parameter is 1 (grass_filter_similar).
  * out: a new sparsifier (tree + added edges).  stats: host, optional. */
 grass_status grass_densify(grass_ctx_t ctx, grass_tree_t tree, const grass_params_t *params,

@@ -146,6 +146,8 @@ class DensifyResult:
     lmin: list = field(default_factory=list)
     lmax: list = field(default_factory=list)
     theta: list = field(default_factory=list)
+    # per round: inner solves of the lambda_max estimate that reached inner_maxit
+    capped: list = field(default_factory=list)
     stopped_similar: bool = False
     # per round, when densify(record=True): the heats of the off-S edges,
     # their ids, the threshold theta * heat_max and, with a cap, the heat of
@@ -418,24 +420,34 @@ def densify(og: OGraph, tree: OTree, h0s, v0s, sigma2: float, t: int, max_rounds
     (3) stop when lmax/lmin <= sigma^2, (4) t-step power iteration with the
     round's r start vectors, (5) filter by theta_sigma, (6) with
     similarity=True keep only the edges similarity_check keeps (the paper
-    leaves step 6 undefined; off by default), add the kept edges."""
+    leaves step 6 undefined; off by default), add the kept edges.
+
+    An estimate whose inner solves stopped at inner_maxit is not trusted:
+    it does not stop the loop, and theta_sigma takes the last trusted
+    estimate instead (round 1's solves are direct tree solves, so there is
+    always one).  Adding edges to S can only lower lambda_max(L_S^+ L_G),
+    so that estimate is the best upper value at hand."""
     in_s = tree.in_tree.copy()
     res = DensifyResult(in_s)
+    lmax_trusted = None
     for rd in range(max_rounds):
         lmin = lambda_min_est(og, in_s)
         lmax, capped = lambda_max_est_checked(og, tree, in_s, v0s[rd], lmax_iters, inner_tol,
                                               inner_maxit)
         res.lmin.append(lmin)
         res.lmax.append(lmax)
+        res.capped.append(capped)
         # (3) a Rayleigh quotient bounds lambda_max from below only; one taken
         # after inner solves that stopped at their cap is not evidence of
         # similarity, so the stop test needs every solve to meet inner_tol
         if capped == 0 and lmax / lmin <= sigma2:
             res.stopped_similar = True
             break
+        if capped == 0 or lmax_trusted is None:
+            lmax_trusted = lmax
         H = embed(og, tree, in_s, h0s[rd], t, inner_tol, inner_maxit)
         hv, off = heat(og, in_s, H)
-        th = theta_sigma(sigma2, lmin, lmax, t)
+        th = theta_sigma(sigma2, lmin, lmax_trusted, t)
         res.theta.append(th)
         if similarity:
             acc = similarity_check(og, hv, off, th, cap)

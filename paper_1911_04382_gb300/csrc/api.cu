@@ -858,6 +858,9 @@ grass_status grass_densify(grass_ctx_t ctx, grass_tree_t T, const grass_params_t
     try {
         void *heat = ctx->scr<char>(SCR_HEAT, (T->g.m + 1) * esize(P->embed_prec));
         int64_t *acc = ctx->scr<int64_t>(SCR_PCG_E, T->g.m + 1);
+        // the last lambda_max estimate whose inner solves all converged;
+        // round 1's are direct tree solves, so it is set in round 1
+        double lmax_trusted = 0.0;
         for (int k = 0; k < P->max_rounds; ++k) {
             double ta = now_ms();
             double lmin = 0.0;
@@ -882,6 +885,11 @@ grass_status grass_densify(grass_ctx_t ctx, grass_tree_t T, const grass_params_t
                 st.inner_iters += inner;
                 break;
             }
+            // an untrusted estimate does not set theta_sigma either: adding
+            // edges to S only lowers lambda_max(L_S^+ L_G), so the last
+            // trusted estimate is the best upper value at hand (a capped
+            // one can make theta_sigma > 1 and reject every edge)
+            if (capped == 0.0 || lmax_trusted == 0.0) lmax_trusted = lmax;
             int64_t moff = S->m_off;
             EmbedOut eo = embed_impl(ctx, S, h0 + (int64_t)k * n * r, r, P->t, P->embed_prec,
                                      P->inner_tol, P->inner_maxit, nullptr, heat);
@@ -890,7 +898,7 @@ grass_status grass_densify(grass_ctx_t ctx, grass_tree_t T, const grass_params_t
             double tc = now_ms();
             st.ms_embed += tc - tb;
             st.ms_embed_round[k] = tc - tb;
-            double th = theta_sigma(P->sigma2, lmin, lmax, P->t);
+            double th = theta_sigma(P->sigma2, lmin, lmax_trusted, P->t);
             st.theta[k] = th;
             st.heat_max[k] = eo.heat_max;
             st.embedded_round[k] = moff;

@@ -397,6 +397,42 @@ def test_densify_stops_when_similar():
     assert res.stopped_similar and res.rounds == 0
 
 
+def test_densify_untrusted_estimate_keeps_filtering():
+    """One inner CG iteration: from round 2 on, the lambda_max estimate comes
+    from capped solves.  Round 2's estimate (about 1.5) claims similarity
+    under sigma^2 = 5 while the dense generalized eigensolve puts the
+    sparsifier's kappa near 17; theta_sigma from that estimate exceeds 1 and
+    would reject every edge.  The loop neither stops nor takes that theta:
+    it filters with the last trusted estimate, which can only be an upper
+    value (lambda_max falls as edges are added), and each round's edges
+    lower the true kappa."""
+    g = graphs.grid3d_loguniform(8, 8, 8, seed=2)
+    og = oracle.from_graph(g)
+    tree = oracle.build_tree(og)
+    R, sigma2, t = 3, 5.0, 2
+    h0s = [rng.gaussian_block(9, rng.STREAM_H0 + k, g.n, 8) for k in range(R)]
+    v0s = [rng.normal(9, rng.STREAM_V0 + k, g.n) for k in range(R)]
+    LG = dense_lap(g.n, og.eu, og.ev, og.ew)
+    res = oracle.densify(og, tree, h0s, v0s, sigma2, t, R, 8, cap=30, inner_tol=1e-13,
+                         inner_maxit=1)
+    assert res.capped[0] == 0 and all(c > 0 for c in res.capped[1:])
+    assert res.rounds == R and res.added == [30, 30, 30]
+    kappas = []
+    for k in range(R + 1):
+        in_s = tree.in_tree if k == 0 else oracle.densify(
+            og, tree, h0s, v0s, sigma2, t, k, 8, cap=30, inner_tol=1e-13, inner_maxit=1).in_s
+        lam = gen_eigs(LG, dense_lap(g.n, og.eu, og.ev, og.ew, in_s))
+        kappas.append(lam.max() / lam.min())
+        if 0 < k < R:
+            # round k+1's estimate is far below the truth and claims similarity
+            assert res.lmax[k] / res.lmin[k] <= sigma2 < kappas[k]
+            assert oracle.theta_sigma(sigma2, res.lmin[k], res.lmax[k], t) > 1.0
+            # the theta used is no stricter than the one the exact lambda_max gives
+            exact = (sigma2 * res.lmin[k] / lam.max()) ** (2 * t + 1)
+            assert res.theta[k] <= exact
+    assert all(a > b for a, b in zip(kappas, kappas[1:]))
+
+
 # ---------------------------------------------------------------- PCG
 
 def test_pcg_matches_dense_solve():
