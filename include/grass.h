@@ -97,7 +97,8 @@ typedef struct {
     double ms_estimate, ms_embed, ms_filter, ms_update, ms_total;
     double ms_embed_round[GRASS_MAX_ROUNDS]; /* each round's power steps + heat (ms)  */
     int64_t lmax_capped[GRASS_MAX_ROUNDS];   /* inner solves of round k's lambda_max
-                                                estimate that reached inner_maxit      */
+                                                estimate that reached inner_maxit (0 or
+                                                1: the estimate ends at the first)     */
 } grass_sparsify_stats_t;
 
 typedef struct {
@@ -167,6 +168,13 @@ grass_status grass_ctx_set_wait_limit(grass_ctx_t ctx, int64_t polls, int hold_b
  *                         grass_fiedler's solves
  *   "amg_sweeps"          weighted-Jacobi sweeps before and after each
  *                         coarse correction of the V-cycle (1-8, default 1)
+ *   "amg_fused"           1: with one sweep, each multigrid PCG pass runs
+ *                         as one cooperative kernel (every level, the
+ *                         coarsest solve and the PCG scalars on the
+ *                         device); 0 (default): one launch per level step,
+ *                         replayed as a CUDA graph
+ *   "amg_tail_n"          levels of at most this many vertices (default
+ *                         4096) run in one block of the fused kernel
  *   "lmax_amg"            0 (default) or 1: the lambda_max estimate's solves
  *                         with L_S (one column) are CG preconditioned by the
  *                         multigrid V-cycle of L_S, in FP64, to inner_tol
@@ -439,7 +447,8 @@ grass_status grass_filter_similar(grass_ctx_t ctx, grass_sparsifier_t S, const v
  * (2) lambda estimates on the current S, (3) stop if lmax/lmin <= sigma2
  * and every inner CG solve of the lambda_max estimate met inner_tol before
  * inner_maxit (a Rayleigh quotient after inexact solves can fall far below
- * lambda_max; stats->lmax_capped[k] counts the solves that did not),
+ * lambda_max; the estimate's power steps end at the first solve that did
+ * not, and stats->lmax_capped[k] is then 1),
  * (4) embed with h0 + k*n*r (device, max_rounds*n*r doubles) and the
  * lambda_max start v0 + k*n (device, max_rounds*n doubles), (5) filter by
  * theta_sigma, add the kept edges.  theta_sigma takes the round's

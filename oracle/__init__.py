@@ -347,9 +347,12 @@ def lambda_max_est(og: OGraph, tree: OTree, in_s: np.ndarray, v0: np.ndarray, it
 
 
 def lambda_max_est_checked(og: OGraph, tree: OTree, in_s: np.ndarray, v0: np.ndarray, iters: int,
-                           inner_tol: float = 1e-12, inner_maxit: int = 1000):
+                           inner_tol: float = 1e-12, inner_maxit: int = 1000,
+                           stop_when_capped: bool = False):
     """lambda_max_est and the number of its inner CG solves that reached
-    inner_maxit (0 when S is the tree: those solves are direct)."""
+    inner_maxit (0 when S is the tree: those solves are direct).  With
+    stop_when_capped the power steps end after the first such solve and
+    the quotient is taken on that step's vector."""
     v = np.asarray(v0, dtype=np.float64).reshape(-1, 1)
     v = v - v.mean()
     mask = _s_mask(tree, in_s)
@@ -357,9 +360,11 @@ def lambda_max_est_checked(og: OGraph, tree: OTree, in_s: np.ndarray, v0: np.nda
     for _ in range(iters):
         y = lap_apply(og, v)
         v, it = s_solve(og, tree, mask, y, None, inner_tol, inner_maxit)
+        v = pow2_rescale(v)
         if mask is not None and int(np.max(it)) >= inner_maxit:
             capped += 1
-        v = pow2_rescale(v)
+            if stop_when_capped:
+                break
     qG, qS = quad_forms(og, in_s, v)
     return float(qG[0] / qS[0]), capped
 
@@ -432,8 +437,10 @@ def densify(og: OGraph, tree: OTree, h0s, v0s, sigma2: float, t: int, max_rounds
     lmax_trusted = None
     for rd in range(max_rounds):
         lmin = lambda_min_est(og, in_s)
+        # an estimate with a capped solve can neither stop the loop nor set
+        # theta_sigma (below), so its power steps end at that solve
         lmax, capped = lambda_max_est_checked(og, tree, in_s, v0s[rd], lmax_iters, inner_tol,
-                                              inner_maxit)
+                                              inner_maxit, stop_when_capped=True)
         res.lmin.append(lmin)
         res.lmax.append(lmax)
         res.capped.append(capped)

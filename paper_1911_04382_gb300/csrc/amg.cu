@@ -37,7 +37,7 @@
 
 namespace grass {
 
-constexpr int64_t kCoarse = 256;        // the coarsest level has at most this many vertices
+constexpr int64_t kCoarse = kAmgCoarse;   // the coarsest level has at most this many vertices
 constexpr int kMaxLevels = 40;
 constexpr int kMatchRounds = 8;
 constexpr double kOmega = 2.0 / 3.0;
@@ -617,7 +617,10 @@ int amg_pcg(grass_ctx_t ctx, grass_sparsifier_t S, const T *rhs, T *e, double to
     const GraphData &g = S->tree->g;
     const int64_t n = g.n, gn = cdiv(n, kBlock);
     const grass_prec prec = sizeof(T) == 8 ? GRASS_FP64 : GRASS_FP32;
-    amg_get(ctx, S, true);
+    AmgHier &H = amg_get(ctx, S, true);
+    if (ctx->amg_fused && ctx->num_sms > 0 && ctx->amg_sweeps == 1 &&
+        (int)H.lv.size() <= kAmgFusedLevels)
+        return amg_pcg_fused<T>(ctx, S, H, rhs, e, tol_abs, maxit);
     T *r = ctx->scr<T>(SCR_PCG_R, n);
     T *z = ctx->scr<T>(SCR_PCG_Z, n);
     T *p = ctx->scr<T>(SCR_PCG_P, n);

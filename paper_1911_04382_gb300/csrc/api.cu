@@ -82,9 +82,11 @@ void ensure_sdd(grass_ctx_t ctx, grass_tree_t T) {
 // Sec. III-F, Eq. (formula_pwr_iter): t steps H <- L_S^{-1} L_G H.  H holds
 // the unscaled last iterate on return; *scale_slot the max-abs bits that
 // give its pending power-of-two factor.  Returns inner CG iterations.
-int64_t power_steps(grass_ctx_t ctx, grass_sparsifier_t S, const double *h0, int r, int t,
-                    grass_prec prec, double inner_tol, int inner_maxit, void *H, void *Y,
-                    int *scale_slot) {
+// stop_when_capped ends the steps after the first inner solve that reached
+// inner_maxit (the DS_CAPPED counter, zeroed by the caller).
+static int64_t power_steps_until(grass_ctx_t ctx, grass_sparsifier_t S, const double *h0, int r,
+                                 int t, grass_prec prec, double inner_tol, int inner_maxit,
+                                 void *H, void *Y, int *scale_slot, bool stop_when_capped) {
     const GraphData &g = S->tree->g;
     const int64_t n = g.n;
     convert_block(ctx, prec, n * r, h0, H);
@@ -98,9 +100,22 @@ int64_t power_steps(grass_ctx_t ctx, grass_sparsifier_t S, const double *h0, int
         inner += s_solve(ctx, S, false, r, prec, Y, H, inner_tol, inner_maxit, maxslot(ctx, cur));
         prev = cur;
         cur ^= 1;
+        if (stop_when_capped && !S->is_tree && s + 1 < t) {
+            // the caller's counter of solves that reached inner_maxit
+            double capped = 0.0;
+            d2h(ctx, &capped, ctx->scal.p + DS_RED + DS_CAPPED, sizeof(double));
+            if (capped > 0.0) break;
+        }
     }
     *scale_slot = prev;
     return inner;
+}
+
+int64_t power_steps(grass_ctx_t ctx, grass_sparsifier_t S, const double *h0, int r, int t,
+                    grass_prec prec, double inner_tol, int inner_maxit, void *H, void *Y,
+                    int *scale_slot) {
+    return power_steps_until(ctx, S, h0, r, t, prec, inner_tol, inner_maxit, H, Y, scale_slot,
+                             false);
 }
 
 struct EmbedOut {
@@ -129,14 +144,18 @@ EmbedOut embed_impl(grass_ctx_t ctx, grass_sparsifier_t S, const double *h0, int
 }
 
 // Sec. IV-C-1: iters generalized power steps, then v^T L_G v / v^T L_S v.
+// stop_when_capped: end the steps after the first inner solve that reached
+// inner_maxit; the quotient is then taken on that step's vector.
 double lambda_max_impl(grass_ctx_t ctx, grass_sparsifier_t S, const double *v0, int iters,
-                       grass_prec prec, double inner_tol, int inner_maxit, int64_t *inner) {
+                       grass_prec prec, double inner_tol, int inner_maxit, int64_t *inner,
+                       bool stop_when_capped) {
     const int64_t n = S->tree->g.n;
     void *v = ctx->scr<char>(SCR_LMAX_V, n * esize(prec));
     void *y = ctx->scr<char>(SCR_LMAX_Y, n * esize(prec));
     int slot = -1;
     if (iters > 0) {
-        *inner += power_steps(ctx, S, v0, 1, iters, prec, inner_tol, inner_maxit, v, y, &slot);
+        *inner += power_steps_until(ctx, S, v0, 1, iters, prec, inner_tol, inner_maxit, v, y,
+                                    &slot, stop_when_capped);
         apply_pow2(ctx, prec, n, v, maxslot(ctx, slot));
     } else {
         convert_block(ctx, prec, n, v0, v);
@@ -389,6 +408,12 @@ grass_status grass_ctx_set_param(grass_ctx_t ctx, const char *name, int64_t valu
     } else if (k == "amg_sweeps") {
         need(value >= 1 && value <= 8, "amg_sweeps must be in [1, 8]");
         ctx->amg_sweeps = (int)value;
+    } else if (k == "amg_fused") {
+        need(value == 0 || value == 1, "amg_fused must be 0 or 1");
+        ctx->amg_fused = (int)value;
+    } else if (k == "amg_tail_n") {
+        need(value >= 0, "amg_tail_n must be >= 0");
+        ctx->amg_tail_n = value;
     } else if (k == "lmax_amg") {
         need(value == 0 || value == 1, "lmax_amg must be 0 or 1");
         ctx->lmax_amg = (int)value;
@@ -773,7 +798,7 @@ grass_status grass_lambda_max(grass_ctx_t ctx, grass_sparsifier_t S, const doubl
     need(iters >= 0, "iters must be >= 0");
     int64_t inner = 0;
     clear_timeout(ctx);
-    *lmax = lambda_max_impl(ctx, S, v0, iters, prec, inner_tol, inner_maxit, &inner);
+    *lmax = lambda_max_impl(ctx, S, v0, iters, prec, inner_tol, inner_maxit, &inner, false);
     check_timeout(ctx);
     API_END
 }
@@ -867,8 +892,11 @@ grass_status grass_densify(grass_ctx_t ctx, grass_tree_t T, const grass_params_t
             lambda_min(ctx, S, &lmin);
             int64_t inner = 0;
             memset_d(ctx, ctx->scal.p + DS_RED + DS_CAPPED, 0, sizeof(double));
+            // an estimate with a capped solve can neither stop the loop nor
+            // set theta_sigma (below), so its power steps end at that solve
             double lmax = lambda_max_impl(ctx, S, v0 + (int64_t)k * n, P->lmax_iters,
-                                          P->embed_prec, P->inner_tol, P->inner_maxit, &inner);
+                                          P->embed_prec, P->inner_tol, P->inner_maxit, &inner,
+                                          true);
             double capped = 0.0;
             d2h(ctx, &capped, ctx->scal.p + DS_RED + DS_CAPPED, sizeof(double));
             st.lmin_est[k] = lmin;

@@ -122,6 +122,8 @@ struct grass_ctx_s {
     int pcg_precond = 0;        // 1: the sparsifier's multigrid V-cycle preconditions PCG
     int amg_sweeps = 1;         // Jacobi sweeps before and after each coarse correction
     int lmax_amg = 0;           // 1: lambda_max estimates solve L_S by multigrid-preconditioned CG
+    int amg_fused = 0;          // 1: the multigrid PCG runs as one cooperative kernel (amg_fused.cu)
+    int64_t amg_tail_n = 4096;  // its levels of at most this many vertices run in one block
     // a non-blocking stream of the context's own, on which multi-kernel
     // iterations are captured into CUDA graphs and replayed (ordered with the
     // caller's stream by events); created on first use
@@ -236,6 +238,8 @@ constexpr int kPersistMaxThreads = 1024;
 // hold more live values than 64 registers a thread: at most 512 threads per
 // block, so that a thread may keep 128 registers instead of spilling.
 constexpr int kFusedMaxThreads = 512;
+constexpr int64_t kAmgCoarse = 256;   // the multigrid's coarsest level has at most this many vertices
+constexpr int kAmgFusedLevels = 24;   // levels the fused multigrid PCG takes (kernel parameters)
 // threads of a persistent kernel launched with the knob value but bounded
 // by the kernel's own maximum
 inline int bounded_threads(int knob, int bound) { return knob < bound ? knob : bound; }
@@ -397,6 +401,12 @@ struct AmgHier {
     DBuf<float> cinv32;
     DBuf<char> t0;                    // level-0 scratch vector
 };
+
+// PCG on A = L_G + D with one V-cycle of H per iteration, one cooperative
+// launch (amg_fused.cu); returns the iterations
+template <typename T>
+int amg_pcg_fused(grass_ctx_t ctx, grass_sparsifier_t S, AmgHier &H, const T *rhs, T *e,
+                  double tol_abs, int maxit);
 
 }  // namespace grass
 

@@ -8,7 +8,9 @@ and for the lambda_max estimate's solves with L_S.
   mesh, where every matching choice is a tie);
 * the lambda_max estimate with multigrid-CG solves equals the oracle's
   (tight inner solves on both sides) to 1e-9;
-* a pure Laplacian (D = 0, singular): the partitioner's solves converge.
+* a pure Laplacian (D = 0, singular): the partitioner's solves converge;
+* the multigrid PCG as one cooperative kernel per pass equals the form with
+  one launch per level step.
 """
 import numpy as np
 import pytest
@@ -59,6 +61,51 @@ def test_amg_preconditioned_pcg(gpu, which, prec):
             rel = np.linalg.norm(b - A @ host(x)) / np.linalg.norm(b)
             assert rel <= tol and s1.rel_resid_fp64 == pytest.approx(rel, rel=1e-6)
             assert s1.iters < s0.iters, (s1.iters, s0.iters)
+        finally:
+            gpu.grass_sparsifier_destroy(S)
+
+
+@pytest.mark.parametrize("which", ["grid3d", "powergrid", "unitmesh", "one_level"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_fused_multigrid_pcg_matches_launch_form(gpu, which, prec):
+    """The multigrid PCG as one cooperative kernel per pass against the same
+    iteration run as one launch per level step (CUDA graph replay): the same
+    V-cycle, so the iteration counts agree within 2 and the solutions within
+    the tolerance, for every split of the levels between the grid and
+    block 0 (none but the coarsest solve, the default 4096, all of them);
+    "one_level" has at most 256 vertices, so the V-cycle is the coarsest
+    dense solve alone."""
+    import torch
+    g = {"grid3d": lambda: graphs.grid3d_loguniform(30, 27, 25, seed=101),
+         "powergrid": lambda: graphs.power_grid(150, seed=102),
+         "unitmesh": lambda: graphs.grid((170, 160), None, 1e-3),
+         "one_level": lambda: graphs.grid2d_uniform(15, 16, seed=106, D=1e-3)}[which]()
+    og = oracle.from_graph(g)
+    ot = oracle.build_tree(og)
+    b = rng.normal(107, rng.STREAM_RHS, g.n)
+    A = sp.csr_matrix((g.val, g.col, g.rowptr), shape=(g.n, g.n))
+    tol = 1e-8
+    P = gpu.GRASS_FP64 if prec == "fp64" else gpu.GRASS_FP32
+    with gpu_graph(g) as (ctx, tree, _):
+        S, _ = _with_extra(gpu, ctx, tree, og, ot, 10)
+        try:
+            gpu.grass_ctx_set_param(ctx, "pcg_precond", 1)
+            gpu.grass_ctx_set_param(ctx, "amg_fused", 0)
+            x = torch.zeros(g.n, dtype=torch.float64, device="cuda")
+            st0, s0 = gpu.grass_pcg_solve(ctx, S, dev(b), x, tol, 20000, P, 1e-2, 1e-2, 0)
+            assert st0 == gpu.GRASS_OK
+            x0 = host(x)
+            gpu.grass_ctx_set_param(ctx, "amg_fused", 1)
+            for tail in (0, 4096, 1 << 40):
+                gpu.grass_ctx_set_param(ctx, "amg_tail_n", tail)
+                x.zero_()
+                st1, s1 = gpu.grass_pcg_solve(ctx, S, dev(b), x, tol, 20000, P, 1e-2, 1e-2, 0)
+                assert st1 == gpu.GRASS_OK
+                x1 = host(x)
+                rel = np.linalg.norm(b - A @ x1) / np.linalg.norm(b)
+                assert rel <= tol and s1.rel_resid_fp64 == pytest.approx(rel, rel=1e-6)
+                assert abs(s1.iters - s0.iters) <= 2, (tail, s1.iters, s0.iters)
+                assert np.linalg.norm(x1 - x0) <= 1e-6 * np.linalg.norm(x0), tail
         finally:
             gpu.grass_sparsifier_destroy(S)
 
