@@ -168,13 +168,16 @@ grass_status grass_ctx_set_wait_limit(grass_ctx_t ctx, int64_t polls, int hold_b
  *                         grass_fiedler's solves
  *   "amg_sweeps"          weighted-Jacobi sweeps before and after each
  *                         coarse correction of the V-cycle (1-8, default 1)
- *   "amg_fused"           1: with one sweep, each multigrid PCG pass runs
- *                         as one cooperative kernel (every level, the
- *                         coarsest solve and the PCG scalars on the
- *                         device); 0 (default): one launch per level step,
- *                         replayed as a CUDA graph
- *   "amg_tail_n"          levels of at most this many vertices (default
- *                         4096) run in one block of the fused kernel
+ *   "amg_fused"           1 (default): with one sweep, each multigrid PCG
+ *                         pass runs as one cooperative kernel (every level,
+ *                         the coarsest solve and the PCG scalars on the
+ *                         device); 0: one launch per level step, replayed
+ *                         as a CUDA graph
+ *   "amg_warp_n"          levels of at most this many vertices (default
+ *                         16384) take one warp per row in the fused kernel
+ *   "amg_tail_n"          levels of at most this many vertices (default 0:
+ *                         none but the coarsest dense solve) run in one
+ *                         block of the fused kernel
  *   "lmax_amg"            0 (default) or 1: the lambda_max estimate's solves
  *                         with L_S (one column) are CG preconditioned by the
  *                         multigrid V-cycle of L_S, in FP64, to inner_tol

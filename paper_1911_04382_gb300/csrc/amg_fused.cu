@@ -4,9 +4,11 @@
 // one cooperative launch: no host round trip and no launch per level.
 //
 // The iteration and the V-cycle are those of amg_pcg / vcycle_T (one
-// weighted-Jacobi sweep before and one after each coarse correction), with
-// the same arithmetic per element in the same order; only the phases are
-// merged:
+// weighted-Jacobi sweep before and one after each coarse correction); the
+// sums over a row's entries, an aggregate's members or a row of the
+// coarsest inverse run in index order in the thread form, and lane-strided
+// with a fixed xor tree in the warp form, so results are deterministic but
+// not bit-identical to the launch form.  The phases are merged:
 //  * the pre-smoothing of level 0 from zero (x = omega D^-1 r) is written by
 //    the phase that updates r;
 //  * level l going down: residual phase (one row per item), then the
@@ -15,9 +17,13 @@
 //  * level l going up: the prolongation x + x_c[agg] is formed on the fly
 //    inside the post-smoothing sweep (at the row and at every neighbour);
 //    level 0's sweep writes z and the partial sums of r.z;
-//  * levels of at most tail_n vertices, the coarsest dense solve included,
-//    run in block 0 with block barriers while the other blocks wait at the
-//    next grid barrier.
+//  * levels of at most amg_warp_n vertices take one warp per row (their
+//    rows are long: they carry the fine edges between aggregates), the rest
+//    one thread per row, two rows in flight;
+//  * the coarsest dense solve takes one warp per row across the grid;
+//    optionally the levels of at most amg_tail_n vertices run in block 0
+//    with block barriers while the other blocks wait at the next grid
+//    barrier.
 // Dot products: thread accumulators (Acc), per-block partials, and every
 // block sums all blocks' partials in one fixed order, so all blocks hold the
 // same scalars and stop together.  Grid barriers are the bounded ones of
@@ -55,6 +61,7 @@ struct AmgPcgArgs {
     const T *cinv;                 // coarsest level's dense (grounded) inverse
     int L;                         // levels (the last is the coarsest)
     int lt;                        // first level run by block 0 alone
+    int64_t warp_n;                // levels of at most this many vertices: a warp per row
     double tol_abs;
     int maxit;
     double *part;                  // [2][gridDim.x][32]
@@ -64,56 +71,115 @@ struct AmgPcgArgs {
     int *err;
 };
 
-// sum_j w_j x[col_j] over [jb, je), in j order; four entries' loads first
-template <typename T>
-__device__ __forceinline__ T row_wx(const int32_t *col, const T *w, const T *x, int32_t jb,
-                                    int32_t je) {
-    T s = (T)0;
-    for (; jb < je; jb += 4) {
-        int32_t c[4];
-        T wv[4], xv[4];
+// Rows v0 + u st (u < U) of a CSR: s[u] = sum_j w_j x'_j over each row in j
+// order, x'_j = x[col_j] (+ xc[agg[col_j]] with PRO).  Four entries of every
+// row are loaded (indices and weights, then the gathers) before any sum: the
+// fused kernel runs few threads per SM, so each keeps U rows in flight.
+template <typename T, int U, bool PRO>
+__device__ __forceinline__ void rows_wx(const int32_t *ptr, const int32_t *col, const T *w,
+                                        const T *x, const int32_t *agg, const T *xc, int64_t n,
+                                        int64_t v0, int64_t st, T (&s)[U]) {
+    int32_t jb[U], je[U];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const bool ok = jb + k < je;
-            c[k] = ok ? col[jb + k] : 0;
-            wv[k] = ok ? w[jb + k] : (T)0;
-        }
-#pragma unroll
-        for (int k = 0; k < 4; ++k) xv[k] = jb + k < je ? x[c[k]] : (T)0;
-#pragma unroll
-        for (int k = 0; k < 4; ++k)
-            if (jb + k < je) s += wv[k] * xv[k];
+    for (int u = 0; u < U; ++u) {
+        const int64_t v = v0 + u * st;
+        const bool ok = v < n;
+        jb[u] = ok ? ptr[v] : 0;
+        je[u] = ok ? ptr[v + 1] : 0;
+        s[u] = (T)0;
     }
-    return s;
+    bool more = true;
+    while (more) {
+        int32_t c[U][4];
+        T wv[U][4], xv[U][4];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const bool ok = jb[u] + k < je[u];
+                c[u][k] = ok ? col[jb[u] + k] : 0;
+                wv[u][k] = ok ? w[jb[u] + k] : (T)0;
+            }
+        }
+        if constexpr (PRO) {
+            int32_t ag[U][4];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const bool ok = jb[u] + k < je[u];
+                    xv[u][k] = ok ? x[c[u][k]] : (T)0;
+                    ag[u][k] = ok ? agg[c[u][k]] : 0;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    if (jb[u] + k < je[u]) xv[u][k] = xv[u][k] + xc[ag[u][k]];
+            }
+        } else {
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) xv[u][k] = jb[u] + k < je[u] ? x[c[u][k]] : (T)0;
+            }
+        }
+        more = false;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (jb[u] + k < je[u]) s[u] += wv[u][k] * xv[u][k];
+            jb[u] += 4;
+            more = more || jb[u] < je[u];
+        }
+    }
 }
 
-// the same sum over the prolonged iterate x_j + xc[agg_j]
-template <typename T>
-__device__ __forceinline__ T row_wx_pro(const int32_t *col, const T *w, const T *x,
-                                        const int32_t *agg, const T *xc, int32_t jb, int32_t je) {
-    T s = (T)0;
-    for (; jb < je; jb += 4) {
-        int32_t c[4], ag[4];
-        T wv[4], xv[4], cv[4];
+// Rows v0 + u st of A's Laplacian part: s[u] = sum_j w_j (pv[u] - p[col_j])
+// in j order (the fused PCG's SpMV form), loads of all U rows first.
+template <typename T, int U>
+__device__ __forceinline__ void rows_lap(const int32_t *ptr, const int32_t *col, const T *w,
+                                         const T *p, int64_t n, int64_t v0, int64_t st,
+                                         const T (&pv)[U], T (&s)[U]) {
+    int32_t jb[U], je[U];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const bool ok = jb + k < je;
-            c[k] = ok ? col[jb + k] : 0;
-            wv[k] = ok ? w[jb + k] : (T)0;
-        }
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const bool ok = jb + k < je;
-            xv[k] = ok ? x[c[k]] : (T)0;
-            ag[k] = ok ? agg[c[k]] : 0;
-        }
-#pragma unroll
-        for (int k = 0; k < 4; ++k) cv[k] = jb + k < je ? xc[ag[k]] : (T)0;
-#pragma unroll
-        for (int k = 0; k < 4; ++k)
-            if (jb + k < je) s += wv[k] * (xv[k] + cv[k]);
+    for (int u = 0; u < U; ++u) {
+        const int64_t v = v0 + u * st;
+        const bool ok = v < n;
+        jb[u] = ok ? ptr[v] : 0;
+        je[u] = ok ? ptr[v + 1] : 0;
+        s[u] = (T)0;
     }
-    return s;
+    bool more = true;
+    while (more) {
+        int32_t c[U][4];
+        T wv[U][4], xv[U][4];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const bool ok = jb[u] + k < je[u];
+                c[u][k] = ok ? col[jb[u] + k] : 0;
+                wv[u][k] = ok ? w[jb[u] + k] : (T)0;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) xv[u][k] = jb[u] + k < je[u] ? p[c[u][k]] : (T)0;
+        }
+        more = false;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (jb[u] + k < je[u]) s[u] += wv[u][k] * (pv[u] - xv[u][k]);
+            jb[u] += 4;
+            more = more || jb[u] < je[u];
+        }
+    }
 }
 
 template <typename T>
@@ -167,61 +233,175 @@ __device__ __forceinline__ void grid_sums(const double *part, double *s_out) {
 // Each phase walks its items from item `i0` with stride `st` (the grid's
 // threads, or block 0's).
 
-// res = b - (diag x - sum w x_j) on level L
+// res = b - (diag x - sum w x_j) on level L (two rows per step)
 template <typename T>
 __device__ __forceinline__ void ph_residual(const FLevel<T> &L, T *res, int64_t i0, int64_t st) {
-    for (int64_t v = i0; v < L.n; v += st) {
-        const T s = row_wx(L.col, L.w, L.x, L.ptr[v], L.ptr[v + 1]);
-        res[v] = L.b[v] - (L.diag[v] * L.x[v] - s);
+    for (int64_t v0 = i0; v0 < L.n; v0 += 2 * st) {
+        T xo[2], bo[2], d[2], sm[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int64_t v = v0 + u * st;
+            const bool ok = v < L.n;
+            xo[u] = ok ? L.x[v] : (T)0;
+            bo[u] = ok ? L.b[v] : (T)0;
+            d[u] = ok ? L.diag[v] : (T)0;
+        }
+        rows_wx<T, 2, false>(L.ptr, L.col, L.w, L.x, nullptr, nullptr, L.n, v0, st, sm);
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int64_t v = v0 + u * st;
+            if (v < L.n) res[v] = bo[u] - (d[u] * xo[u] - sm[u]);
+        }
     }
 }
 
 // C.b[c] = sum of res over the members of c (member order); C.x[c] =
-// omega C.b[c] / C.diag[c] unless C is the coarsest level
+// omega C.b[c] / C.diag[c] unless C is the coarsest level.  Two coarse
+// vertices per step, the first four members' loads of both first.
 template <typename T>
 __device__ __forceinline__ void ph_restrict(const FLevel<T> &L, const FLevel<T> &C, const T *res,
                                             bool coarsest, int64_t i0, int64_t st) {
-    for (int64_t c = i0; c < C.n; c += st) {
-        const int32_t q0 = L.mptr[c], q1 = L.mptr[c + 1];
-        T v[4];
+    for (int64_t c0 = i0; c0 < C.n; c0 += 2 * st) {
+        int32_t q0[2], q1[2], m[2][4];
+        T v[2][4], dc[2];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) v[k] = q0 + k < q1 ? res[L.mem[q0 + k]] : (T)0;
-        T acc = v[0];
+        for (int u = 0; u < 2; ++u) {
+            const int64_t c = c0 + u * st;
+            const bool ok = c < C.n;
+            q0[u] = ok ? L.mptr[c] : 0;
+            q1[u] = ok ? L.mptr[c + 1] : 0;
+            dc[u] = ok && !coarsest ? C.diag[c] : (T)0;
+        }
 #pragma unroll
-        for (int k = 1; k < 4; ++k)
-            if (q0 + k < q1) acc += v[k];
-        for (int32_t q = q0 + 4; q < q1; ++q) acc += res[L.mem[q]];
-        C.b[c] = acc;
-        if (!coarsest) C.x[c] = jac0_of(acc, C.diag[c]);
+        for (int u = 0; u < 2; ++u) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) m[u][k] = q0[u] + k < q1[u] ? L.mem[q0[u] + k] : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) v[u][k] = q0[u] + k < q1[u] ? res[m[u][k]] : (T)0;
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int64_t c = c0 + u * st;
+            if (c >= C.n) break;
+            T acc = v[u][0];
+#pragma unroll
+            for (int k = 1; k < 4; ++k)
+                if (q0[u] + k < q1[u]) acc += v[u][k];
+            for (int32_t q = q0[u] + 4; q < q1[u]; ++q) acc += res[L.mem[q]];
+            C.b[c] = acc;
+            if (!coarsest) C.x[c] = jac0_of(acc, dc[u]);
+        }
     }
 }
 
 // t = x' + omega (b - (diag x' - sum w x'_j)) / diag with x' = x + xc[agg];
-// with rz, accumulates b t (level 0: r.z)
+// with rz, accumulates b t (level 0: r.z).  Two rows per step.
 template <typename T>
 __device__ __forceinline__ void ph_post(const FLevel<T> &L, const T *xc, int64_t i0, int64_t st,
                                         Acc<T> *rz) {
-    for (int64_t v = i0; v < L.n; v += st) {
-        const T s = row_wx_pro(L.col, L.w, L.x, L.agg, xc, L.ptr[v], L.ptr[v + 1]);
-        const T xv = L.x[v] + xc[L.agg[v]];
-        const T d = L.diag[v], bv = L.b[v];
-        const T o = d > (T)0 ? xv + (T)kOmegaF * (bv - (d * xv - s)) / d : xv;
-        L.t[v] = o;
-        if (rz) rz->add_prod(bv, o);
+    for (int64_t v0 = i0; v0 < L.n; v0 += 2 * st) {
+        T xv[2], bv[2], d[2], sm[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int64_t v = v0 + u * st;
+            const bool ok = v < L.n;
+            xv[u] = ok ? L.x[v] : (T)0;
+            bv[u] = ok ? L.b[v] : (T)0;
+            d[u] = ok ? L.diag[v] : (T)0;
+            const int32_t ag = ok ? L.agg[v] : 0;
+            if (ok) xv[u] = xv[u] + xc[ag];
+        }
+        rows_wx<T, 2, true>(L.ptr, L.col, L.w, L.x, L.agg, xc, L.n, v0, st, sm);
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int64_t v = v0 + u * st;
+            if (v >= L.n) break;
+            const T o = d[u] > (T)0 ? xv[u] + (T)kOmegaF * (bv[u] - (d[u] * xv[u] - sm[u])) / d[u]
+                                    : xv[u];
+            L.t[v] = o;
+            if (rz) rz->add_prod(bv[u], o);
+        }
     }
 }
 
-// coarsest: t = Cinv b (block 0; b staged in shared memory)
+// coarsest: t = Cinv b, one warp per row (lanes read the row coalesced and
+// are summed by a fixed xor tree); warps w0, w0 + ws, ... of the caller
 template <typename T>
-__device__ __forceinline__ void ph_coarse(const FLevel<T> &L, const T *cinv, T *sb, Acc<T> *rz) {
+__device__ __forceinline__ void ph_coarse(const FLevel<T> &L, const T *cinv, int64_t w0,
+                                          int64_t ws, Acc<T> *rz) {
     const int64_t nc = L.n;
-    for (int64_t j = threadIdx.x; j < nc; j += blockDim.x) sb[j] = L.b[j];
-    __syncthreads();
-    for (int64_t i = threadIdx.x; i < nc; i += blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t i = w0; i < nc; i += ws) {
         T s = (T)0;
-        for (int64_t j = 0; j < nc; ++j) s += cinv[i * nc + j] * sb[j];
-        L.t[i] = s;
-        if (rz) rz->add_prod(sb[i], s);
+        for (int64_t j = lane; j < nc; j += 32) s += cinv[i * nc + j] * L.b[j];
+        for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(0xffffffffu, s, d);
+        if (lane == 0) {
+            L.t[i] = s;
+            if (rz) rz->add_prod(L.b[i], s);
+        }
+    }
+}
+
+// Warp forms of the three level phases for small levels, whose rows are
+// long (their entries are the fine edges between aggregates): one warp per
+// row (or per coarse vertex), lanes strided over the entries, the lane sums
+// added by a fixed xor tree; warps w0, w0 + ws, ... of the caller.
+template <typename T>
+__device__ __forceinline__ T warp_sum(T s) {
+    for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(0xffffffffu, s, d);
+    return s;
+}
+
+template <typename T>
+__device__ __forceinline__ void ph_residual_w(const FLevel<T> &L, T *res, int64_t w0, int64_t ws) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t v = w0; v < L.n; v += ws) {
+        const int32_t jb = L.ptr[v], je = L.ptr[v + 1];
+        T s = (T)0;
+        for (int32_t j = jb + lane; j < je; j += 32) s += L.w[j] * L.x[L.col[j]];
+        s = warp_sum(s);
+        if (lane == 0) res[v] = L.b[v] - (L.diag[v] * L.x[v] - s);
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void ph_restrict_w(const FLevel<T> &L, const FLevel<T> &C, const T *res,
+                                              bool coarsest, int64_t w0, int64_t ws) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t c = w0; c < C.n; c += ws) {
+        const int32_t q0 = L.mptr[c], q1 = L.mptr[c + 1];
+        T s = (T)0;
+        for (int32_t q = q0 + lane; q < q1; q += 32) s += res[L.mem[q]];
+        s = warp_sum(s);
+        if (lane == 0) {
+            C.b[c] = s;
+            if (!coarsest) C.x[c] = jac0_of(s, C.diag[c]);
+        }
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void ph_post_w(const FLevel<T> &L, const T *xc, int64_t w0, int64_t ws,
+                                          Acc<T> *rz) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t v = w0; v < L.n; v += ws) {
+        const int32_t jb = L.ptr[v], je = L.ptr[v + 1];
+        T s = (T)0;
+        for (int32_t j = jb + lane; j < je; j += 32) {
+            const int32_t c = L.col[j];
+            s += L.w[j] * (L.x[c] + xc[L.agg[c]]);
+        }
+        s = warp_sum(s);
+        if (lane == 0) {
+            const T xv = L.x[v] + xc[L.agg[v]];
+            const T d = L.diag[v], bv = L.b[v];
+            const T o = d > (T)0 ? xv + (T)kOmegaF * (bv - (d * xv - s)) / d : xv;
+            L.t[v] = o;
+            if (rz) rz->add_prod(bv, o);
+        }
     }
 }
 
@@ -230,17 +410,24 @@ __device__ __forceinline__ void ph_coarse(const FLevel<T> &L, const T *cinv, T *
 // barrier gave up (every block returns).
 template <typename T>
 __device__ bool vcycle_fused(const AmgPcgArgs<T> &a, const FLevels<T> &F, unsigned int &epoch,
-                             T *sb, Acc<T> &rz) {
+                             Acc<T> &rz) {
     const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t nth = (int64_t)gridDim.x * blockDim.x;
     const int L = a.L, lt = a.lt;
+    const int64_t gw = gt >> 5, nw = nth >> 5;
     for (int l = 0; l < lt; ++l) {
-        ph_residual(F.l[l], a.res, gt, nth);
+        const bool last = l + 1 == L - 1;
+        if (F.l[l].n <= a.warp_n) ph_residual_w(F.l[l], a.res, gw, nw);
+        else ph_residual(F.l[l], a.res, gt, nth);
         if (!grid_sync(a.bar, a.budget, a.err, epoch)) return false;
-        ph_restrict(F.l[l], F.l[l + 1], a.res, l + 1 == L - 1, gt, nth);
+        if (F.l[l + 1].n <= a.warp_n) ph_restrict_w(F.l[l], F.l[l + 1], a.res, last, gw, nw);
+        else ph_restrict(F.l[l], F.l[l + 1], a.res, last, gt, nth);
         if (!grid_sync(a.bar, a.budget, a.err, epoch)) return false;
     }
-    if (blockIdx.x == 0) {
+    if (lt == L - 1) {
+        // no level in the tail: the coarsest solve across the grid's warps
+        ph_coarse(F.l[L - 1], a.cinv, gw, nw, L == 1 ? &rz : nullptr);
+    } else if (blockIdx.x == 0) {
         const int64_t t0 = threadIdx.x, bs = blockDim.x;
         for (int l = lt; l < L - 1; ++l) {
             ph_residual(F.l[l], a.res, t0, bs);
@@ -248,7 +435,7 @@ __device__ bool vcycle_fused(const AmgPcgArgs<T> &a, const FLevels<T> &F, unsign
             ph_restrict(F.l[l], F.l[l + 1], a.res, l + 1 == L - 1, t0, bs);
             __syncthreads();
         }
-        ph_coarse(F.l[L - 1], a.cinv, sb, L == 1 ? &rz : nullptr);
+        ph_coarse<T>(F.l[L - 1], a.cinv, t0 >> 5, bs >> 5, nullptr);
         __syncthreads();
         for (int l = L - 2; l >= lt; --l) {
             ph_post(F.l[l], F.l[l + 1].t, t0, bs, l == 0 ? &rz : nullptr);
@@ -257,7 +444,8 @@ __device__ bool vcycle_fused(const AmgPcgArgs<T> &a, const FLevels<T> &F, unsign
     }
     if (!grid_sync(a.bar, a.budget, a.err, epoch)) return false;
     for (int l = lt - 1; l >= 0; --l) {
-        ph_post(F.l[l], F.l[l + 1].t, gt, nth, l == 0 ? &rz : nullptr);
+        if (F.l[l].n <= a.warp_n) ph_post_w(F.l[l], F.l[l + 1].t, gw, nw, l == 0 ? &rz : nullptr);
+        else ph_post(F.l[l], F.l[l + 1].t, gt, nth, l == 0 ? &rz : nullptr);
         if (l > 0 && !grid_sync(a.bar, a.budget, a.err, epoch)) return false;
     }
     return true;
@@ -268,7 +456,6 @@ __global__ void __launch_bounds__(kFusedMaxThreads, 1)
     k_amg_pcg_persist(AmgPcgArgs<T> a, FLevels<T> F) {
     __shared__ double s_red[32][32];
     __shared__ double s_v[4];
-    __shared__ T sb[kAmgCoarse];
     unsigned int epoch = 0;
     const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t nth = (int64_t)gridDim.x * blockDim.x;
@@ -309,7 +496,7 @@ __global__ void __launch_bounds__(kFusedMaxThreads, 1)
         double rz = 0.0;
         {
             Acc<T> arz;
-            if (!vcycle_fused(a, F, epoch, sb, arz)) return;
+            if (!vcycle_fused(a, F, epoch, arz)) return;
             double v1[1] = {arz.value()};
             block_sums<1>(v1, s_red, my);
             if (!grid_sync(a.bar, a.budget, a.err, epoch)) return;
@@ -324,29 +511,26 @@ __global__ void __launch_bounds__(kFusedMaxThreads, 1)
         });
         if (!grid_sync(a.bar, a.budget, a.err, epoch)) return;
         for (;;) {
-            // q = A p, p.q
+            // q = A p, p.q (two rows per step, every load of both first)
             Acc<T> apq;
-            for (int64_t v = gt; v < a.n; v += nth) {
-                const T pv = a.p[v];
-                T qv = a.aD[v] * pv;
-                const int32_t jb = a.aptr[v], je = a.aptr[v + 1];
-                for (int32_t j0 = jb; j0 < je; j0 += 4) {
-                    int32_t c[4];
-                    T wv[4], xv[4];
+            for (int64_t v0 = gt; v0 < a.n; v0 += 2 * nth) {
+                T pv[2], dv[2], sm[2];
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const bool ok = j0 + u < je;
-                        c[u] = ok ? a.acol[j0 + u] : 0;
-                        wv[u] = ok ? a.aw[j0 + u] : (T)0;
-                    }
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) xv[u] = j0 + u < je ? a.p[c[u]] : (T)0;
-#pragma unroll
-                    for (int u = 0; u < 4; ++u)
-                        if (j0 + u < je) qv += wv[u] * (pv - xv[u]);
+                for (int u = 0; u < 2; ++u) {
+                    const int64_t v = v0 + u * nth;
+                    const bool ok = v < a.n;
+                    pv[u] = ok ? a.p[v] : (T)0;
+                    dv[u] = ok ? a.aD[v] : (T)0;
                 }
-                a.q[v] = qv;
-                apq.add_prod(pv, qv);
+                rows_lap<T, 2>(a.aptr, a.acol, a.aw, a.p, a.n, v0, nth, pv, sm);
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const int64_t v = v0 + u * nth;
+                    if (v >= a.n) break;
+                    const T qv = dv[u] * pv[u] + sm[u];
+                    a.q[v] = qv;
+                    apq.add_prod(pv[u], qv);
+                }
             }
             {
                 double v1[1] = {apq.value()};
@@ -390,7 +574,7 @@ __global__ void __launch_bounds__(kFusedMaxThreads, 1)
             if (!(rr > tol2) || k >= a.maxit) break;
             // z = V-cycle(r), r.z
             Acc<T> arz;
-            if (!vcycle_fused(a, F, epoch, sb, arz)) return;
+            if (!vcycle_fused(a, F, epoch, arz)) return;
             {
                 double v1[1] = {arz.value()};
                 block_sums<1>(v1, s_red, my);
@@ -479,6 +663,7 @@ int amg_pcg_fused(grass_ctx_t ctx, grass_sparsifier_t S, AmgHier &H, const T *rh
     }
     // block 0 takes the levels from the first of at most amg_tail_n vertices
     a.L = L;
+    a.warp_n = ctx->amg_warp_n;
     a.lt = L - 1;
     for (int l = 0; l < L - 1; ++l)
         if (H.lv[l]->n <= ctx->amg_tail_n) {
@@ -502,12 +687,45 @@ int amg_pcg_fused(grass_ctx_t ctx, grass_sparsifier_t S, AmgHier &H, const T *rh
     a.err = ctx->flags.p + 3;       // the timeout flag of the bounded waits
     memset_d(ctx, out, 0, 2 * sizeof(double));
     GCK(cudaMemsetAsync(a.bar, 0, sizeof(unsigned int), ctx->stream));
+    // roofline accounting, each array counted once per phase that touches it
+    // (s bytes an element, n_l vertices and nnz_l entries on level l):
+    //  residual: CSR + x, b, diag read, res written;
+    //  restriction: member lists, res read, b (and x, diag) of level l+1;
+    //  post-smoothing: CSR + agg, x, b, diag read, x_c gathered, t written;
+    //  coarsest: its dense inverse and two vectors;
+    //  per outer iteration: SpMV with A (CSR + p, D read, q written), the
+    //  update (e, r read and written, p, q, diag read, x written: 8 ns), the
+    //  V-cycle and p = z + beta p (3 ns); the run starts with 7 ns and one
+    //  V-cycle and its last iteration skips one V-cycle and p (about 4 ns
+    //  net).
+    {
+        const double sz = (double)sizeof(T), ns = (double)n * sz;
+        double vc = 0.0;
+        for (int l = 0; l + 1 < L; ++l) {
+            const double nl = (double)H.lv[l]->n, nn = (double)H.lv[l + 1]->n;
+            const double csr = 4.0 * (nl + 1) + (double)H.lv[l]->nnz * (4.0 + sz);
+            const bool coarsest = l + 2 == L;
+            vc += csr + 4.0 * nl * sz;                                            // residual
+            vc += 4.0 * (nn + 1) + 4.0 * nl + nl * sz + (coarsest ? 1.0 : 3.0) * nn * sz;
+            vc += csr + 4.0 * nl + 4.0 * nl * sz + nn * sz;                       // post-smoothing
+        }
+        const double nc = (double)H.nc;
+        vc += nc * nc * sz + 2.0 * nc * sz;
+        const double spmv_a = 4.0 * (n + 1) + 2.0 * g.m * (4.0 + sz) + 3.0 * ns;
+        const double per_outer = spmv_a + 8.0 * ns + vc + 3.0 * ns;
+        if (ctx->tfam == GRASS_KF_PCG) {
+            const size_t snap = ctx->iter_launches.size();
+            ctx->t_snap(out, snap, 0);
+            ctx->iter_launches.push_back({4.0 * ns, per_outer, snap});
+        }
+    }
     bool timed = ctx->t_begin(GRASS_KF_PCG, 0.0);
     void *args[] = {&a, &F};
     GCK(cudaLaunchCooperativeKernel((const void *)k_amg_pcg_persist<T>, dim3(grid), dim3(threads),
                                     args, 0, ctx->stream));
     ctx->launches++;
     ctx->t_end(timed);
+    if (ctx->tfam == GRASS_KF_PCG) ctx->t_snap(out, ctx->iter_launches.back().slot, 1);
     double h[2] = {0.0, 0.0};
     d2h(ctx, h, out, sizeof(h));
     return (int)h[0];

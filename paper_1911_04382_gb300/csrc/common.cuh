@@ -122,8 +122,9 @@ struct grass_ctx_s {
     int pcg_precond = 0;        // 1: the sparsifier's multigrid V-cycle preconditions PCG
     int amg_sweeps = 1;         // Jacobi sweeps before and after each coarse correction
     int lmax_amg = 0;           // 1: lambda_max estimates solve L_S by multigrid-preconditioned CG
-    int amg_fused = 0;          // 1: the multigrid PCG runs as one cooperative kernel (amg_fused.cu)
-    int64_t amg_tail_n = 4096;  // its levels of at most this many vertices run in one block
+    int amg_fused = 1;          // 1: the multigrid PCG runs as one cooperative kernel (amg_fused.cu)
+    int64_t amg_tail_n = 0;     // its levels of at most this many vertices run in one block
+    int64_t amg_warp_n = 16384; // its levels of at most this many vertices take a warp per row
     // a non-blocking stream of the context's own, on which multi-kernel
     // iterations are captured into CUDA graphs and replayed (ordered with the
     // caller's stream by events); created on first use

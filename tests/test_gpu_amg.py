@@ -72,7 +72,8 @@ def test_fused_multigrid_pcg_matches_launch_form(gpu, which, prec):
     iteration run as one launch per level step (CUDA graph replay): the same
     V-cycle, so the iteration counts agree within 2 and the solutions within
     the tolerance, for every split of the levels between the grid and
-    block 0 (none but the coarsest solve, the default 4096, all of them);
+    block 0 (none but the coarsest solve, 4096, all of them) and between
+    thread-per-row and warp-per-row phases;
     "one_level" has at most 256 vertices, so the V-cycle is the coarsest
     dense solve alone."""
     import torch
@@ -96,16 +97,17 @@ def test_fused_multigrid_pcg_matches_launch_form(gpu, which, prec):
             assert st0 == gpu.GRASS_OK
             x0 = host(x)
             gpu.grass_ctx_set_param(ctx, "amg_fused", 1)
-            for tail in (0, 4096, 1 << 40):
+            for tail, warp in ((0, 0), (0, 4096), (0, 1 << 40), (4096, 4096), (1 << 40, 0)):
                 gpu.grass_ctx_set_param(ctx, "amg_tail_n", tail)
+                gpu.grass_ctx_set_param(ctx, "amg_warp_n", warp)
                 x.zero_()
                 st1, s1 = gpu.grass_pcg_solve(ctx, S, dev(b), x, tol, 20000, P, 1e-2, 1e-2, 0)
                 assert st1 == gpu.GRASS_OK
                 x1 = host(x)
                 rel = np.linalg.norm(b - A @ x1) / np.linalg.norm(b)
                 assert rel <= tol and s1.rel_resid_fp64 == pytest.approx(rel, rel=1e-6)
-                assert abs(s1.iters - s0.iters) <= 2, (tail, s1.iters, s0.iters)
-                assert np.linalg.norm(x1 - x0) <= 1e-6 * np.linalg.norm(x0), tail
+                assert abs(s1.iters - s0.iters) <= 2, (tail, warp, s1.iters, s0.iters)
+                assert np.linalg.norm(x1 - x0) <= 1e-6 * np.linalg.norm(x0), (tail, warp)
         finally:
             gpu.grass_sparsifier_destroy(S)
 
