@@ -202,7 +202,8 @@ def run_reference(args, w):
 
 KERNEL_SOURCES = ["paper_1911_04382_gb300/csrc/krylov.cu", "paper_1911_04382_gb300/csrc/solve.cu",
                   "paper_1911_04382_gb300/csrc/tree_solve.cuh",
-                  "paper_1911_04382_gb300/csrc/common.cuh"]
+                  "paper_1911_04382_gb300/csrc/common.cuh",
+                  "paper_1911_04382_gb300/csrc/amg_fused.cu"]
 
 
 def kernel_sources_hash(read=None) -> str:
@@ -223,11 +224,12 @@ def kernel_sources_hash(read=None) -> str:
 def profile_kernel(G, ctx, which, g, rp, col, val, v0d, w) -> int:
     """One warm and one timed launch of the fused inner CG (exactly 30
     iterations, r = 1 -- "cg" -- or r = 16 -- "cg16", one embedding step --,
-    FP32, sparsifier = tree + every 197th off-tree edge), of the fused PCG, or
-    of the tree solve (r = 16, FP32); prints its algorithmic bytes."""
+    FP32, sparsifier = tree + every 197th off-tree edge), of the fused PCG
+    ("pcg": tree solve and one inner step; "amgpcg": the multigrid V-cycle),
+    or of the tree solve (r = 16, FP32); prints its algorithmic bytes."""
     import torch
     tree = G.grass_build_tree(ctx, rp, col, val, 0)
-    if which in ("cg", "pcg", "cg16"):
+    if which in ("cg", "pcg", "cg16", "amgpcg"):
         S = G.grass_sparsifier_create(ctx, tree)
         _, moff = G.grass_sparsifier_info(S)
         ids = torch.empty(moff, dtype=torch.int64, device="cuda")
@@ -244,9 +246,14 @@ def profile_kernel(G, ctx, which, g, rp, col, val, v0d, w) -> int:
         else:
             bq = v0d[:g.n].contiguous()
             xq = torch.zeros(g.n, dtype=torch.float64, device="cuda")
-            # one FP32 pass of exactly 30 outer iterations (tolerance out of reach)
-            run = lambda: G.grass_pcg_solve(ctx, S, bq, xq, 1e-30, 30, G.GRASS_FP32, 1e-20, 1e-2, 1)
-            fam, units = G.GRASS_KF_PCG, "30 outer iterations, inner 1"
+            # one FP32 pass of exactly 30 outer iterations (tolerance out of reach);
+            # "amgpcg": the fused multigrid PCG (the warm run builds the hierarchy)
+            mg = which == "amgpcg"
+            G.grass_ctx_set_param(ctx, "pcg_precond", 1 if mg else 0)
+            run = lambda: G.grass_pcg_solve(ctx, S, bq, xq, 1e-30, 30, G.GRASS_FP32, 1e-20, 1e-2,
+                                            0 if mg else 1)
+            fam, units = G.GRASS_KF_PCG, ("30 outer iterations, one V-cycle each" if mg
+                                          else "30 outer iterations, inner 1")
     else:
         B = torch.randn(g.n, 16, dtype=torch.float32, device="cuda")
         X = torch.empty_like(B)
@@ -629,7 +636,8 @@ def per_round(st: dict, g, w: dict, peak: float) -> list:
     return out
 
 
-def c2_extras(G, ctx, w: dict, g, rp, col, val, h0d, v0d, bd, P, peak: float) -> dict:
+def c2_extras(G, ctx, w: dict, g, rp, col, val, h0d, v0d, bd, P, peak: float,
+              pcg_mg: bool = True) -> dict:
     """On the step's sparsifier: the lambda estimates with tight inner solves
     (certifying the stop decision), the plain FP64 method at the same 1e-8
     accuracy, and the PCG iteration count and time for inner budgets 0 (tree
@@ -655,6 +663,8 @@ def c2_extras(G, ctx, w: dict, g, rp, col, val, h0d, v0d, bd, P, peak: float) ->
             "s": time.perf_counter() - t0}
         sweep = []
         x = torch.zeros(g.n, dtype=torch.float64, device="cuda")
+        # the tree solve with 0-8 inner steps on the sparsifier, then the V-cycle
+        G.grass_ctx_set_param(ctx, "pcg_precond", 0)
         for inner in (0, 1, 2, 4, 8):
             x.zero_()
             torch.cuda.synchronize()
@@ -678,7 +688,7 @@ def c2_extras(G, ctx, w: dict, g, rp, col, val, h0d, v0d, bd, P, peak: float) ->
                           "multigrid V-cycle of L_S + D (fp64)", "iters": ps.iters,
                           "ms": 1e3 * (time.perf_counter() - t0),
                           "rel_resid_fp64": ps.rel_resid_fp64, "status": stt})
-        G.grass_ctx_set_param(ctx, "pcg_precond", 0)
+        G.grass_ctx_set_param(ctx, "pcg_precond", 1 if pcg_mg else 0)
         out["pcg_inner_sweep"] = sweep
         # lambda_max of the final sparsifier by multigrid-CG solves (8 steps, 1e-6)
         G.grass_ctx_set_param(ctx, "lmax_amg", 1)
@@ -1128,13 +1138,16 @@ def main() -> int:
     ap.add_argument("--family", default="pcg", choices=sorted(FAMILIES),
                     help="kernel family timed for the roofline object")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--pcg-precond", default="multigrid", choices=["tree", "multigrid"],
+                    help="the step's PCG preconditioner: the tree solve with one inner step on "
+                         "the sparsifier, or one V-cycle of the sparsifier's multigrid")
     ap.add_argument("--no-breakdown", action="store_true")
     ap.add_argument("--profile-step", action="store_true",
                     help="run exactly one step and exit (for ncu launch lists)")
     ap.add_argument("--profile-amg", action="store_true",
                     help="one warm and one NVTX-ranged ('amgpcg') multigrid-preconditioned PCG solve "
                          "(FP32 + FP64 refinement, 1e-8) on the step's sparsifier, for ncu launch lists")
-    ap.add_argument("--profile-kernel", choices=["cg", "cg16", "tree", "pcg"], default=None,
+    ap.add_argument("--profile-kernel", choices=["cg", "cg16", "tree", "pcg", "amgpcg"], default=None,
                     help="one warm launch, then one timed launch of the kernel (for ncu captures)")
     ap.add_argument("--no-solve40m", action="store_true",
                     help="skip the 40M-unknown solve (solve_40m key of the line)")
@@ -1183,6 +1196,8 @@ def main() -> int:
     g, h0, v0, b = make_inputs(w)
     stream = torch.cuda.current_stream()
     ctx = G.grass_ctx_create(stream)
+    if args.pcg_precond == "multigrid":
+        G.grass_ctx_set_param(ctx, "pcg_precond", 1)
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
     rp, col, val = dev(g.rowptr), dev(g.col), dev(g.val)
     h0d, v0d, bd = dev(h0), dev(v0), dev(b)
@@ -1346,15 +1361,17 @@ def main() -> int:
     # algorithmic bytes of the captured launch, times this run's algorithmic
     # bytes per launch); null when the kernel sources changed since
     traffic_note = None
+    # the PCG family's kernel is the fused multigrid PCG under --pcg-precond multigrid
+    fam_key = "amgpcg" if args.family == "pcg" and args.pcg_precond == "multigrid" else args.family
     try:
         tr = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
-        rec = tr.get(args.workload, {}).get(args.family)
+        rec = tr.get(args.workload, {}).get(fam_key)
         if rec and rec.get("sources") == kernel_sources_hash() and kl:
             traffic_note = rec["dram_bytes"] / rec["algorithmic_bytes"] * (kbytes / kl)
     except Exception:
         pass
     roofline = {
-        "kernel": args.family, "bound": "hbm", "achieved": achieved, "peak": peak,
+        "kernel": fam_key, "bound": "hbm", "achieved": achieved, "peak": peak,
         "unit": "GB/s", "frac": (achieved / peak) if achieved else None,
         "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks else "fallback 6800 GB/s",
         "traffic": traffic_note, "launches_timed": kl,
@@ -1375,7 +1392,8 @@ def main() -> int:
 
     extras = {}
     if rank == 0 and not args.no_extras and args.workload == "grid3d_100":
-        for name, fn in (("c2", lambda: c2_extras(G, ctx, w, g, rp, col, val, h0d, v0d, bd, P, peak)),
+        for name, fn in (("c2", lambda: c2_extras(G, ctx, w, g, rp, col, val, h0d, v0d, bd, P, peak,
+                                                      args.pcg_precond == "multigrid")),
                          ("c1_latency", lambda: c1_latency(G)),
                          ("c3_powerlaw", lambda: c3_powerlaw(G, peak)),
                          ("hair_comb", lambda: hair_comb(G)),
@@ -1410,6 +1428,7 @@ def main() -> int:
                        "nnz": g.nnz, "per_round_cap": cap,
                        "l2": "inputs larger than L2 (CSR + start vectors resident: "
                              f"{(g.nnz * 12 + h0.nbytes + v0.nbytes) / 1e6:.0f} MB)",
+                       "pcg_preconditioner": args.pcg_precond,
                        "parallelism": f"replicas x{world}"},
             "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu,
             "clocks": clk, "edges_embedded_per_step": edges_per_step,

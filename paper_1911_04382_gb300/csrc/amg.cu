@@ -34,6 +34,7 @@
 #include <cmath>
 
 #include "common.cuh"
+#include "tree_solve.cuh"
 
 namespace grass {
 
@@ -73,10 +74,12 @@ __global__ void k_amg_diag(int64_t n, const int32_t *ptr, const double *w, const
     diag[v] = s;
 }
 
+// go: the previous round matched something (rounds after one that matched
+// nothing would match nothing either, so they return at once)
 __global__ void k_amg_cand(int64_t n, const int32_t *ptr, const int32_t *col, const double *w,
-                           const int32_t *mate, int32_t *cand) {
+                           const int32_t *mate, int32_t *cand, const int *go) {
     int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= n) return;
+    if (v >= n || !*go) return;
     if (mate[v] >= 0) {
         cand[v] = -1;
         return;
@@ -97,9 +100,10 @@ __global__ void k_amg_cand(int64_t n, const int32_t *ptr, const int32_t *col, co
     cand[v] = bu;
 }
 
-__global__ void k_amg_pair(int64_t n, const int32_t *cand, int32_t *mate, int *changed) {
+__global__ void k_amg_pair(int64_t n, const int32_t *cand, int32_t *mate, const int *go,
+                           int *changed) {
     int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= n || mate[v] >= 0) return;
+    if (v >= n || !*go || mate[v] >= 0) return;
     const int32_t u = cand[v];
     if (u >= 0 && cand[u] == (int32_t)v) {
         mate[v] = u;
@@ -234,13 +238,13 @@ __global__ void k_amg_f32(int64_t n, const double *a, float *b) {
     if (i < n) b[i] = (float)a[i];
 }
 
-// dense coarsest matrix (row i by thread i, its entries added in row order)
+// dense coarsest matrix (row i by thread i, its entries added in row order;
+// M zeroed before)
 __global__ void k_amg_dense(int64_t nc, const int32_t *ptr, const int32_t *col, const double *w,
                             const double *diag, int ground, double *M) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nc) return;
     double *row = M + i * nc;
-    for (int64_t j = 0; j < nc; ++j) row[j] = 0.0;
     if (ground && i == nc - 1) {
         row[i] = 1.0;
         return;
@@ -282,6 +286,43 @@ __global__ void k_amg_gauss_jordan(int64_t nc, double *M, int ground) {
             M[(nc - 1) * nc + j] = 0.0;
             M[j * nc + (nc - 1)] = 0.0;
         }
+    }
+}
+
+// The same Gauss-Jordan inverse across a cooperative grid: step p reads the
+// matrix after step p - 1 from one buffer and writes step p's into the other
+// (one grid barrier a step, the same arithmetic per element as above); block
+// b updates rows b, b + gridDim.x, ...  Returns through *which the buffer
+// (0: M0, 1: M1) holding the inverse.  The FP64 work of the one-block form
+// (about nc^3 multiply-adds) is spread over the SMs.
+__global__ void k_amg_gj_grid(int64_t nc, double *M0, double *M1, unsigned int *bar, long long budget,
+                              int *err) {
+    __shared__ double rowp[kCoarse];
+    unsigned int epoch = 0;
+    for (int64_t p = 0; p < nc; ++p) {
+        const double *src = (p & 1) ? M1 : M0;
+        double *dst = (p & 1) ? M0 : M1;
+        const double inv = 1.0 / src[p * nc + p];
+        for (int64_t j = threadIdx.x; j < nc; j += blockDim.x) rowp[j] = src[p * nc + j];
+        __syncthreads();
+        for (int64_t i = blockIdx.x; i < nc; i += gridDim.x) {
+            const double aip = src[i * nc + p];
+            for (int64_t j = threadIdx.x; j < nc; j += blockDim.x) {
+                double v;
+                if (i == p) v = j == p ? inv : rowp[j] * inv;
+                else if (j == p) v = -aip * inv;
+                else v = src[i * nc + j] - aip * (rowp[j] * inv);
+                dst[i * nc + j] = v;
+            }
+        }
+        if (!grid_sync(bar, budget, err, epoch)) return;
+    }
+}
+
+__global__ void k_amg_ground_inv(int64_t nc, double *M) {
+    for (int64_t j = threadIdx.x; j < nc; j += blockDim.x) {
+        M[(nc - 1) * nc + j] = 0.0;
+        M[j * nc + (nc - 1)] = 0.0;
     }
 }
 
@@ -370,72 +411,77 @@ T *lvl_diag(AmgLevel &L) {
 }
 
 // level 0 from the sparsifier's adjacency (a copy: the hierarchy owns it)
-std::unique_ptr<AmgLevel> level0(grass_ctx_t ctx, grass_sparsifier_t S, bool with_D) {
+std::unique_ptr<AmgLevel> level0(grass_ctx_t ctx, AmgHier &H, grass_sparsifier_t S, bool with_D) {
     const GraphData &g = S->tree->g;
     auto L = std::make_unique<AmgLevel>();
     L->n = g.n;
     L->nnz = S->s_nnz;
-    L->ptr.alloc(g.n + 1);
-    L->col.alloc(S->s_nnz);
-    L->w64.alloc(S->s_nnz);
+    H.arena.get(L->ptr, g.n + 1);
+    H.arena.get(L->col, S->s_nnz);
+    H.arena.get(L->w64, S->s_nnz);
     copy_d(ctx, L->ptr.p, S->s_ptr.p, (g.n + 1) * sizeof(int32_t));
     copy_d(ctx, L->col.p, S->s_col.p, S->s_nnz * sizeof(int32_t));
     copy_d(ctx, L->w64.p, S->s_w64.p, S->s_nnz * sizeof(double));
-    L->D64.alloc(g.n);
+    H.arena.get(L->D64, g.n);
     if (with_D) copy_d(ctx, L->D64.p, g.D64.p, g.n * sizeof(double));
     else memset_d(ctx, L->D64.p, 0, g.n * sizeof(double));
-    L->diag64.alloc(g.n);
+    H.arena.get(L->diag64, g.n);
     launch(ctx, k_amg_diag, cdiv(g.n, kBlock), kBlock, 0, g.n, (const int32_t *)L->ptr.p,
            (const double *)L->w64.p, (const double *)L->D64.p, L->diag64.p);
     return L;
 }
 
 // aggregate level L into a new coarse level
-std::unique_ptr<AmgLevel> coarsen(grass_ctx_t ctx, AmgLevel &L) {
+std::unique_ptr<AmgLevel> coarsen(grass_ctx_t ctx, AmgHier &H, AmgLevel &L) {
     const int64_t n = L.n;
-    DBuf<int32_t> mate, cand, anchor, leader, jslot, jcount;
-    mate.alloc(n);
-    cand.alloc(n);
-    anchor.alloc(n);
-    leader.alloc(n);
-    jslot.alloc(n);
-    jcount.alloc(n);
+    Arena &tmp = ctx->amg_tmp;        // this level's temporaries
+    tmp.reset();
+    ASpan<int32_t> mate, cand, anchor, leader, jslot, jcount;
+    tmp.get(mate, n);
+    tmp.get(cand, n);
+    tmp.get(anchor, n);
+    tmp.get(leader, n);
+    tmp.get(jslot, n);
+    tmp.get(jcount, n);
     memset_d(ctx, mate.p, 0xFF, n * sizeof(int32_t));     // -1
     memset_d(ctx, jslot.p, 0xFF, n * sizeof(int32_t));
-    int *changed = ctx->flags.p + 4;
+    // flags[4 + (round & 1)]: round `round` matched something; the next
+    // round reads it (no host round trip per round)
+    int *chg = ctx->flags.p + 4;
     const int64_t g = cdiv(n, kBlock);
+    const int one = 1;
+    GCK(cudaMemcpyAsync(chg + 1, &one, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
     for (int round = 0; round < kMatchRounds; ++round) {
-        memset_d(ctx, changed, 0, sizeof(int));
+        int *cur = chg + (round & 1);
+        const int *prev = chg + ((round + 1) & 1);
+        memset_d(ctx, cur, 0, sizeof(int));
         launch(ctx, k_amg_cand, g, kBlock, 0, n, (const int32_t *)L.ptr.p, (const int32_t *)L.col.p,
-               (const double *)L.w64.p, (const int32_t *)mate.p, cand.p);
-        launch(ctx, k_amg_pair, g, kBlock, 0, n, (const int32_t *)cand.p, mate.p, changed);
-        int ch = 0;
-        d2h(ctx, &ch, changed, sizeof(int));
-        if (!ch) break;
+               (const double *)L.w64.p, (const int32_t *)mate.p, cand.p, prev);
+        launch(ctx, k_amg_pair, g, kBlock, 0, n, (const int32_t *)cand.p, mate.p, prev, cur);
     }
     launch(ctx, k_amg_join, g, kBlock, 0, n, (const int32_t *)L.ptr.p, (const int32_t *)L.col.p,
            (const double *)L.w64.p, (const int32_t *)mate.p, anchor.p, leader.p);
     launch(ctx, k_amg_slots, g, kBlock, 0, n, (const int32_t *)L.ptr.p, (const int32_t *)L.col.p,
            (const int32_t *)mate.p, (const int32_t *)anchor.p, jslot.p, jcount.p);
-    DBuf<int64_t> flag, pos;
-    flag.alloc(n + 1);
-    pos.alloc(n + 1);
+    ASpan<int64_t> flag, pos;
+    tmp.get(flag, n + 1);
+    tmp.get(pos, n + 1);
     launch(ctx, k_amg_leadflag, g, kBlock, 0, n, (const int32_t *)leader.p, flag.p);
     int64_t nc = 0;
     scan_i64(ctx, flag.p, pos.p, n, &nc);
     auto C = std::make_unique<AmgLevel>();
     C->n = nc;
-    L.agg.alloc(n);
-    DBuf<int64_t> mcnt, moff;
-    mcnt.alloc(nc + 1);
-    moff.alloc(nc + 1);
+    H.arena.get(L.agg, n);
+    ASpan<int64_t> mcnt, moff;
+    tmp.get(mcnt, nc + 1);
+    tmp.get(moff, nc + 1);
     launch(ctx, k_amg_agg, g, kBlock, 0, n, (const int32_t *)leader.p, (const int64_t *)pos.p,
            (const int32_t *)mate.p, (const int32_t *)jcount.p, L.agg.p, mcnt.p);
     int64_t nm = 0;
     scan_i64(ctx, mcnt.p, moff.p, nc, &nm);
     if (nm != n) fail(GRASS_ERR_CUDA, "multigrid aggregation lost vertices");
-    L.mem.alloc(n);
-    L.mptr.alloc(nc + 1);
+    H.arena.get(L.mem, n);
+    H.arena.get(L.mptr, nc + 1);
     launch(ctx, k_amg_members, g, kBlock, 0, n, (const int32_t *)leader.p, (const int32_t *)mate.p,
            (const int32_t *)anchor.p, (const int32_t *)jslot.p, (const int32_t *)jcount.p,
            (const int32_t *)L.agg.p, (const int64_t *)moff.p, L.mem.p);
@@ -443,19 +489,19 @@ std::unique_ptr<AmgLevel> coarsen(grass_ctx_t ctx, AmgLevel &L) {
            L.mptr.p);
     // coarse matrix
     const int64_t gc = cdiv(nc, kBlock);
-    DBuf<int64_t> ccnt, coff;
-    ccnt.alloc(nc + 1);
-    coff.alloc(nc + 1);
+    ASpan<int64_t> ccnt, coff;
+    tmp.get(ccnt, nc + 1);
+    tmp.get(coff, nc + 1);
     launch(ctx, k_amg_ccount, gc, kBlock, 0, nc, (const int32_t *)L.mptr.p, (const int32_t *)L.mem.p,
            (const int32_t *)L.ptr.p, (const int32_t *)L.col.p, (const int32_t *)L.agg.p, ccnt.p);
     int64_t cnnz = 0;
     scan_i64(ctx, ccnt.p, coff.p, nc, &cnnz);
     C->nnz = cnnz;
-    C->ptr.alloc(nc + 1);
-    C->col.alloc(cnnz);
-    C->w64.alloc(cnnz);
-    C->D64.alloc(nc);
-    C->diag64.alloc(nc);
+    H.arena.get(C->ptr, nc + 1);
+    H.arena.get(C->col, cnnz);
+    H.arena.get(C->w64, cnnz);
+    H.arena.get(C->D64, nc);
+    H.arena.get(C->diag64, nc);
     launch(ctx, k_amg_cfill, gc, kBlock, 0, nc, (const int32_t *)L.mptr.p, (const int32_t *)L.mem.p,
            (const int32_t *)L.ptr.p, (const int32_t *)L.col.p, (const double *)L.w64.p,
            (const double *)L.D64.p, (const int32_t *)L.agg.p, (const int64_t *)coff.p, C->ptr.p,
@@ -484,10 +530,10 @@ AmgHier &amg_get(grass_ctx_t ctx, grass_sparsifier_t S, bool with_D) {
     if (slot) return *slot;
     if (S->is_tree || S->s_nnz == 0) fail(GRASS_ERR_INVALID, "multigrid needs a sparsifier with off-tree edges");
     auto H = std::make_unique<AmgHier>();
-    H->lv.push_back(level0(ctx, S, with_D));
+    H->lv.push_back(level0(ctx, *H, S, with_D));
     while (H->lv.back()->n > kCoarse) {
         if ((int)H->lv.size() >= kMaxLevels) fail(GRASS_ERR_CUDA, "multigrid: too many levels");
-        auto C = coarsen(ctx, *H->lv.back());
+        auto C = coarsen(ctx, *H, *H->lv.back());
         if (C->n > H->lv.back()->n * 95 / 100)
             fail(GRASS_ERR_CUDA, "multigrid coarsening stalled at " + std::to_string(C->n) + " vertices");
         H->lv.push_back(std::move(C));
@@ -495,16 +541,16 @@ AmgHier &amg_get(grass_ctx_t ctx, grass_sparsifier_t S, bool with_D) {
     // FP32 copies and V-cycle vectors
     for (size_t l = 0; l < H->lv.size(); ++l) {
         AmgLevel &L = *H->lv[l];
-        L.w32.alloc(std::max<int64_t>(L.nnz, 1));
-        L.diag32.alloc(L.n);
+        H->arena.get(L.w32, std::max<int64_t>(L.nnz, 1));
+        H->arena.get(L.diag32, L.n);
         launch(ctx, k_amg_f32, cdiv(L.nnz, kBlock), kBlock, 0, L.nnz, (const double *)L.w64.p, L.w32.p);
         launch(ctx, k_amg_f32, cdiv(L.n, kBlock), kBlock, 0, L.n, (const double *)L.diag64.p,
                L.diag32.p);
         if (l > 0) {
-            L.vb.alloc(L.n * sizeof(double) + 256);
-            L.vx.alloc(L.n * sizeof(double) + 256);
+            H->arena.get(L.vb, L.n * sizeof(double) + 256);
+            H->arena.get(L.vx, L.n * sizeof(double) + 256);
         }
-        L.vt.alloc(L.n * sizeof(double) + 256);
+        H->arena.get(L.vt, L.n * sizeof(double) + 256);
     }
     // coarsest: dense (grounded) inverse
     AmgLevel &Lc = *H->lv.back();
@@ -516,13 +562,39 @@ AmgHier &amg_get(grass_ctx_t ctx, grass_sparsifier_t S, bool with_D) {
     H->singular = !(ds > 0.0);
     H->cinv64.alloc(Lc.n * Lc.n);
     H->cinv32.alloc(Lc.n * Lc.n);
+    memset_d(ctx, H->cinv64.p, 0, Lc.n * Lc.n * sizeof(double));
     launch(ctx, k_amg_dense, cdiv(Lc.n, kBlock), kBlock, 0, Lc.n, (const int32_t *)Lc.ptr.p,
            (const int32_t *)Lc.col.p, (const double *)Lc.w64.p, (const double *)Lc.diag64.p,
            H->singular ? 1 : 0, H->cinv64.p);
-    launch(ctx, k_amg_gauss_jordan, 1, 1024, 0, Lc.n, H->cinv64.p, H->singular ? 1 : 0);
+    if (ctx->num_sms > 0 && Lc.n > 1) {
+        // across the grid (cooperative): nc steps, one barrier each
+        ctx->amg_tmp.reset();
+        ASpan<double> other;
+        ctx->amg_tmp.get(other, Lc.n * Lc.n);
+        const int grid = (int)std::min<int64_t>(Lc.n, coop_grid(ctx, k_amg_gj_grid, 256, 0, Lc.n * 256));
+        int64_t nc = Lc.n;
+        double *m0 = H->cinv64.p, *m1 = other.p;
+        unsigned int *bar = ctx->gbar.p;
+        long long budget = ctx->wait_budget;
+        int *err = ctx->flags.p + 3;
+        GCK(cudaMemsetAsync(bar, 0, sizeof(unsigned int), ctx->stream));
+        void *args[] = {&nc, &m0, &m1, &bar, &budget, &err};
+        GCK(cudaLaunchCooperativeKernel((const void *)k_amg_gj_grid, dim3(grid), dim3(256), args, 0,
+                                        ctx->stream));
+        ctx->launches++;
+        // the last step (p = nc - 1) wrote M1 when nc - 1 is even
+        if (((nc - 1) & 1) == 0) copy_d(ctx, H->cinv64.p, other.p, nc * nc * sizeof(double));
+        if (H->singular) launch(ctx, k_amg_ground_inv, 1, 256, 0, nc, H->cinv64.p);
+        ctx->sync();
+        check_timeout(ctx);
+    } else {
+        launch(ctx, k_amg_gauss_jordan, 1, 1024, 0, Lc.n, H->cinv64.p, H->singular ? 1 : 0);
+    }
     launch(ctx, k_amg_f32, cdiv(Lc.n * Lc.n, kBlock), kBlock, 0, Lc.n * Lc.n,
            (const double *)H->cinv64.p, H->cinv32.p);
     ctx->sync();
+    // keep up to 256 MB of temporaries for the next hierarchy
+    if (ctx->amg_tmp.bytes() > ((size_t)256 << 20)) ctx->amg_tmp = Arena();
     slot = std::move(H);
     return *slot;
 }

@@ -65,6 +65,49 @@ struct DBuf {
     T *get() const { return p; }
 };
 
+// A device array carved from an Arena (not owning).
+template <typename T>
+struct ASpan {
+    T *p = nullptr;
+    size_t n = 0;
+};
+
+// Bump allocation from device chunks of at least 64 MB, freed together: one
+// cudaMalloc per chunk instead of one per array (and no synchronising
+// cudaFree per array).  reset() reuses the chunks from the start.
+struct Arena {
+    std::vector<std::unique_ptr<DBuf<char>>> chunks;
+    size_t cur = 0, off = 0;
+    void reset() { cur = off = 0; }
+    size_t bytes() const {
+        size_t b = 0;
+        for (const auto &c : chunks) b += c->n;
+        return b;
+    }
+    template <typename T>
+    T *get(size_t count) {
+        const size_t bytes = ((count ? count : 1) * sizeof(T) + 255) & ~(size_t)255;
+        while (cur < chunks.size() && off + bytes > chunks[cur]->n) {
+            ++cur;
+            off = 0;
+        }
+        if (cur == chunks.size()) {
+            auto c = std::make_unique<DBuf<char>>();
+            c->alloc(bytes > ((size_t)64 << 20) ? bytes : ((size_t)64 << 20));
+            chunks.push_back(std::move(c));
+            off = 0;
+        }
+        T *q = reinterpret_cast<T *>(chunks[cur]->p + off);
+        off += bytes;
+        return q;
+    }
+    template <typename T>
+    void get(ASpan<T> &a, size_t count) {
+        a.p = get<T>(count);
+        a.n = count ? count : 1;
+    }
+};
+
 // ---------------------------------------------------------------- context
 
 enum ScratchSlot {
@@ -122,6 +165,7 @@ struct grass_ctx_s {
     int pcg_precond = 0;        // 1: the sparsifier's multigrid V-cycle preconditions PCG
     int amg_sweeps = 1;         // Jacobi sweeps before and after each coarse correction
     int lmax_amg = 0;           // 1: lambda_max estimates solve L_S by multigrid-preconditioned CG
+    grass::Arena amg_tmp;       // the multigrid setup's temporary arrays
     int amg_fused = 1;          // 1: the multigrid PCG runs as one cooperative kernel (amg_fused.cu)
     int64_t amg_tail_n = 0;     // its levels of at most this many vertices run in one block
     int64_t amg_warp_n = 16384; // its levels of at most this many vertices take a warp per row
@@ -386,15 +430,16 @@ struct EulerTour {
 // separate entries) with the aggregates' summed diagonal loads.
 struct AmgLevel {
     int64_t n = 0, nnz = 0;
-    DBuf<int32_t> ptr, col;           // off-diagonal adjacency (a column may repeat)
-    DBuf<double> w64, diag64, D64;    // weights, diagonal = weighted degree + D, D
-    DBuf<float> w32, diag32;
-    DBuf<int32_t> agg;                // [n] coarse vertex of each vertex (not on the coarsest)
-    DBuf<int32_t> mptr, mem;          // members of coarse vertex c: mem[mptr[c] .. mptr[c+1])
-    DBuf<char> vb, vx, vt;            // V-cycle vectors of this level (coarse levels)
+    ASpan<int32_t> ptr, col;          // off-diagonal adjacency (a column may repeat)
+    ASpan<double> w64, diag64, D64;   // weights, diagonal = weighted degree + D, D
+    ASpan<float> w32, diag32;
+    ASpan<int32_t> agg;               // [n] coarse vertex of each vertex (not on the coarsest)
+    ASpan<int32_t> mptr, mem;         // members of coarse vertex c: mem[mptr[c] .. mptr[c+1])
+    ASpan<char> vb, vx, vt;           // V-cycle vectors of this level (coarse levels)
 };
 
 struct AmgHier {
+    Arena arena;                      // every level's arrays
     std::vector<std::unique_ptr<AmgLevel>> lv;
     bool singular = false;            // D = 0: the coarsest solve is grounded
     int64_t nc = 0;                   // coarsest size
