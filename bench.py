@@ -1220,10 +1220,12 @@ def main() -> int:
                       w["inner_tol"], w["inner_maxit"])
     last = {}
 
-    def step(rp, col, val, h0d, v0d, bd, x):
+    def step(rp, col, val, h0d, v0d, bd, x, before_densify=None):
         t0 = time.perf_counter()
         tree = G.grass_build_tree(ctx, rp, col, val, 0)
         t1 = time.perf_counter()
+        if before_densify is not None:
+            before_densify()
         S, st = G.grass_densify(ctx, tree, P, h0d, v0d)
         t2 = time.perf_counter()
         status, sst = G.grass_pcg_solve(ctx, S, bd, x, w["pcg_tol"], w["pcg_maxit"], pcg_prec,
@@ -1332,21 +1334,33 @@ def main() -> int:
     edges_per_step = edges / args.steps
     value = replica_value(world, edges_per_step, ms)
 
-    # e2e: host (pinned) inputs copied in and the result copied out, every step
+    # e2e: host (pinned) inputs copied in and the result copied out, every
+    # step.  The copies run on a copy stream: the CSR first (the tree build
+    # waits for it), then the start vectors and b, which the step waits for
+    # only before densification, so they overlap the tree build
     host = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
     hp = [host(g.rowptr), host(g.col), host(g.val), host(h0), host(v0), host(b)]
     dbufs = [torch.empty_like(t, device="cuda") for t in hp]
     xh = torch.empty(g.n, dtype=torch.float64).pin_memory()
     h2d = sum(t.numel() * t.element_size() for t in hp)
     d2h = xh.numel() * xh.element_size()
+    cstream = torch.cuda.Stream()
+    ev_csr, ev_rest = torch.cuda.Event(), torch.cuda.Event()
     barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     e_edges = 0
     for _ in range(args.steps):
-        for d, h in zip(dbufs, hp):
-            d.copy_(h, non_blocking=True)
-        e_edges += step(*dbufs, x)
+        cstream.wait_stream(stream)          # the previous step is done with the buffers
+        with torch.cuda.stream(cstream):
+            for d, h in zip(dbufs[:3], hp[:3]):
+                d.copy_(h, non_blocking=True)
+            ev_csr.record(cstream)
+            for d, h in zip(dbufs[3:], hp[3:]):
+                d.copy_(h, non_blocking=True)
+            ev_rest.record(cstream)
+        stream.wait_event(ev_csr)
+        e_edges += step(*dbufs, x, before_densify=lambda: stream.wait_event(ev_rest))
         xh.copy_(x, non_blocking=True)
     e1.record(stream)
     barrier()

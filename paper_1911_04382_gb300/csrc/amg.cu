@@ -111,6 +111,117 @@ __global__ void k_amg_pair(int64_t n, const int32_t *cand, int32_t *mate, const 
     }
 }
 
+// Warp forms of k_amg_cand, k_amg_ccount and k_amg_cfill for small levels,
+// whose rows are long (they carry the fine edges between aggregates): one
+// warp per vertex, lanes strided over the row.  They give the same results
+// as the thread forms: the candidate is the heaviest by (w, pair key), the
+// first in row order among equal ones (each lane keeps its first best, the
+// lanes' bests are compared with the row position as the last key), and the
+// coarse rows are written and their weights summed in row order.
+constexpr int64_t kAmgWarpSetup = 16384;   // levels of at most this many vertices
+
+__global__ void k_amg_cand_w(int64_t n, const int32_t *ptr, const int32_t *col, const double *w,
+                             const int32_t *mate, int32_t *cand, const int *go) {
+    const int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (v >= n || !*go) return;
+    if (mate[v] >= 0) {
+        if (lane == 0) cand[v] = -1;
+        return;
+    }
+    double bw = -1.0;
+    int32_t bu = -1, bj = INT_MAX;
+    unsigned long long bk = 0;
+    for (int32_t j = ptr[v] + lane; j < ptr[v + 1]; j += 32) {
+        const int32_t u = col[j];
+        if (u == v || mate[u] >= 0) continue;
+        const unsigned long long k = pair_key((int32_t)v, u);
+        if (bu < 0 || better(w[j], k, bw, bk)) {
+            bw = w[j];
+            bu = u;
+            bk = k;
+            bj = j;
+        }
+    }
+    for (int d = 16; d > 0; d >>= 1) {
+        const double ow = __shfl_xor_sync(0xffffffffu, bw, d);
+        const int32_t ou = __shfl_xor_sync(0xffffffffu, bu, d);
+        const int32_t oj = __shfl_xor_sync(0xffffffffu, bj, d);
+        const unsigned long long ok = __shfl_xor_sync(0xffffffffu, bk, d);
+        const bool take = ou >= 0 && (bu < 0 || better(ow, ok, bw, bk) ||
+                                      (ow == bw && ok == bk && oj < bj));
+        if (take) {
+            bw = ow;
+            bu = ou;
+            bk = ok;
+            bj = oj;
+        }
+    }
+    if (lane == 0) cand[v] = bu;
+}
+
+__global__ void k_amg_ccount_w(int64_t nc, const int32_t *mptr, const int32_t *mem,
+                               const int32_t *ptr, const int32_t *col, const int32_t *agg,
+                               int64_t *ccnt) {
+    const int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (c >= nc) return;
+    int64_t k = 0;
+    for (int32_t q = mptr[c]; q < mptr[c + 1]; ++q) {
+        const int32_t v = mem[q];
+        for (int32_t j = ptr[v] + lane; j < ptr[v + 1]; j += 32) k += agg[col[j]] != (int32_t)c;
+    }
+    for (int d = 16; d > 0; d >>= 1) k += __shfl_xor_sync(0xffffffffu, k, d);
+    if (lane == 0) ccnt[c] = k;
+}
+
+__global__ void k_amg_cfill_w(int64_t nc, const int32_t *mptr, const int32_t *mem,
+                              const int32_t *ptr, const int32_t *col, const double *w,
+                              const double *D, const int32_t *agg, const int64_t *coff,
+                              int32_t *cptr, int32_t *ccol, double *cw, double *cD, double *cdiag) {
+    const int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (c >= nc) return;
+    int64_t k = coff[c];
+    if (lane == 0) {
+        cptr[c] = (int32_t)k;
+        if (c == nc - 1) cptr[nc] = (int32_t)coff[nc];
+    }
+    double dsum = 0.0, wsum = 0.0;
+    for (int32_t q = mptr[c]; q < mptr[c + 1]; ++q) {
+        const int32_t v = mem[q];
+        dsum += D[v];
+        const int32_t jb = ptr[v], je = ptr[v + 1];
+        for (int32_t j0 = jb; j0 < je; j0 += 32) {
+            const int32_t j = j0 + lane;
+            int32_t a = 0;
+            double wj = 0.0;
+            bool keep = false;
+            if (j < je) {
+                a = agg[col[j]];
+                wj = w[j];
+                keep = a != (int32_t)c;
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, keep);
+            if (keep) {
+                const int64_t at = k + __popc(m & ((1u << lane) - 1u));
+                ccol[at] = a;
+                cw[at] = wj;
+            }
+            // the kept weights added in row order
+            for (int i = 0; i < 32; ++i) {
+                const double wi = __shfl_sync(0xffffffffu, wj, i);
+                if ((m >> i) & 1u) wsum += wi;
+            }
+            k += __popc(m);
+        }
+    }
+    if (lane == 0) {
+        cD[c] = dsum;
+        cdiag[c] = dsum + wsum;
+    }
+}
+
 // anchor[v]: for an unmatched v, its heaviest matched neighbour (-1: none);
 // -2 for matched vertices.  leader[v]: smallest id of v's aggregate.
 __global__ void k_amg_join(int64_t n, const int32_t *ptr, const int32_t *col, const double *w,
@@ -455,8 +566,13 @@ std::unique_ptr<AmgLevel> coarsen(grass_ctx_t ctx, AmgHier &H, AmgLevel &L) {
         int *cur = chg + (round & 1);
         const int *prev = chg + ((round + 1) & 1);
         memset_d(ctx, cur, 0, sizeof(int));
-        launch(ctx, k_amg_cand, g, kBlock, 0, n, (const int32_t *)L.ptr.p, (const int32_t *)L.col.p,
-               (const double *)L.w64.p, (const int32_t *)mate.p, cand.p, prev);
+        if (n <= kAmgWarpSetup)
+            launch(ctx, k_amg_cand_w, cdiv(n * 32, kBlock), kBlock, 0, n, (const int32_t *)L.ptr.p,
+                   (const int32_t *)L.col.p, (const double *)L.w64.p, (const int32_t *)mate.p, cand.p,
+                   prev);
+        else
+            launch(ctx, k_amg_cand, g, kBlock, 0, n, (const int32_t *)L.ptr.p, (const int32_t *)L.col.p,
+                   (const double *)L.w64.p, (const int32_t *)mate.p, cand.p, prev);
         launch(ctx, k_amg_pair, g, kBlock, 0, n, (const int32_t *)cand.p, mate.p, prev, cur);
     }
     launch(ctx, k_amg_join, g, kBlock, 0, n, (const int32_t *)L.ptr.p, (const int32_t *)L.col.p,
@@ -492,8 +608,14 @@ std::unique_ptr<AmgLevel> coarsen(grass_ctx_t ctx, AmgHier &H, AmgLevel &L) {
     ASpan<int64_t> ccnt, coff;
     tmp.get(ccnt, nc + 1);
     tmp.get(coff, nc + 1);
-    launch(ctx, k_amg_ccount, gc, kBlock, 0, nc, (const int32_t *)L.mptr.p, (const int32_t *)L.mem.p,
-           (const int32_t *)L.ptr.p, (const int32_t *)L.col.p, (const int32_t *)L.agg.p, ccnt.p);
+    const bool wf = n <= kAmgWarpSetup;
+    if (wf)
+        launch(ctx, k_amg_ccount_w, cdiv(nc * 32, kBlock), kBlock, 0, nc, (const int32_t *)L.mptr.p,
+               (const int32_t *)L.mem.p, (const int32_t *)L.ptr.p, (const int32_t *)L.col.p,
+               (const int32_t *)L.agg.p, ccnt.p);
+    else
+        launch(ctx, k_amg_ccount, gc, kBlock, 0, nc, (const int32_t *)L.mptr.p, (const int32_t *)L.mem.p,
+               (const int32_t *)L.ptr.p, (const int32_t *)L.col.p, (const int32_t *)L.agg.p, ccnt.p);
     int64_t cnnz = 0;
     scan_i64(ctx, ccnt.p, coff.p, nc, &cnnz);
     C->nnz = cnnz;
@@ -502,10 +624,16 @@ std::unique_ptr<AmgLevel> coarsen(grass_ctx_t ctx, AmgHier &H, AmgLevel &L) {
     H.arena.get(C->w64, cnnz);
     H.arena.get(C->D64, nc);
     H.arena.get(C->diag64, nc);
-    launch(ctx, k_amg_cfill, gc, kBlock, 0, nc, (const int32_t *)L.mptr.p, (const int32_t *)L.mem.p,
-           (const int32_t *)L.ptr.p, (const int32_t *)L.col.p, (const double *)L.w64.p,
-           (const double *)L.D64.p, (const int32_t *)L.agg.p, (const int64_t *)coff.p, C->ptr.p,
-           C->col.p, C->w64.p, C->D64.p, C->diag64.p);
+    if (wf)
+        launch(ctx, k_amg_cfill_w, cdiv(nc * 32, kBlock), kBlock, 0, nc, (const int32_t *)L.mptr.p,
+               (const int32_t *)L.mem.p, (const int32_t *)L.ptr.p, (const int32_t *)L.col.p,
+               (const double *)L.w64.p, (const double *)L.D64.p, (const int32_t *)L.agg.p,
+               (const int64_t *)coff.p, C->ptr.p, C->col.p, C->w64.p, C->D64.p, C->diag64.p);
+    else
+        launch(ctx, k_amg_cfill, gc, kBlock, 0, nc, (const int32_t *)L.mptr.p, (const int32_t *)L.mem.p,
+               (const int32_t *)L.ptr.p, (const int32_t *)L.col.p, (const double *)L.w64.p,
+               (const double *)L.D64.p, (const int32_t *)L.agg.p, (const int64_t *)coff.p, C->ptr.p,
+               C->col.p, C->w64.p, C->D64.p, C->diag64.p);
     return C;
 }
 
