@@ -175,6 +175,10 @@ grass_status grass_ctx_set_wait_limit(grass_ctx_t ctx, int64_t polls, int hold_b
  *                         as a CUDA graph
  *   "amg_warp_n"          levels of at most this many vertices (default
  *                         16384) take one warp per row in the fused kernel
+ *   "amg_warp_setup_n"    the hierarchy's setup takes one warp per vertex
+ *                         for its long-row steps on levels of at most this
+ *                         many vertices (default 16384; the same hierarchy
+ *                         as one thread per vertex)
  *   "amg_tail_n"          levels of at most this many vertices (default 0:
  *                         none but the coarsest dense solve) run in one
  *                         block of the fused kernel

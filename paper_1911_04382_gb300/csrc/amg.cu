@@ -117,9 +117,8 @@ __global__ void k_amg_pair(int64_t n, const int32_t *cand, int32_t *mate, const 
 // as the thread forms: the candidate is the heaviest by (w, pair key), the
 // first in row order among equal ones (each lane keeps its first best, the
 // lanes' bests are compared with the row position as the last key), and the
-// coarse rows are written and their weights summed in row order.
-constexpr int64_t kAmgWarpSetup = 16384;   // levels of at most this many vertices
-
+// coarse rows are written and their weights summed in row order.  Used on
+// levels of at most ctx->amg_warp_setup_n vertices.
 __global__ void k_amg_cand_w(int64_t n, const int32_t *ptr, const int32_t *col, const double *w,
                              const int32_t *mate, int32_t *cand, const int *go) {
     const int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -566,7 +565,7 @@ std::unique_ptr<AmgLevel> coarsen(grass_ctx_t ctx, AmgHier &H, AmgLevel &L) {
         int *cur = chg + (round & 1);
         const int *prev = chg + ((round + 1) & 1);
         memset_d(ctx, cur, 0, sizeof(int));
-        if (n <= kAmgWarpSetup)
+        if (n <= ctx->amg_warp_setup_n)
             launch(ctx, k_amg_cand_w, cdiv(n * 32, kBlock), kBlock, 0, n, (const int32_t *)L.ptr.p,
                    (const int32_t *)L.col.p, (const double *)L.w64.p, (const int32_t *)mate.p, cand.p,
                    prev);
@@ -608,7 +607,7 @@ std::unique_ptr<AmgLevel> coarsen(grass_ctx_t ctx, AmgHier &H, AmgLevel &L) {
     ASpan<int64_t> ccnt, coff;
     tmp.get(ccnt, nc + 1);
     tmp.get(coff, nc + 1);
-    const bool wf = n <= kAmgWarpSetup;
+    const bool wf = n <= ctx->amg_warp_setup_n;
     if (wf)
         launch(ctx, k_amg_ccount_w, cdiv(nc * 32, kBlock), kBlock, 0, nc, (const int32_t *)L.mptr.p,
                (const int32_t *)L.mem.p, (const int32_t *)L.ptr.p, (const int32_t *)L.col.p,

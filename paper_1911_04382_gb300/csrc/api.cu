@@ -414,6 +414,9 @@ grass_status grass_ctx_set_param(grass_ctx_t ctx, const char *name, int64_t valu
     } else if (k == "amg_warp_n") {
         need(value >= 0, "amg_warp_n must be >= 0");
         ctx->amg_warp_n = value;
+    } else if (k == "amg_warp_setup_n") {
+        need(value >= 0, "amg_warp_setup_n must be >= 0");
+        ctx->amg_warp_setup_n = value;
     } else if (k == "amg_tail_n") {
         need(value >= 0, "amg_tail_n must be >= 0");
         ctx->amg_tail_n = value;

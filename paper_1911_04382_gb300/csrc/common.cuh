@@ -169,6 +169,8 @@ struct grass_ctx_s {
     int amg_fused = 1;          // 1: the multigrid PCG runs as one cooperative kernel (amg_fused.cu)
     int64_t amg_tail_n = 0;     // its levels of at most this many vertices run in one block
     int64_t amg_warp_n = 16384; // its levels of at most this many vertices take a warp per row
+    int64_t amg_warp_setup_n = 16384;   // hierarchy setup: levels of at most this many
+                                        // vertices use the warp forms of the long-row kernels
     // a non-blocking stream of the context's own, on which multi-kernel
     // iterations are captured into CUDA graphs and replayed (ordered with the
     // caller's stream by events); created on first use

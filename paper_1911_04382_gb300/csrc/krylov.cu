@@ -792,10 +792,13 @@ static void cg_R(const CGCall &c) {
         cg_persistent<float, R>(c.ctx, c.S, c.with_D, c.Y, c.X, c.tol, c.maxit, c.maxbits);
 }
 
-__global__ void k_acc_iters(int r, const double *cg_it, double *acc) {
+// acc[0] += the most iterations over the columns; acc[1] += 1 when a column
+// reached the iteration cap (the capped-solve count of the fused kernels)
+__global__ void k_acc_iters(int r, const double *cg_it, double maxit, double *acc) {
     double m = 0.0;
     for (int j = 0; j < r; ++j) m = fmax(m, cg_it[j]);
-    *acc += m;
+    acc[0] += m;
+    if (m >= maxit) acc[1] += 1.0;
 }
 
 __global__ void k_f2d(int64_t n, const float *a, double *b) {
@@ -899,7 +902,7 @@ int64_t s_solve(grass_ctx_t ctx, grass_sparsifier_t S, bool with_D, int r, grass
                    (const float *)Z, (float *)P);
     }
     if (maxbits) max_abs_bits(ctx, prec, total, X, maxbits);
-    launch(ctx, k_acc_iters, 1, 1, 0, r, (const double *)(cg + CG_IT * 32),
+    launch(ctx, k_acc_iters, 1, 1, 0, r, (const double *)(cg + CG_IT * 32), (double)maxit,
            ctx->scal.p + DS_RED + DS_ITER);
     return 0;
 }

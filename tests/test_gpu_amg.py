@@ -112,6 +112,37 @@ def test_fused_multigrid_pcg_matches_launch_form(gpu, which, prec):
             gpu.grass_sparsifier_destroy(S)
 
 
+@pytest.mark.parametrize("which", ["grid3d", "powergrid"])
+def test_warp_setup_builds_the_same_hierarchy(gpu, which):
+    """The setup's warp forms (matching candidates, coarse-row counts and
+    fill, one warp per vertex on small levels) build the hierarchy the
+    thread forms build: the multigrid PCG on it then runs the same
+    iterations to the same FP64 solution, bit for bit."""
+    import torch
+    g = {"grid3d": lambda: graphs.grid3d_loguniform(30, 27, 25, seed=101),
+         "powergrid": lambda: graphs.power_grid(150, seed=102)}[which]()
+    og = oracle.from_graph(g)
+    ot = oracle.build_tree(og)
+    b = rng.normal(108, rng.STREAM_RHS, g.n)
+    xs, its = [], []
+    for warp_setup in (0, 1 << 40):
+        with gpu_graph(g) as (ctx, tree, _):
+            gpu.grass_ctx_set_param(ctx, "amg_warp_setup_n", warp_setup)
+            gpu.grass_ctx_set_param(ctx, "pcg_precond", 1)
+            S, _ = _with_extra(gpu, ctx, tree, og, ot, 10)
+            try:
+                x = torch.zeros(g.n, dtype=torch.float64, device="cuda")
+                st, s = gpu.grass_pcg_solve(ctx, S, dev(b), x, 1e-8, 20000, gpu.GRASS_FP64, 1e-2,
+                                            1e-2, 0)
+                assert st == gpu.GRASS_OK
+                xs.append(host(x))
+                its.append(s.iters)
+            finally:
+                gpu.grass_sparsifier_destroy(S)
+    assert its[0] == its[1]
+    assert np.array_equal(xs[0], xs[1])
+
+
 def test_amg_lambda_max_matches_oracle(gpu):
     g = graphs.grid2d_uniform(60, 45, seed=104)
     og = oracle.from_graph(g)
