@@ -636,6 +636,12 @@ std::unique_ptr<AmgLevel> coarsen(grass_ctx_t ctx, AmgHier &H, AmgLevel &L) {
     return C;
 }
 
+// aggcol[j] = agg[col[j]]: the coarse vertex of each entry's column
+__global__ void k_amg_aggcol(int64_t nnz, const int32_t *col, const int32_t *agg, int32_t *aggcol) {
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < nnz) aggcol[j] = agg[col[j]];
+}
+
 __global__ void k_sum_d(int64_t n, const double *D, double *out) {
     // one block: deterministic sum of a small vector
     __shared__ double sh[kBlock];
@@ -678,6 +684,11 @@ AmgHier &amg_get(grass_ctx_t ctx, grass_sparsifier_t S, bool with_D) {
             H->arena.get(L.vx, L.n * sizeof(double) + 256);
         }
         H->arena.get(L.vt, L.n * sizeof(double) + 256);
+        if (l + 1 < H->lv.size()) {
+            H->arena.get(L.aggcol, std::max<int64_t>(L.nnz, 1));
+            launch(ctx, k_amg_aggcol, cdiv(L.nnz, kBlock), kBlock, 0, L.nnz, (const int32_t *)L.col.p,
+                   (const int32_t *)L.agg.p, L.aggcol.p);
+        }
     }
     // coarsest: dense (grounded) inverse
     AmgLevel &Lc = *H->lv.back();

@@ -15,7 +15,8 @@
 //    restriction phase, which also writes the next level's pre-smoothing
 //    x = omega b / diag;
 //  * level l going up: the prolongation x + x_c[agg] is formed on the fly
-//    inside the post-smoothing sweep (at the row and at every neighbour);
+//    inside the post-smoothing sweep (at the row and at every neighbour,
+//    whose coarse vertex comes with the column: aggcol[j] = agg[col[j]]);
 //    level 0's sweep writes z and the partial sums of r.z;
 //  * levels of at most amg_warp_n vertices take one warp per row (their
 //    rows are long: they carry the fine edges between aggregates), the rest
@@ -41,6 +42,7 @@ struct FLevel {
     const int32_t *ptr, *col;      // off-diagonal adjacency
     const T *w, *diag;             // weights; diagonal = weighted degree + D
     const int32_t *agg;            // [n] coarse vertex (not on the coarsest level)
+    const int32_t *aggcol;         // [nnz] agg[col[j]]
     const int32_t *mptr, *mem;     // members of the next level's vertices
     T *b, *x, *t;                  // right-hand side, pre-smoothed iterate, result
 };
@@ -77,7 +79,7 @@ struct AmgPcgArgs {
 // fused kernel runs few threads per SM, so each keeps U rows in flight.
 template <typename T, int U, bool PRO>
 __device__ __forceinline__ void rows_wx(const int32_t *ptr, const int32_t *col, const T *w,
-                                        const T *x, const int32_t *agg, const T *xc, int64_t n,
+                                        const T *x, const int32_t *aggcol, const T *xc, int64_t n,
                                         int64_t v0, int64_t st, T (&s)[U]) {
     int32_t jb[U], je[U];
 #pragma unroll
@@ -102,21 +104,29 @@ __device__ __forceinline__ void rows_wx(const int32_t *ptr, const int32_t *col, 
             }
         }
         if constexpr (PRO) {
+            // the entries' coarse vertices come with the columns (aggcol), so
+            // x and the coarse correction are gathered in the same round
             int32_t ag[U][4];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) ag[u][k] = jb[u] + k < je[u] ? aggcol[jb[u] + k] : 0;
+            }
+            T cv[U][4];
 #pragma unroll
             for (int u = 0; u < U; ++u) {
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
                     const bool ok = jb[u] + k < je[u];
                     xv[u][k] = ok ? x[c[u][k]] : (T)0;
-                    ag[u][k] = ok ? agg[c[u][k]] : 0;
+                    cv[u][k] = ok ? xc[ag[u][k]] : (T)0;
                 }
             }
 #pragma unroll
             for (int u = 0; u < U; ++u) {
 #pragma unroll
                 for (int k = 0; k < 4; ++k)
-                    if (jb[u] + k < je[u]) xv[u][k] = xv[u][k] + xc[ag[u][k]];
+                    if (jb[u] + k < je[u]) xv[u][k] = xv[u][k] + cv[u][k];
             }
         } else {
 #pragma unroll
@@ -314,7 +324,7 @@ __device__ __forceinline__ void ph_post(const FLevel<T> &L, const T *xc, int64_t
             const int32_t ag = ok ? L.agg[v] : 0;
             if (ok) xv[u] = xv[u] + xc[ag];
         }
-        rows_wx<T, 2, true>(L.ptr, L.col, L.w, L.x, L.agg, xc, L.n, v0, st, sm);
+        rows_wx<T, 2, true>(L.ptr, L.col, L.w, L.x, L.aggcol, xc, L.n, v0, st, sm);
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
             const int64_t v = v0 + u * st;
@@ -390,10 +400,7 @@ __device__ __forceinline__ void ph_post_w(const FLevel<T> &L, const T *xc, int64
     for (int64_t v = w0; v < L.n; v += ws) {
         const int32_t jb = L.ptr[v], je = L.ptr[v + 1];
         T s = (T)0;
-        for (int32_t j = jb + lane; j < je; j += 32) {
-            const int32_t c = L.col[j];
-            s += L.w[j] * (L.x[c] + xc[L.agg[c]]);
-        }
+        for (int32_t j = jb + lane; j < je; j += 32) s += L.w[j] * (L.x[L.col[j]] + xc[L.aggcol[j]]);
         s = warp_sum(s);
         if (lane == 0) {
             const T xv = L.x[v] + xc[L.agg[v]];
@@ -649,6 +656,7 @@ int amg_pcg_fused(grass_ctx_t ctx, grass_sparsifier_t S, AmgHier &H, const T *rh
             f.diag = Lv.diag32.p;
         }
         f.agg = Lv.agg.p;
+        f.aggcol = Lv.aggcol.p;
         f.mptr = Lv.mptr.p;
         f.mem = Lv.mem.p;
         if (l == 0) {
@@ -691,7 +699,8 @@ int amg_pcg_fused(grass_ctx_t ctx, grass_sparsifier_t S, AmgHier &H, const T *rh
     // (s bytes an element, n_l vertices and nnz_l entries on level l):
     //  residual: CSR + x, b, diag read, res written;
     //  restriction: member lists, res read, b (and x, diag) of level l+1;
-    //  post-smoothing: CSR + agg, x, b, diag read, x_c gathered, t written;
+    //  post-smoothing: CSR + the entries' coarse vertices (aggcol) + agg, x,
+    //  b, diag read, x_c gathered, t written;
     //  coarsest: its dense inverse and two vectors;
     //  per outer iteration: SpMV with A (CSR + p, D read, q written), the
     //  update (e, r read and written, p, q, diag read, x written: 8 ns), the
@@ -707,7 +716,8 @@ int amg_pcg_fused(grass_ctx_t ctx, grass_sparsifier_t S, AmgHier &H, const T *rh
             const bool coarsest = l + 2 == L;
             vc += csr + 4.0 * nl * sz;                                            // residual
             vc += 4.0 * (nn + 1) + 4.0 * nl + nl * sz + (coarsest ? 1.0 : 3.0) * nn * sz;
-            vc += csr + 4.0 * nl + 4.0 * nl * sz + nn * sz;                       // post-smoothing
+            const double nnz = (double)H.lv[l]->nnz;
+            vc += csr + 4.0 * nnz + 4.0 * nl + 4.0 * nl * sz + nn * sz;           // post-smoothing
         }
         const double nc = (double)H.nc;
         vc += nc * nc * sz + 2.0 * nc * sz;

@@ -436,6 +436,7 @@ struct AmgLevel {
     ASpan<double> w64, diag64, D64;   // weights, diagonal = weighted degree + D, D
     ASpan<float> w32, diag32;
     ASpan<int32_t> agg;               // [n] coarse vertex of each vertex (not on the coarsest)
+    ASpan<int32_t> aggcol;            // [nnz] agg[col[j]] (not on the coarsest)
     ASpan<int32_t> mptr, mem;         // members of coarse vertex c: mem[mptr[c] .. mptr[c+1])
     ASpan<char> vb, vx, vt;           // V-cycle vectors of this level (coarse levels)
 };
