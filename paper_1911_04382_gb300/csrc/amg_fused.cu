@@ -20,7 +20,7 @@
 //    level 0's sweep writes z and the partial sums of r.z;
 //  * levels of at most amg_warp_n vertices take one warp per row (their
 //    rows are long: they carry the fine edges between aggregates), the rest
-//    one thread per row, two rows in flight;
+//    one thread per row, two rows in flight (FP32; one for FP64);
 //  * the coarsest dense solve takes one warp per row across the grid;
 //    optionally the levels of at most amg_tail_n vertices run in block 0
 //    with block barriers while the other blocks wait at the next grid
@@ -243,22 +243,29 @@ __device__ __forceinline__ void grid_sums(const double *part, double *s_out) {
 // Each phase walks its items from item `i0` with stride `st` (the grid's
 // threads, or block 0's).
 
-// res = b - (diag x - sum w x_j) on level L (two rows per step)
+// Rows in flight per thread in the thread-form phases: two for FP32, one
+// for FP64 (whose doubled registers made two slower: 116.8 against 109.7 ms
+// for the 100^3 step's FP64 solve; FP32 63.9 against 65.8 ms with one)
+template <typename T>
+constexpr int kRowsInFlight = sizeof(T) == 4 ? 2 : 1;
+
+// res = b - (diag x - sum w x_j) on level L
 template <typename T>
 __device__ __forceinline__ void ph_residual(const FLevel<T> &L, T *res, int64_t i0, int64_t st) {
-    for (int64_t v0 = i0; v0 < L.n; v0 += 2 * st) {
-        T xo[2], bo[2], d[2], sm[2];
+    constexpr int U = kRowsInFlight<T>;
+    for (int64_t v0 = i0; v0 < L.n; v0 += U * st) {
+        T xo[U], bo[U], d[U], sm[U];
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
+        for (int u = 0; u < U; ++u) {
             const int64_t v = v0 + u * st;
             const bool ok = v < L.n;
             xo[u] = ok ? L.x[v] : (T)0;
             bo[u] = ok ? L.b[v] : (T)0;
             d[u] = ok ? L.diag[v] : (T)0;
         }
-        rows_wx<T, 2, false>(L.ptr, L.col, L.w, L.x, nullptr, nullptr, L.n, v0, st, sm);
+        rows_wx<T, U, false>(L.ptr, L.col, L.w, L.x, nullptr, nullptr, L.n, v0, st, sm);
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
+        for (int u = 0; u < U; ++u) {
             const int64_t v = v0 + u * st;
             if (v < L.n) res[v] = bo[u] - (d[u] * xo[u] - sm[u]);
         }
@@ -308,14 +315,15 @@ __device__ __forceinline__ void ph_restrict(const FLevel<T> &L, const FLevel<T> 
 }
 
 // t = x' + omega (b - (diag x' - sum w x'_j)) / diag with x' = x + xc[agg];
-// with rz, accumulates b t (level 0: r.z).  Two rows per step.
+// with rz, accumulates b t (level 0: r.z)
 template <typename T>
 __device__ __forceinline__ void ph_post(const FLevel<T> &L, const T *xc, int64_t i0, int64_t st,
                                         Acc<T> *rz) {
-    for (int64_t v0 = i0; v0 < L.n; v0 += 2 * st) {
-        T xv[2], bv[2], d[2], sm[2];
+    constexpr int U = kRowsInFlight<T>;
+    for (int64_t v0 = i0; v0 < L.n; v0 += U * st) {
+        T xv[U], bv[U], d[U], sm[U];
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
+        for (int u = 0; u < U; ++u) {
             const int64_t v = v0 + u * st;
             const bool ok = v < L.n;
             xv[u] = ok ? L.x[v] : (T)0;
@@ -324,9 +332,9 @@ __device__ __forceinline__ void ph_post(const FLevel<T> &L, const T *xc, int64_t
             const int32_t ag = ok ? L.agg[v] : 0;
             if (ok) xv[u] = xv[u] + xc[ag];
         }
-        rows_wx<T, 2, true>(L.ptr, L.col, L.w, L.x, L.aggcol, xc, L.n, v0, st, sm);
+        rows_wx<T, U, true>(L.ptr, L.col, L.w, L.x, L.aggcol, xc, L.n, v0, st, sm);
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
+        for (int u = 0; u < U; ++u) {
             const int64_t v = v0 + u * st;
             if (v >= L.n) break;
             const T o = d[u] > (T)0 ? xv[u] + (T)kOmegaF * (bv[u] - (d[u] * xv[u] - sm[u])) / d[u]
