@@ -32,6 +32,7 @@
 // the root and the ancestor table by pointer doubling (sums of positive
 // terms only), and each edge's lowest common ancestor by binary lifting.
 #include "common.cuh"
+#include "tree_solve.cuh"
 
 namespace grass {
 
@@ -220,6 +221,74 @@ __global__ void k_ls_commit(int64_t nx, const int32_t *xl, int t, const unsigned
     }
 }
 
+// The four passes of round t over items i0, i0 + st, ... (one block's
+// threads, or the grid's).
+__device__ __forceinline__ void ls_pass_offer(int64_t na, const int32_t *ca, const int32_t *cb,
+                                              const int32_t *ctr, const int32_t *when,
+                                              const int32_t *start, int t, unsigned long long *key,
+                                              int64_t i0, int64_t st) {
+    for (int64_t k = i0; k < na; k += st) {
+        const int32_t x = ca[k], y = cb[k];
+        const int32_t cx = ctr[x], cy = ctr[y];
+        if (cx < 0 && cy >= 0 && when[y] == t - 1) atomicMin(key + x, ls_key(start, cy));
+        else if (cy < 0 && cx >= 0 && when[x] == t - 1) atomicMin(key + y, ls_key(start, cx));
+    }
+}
+
+__device__ __forceinline__ void ls_pass_heavy(int64_t na, const int32_t *act, const int32_t *ca,
+                                              const int32_t *cb, const int32_t *ctr,
+                                              const int32_t *when, const int32_t *start, int t,
+                                              const unsigned long long *key, const double *ew,
+                                              unsigned long long *wb, int64_t i0, int64_t st) {
+    for (int64_t k = i0; k < na; k += st) {
+        const int32_t x = ca[k], y = cb[k];
+        const int32_t cx = ctr[x], cy = ctr[y];
+        if (cx < 0 && cy >= 0 && when[y] == t - 1) {
+            if (ls_key(start, cy) == key[x]) atomicMax(wb + x, wbits(ew[act[k]]));
+        } else if (cy < 0 && cx >= 0 && when[x] == t - 1) {
+            if (ls_key(start, cx) == key[y]) atomicMax(wb + y, wbits(ew[act[k]]));
+        }
+    }
+}
+
+__device__ __forceinline__ void ls_pass_eid(int64_t na, const int32_t *act, const int32_t *ca,
+                                            const int32_t *cb, const int32_t *ctr,
+                                            const int32_t *when, const int32_t *start, int t,
+                                            const unsigned long long *key, const double *ew,
+                                            const unsigned long long *wb, int32_t *eb, int64_t i0,
+                                            int64_t st) {
+    for (int64_t k = i0; k < na; k += st) {
+        const int32_t x = ca[k], y = cb[k];
+        const int32_t cx = ctr[x], cy = ctr[y];
+        const int32_t e = act[k];
+        if (cx < 0 && cy >= 0 && when[y] == t - 1) {
+            if (ls_key(start, cy) == key[x] && wbits(ew[e]) == wb[x]) atomicMin(eb + x, e);
+        } else if (cy < 0 && cx >= 0 && when[x] == t - 1) {
+            if (ls_key(start, cx) == key[y] && wbits(ew[e]) == wb[y]) atomicMin(eb + y, e);
+        }
+    }
+}
+
+__device__ __forceinline__ void ls_pass_commit(int64_t nx, const int32_t *xl, int t,
+                                               const unsigned long long *key, const int32_t *eb,
+                                               const int32_t *start, int32_t *ctr, int32_t *when,
+                                               uint8_t *in_tree, int64_t i0, int64_t st) {
+    for (int64_t i = i0; i < nx; i += st) {
+        const int32_t x = xl[i];
+        if (ctr[x] >= 0) continue;
+        const unsigned long long kk = key[x];
+        if (kk != kNoKey) {
+            ctr[x] = (int32_t)(uint32_t)(kk & 0xFFFFFFFFull);
+            when[x] = t;
+            const int32_t e = eb[x];
+            if (e != kNoEdgeId) in_tree[e] = 1;
+        } else if (start[x] == t) {
+            ctr[x] = x;
+            when[x] = t;
+        }
+    }
+}
+
 // A whole level (rounds 0..S, the same four passes) in one block, for the
 // many small levels (at most ctx->lsst_small_level active edges):
 // __syncthreads between the passes in place of launches.
@@ -231,50 +300,40 @@ __global__ void __launch_bounds__(kLevelBlock) k_ls_level(
     int32_t *when, unsigned long long *key, unsigned long long *wb, int32_t *eb,
     uint8_t *in_tree) {
     const int S = *smax;
+    const int64_t i0 = threadIdx.x, st = blockDim.x;
     for (int t = 0; t <= S; ++t) {
-        for (int64_t k = threadIdx.x; k < na; k += blockDim.x) {
-            const int32_t x = ca[k], y = cb[k];
-            const int32_t cx = ctr[x], cy = ctr[y];
-            if (cx < 0 && cy >= 0 && when[y] == t - 1) atomicMin(key + x, ls_key(start, cy));
-            else if (cy < 0 && cx >= 0 && when[x] == t - 1) atomicMin(key + y, ls_key(start, cx));
-        }
+        ls_pass_offer(na, ca, cb, ctr, when, start, t, key, i0, st);
         __syncthreads();
-        for (int64_t k = threadIdx.x; k < na; k += blockDim.x) {
-            const int32_t x = ca[k], y = cb[k];
-            const int32_t cx = ctr[x], cy = ctr[y];
-            if (cx < 0 && cy >= 0 && when[y] == t - 1) {
-                if (ls_key(start, cy) == key[x]) atomicMax(wb + x, wbits(ew[act[k]]));
-            } else if (cy < 0 && cx >= 0 && when[x] == t - 1) {
-                if (ls_key(start, cx) == key[y]) atomicMax(wb + y, wbits(ew[act[k]]));
-            }
-        }
+        ls_pass_heavy(na, act, ca, cb, ctr, when, start, t, key, ew, wb, i0, st);
         __syncthreads();
-        for (int64_t k = threadIdx.x; k < na; k += blockDim.x) {
-            const int32_t x = ca[k], y = cb[k];
-            const int32_t cx = ctr[x], cy = ctr[y];
-            const int32_t e = act[k];
-            if (cx < 0 && cy >= 0 && when[y] == t - 1) {
-                if (ls_key(start, cy) == key[x] && wbits(ew[e]) == wb[x]) atomicMin(eb + x, e);
-            } else if (cy < 0 && cx >= 0 && when[x] == t - 1) {
-                if (ls_key(start, cx) == key[y] && wbits(ew[e]) == wb[y]) atomicMin(eb + y, e);
-            }
-        }
+        ls_pass_eid(na, act, ca, cb, ctr, when, start, t, key, ew, wb, eb, i0, st);
         __syncthreads();
-        for (int64_t i = threadIdx.x; i < nx; i += blockDim.x) {
-            const int32_t x = xl[i];
-            if (ctr[x] >= 0) continue;
-            const unsigned long long kk = key[x];
-            if (kk != kNoKey) {
-                ctr[x] = (int32_t)(uint32_t)(kk & 0xFFFFFFFFull);
-                when[x] = t;
-                const int32_t e = eb[x];
-                if (e != kNoEdgeId) in_tree[e] = 1;
-            } else if (start[x] == t) {
-                ctr[x] = x;
-                when[x] = t;
-            }
-        }
+        ls_pass_commit(nx, xl, t, key, eb, start, ctr, when, in_tree, i0, st);
         __syncthreads();
+    }
+}
+
+// The larger levels in one cooperative launch per level: the same passes
+// over the grid's threads, bounded grid barriers between them in place of
+// four launches per round.
+__global__ void __launch_bounds__(kLevelBlock) k_ls_level_grid(
+    int64_t na, int64_t nx, const int32_t *act, const int32_t *ca, const int32_t *cb,
+    const int32_t *xl, const int *smax, const int32_t *start, const double *ew, int32_t *ctr,
+    int32_t *when, unsigned long long *key, unsigned long long *wb, int32_t *eb,
+    uint8_t *in_tree, unsigned int *bar, long long budget, int *err) {
+    const int S = *smax;
+    const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t st = (int64_t)gridDim.x * blockDim.x;
+    unsigned int epoch = 0;
+    for (int t = 0; t <= S; ++t) {
+        ls_pass_offer(na, ca, cb, ctr, when, start, t, key, i0, st);
+        if (!grid_sync(bar, budget, err, epoch)) return;
+        ls_pass_heavy(na, act, ca, cb, ctr, when, start, t, key, ew, wb, i0, st);
+        if (!grid_sync(bar, budget, err, epoch)) return;
+        ls_pass_eid(na, act, ca, cb, ctr, when, start, t, key, ew, wb, eb, i0, st);
+        if (!grid_sync(bar, budget, err, epoch)) return;
+        ls_pass_commit(nx, xl, t, key, eb, start, ctr, when, in_tree, i0, st);
+        if (!grid_sync(bar, budget, err, epoch)) return;
     }
 }
 
@@ -440,6 +499,7 @@ void lsst_build(grass_ctx_t ctx, const GraphData &g, uint64_t seed, uint8_t *in_
     pos.alloc(m + 1);
     small.alloc(4);
 
+    clear_timeout(ctx);
     const int init_small[4] = {INT_MIN, 0, 0, 0};
     h2d(ctx, small.p, init_small, sizeof(init_small));
     launch(ctx, k_ls_exp, cdiv(m, kBlock), kBlock, 0, m, (const double *)g.ew64.p, cls.p, small.p);
@@ -491,7 +551,28 @@ void lsst_build(grass_ctx_t ctx, const GraphData &g, uint64_t seed, uint8_t *in_
                        (const double *)g.ew64.p, ctr.p, when.p, key.p, wb.p, eb.p, in_tree);
                 edge_passes += 3 * (S + 1);
             }
-            for (int t = 0; t <= S && na > ctx->lsst_small_level; ++t) {
+            if (na > ctx->lsst_small_level && ctx->num_sms > 0) {
+                int64_t na_ = na, nx_ = nx;
+                const int32_t *act_ = act[cur].p, *ca_ = ca[cur].p, *cb_ = cb[cur].p, *xl_ = xl.p;
+                const int *smax_ = small.p + 2;
+                const int32_t *start_ = start.p;
+                const double *ew_ = g.ew64.p;
+                int32_t *ctr_ = ctr.p, *when_ = when.p, *eb_ = eb.p;
+                unsigned long long *key_ = key.p, *wb_ = wb.p;
+                uint8_t *tree_ = in_tree;
+                unsigned int *bar = ctx->gbar.p;
+                long long budget = ctx->wait_budget;
+                int *err = ctx->flags.p + 3;
+                const int grid = coop_grid(ctx, k_ls_level_grid, kLevelBlock, 0, na);
+                GCK(cudaMemsetAsync(bar, 0, sizeof(unsigned int), ctx->stream));
+                void *args[] = {&na_, &nx_, &act_, &ca_, &cb_, &xl_, &smax_, &start_, &ew_, &ctr_,
+                                &when_, &key_, &wb_, &eb_, &tree_, &bar, &budget, &err};
+                GCK(cudaLaunchCooperativeKernel((const void *)k_ls_level_grid, dim3(grid),
+                                                dim3(kLevelBlock), args, 0, ctx->stream));
+                ctx->launches++;
+                edge_passes += 3 * (S + 1);
+            }
+            for (int t = 0; t <= S && na > ctx->lsst_small_level && ctx->num_sms == 0; ++t) {
                 launch(ctx, k_ls_offer, cdiv(na, kBlock), kBlock, 0, na, (const int32_t *)ca[cur].p,
                        (const int32_t *)cb[cur].p, (const int32_t *)ctr.p, (const int32_t *)when.p,
                        (const int32_t *)start.p, t, key.p);
@@ -525,6 +606,7 @@ void lsst_build(grass_ctx_t ctx, const GraphData &g, uint64_t seed, uint8_t *in_
             na = nn;
         }
     }
+    check_timeout(ctx);   // a level whose grid barrier gave up
     DBuf<unsigned long long> cnt;
     cnt.alloc(1);
     memset_d(ctx, cnt.p, 0, sizeof(unsigned long long));
